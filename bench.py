@@ -1,0 +1,418 @@
+"""Benchmark of the FFT function block on GB300.
+
+Workload (default): 3-D complex64 C2C 256x256x128, re/im iid standard normal
+from a fixed seed, forward then inverse with 1/N scale; one step = one forward
+and one inverse exec of that volume (the whole hot path).  Metric: effective
+HBM bandwidth, algorithmic bytes (one read + one write of the volume per exec,
+2 * 2 * 8 * N per step) / time, in GB/s; 5 N log2 N flops per exec are reported
+beside it.  Four input/output buffer pairs (512 MiB) rotate between steps so
+the working set exceeds the 126 MB L2.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+                  [--workload 3d|1d4096|1d2p20]
+
+Under torchrun each rank runs its own replica (independent transforms, no
+collective on the data path); rank 0 prints one JSON line.  --impl reference
+times the CPU oracle (FP64) on this machine's cores on the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2004_09883_gb300 import inputs  # noqa: E402
+
+METRIC = "C2C FFT GB/s vs HBM peak; 5NlogN GFLOP/s; served p50/p99 vs plain path"
+WORKLOADS = {
+    "3d": dict(name="3d_c2c_256x256x128_fwd_then_inv_scaled", dims=[256, 256, 128], batch=1,
+               seed=inputs.seed_for(inputs.WORKLOAD_3D_256x256x128), dist="normal", inverse=True),
+    "1d4096": dict(name="1d_c2c_4096_batch64_fwd", dims=[4096], batch=64,
+                   seed=inputs.seed_for(inputs.WORKLOAD_1D_4096x64), dist="uniform", inverse=False),
+    "1d2p20": dict(name="1d_c2c_2p20_batch32_fwd", dims=[1 << 20], batch=32,
+                   seed=inputs.seed_for(inputs.WORKLOAD_1D_2P20x32), dist="normal", inverse=False),
+}
+KERNEL_SOURCES = ["paper_2004_09883_gb300/csrc/fft_device.cuh", "paper_2004_09883_gb300/csrc/fb_internal.h",
+                  "paper_2004_09883_gb300/csrc/fb_fft.cu"]
+
+
+def kernel_hash() -> str:
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def load_peaks() -> dict:
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return {"hbm_gbs": float(d["hbm_gbs"]), "source": "measured"}
+    return {"hbm_gbs": 6800.0, "source": "fallback"}
+
+
+def load_traffic(workload: str) -> dict | None:
+    """DRAM bytes per launch from a committed ncu capture, valid only while the
+    kernel sources are unchanged since the capture."""
+    p = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(p):
+        return None
+    with open(p) as f:
+        d = json.load(f)
+    e = d.get(workload)
+    if not e or e.get("kernel_hash") != kernel_hash():
+        return None
+    return e
+
+
+class ClockSampler:
+    """nvidia-smi clock/throttle samples (200 ms) with host timestamps."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.samples = []
+        self.proc = None
+        self.gpu = gpu_index
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={gpu_index}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 9:
+                self.samples.append((time.time(), parts))
+
+    def stop(self):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self, t0: float, t1: float) -> dict:
+        win = [s for t, s in self.samples if t0 <= t <= t1]
+        where = "timed"
+        if not win:  # timed region shorter than the sampling period: widen to the pre-roll
+            win = [s for t, s in self.samples if t0 - 2.0 <= t <= t1 + 0.5]
+            where = "timed+preroll"
+        if not win:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"], "window": where}
+
+        def num(v):
+            try:
+                return float(v)
+            except ValueError:
+                return None
+
+        sm = [num(s[1]) for s in win if num(s[1]) is not None]
+        mx = [num(s[2]) for s in win if num(s[2]) is not None]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for s in win for i in range(4) if s[5 + i].lower() == "active"})
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "power_w_max": max((num(s[3]) or 0.0) for s in win), "reasons": reasons,
+                "samples": len(win), "window": where}
+
+
+def dist_setup():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def make_input(wl: dict, rep: int) -> np.ndarray:
+    shape = [wl["batch"]] + wl["dims"]
+    gen = inputs.normal_c64 if wl["dist"] == "normal" else inputs.uniform_c64
+    return gen(shape, wl["seed"] + 1000 * rep)
+
+
+def algorithmic(wl: dict) -> tuple[float, float, int]:
+    """(bytes per step, flops per step, execs per step)."""
+    n = int(np.prod(wl["dims"]))
+    execs = 2 if wl["inverse"] else 1
+    return execs * 2 * 8.0 * n * wl["batch"], execs * 5.0 * n * math.log2(n) * wl["batch"], execs
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle timing (reference arm and the cpu_baseline object)
+# ---------------------------------------------------------------------------
+def oracle_sample(wl: dict, budget_s: float, threads: int) -> dict:
+    """Time the FP64 oracle on the workload.  Runs whole steps (forward, plus
+    inverse when the workload has one) until `budget_s` is spent (at least
+    one); returns GB/s in the workload's own byte accounting."""
+    import oracle
+
+    x = make_input(wl, 0).astype(np.complex128)
+    bytes_step, _, _ = algorithmic(wl)
+    dims = wl["dims"]
+    reps, t_total = 0, 0.0
+    while reps == 0 or t_total < budget_s:
+        t = time.perf_counter()
+        y = oracle.fft(x, dims, -1, False, threads)
+        if wl["inverse"]:
+            oracle.fft(y, dims, 1, True, threads)
+        t_total += time.perf_counter() - t
+        reps += 1
+    return {"value": bytes_step * reps / t_total / 1e9, "seconds": t_total, "steps": reps}
+
+
+def cpu_model() -> str:
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                if line.lower().startswith(("model name", "cpu part", "hardware")):
+                    return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    return "unknown"
+
+
+def run_reference(args, wl: dict) -> None:
+    world, rank, _ = dist_setup()
+    if rank != 0:
+        return
+    threads = len(os.sched_getaffinity(0))
+    bytes_step, flops_step, _ = algorithmic(wl)
+    # one step = one forward(+inverse) of the workload by the oracle; for long
+    # runs each step is a bounded sample: a share of the batch items (the
+    # 3-D volume is one item, so it always runs whole).
+    per_step_budget = max(0.5, 150.0 / max(1, args.steps + args.warmup))
+    import oracle
+
+    x = make_input(wl, 0).astype(np.complex128)
+    dims = wl["dims"]
+    n = int(np.prod(dims))
+    # size the per-step sample (batch items) to the budget
+    t = time.perf_counter()
+    oracle.fft(x[:1], dims, -1, False, threads)
+    one = max(1e-6, time.perf_counter() - t) * (2 if wl["inverse"] else 1)
+    items = int(max(1, min(wl["batch"], per_step_budget // one)))
+    sample = x[:items]
+
+    def step():
+        y = oracle.fft(sample, dims, -1, False, threads)
+        if wl["inverse"]:
+            oracle.fft(y, dims, 1, True, threads)
+
+    for _ in range(args.warmup):
+        step()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        step()
+    dt = (time.perf_counter() - t0) / args.steps
+    frac = items / wl["batch"]
+    value = bytes_step * frac / dt / 1e9
+    desc = (f"{items} of {wl['batch']} batch item(s) of {wl['name']} per step, FP64 oracle, "
+            f"{threads} threads on {cpu_model()}")
+    line = {
+        "impl": "reference", "metric": METRIC, "value": round(value, 4), "unit": "GB/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": wl["name"], "dims": dims, "batch": wl["batch"], "l2": "n/a (CPU)",
+                   "parallelism": "host threads"},
+        "gflops": flops_step * frac / dt / 1e9,
+        "cpu_baseline": {"value": round(value, 4), "unit": "GB/s", "cores": threads, "kind": "oracle",
+                         "sample": desc},
+        "e2e": {"value": round(value, 4), "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------
+# GPU arm
+# ---------------------------------------------------------------------------
+def run_gpu(args, wl: dict) -> None:
+    import torch
+
+    world, rank, local = dist_setup()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+    else:
+        dist = None
+
+    from paper_2004_09883_gb300 import build as fbbuild
+    fbbuild.build()
+    from paper_2004_09883_gb300 import fbfft
+
+    dims, batch = wl["dims"], wl["batch"]
+    n = int(np.prod(dims))
+    bytes_step, flops_step, execs = algorithmic(wl)
+    nbuf = max(2, int(math.ceil(512 * 2 ** 20 / (2 * 8 * n * batch))))
+    nbuf = min(nbuf, 8)
+    stream = torch.cuda.current_stream(dev)
+    host_inputs = [make_input(wl, rank * 16 + r) for r in range(nbuf)]
+    xin = [torch.from_numpy(h.reshape(-1)).to(dev) for h in host_inputs]
+    xout = [torch.empty_like(xin[0]) for _ in range(nbuf)]
+    plan = fbfft.Plan(dims, batch, scale_inv_n=wl["inverse"], stream=stream)
+
+    def step(i):
+        a, b = xin[i % nbuf], xout[i % nbuf]
+        plan.exec_ptr(a.data_ptr(), b.data_ptr(), fbfft.FORWARD)
+        if wl["inverse"]:
+            plan.exec_ptr(b.data_ptr(), b.data_ptr(), fbfft.INVERSE)
+
+    def barrier():
+        torch.cuda.synchronize(dev)
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize(dev)
+
+    clocks = ClockSampler(local) if rank == 0 else None
+    for i in range(args.warmup):
+        step(i)
+    # pre-roll: untimed extra warm-up so the clock samples see a loaded GPU
+    t_pre = time.time()
+    i = 0
+    while time.time() - t_pre < 1.0:
+        step(i)
+        i += 1
+        if i % 64 == 0:
+            torch.cuda.synchronize(dev)
+    barrier()
+    plan.profile(True)
+    launches0 = fbfft.launch_count()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    wall0 = time.time()
+    ev0.record(stream)
+    for i in range(args.steps):
+        step(i)
+    ev1.record(stream)
+    barrier()
+    wall1 = time.time()
+    launches = fbfft.launch_count() - launches0
+    ms = ev0.elapsed_time(ev1) / args.steps
+    passes = plan.profile_read()
+    plan.profile(False)
+    plan.check()
+    if dist is not None:
+        t = torch.tensor([ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    clk = clocks.summary(wall0, wall1) if clocks else None
+    if clocks:
+        clocks.stop()
+
+    # end to end through the drop-in host-array call: every step copies the
+    # input host->device and the result device->host inside the call
+    if True:  # scoped block
+        hbuf = [torch.from_numpy(h.reshape(-1)).pin_memory() for h in host_inputs[:2]]
+        hres = [torch.empty_like(hbuf[0]).pin_memory() for _ in range(2)]
+        e2e_steps = max(3, min(args.steps, 20))
+
+        def e2e_step(i):
+            src, dst = hbuf[i % 2], hres[i % 2]
+            plan.exec_host(src.numpy(), dst.numpy(), fbfft.FORWARD)
+            if wl["inverse"]:
+                plan.exec_host(dst.numpy(), dst.numpy(), fbfft.INVERSE)
+
+        for i in range(2):
+            e2e_step(i)
+        barrier()
+        t0 = time.perf_counter()
+        for i in range(e2e_steps):
+            e2e_step(i)
+        barrier()
+        e2e_ms = (time.perf_counter() - t0) / e2e_steps * 1e3
+        if dist is not None:
+            t = torch.tensor([e2e_ms], device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            e2e_ms = float(t.item())
+        io = 8 * n * batch * execs
+        e2e = {"value": round(world * bytes_step / (e2e_ms / 1e3) / 1e9, 3), "unit": "GB/s",
+               "h2d_bytes_per_step": io, "d2h_bytes_per_step": io, "ms_per_step": e2e_ms,
+               "path": "fb_fft_exec_host (pinned host arrays), forward then inverse"}
+
+    if rank == 0:
+        peaks = load_peaks()
+        value = world * bytes_step / (ms / 1e3) / 1e9
+        # dominant kernel: the pass role with the largest measured time
+        dom = max(passes, key=lambda r: r[1]) if passes else None
+        roofline = None
+        if dom and dom[2] > 0:
+            per_launch_ms = dom[1] / dom[2]
+            launch_bytes = 2 * 8.0 * n * batch  # one read + one write of the array
+            achieved = launch_bytes / (per_launch_ms / 1e3) / 1e9
+            tr = load_traffic(wl["name"])
+            roofline = {"bound": "hbm", "achieved": round(achieved, 2), "peak": peaks["hbm_gbs"],
+                        "unit": "GB/s", "frac": round(achieved / peaks["hbm_gbs"], 4),
+                        "traffic": tr["dram_bytes_per_launch"] if tr and tr.get("pass") == dom[0] else None,
+                        "kernel_pass": dom[0], "launch_ms": round(per_launch_ms, 5),
+                        "algorithmic_bytes_per_launch": launch_bytes,
+                        "peak_source": f"{peaks['source']} (MEASURED_PEAKS.json hbm_gbs, burst copy)"
+                        if peaks["source"] == "measured" else "fallback 6.8 TB/s"}
+        threads = len(os.sched_getaffinity(0))
+        cb = oracle_sample(wl, budget_s=float(args.cpu_budget), threads=threads)
+        cpu_baseline = {"value": round(cb["value"], 4), "unit": "GB/s", "cores": threads, "kind": "oracle",
+                        "sample": f"{cb['steps']} full step(s) of {wl['name']} by the FP64 oracle in "
+                                  f"{cb['seconds']:.1f} s on {cpu_model()}"}
+        line = {
+            "metric": METRIC, "value": round(value, 3), "unit": "GB/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": round(ms, 5), "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": wl["name"], "dims": dims, "batch": batch, "dtype_storage": "complex64",
+                       "l2": f"{nbuf} rotating input/output buffer pairs "
+                             f"({nbuf * 2 * 8 * n * batch / 2 ** 20:.0f} MiB) > 126 MB L2",
+                       "parallelism": "replicas" if world > 1 else "single GPU"},
+            "gflops": round(world * flops_step / (ms / 1e3) / 1e9, 2),
+            "hbm_frac_effective": round(value / world / peaks["hbm_gbs"], 4),
+            "roofline": roofline,
+            "cpu_baseline": cpu_baseline,
+            "e2e": e2e,
+            "gpu_launches": int(launches),
+            "clocks": clk,
+            "passes": [{"pass": p[0], "ms_per_launch": round(p[1] / max(1, p[2]), 5), "launches": p[2]}
+                       for p in passes],
+            "kernel_hash": kernel_hash(),
+        }
+        print(json.dumps(line), flush=True)
+    plan.close()
+    if dist is not None:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="3d", choices=sorted(WORKLOADS))
+    ap.add_argument("--cpu-budget", default=10.0, type=float, help="seconds of oracle time for cpu_baseline")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    wl = WORKLOADS[args.workload]
+    if args.impl == "reference":
+        run_reference(args, wl)
+    else:
+        run_gpu(args, wl)
+
+
+if __name__ == "__main__":
+    main()

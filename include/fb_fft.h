@@ -1,0 +1,191 @@
+/*
+ * fb_fft.h -- C ABI of the GB300 complex FFT function block.
+ *
+ * The paper (Sec. 3.3, Sec. 3.4 C-1/C-2) offloads a whole "function block" of
+ * a C application -- its example is the Fourier transform, Sec. 5.1(a) --
+ * by deleting the CPU code and calling a device implementation through an
+ * interface that matches the host program's call: the array, its dimensions,
+ * the direction, in place or not.  This header is that interface for the
+ * complex-to-complex DFT, implemented from scratch for sm_103a:
+ *
+ *     X[k] = c * sum_{n=0}^{N-1} x[n] * exp(s * 2*pi*i * n*k / N)
+ *
+ * (the textbook DFT; the paper itself defers the formula to the library it
+ * swaps in, Sec. 5.1(a)), with exponent sign s = `direction`, c = 1 unless
+ * FB_FFT_SCALE_INV_N asks for 1/N on inverse transforms, applied along every
+ * axis of a rank-1..3 array and independently for each batch item.
+ *
+ * Data layout (all entry points): complex64 interleaved {float re, float im},
+ * row-major, last dimension fastest, batch items contiguous one after
+ * another (batch stride = prod(dims) elements).  Every call returns an
+ * fb_fft_status value; on an argument error no output is touched.
+ *
+ * Thread safety: distinct plans may be used from distinct host threads; one
+ * plan must not be executed concurrently from two threads.
+ */
+#ifndef FB_FFT_H
+#define FB_FFT_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct fb_fft_plan_s* fb_fft_plan_t;
+
+typedef enum fb_fft_status {
+    FB_FFT_OK = 0,
+    FB_FFT_ERR_INVALID_ARG = -1,      /* null pointer, bad rank/dim/direction, misaligned */
+    FB_FFT_ERR_UNSUPPORTED_SIZE = -2, /* a dim is not 2^a*3^b*5^c or exceeds the limits */
+    FB_FFT_ERR_ALLOC = -3,            /* device or host allocation failed */
+    FB_FFT_ERR_CUDA = -4,             /* a CUDA runtime call or kernel launch failed */
+    FB_FFT_ERR_TIMEOUT = -5,          /* a bounded device-side wait gave up */
+    FB_FFT_ERR_BAD_PLAN = -6,         /* null or destroyed plan handle */
+    FB_FFT_ERR_NO_DEVICE = -7         /* no CUDA device is visible */
+} fb_fft_status;
+
+/* Exponent sign of the transform kernel exp(s*2*pi*i*n*k/N). */
+#define FB_FFT_FORWARD (-1)
+#define FB_FFT_INVERSE (+1)
+
+/* Plan flags. */
+#define FB_FFT_SCALE_INV_N 0x1u /* multiply the result of every INVERSE exec by 1/prod(dims) */
+
+/* Largest supported length along one axis of a rank-2/3 plan, and of a
+ * rank-1 plan (a rank-1 length above FB_FFT_MAX_SMEM_LEN runs as a two-pass
+ * "four-step" transform, N = N1 * N2). */
+#define FB_FFT_MAX_SMEM_LEN 4096LL
+#define FB_FFT_MAX_1D_LEN (4096LL * 4096LL)
+
+/*
+ * fb_fft_plan -- prepare a transform (Sec. 3.4 C-1: the replaced block is
+ * connected once, then called like the CPU routine it replaces).
+ *   plan   out: new handle, owned by the caller until fb_fft_destroy.
+ *   rank   1, 2 or 3.
+ *   dims   rank lengths, row-major (dims[rank-1] is contiguous); each >= 1
+ *          and 5-smooth (2^a 3^b 5^c); <= FB_FFT_MAX_SMEM_LEN for rank >= 2,
+ *          <= FB_FFT_MAX_1D_LEN for rank 1.
+ *   batch  number of transforms (>= 0) laid out back to back.
+ *   flags  FB_FFT_SCALE_INV_N or 0.
+ *   stream cudaStream_t the plan launches on (NULL = legacy default stream).
+ * Builds the twiddle tables on the GPU (FP64 evaluation, rounded to FP32) and
+ * allocates the plan's scratch; both are owned by the plan.  Uses the current
+ * CUDA device; the plan must later be used with that device current.
+ * Errors: INVALID_ARG, UNSUPPORTED_SIZE, ALLOC, CUDA, NO_DEVICE.
+ */
+int fb_fft_plan(fb_fft_plan_t* plan, int rank, const long long* dims, long long batch,
+                unsigned flags, void* stream);
+
+/*
+ * fb_fft_exec -- run the transform on device buffers (Sec. 3.3 / Sec. 5.1(a):
+ * the Fourier transform block itself).
+ *   in        device pointer to batch*prod(dims) complex64 values, 8-byte aligned.
+ *   out       device pointer of the same size; out == in transforms in place.
+ *             Partial overlap of in and out is an INVALID_ARG.
+ *   direction FB_FFT_FORWARD or FB_FFT_INVERSE (the exponent sign).
+ * Asynchronous: enqueued on the plan's stream, no host synchronisation.
+ * `in` is read only (never clobbered) when out != in.  The caller keeps
+ * ownership of both buffers.  Errors: BAD_PLAN, INVALID_ARG, CUDA.
+ */
+int fb_fft_exec(fb_fft_plan_t plan, const void* in, void* out, int direction);
+
+/*
+ * fb_fft_exec_host -- the drop-in form of the replaced CPU call (Sec. 3.4
+ * C-1, Sec. 5.1(b)): host arrays in and out.  Copies host_in to a
+ * plan-owned device buffer, transforms, copies the result to host_out and
+ * waits for it.  host_in/host_out may be the same array (in place) and may be
+ * pageable or pinned host memory.  The first call allocates the device
+ * staging buffer (owned by the plan).  Errors: BAD_PLAN, INVALID_ARG, ALLOC, CUDA.
+ */
+int fb_fft_exec_host(fb_fft_plan_t plan, const void* host_in, void* host_out, int direction);
+
+/*
+ * fb_fft_check -- wait for the plan's stream and report whether any kernel of
+ * this plan gave up on a bounded device-side wait since the last check
+ * (FB_FFT_ERR_TIMEOUT; the word is then cleared).  exec_host calls it.
+ */
+int fb_fft_check(fb_fft_plan_t plan);
+
+/*
+ * fb_fft_debug_inject_timeout -- test hook for the failure path.  While
+ * enabled, every TMA-fed kernel of this plan announces 16 more bytes per tile
+ * than it copies, so its bounded wait runs out (after about one second),
+ * the kernel records the error and returns early, and the next fb_fft_check
+ * reports FB_FFT_ERR_TIMEOUT.  Nothing faults and the context stays usable;
+ * the output of such an exec is undefined.  Not for production use.
+ */
+int fb_fft_debug_inject_timeout(fb_fft_plan_t plan, int enable);
+
+/* fb_fft_set_stream -- change the stream later execs launch on. */
+int fb_fft_set_stream(fb_fft_plan_t plan, void* stream);
+
+/* fb_fft_destroy -- free the plan and everything it owns; NULL is a no-op.
+ * Synchronises the plan's stream first. */
+int fb_fft_destroy(fb_fft_plan_t plan);
+
+/* fb_fft_status_string -- static English text for a status code. */
+const char* fb_fft_status_string(int status);
+
+/*
+ * Plan description (host-side facts of the schedule).
+ *   passes         kernel launches per exec
+ *   smem_len_max   longest line held in one CTA's shared memory
+ *   scratch_bytes  plan-owned device scratch (four-step intermediate)
+ *   twiddle_bytes  plan-owned device twiddle tables
+ *   elements       prod(dims);  batch  as planned
+ */
+typedef struct fb_fft_info {
+    int passes;
+    int reserved;
+    long long smem_len_max;
+    long long scratch_bytes;
+    long long twiddle_bytes;
+    long long elements;
+    long long batch;
+} fb_fft_info;
+int fb_fft_plan_info(fb_fft_plan_t plan, fb_fft_info* info);
+
+/*
+ * fb_fft_factorize -- the planner's radix schedule for one in-shared-memory
+ * line length n (host only, needs no GPU).  Writes the radices (each of
+ * 2,3,4,5,8,16, product n) to radices[0..*count).  Errors: INVALID_ARG,
+ * UNSUPPORTED_SIZE (n not 5-smooth or > FB_FFT_MAX_SMEM_LEN).
+ */
+int fb_fft_factorize(long long n, int* radices, int capacity, int* count);
+
+/*
+ * fb_fft_split -- the planner's four-step split of a rank-1 length n
+ * (host only): n = *n1 * *n2 with n1, n2 <= FB_FFT_MAX_SMEM_LEN; *n1 = n,
+ * *n2 = 1 when n fits one pass.  Errors: INVALID_ARG, UNSUPPORTED_SIZE.
+ */
+int fb_fft_split(long long n, long long* n1, long long* n2);
+
+/*
+ * Profiling.  fb_fft_profile(plan, 1) makes every later exec record a CUDA
+ * event pair around each of its kernel launches (on the plan's stream);
+ * fb_fft_profile_read synchronises on them, writes per-pass totals
+ * (ms_total[p], launches[p], p < *npasses, at most `capacity`) and clears the
+ * record.  Events are cheap but not free; leave profiling off in production.
+ */
+int fb_fft_profile(fb_fft_plan_t plan, int enable);
+int fb_fft_profile_read(fb_fft_plan_t plan, double* ms_total, long long* launches,
+                        int capacity, int* npasses);
+
+/* Name of the kernel pass p launches (static string), or NULL. */
+const char* fb_fft_pass_name(fb_fft_plan_t plan, int pass);
+
+/* Total kernels this library has launched in this process (all plans). */
+long long fb_fft_launch_count(void);
+
+/*
+ * fb_fft_twiddles -- evaluate exp(-2*pi*i*m/d) for m = 0..count-1 with the
+ * library's twiddle kernel (FP64 on the GPU, rounded to FP32) and copy the
+ * float pairs to host_out[2*count].  Exposed so tests can check the tables.
+ * Errors: INVALID_ARG, ALLOC, CUDA, NO_DEVICE.
+ */
+int fb_fft_twiddles(long long d, long long count, float* host_out);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FB_FFT_H */

@@ -1,0 +1,703 @@
+// fb_fft.cu -- host side of the FFT function block: planner, plan object and
+// the C ABI declared in include/fb_fft.h.
+//
+// Schedules (all passes are launches of the Stockham line-pass kernel):
+//   rank 1, N <= 4096    one pass, lines contiguous.
+//   rank 1, N  > 4096    "four-step" N = N1*N2, n = N2*n1 + n2, k = k1 + N1*k2:
+//                        pass A: length-N1 DFTs down the N2 columns, output
+//                                multiplied by exp(s*2*pi*i*n2*k1/N)  (-> scratch)
+//                        pass B: length-N2 DFTs along the N1 rows, written
+//                                transposed to X[k1 + N1*k2]          (-> out)
+//                        The batch runs in chunks whose intermediate is small
+//                        enough to stay in the 126 MB L2 between A and B.
+//   rank 2/3             one pass per axis (last axis first), in place on out.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <atomic>
+#include <cstdint>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include <cudaTypedefs.h>
+
+#include "fb_fft.h"
+#include "fb_internal.h"
+
+using namespace fbfft;
+
+namespace {
+
+std::atomic<long long> g_launches{0};
+constexpr uint32_t kMagic = 0xFBFF7A11u;
+constexpr uint32_t kDead = 0xDEADFBFFu;
+
+// Four-step batch chunk: intermediate bytes kept L2-resident between passes.
+long long fourstep_chunk_bytes()
+{
+    static long long v = [] {
+        const char* s = std::getenv("FB_FFT_FOURSTEP_CHUNK_BYTES");
+        long long b = s ? std::atoll(s) : 0;
+        return b > 0 ? b : (32LL << 20);
+    }();
+    return v;
+}
+
+enum BufKind { kBufIn = 0, kBufOut = 1, kBufScratch = 2 };
+constexpr size_t kMaxSmemBytes = 227 * 1024;
+
+struct PassPlan {
+    PassDesc d;
+    int threads;  // CTA size of the chosen kernel
+    int lg;       // log2(L) for a compile-time power-of-two schedule, 0 = generic kernel
+    long long grid;
+    size_t smem;
+    bool async_ok;  // tiles can move by TMA (given 16-byte aligned buffer bases)
+    int src, dst;
+    long long src_off, dst_off;  // element offsets into the source / destination buffer
+    int group;                   // profiling group (the pass's role in the schedule)
+    bool last;                   // last pass of its data: gets the 1/N scale
+};
+
+bool is_smooth(long long n)
+{
+    if (n < 1) return false;
+    for (long long p : {2LL, 3LL, 5LL})
+        while (n % p == 0) n /= p;
+    return n == 1;
+}
+
+long long pow2floor(long long x)
+{
+    long long p = 1;
+    while (p * 2 <= x) p *= 2;
+    return p;
+}
+long long pow2ceil(long long x)
+{
+    long long p = 1;
+    while (p < x) p *= 2;
+    return p;
+}
+int ilog2ll(long long x)
+{
+    int l = 0;
+    while ((1LL << l) < x) ++l;
+    return l;
+}
+
+// Radix schedule of an in-shared-memory line: 16s first, then the leftover
+// power of two (8, 4 or 2), then 5s, then 3s.
+int factorize(long long n, int* r, int cap)
+{
+    if (n < 1) return FB_FFT_ERR_INVALID_ARG;
+    if (!is_smooth(n) || n > FB_FFT_MAX_SMEM_LEN) return FB_FFT_ERR_UNSUPPORTED_SIZE;
+    int c = 0;
+    auto push = [&](int v) {
+        if (c < cap) r[c] = v;
+        ++c;
+    };
+    int a = 0;
+    while (n % 2 == 0) n /= 2, ++a;
+    while (a >= 4) push(16), a -= 4;
+    if (a == 3) push(8);
+    if (a == 2) push(4);
+    if (a == 1) push(2);
+    while (n % 5 == 0) n /= 5, push(5);
+    while (n % 3 == 0) n /= 3, push(3);
+    return c;
+}
+
+int split_fourstep(long long n, long long* n1, long long* n2)
+{
+    if (n < 1) return FB_FFT_ERR_INVALID_ARG;
+    if (!is_smooth(n) || n > FB_FFT_MAX_1D_LEN) return FB_FFT_ERR_UNSUPPORTED_SIZE;
+    if (n <= FB_FFT_MAX_SMEM_LEN) {
+        *n1 = n, *n2 = 1;
+        return FB_FFT_OK;
+    }
+    // N1 = the divisor of n closest to sqrt(n) from below with both factors fitting.
+    long long best = 0;
+    for (long long d = 1; d * d <= n; ++d)
+        if (n % d == 0 && n / d <= FB_FFT_MAX_SMEM_LEN) best = d;
+    if (best == 0) return FB_FFT_ERR_UNSUPPORTED_SIZE;
+    *n1 = best, *n2 = n / best;
+    return FB_FFT_OK;
+}
+
+struct TwiddleBuilder {
+    std::vector<TwiddleJob> jobs;
+    long long total = 0;
+    std::vector<std::pair<long long, std::vector<int>>> stage_cache;  // L -> offsets
+
+    long long add_linear(long long count, long long D, long long mult)
+    {
+        TwiddleJob j{total, count, D, mult, 0, 0, 0};
+        jobs.push_back(j);
+        const long long off = total;
+        total += (count + 1) & ~1LL;  // keep every table 16-byte aligned
+        return off;
+    }
+    // Stage tables of length L; returns offsets per stage.
+    std::vector<int> add_stages(long long L, const int* radix, int nst)
+    {
+        for (auto& e : stage_cache)
+            if (e.first == L) return e.second;
+        std::vector<int> off(nst, 0);
+        long long Ns = 1;
+        for (int s = 0; s < nst; ++s) {
+            const long long cnt = Ns * (radix[s] - 1);
+            if (Ns > 1) {
+                TwiddleJob j{total, cnt, 0, 0, 1, radix[s], (int)Ns};
+                jobs.push_back(j);
+                off[s] = (int)total;
+                total += (cnt + 1) & ~1LL;
+            }
+            Ns *= radix[s];
+        }
+        stage_cache.emplace_back(L, off);
+        return off;
+    }
+};
+
+// Fill a line pass: L-point DFTs over lines (o, c); strides in elements.
+int make_line_pass(PassPlan& p, TwiddleBuilder& twb, long long L, long long O, long long C,
+                   long long in_sn, long long in_sc, long long in_so, long long out_sk, long long out_sc,
+                   long long out_so, bool in_tfast, bool out_tfast)
+{
+    std::memset(&p, 0, sizeof(p));
+    PassDesc& d = p.d;
+    int nst = factorize(L, d.radix, kMaxStages);
+    if (nst < 0) return nst;
+    if (nst > kMaxStages) return FB_FFT_ERR_UNSUPPORTED_SIZE;
+    d.nst = nst;
+    long long Ns = 1;
+    for (int s = 0; s < nst; ++s) {
+        d.ns[s] = (int)Ns;
+        Ns *= d.radix[s];
+    }
+    const std::vector<int> off = twb.add_stages(L, d.radix, nst);
+    for (int s = 0; s < nst; ++s) d.twoff[s] = off[s];
+
+    const bool cfast = in_tfast || out_tfast;
+    const bool pow2 = (L & (L - 1)) == 0;
+    p.lg = pow2 ? ilog2ll(L) : 0;
+    // Strided (c-fast) tiles want 16 lines for 128-byte rows: long power-of-two
+    // lines get the 512-thread kernel to double the tile.
+    p.threads = (pow2 && cfast && L >= 512) ? 512 : 256;
+    const long long cap = (long long)p.threads * kElemsPerThread;
+    if (L > cap) return FB_FFT_ERR_UNSUPPORTED_SIZE;
+    long long T = pow2floor(cap / L);
+    T = std::min<long long>(T, cfast ? 16 : p.threads);
+    T = std::max<long long>(1, std::min(T, pow2ceil(C)));
+    if (!line_kernel(p.threads, true, p.lg).launch) return FB_FFT_ERR_UNSUPPORTED_SIZE;
+
+    d.L = (int)L;
+    d.LS = (int)(L + (L >> 4) + 1);
+    d.logT = ilog2ll(T);
+    d.in_sn = in_sn, d.in_sc = in_sc, d.in_so = in_so;
+    d.out_sk = out_sk, d.out_sc = out_sc, d.out_so = out_so;
+    d.C = C;
+    d.tiles_per_o = (C + T - 1) / T;
+    d.ntiles = O * d.tiles_per_o;
+    d.in_tfast = in_tfast ? 1 : 0;
+    d.out_tfast = out_tfast ? 1 : 0;
+    d.scale = 1.0f;
+    // TMA needs 16-byte aligned addresses and 16-byte multiples: n-fast tiles
+    // must be contiguous (line stride L, L even), c-fast views need even strides
+    // and an even tile width.
+    const bool in_ok = in_tfast ? (T % 2 == 0 && in_sn % 2 == 0 && (O == 1 || in_so % 2 == 0))
+                                : (in_sc == L && in_sn == 1 && L % 2 == 0 && (O == 1 || in_so % 2 == 0));
+    const bool out_ok = out_tfast ? (T % 2 == 0 && out_sk % 2 == 0 && (O == 1 || out_so % 2 == 0))
+                                  : (out_sc == L && out_sk == 1 && L % 2 == 0 && (O == 1 || out_so % 2 == 0));
+    p.async_ok = in_ok && out_ok && C < (1LL << 31) && O < (1LL << 31);
+    // 3-D boxes of T x br rows: every box must start 128-byte aligned in
+    // shared memory (one box when L <= 256), br <= 256 and a divisor of L.
+    int br = 0;
+    if (L <= 256)
+        br = (int)L;
+    else
+        for (int b = 256; b >= 1 && !br; --b)
+            if (L % b == 0 && (b * T * 8) % 128 == 0) br = b;
+    if (br == 0 && (in_tfast || out_tfast)) p.async_ok = false;
+    d.box_rows = br > 0 ? br : 1;
+    d.land_stride = (int)land_stride_elems((int)L, (int)T);
+    p.smem = line_smem_bytes((int)L, (int)T, nst, p.async_ok);
+    if (p.smem > kMaxSmemBytes) {
+        p.async_ok = false;
+        p.smem = line_smem_bytes((int)L, (int)T, nst, false);
+    }
+    if (p.smem > kMaxSmemBytes) return FB_FFT_ERR_UNSUPPORTED_SIZE;
+    p.grid = d.ntiles;  // capped to the resident CTA count when the plan is built
+    return FB_FFT_OK;
+}
+
+}  // namespace
+
+struct fb_fft_plan_s {
+    uint32_t magic = kMagic;
+    int device = 0;
+    int rank = 0;
+    long long dims[3] = {1, 1, 1};
+    long long batch = 0;
+    unsigned flags = 0;
+    cudaStream_t stream = nullptr;
+    long long N = 1;
+    std::vector<PassPlan> passes;
+    std::vector<const char*> group_names;
+    float2* tw = nullptr;
+    long long tw_elems = 0;
+    float2* scratch = nullptr;
+    size_t scratch_bytes = 0;
+    float2* staging = nullptr;
+    size_t staging_bytes = 0;
+    int* err = nullptr;  // device error word written by bounded waits
+    long long smem_len_max = 0;
+    bool debug_timeout = false;  // test hook: make every TMA wait run out
+    // profiling
+    bool profiling = false;
+    std::vector<cudaEvent_t> ev;  // pairs
+    std::vector<int> ev_group;
+    size_t ev_used = 0;
+};
+
+namespace {
+
+bool plan_ok(fb_fft_plan_t p) { return p && p->magic == kMagic; }
+
+void free_plan(fb_fft_plan_s* p)
+{
+    if (!p) return;
+    if (p->tw) cudaFree(p->tw);
+    if (p->scratch) cudaFree(p->scratch);
+    if (p->staging) cudaFree(p->staging);
+    if (p->err) cudaFree(p->err);
+    for (cudaEvent_t e : p->ev) cudaEventDestroy(e);
+    p->magic = kDead;
+    delete p;
+}
+
+int build_plan(fb_fft_plan_s* p)
+{
+    TwiddleBuilder twb;
+    const long long B = p->batch;
+    if (p->rank == 1 && p->N > FB_FFT_MAX_SMEM_LEN) {
+        long long N1, N2;
+        int rc = split_fourstep(p->N, &N1, &N2);
+        if (rc != FB_FFT_OK) return rc;
+        const long long N = p->N;
+        const int plog = (ilog2ll(N) + 1) / 2;  // split 2^plog >= sqrt(N)
+        const long long lo_cnt = 1LL << plog;
+        const long long hi_cnt = (N + lo_cnt - 1) >> plog;
+        const long long lo_off = twb.add_linear(lo_cnt, N, 1);
+        const long long hi_off = twb.add_linear(hi_cnt, N, lo_cnt);
+        const long long chunk = std::max(1LL, std::min(B, fourstep_chunk_bytes() / (N * 8)));
+        p->scratch_bytes = (size_t)(chunk * N) * sizeof(float2);
+        p->group_names = {"fourstep.columns", "fourstep.rows"};
+        for (long long b0 = 0; b0 < B; b0 += chunk) {
+            const long long nb = std::min(chunk, B - b0);
+            PassPlan a, r;
+            rc = make_line_pass(a, twb, N1, nb, N2, N2, 1, N, N2, 1, N, true, true);
+            if (rc != FB_FFT_OK) return rc;
+            a.d.ptw = 1;
+            a.d.ptw_log = plog;
+            a.src = kBufIn, a.src_off = b0 * N;
+            a.dst = kBufScratch, a.dst_off = 0;
+            a.group = 0;
+            // stash table offsets in the pointer fields until exec binds them
+            a.d.ptw_lo = reinterpret_cast<const float2*>(lo_off);
+            a.d.ptw_hi = reinterpret_cast<const float2*>(hi_off);
+            rc = make_line_pass(r, twb, N2, nb, N1, 1, N2, N, N1, 1, N, false, true);
+            if (rc != FB_FFT_OK) return rc;
+            r.src = kBufScratch, r.src_off = 0;
+            r.dst = kBufOut, r.dst_off = b0 * N;
+            r.group = 1;
+            r.last = true;
+            p->passes.push_back(a);
+            p->passes.push_back(r);
+        }
+        p->smem_len_max = std::max(N1, N2);
+    } else {
+        static const char* axis_names[3] = {"axis0", "axis1", "axis2"};
+        static const char* one_name[1] = {"lines"};
+        bool first = true;
+        int ngroups = 0;
+        for (int ax = p->rank - 1; ax >= 0; --ax) {
+            const long long L = p->dims[ax];
+            if (L == 1) continue;
+            long long S = 1, Opre = 1;
+            for (int e = ax + 1; e < p->rank; ++e) S *= p->dims[e];
+            for (int e = 0; e < ax; ++e) Opre *= p->dims[e];
+            PassPlan q;
+            int rc;
+            if (S == 1)
+                rc = make_line_pass(q, twb, L, 1, B * Opre, 1, L, 0, 1, L, 0, false, false);
+            else
+                rc = make_line_pass(q, twb, L, B * Opre, S, S, 1, L * S, S, 1, L * S, true, true);
+            if (rc != FB_FFT_OK) return rc;
+            q.src = first ? kBufIn : kBufOut;
+            q.dst = kBufOut;
+            q.group = ngroups++;
+            first = false;
+            p->passes.push_back(q);
+            p->group_names.push_back(p->rank == 1 ? one_name[0] : axis_names[ax]);
+            p->smem_len_max = std::max(p->smem_len_max, L);
+        }
+        if (!p->passes.empty()) p->passes.back().last = true;
+    }
+    // Twiddle tables: one device buffer, built by the FP64 kernel.
+    p->tw_elems = std::max(2LL, twb.total);
+    if (cudaMalloc(&p->tw, (size_t)p->tw_elems * sizeof(float2)) != cudaSuccess) {
+        cudaGetLastError();
+        p->tw = nullptr;
+        return FB_FFT_ERR_ALLOC;
+    }
+    for (const TwiddleJob& j : twb.jobs)
+        if (launch_twiddles(p->tw, j, p->stream) != cudaSuccess) return FB_FFT_ERR_CUDA;
+    if (cudaMalloc(&p->err, sizeof(int)) != cudaSuccess) {
+        cudaGetLastError();
+        p->err = nullptr;
+        return FB_FFT_ERR_ALLOC;
+    }
+    if (cudaMemsetAsync(p->err, 0, sizeof(int), p->stream) != cudaSuccess) return FB_FFT_ERR_CUDA;
+    int sms = 0;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, p->device) != cudaSuccess) return FB_FFT_ERR_CUDA;
+    for (PassPlan& q : p->passes) {
+        int occ = 0;
+        const LineKernel k = line_kernel(q.threads, true, q.lg);
+        if (k.occupancy(q.smem, &occ) != cudaSuccess || occ < 1) return FB_FFT_ERR_CUDA;
+        q.grid = std::min(q.grid, (long long)sms * occ);
+        q.d.err = p->err;
+        q.d.tw = p->tw;
+        if (q.d.ptw) {
+            q.d.ptw_lo = p->tw + reinterpret_cast<long long>(q.d.ptw_lo);
+            q.d.ptw_hi = p->tw + reinterpret_cast<long long>(q.d.ptw_hi);
+        }
+    }
+    if (p->scratch_bytes) {
+        if (cudaMalloc(&p->scratch, p->scratch_bytes) != cudaSuccess) {
+            cudaGetLastError();
+            p->scratch = nullptr;
+            return FB_FFT_ERR_ALLOC;
+        }
+    }
+    if (cudaStreamSynchronize(p->stream) != cudaSuccess) return FB_FFT_ERR_CUDA;
+    return FB_FFT_OK;
+}
+
+// cuTensorMapEncodeTiled, fetched from the driver once (no libcuda link needed).
+PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder()
+{
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = [] {
+        void* f = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault, &q) !=
+                cudaSuccess ||
+            q != cudaDriverEntryPointSuccess) {
+            cudaGetLastError();
+            f = nullptr;
+        }
+        return reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(f);
+    }();
+    return fn;
+}
+
+// 3-D view {C (contiguous), L (stride sn), O (stride so)} of complex64
+// values, moved in boxes of T x box_rows x 1.  Returns 0 on success.
+int encode_view(CUtensorMap* tm, const float2* base, long long C, long long L, long long O, long long sn,
+                long long so, int T, int box_rows)
+{
+    PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
+    if (!enc) return -1;
+    if (O == 1) so = L * sn;
+    cuuint64_t dims[3] = {(cuuint64_t)C, (cuuint64_t)L, (cuuint64_t)O};
+    cuuint64_t strides[2] = {(cuuint64_t)sn * 8, (cuuint64_t)so * 8};
+    cuuint32_t box[3] = {(cuuint32_t)T, (cuuint32_t)box_rows, 1};
+    cuuint32_t estr[3] = {1, 1, 1};
+    CUresult r = enc(tm, CU_TENSOR_MAP_DATA_TYPE_UINT64, 3, const_cast<float2*>(base), dims, strides, box, estr,
+                     CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                     CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS ? 0 : -1;
+}
+
+int exec_device(fb_fft_plan_s* p, const float2* in, float2* out, int direction)
+{
+    const bool fwd = direction == FB_FFT_FORWARD;
+    const size_t bytes = (size_t)(p->N * p->batch) * sizeof(float2);
+    if (p->passes.empty()) {  // every axis has length 1: the DFT is the identity
+        if (bytes && in != out &&
+            cudaMemcpyAsync(out, in, bytes, cudaMemcpyDeviceToDevice, p->stream) != cudaSuccess)
+            return FB_FFT_ERR_CUDA;
+        return FB_FFT_OK;
+    }
+    const bool scale = !fwd && (p->flags & FB_FFT_SCALE_INV_N);
+    for (const PassPlan& q : p->passes) {
+        LineArgs args;
+        std::memset(&args, 0, sizeof(args));
+        args.d = q.d;
+        PassDesc& d = args.d;
+        const float2* src = q.src == kBufIn ? in : (q.src == kBufOut ? out : p->scratch);
+        float2* dst = q.dst == kBufOut ? out : p->scratch;
+        d.in = src + q.src_off;
+        d.out = dst + q.dst_off;
+        d.async_io = 0;
+        if (q.async_ok && (((uintptr_t)d.in | (uintptr_t)d.out) & 15) == 0) {
+            d.async_io = 1;
+            const long long O = d.ntiles / d.tiles_per_o;
+            if (d.in_tfast && encode_view(&args.tm_in, d.in, d.C, d.L, O, d.in_sn, d.in_so, 1 << d.logT, d.box_rows) != 0)
+                d.async_io = 0;
+            if (d.out_tfast &&
+                encode_view(&args.tm_out, d.out, d.C, d.L, O, d.out_sk, d.out_so, 1 << d.logT, d.box_rows) != 0)
+                d.async_io = 0;
+        }
+        if (p->debug_timeout && d.async_io) d.debug_extra_tx = 16;
+        const size_t smem = line_smem_bytes(d.L, 1 << d.logT, d.nst, d.async_io != 0);
+        if (q.last && scale) {
+            d.apply_scale = 1;
+            d.scale = (float)(1.0 / (double)p->N);
+        }
+        cudaEvent_t e0 = nullptr, e1 = nullptr;
+        if (p->profiling) {
+            if (p->ev_used + 2 > p->ev.size()) {
+                for (int i = 0; i < 64; ++i) {
+                    cudaEvent_t e;
+                    if (cudaEventCreate(&e) != cudaSuccess) return FB_FFT_ERR_CUDA;
+                    p->ev.push_back(e);
+                }
+                p->ev_group.resize(p->ev.size() / 2, 0);
+            }
+            e0 = p->ev[p->ev_used];
+            e1 = p->ev[p->ev_used + 1];
+            p->ev_group[p->ev_used / 2] = q.group;
+            p->ev_used += 2;
+            cudaEventRecord(e0, p->stream);
+        }
+        const LineKernel k = line_kernel(q.threads, fwd, q.lg);
+        if (k.launch(args, q.grid, smem, p->stream) != cudaSuccess) return FB_FFT_ERR_CUDA;
+        g_launches.fetch_add(1, std::memory_order_relaxed);
+        if (p->profiling) cudaEventRecord(e1, p->stream);
+    }
+    return FB_FFT_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* fb_fft_status_string(int status)
+{
+    switch (status) {
+    case FB_FFT_OK: return "ok";
+    case FB_FFT_ERR_INVALID_ARG: return "invalid argument";
+    case FB_FFT_ERR_UNSUPPORTED_SIZE: return "unsupported size (dims must be 5-smooth and within limits)";
+    case FB_FFT_ERR_ALLOC: return "allocation failed";
+    case FB_FFT_ERR_CUDA: return "CUDA error";
+    case FB_FFT_ERR_TIMEOUT: return "device wait timed out";
+    case FB_FFT_ERR_BAD_PLAN: return "bad plan handle";
+    case FB_FFT_ERR_NO_DEVICE: return "no CUDA device";
+    default: return "unknown status";
+    }
+}
+
+int fb_fft_factorize(long long n, int* radices, int capacity, int* count)
+{
+    if (!count || (capacity > 0 && !radices) || capacity < 0) return FB_FFT_ERR_INVALID_ARG;
+    int c = factorize(n, radices, capacity);
+    if (c < 0) return c;
+    *count = c;
+    return c <= capacity ? FB_FFT_OK : FB_FFT_ERR_INVALID_ARG;
+}
+
+int fb_fft_split(long long n, long long* n1, long long* n2)
+{
+    if (!n1 || !n2) return FB_FFT_ERR_INVALID_ARG;
+    return split_fourstep(n, n1, n2);
+}
+
+int fb_fft_plan(fb_fft_plan_t* plan, int rank, const long long* dims, long long batch, unsigned flags,
+                void* stream)
+{
+    if (!plan) return FB_FFT_ERR_INVALID_ARG;
+    *plan = nullptr;
+    if (rank < 1 || rank > 3 || !dims || batch < 0 || (flags & ~FB_FFT_SCALE_INV_N)) return FB_FFT_ERR_INVALID_ARG;
+    long long N = 1;
+    for (int d = 0; d < rank; ++d) {
+        if (dims[d] < 1) return FB_FFT_ERR_INVALID_ARG;
+        if (!is_smooth(dims[d])) return FB_FFT_ERR_UNSUPPORTED_SIZE;
+        if (rank > 1 && dims[d] > FB_FFT_MAX_SMEM_LEN) return FB_FFT_ERR_UNSUPPORTED_SIZE;
+        if (rank == 1 && dims[d] > FB_FFT_MAX_1D_LEN) return FB_FFT_ERR_UNSUPPORTED_SIZE;
+        N *= dims[d];
+    }
+    if (batch > 0 && N > (1LL << 58) / batch) return FB_FFT_ERR_UNSUPPORTED_SIZE;
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) {
+        cudaGetLastError();
+        return FB_FFT_ERR_NO_DEVICE;
+    }
+    fb_fft_plan_s* p = new (std::nothrow) fb_fft_plan_s();
+    if (!p) return FB_FFT_ERR_ALLOC;
+    cudaGetDevice(&p->device);
+    p->rank = rank;
+    for (int d = 0; d < rank; ++d) p->dims[d] = dims[d];
+    p->batch = batch;
+    p->flags = flags;
+    p->stream = (cudaStream_t)stream;
+    p->N = N;
+    int rc = build_plan(p);
+    if (rc != FB_FFT_OK) {
+        free_plan(p);
+        return rc;
+    }
+    *plan = p;
+    return FB_FFT_OK;
+}
+
+int fb_fft_exec(fb_fft_plan_t plan, const void* in, void* out, int direction)
+{
+    if (!plan_ok(plan)) return FB_FFT_ERR_BAD_PLAN;
+    if (direction != FB_FFT_FORWARD && direction != FB_FFT_INVERSE) return FB_FFT_ERR_INVALID_ARG;
+    if (plan->batch == 0) return FB_FFT_OK;
+    if (!in || !out) return FB_FFT_ERR_INVALID_ARG;
+    if (((uintptr_t)in | (uintptr_t)out) & 7) return FB_FFT_ERR_INVALID_ARG;
+    const uintptr_t bytes = (uintptr_t)(plan->N * plan->batch) * sizeof(float2);
+    const uintptr_t a = (uintptr_t)in, b = (uintptr_t)out;
+    if (a != b && a < b + bytes && b < a + bytes) return FB_FFT_ERR_INVALID_ARG;
+    return exec_device(plan, (const float2*)in, (float2*)out, direction);
+}
+
+int fb_fft_exec_host(fb_fft_plan_t plan, const void* host_in, void* host_out, int direction)
+{
+    if (!plan_ok(plan)) return FB_FFT_ERR_BAD_PLAN;
+    if (direction != FB_FFT_FORWARD && direction != FB_FFT_INVERSE) return FB_FFT_ERR_INVALID_ARG;
+    if (plan->batch == 0) return FB_FFT_OK;
+    if (!host_in || !host_out) return FB_FFT_ERR_INVALID_ARG;
+    const size_t bytes = (size_t)(plan->N * plan->batch) * sizeof(float2);
+    if (!plan->staging) {
+        if (cudaMalloc(&plan->staging, bytes) != cudaSuccess) {
+            cudaGetLastError();
+            plan->staging = nullptr;
+            return FB_FFT_ERR_ALLOC;
+        }
+        plan->staging_bytes = bytes;
+    }
+    if (cudaMemcpyAsync(plan->staging, host_in, bytes, cudaMemcpyHostToDevice, plan->stream) != cudaSuccess)
+        return FB_FFT_ERR_CUDA;
+    int rc = exec_device(plan, plan->staging, plan->staging, direction);
+    if (rc != FB_FFT_OK) return rc;
+    if (cudaMemcpyAsync(host_out, plan->staging, bytes, cudaMemcpyDeviceToHost, plan->stream) != cudaSuccess)
+        return FB_FFT_ERR_CUDA;
+    return fb_fft_check(plan);
+}
+
+int fb_fft_check(fb_fft_plan_t plan)
+{
+    if (!plan_ok(plan)) return FB_FFT_ERR_BAD_PLAN;
+    if (cudaStreamSynchronize(plan->stream) != cudaSuccess) return FB_FFT_ERR_CUDA;
+    int e = 0;
+    if (cudaMemcpy(&e, plan->err, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) return FB_FFT_ERR_CUDA;
+    if (e) {
+        cudaMemset(plan->err, 0, sizeof(int));
+        return FB_FFT_ERR_TIMEOUT;
+    }
+    return FB_FFT_OK;
+}
+
+int fb_fft_debug_inject_timeout(fb_fft_plan_t plan, int enable)
+{
+    if (!plan_ok(plan)) return FB_FFT_ERR_BAD_PLAN;
+    plan->debug_timeout = enable != 0;
+    return FB_FFT_OK;
+}
+
+int fb_fft_set_stream(fb_fft_plan_t plan, void* stream)
+{
+    if (!plan_ok(plan)) return FB_FFT_ERR_BAD_PLAN;
+    plan->stream = (cudaStream_t)stream;
+    return FB_FFT_OK;
+}
+
+int fb_fft_destroy(fb_fft_plan_t plan)
+{
+    if (!plan) return FB_FFT_OK;
+    if (!plan_ok(plan)) return FB_FFT_ERR_BAD_PLAN;
+    cudaStreamSynchronize(plan->stream);
+    free_plan(plan);
+    return FB_FFT_OK;
+}
+
+int fb_fft_plan_info(fb_fft_plan_t plan, fb_fft_info* info)
+{
+    if (!plan_ok(plan)) return FB_FFT_ERR_BAD_PLAN;
+    if (!info) return FB_FFT_ERR_INVALID_ARG;
+    std::memset(info, 0, sizeof(*info));
+    info->passes = (int)plan->passes.size();
+    info->smem_len_max = plan->smem_len_max;
+    info->scratch_bytes = (long long)plan->scratch_bytes;
+    info->twiddle_bytes = plan->tw_elems * (long long)sizeof(float2);
+    info->elements = plan->N;
+    info->batch = plan->batch;
+    return FB_FFT_OK;
+}
+
+int fb_fft_profile(fb_fft_plan_t plan, int enable)
+{
+    if (!plan_ok(plan)) return FB_FFT_ERR_BAD_PLAN;
+    plan->profiling = enable != 0;
+    plan->ev_used = 0;
+    return FB_FFT_OK;
+}
+
+int fb_fft_profile_read(fb_fft_plan_t plan, double* ms_total, long long* launches, int capacity, int* npasses)
+{
+    if (!plan_ok(plan)) return FB_FFT_ERR_BAD_PLAN;
+    if (!npasses || capacity < 0 || (capacity > 0 && (!ms_total || !launches))) return FB_FFT_ERR_INVALID_ARG;
+    const int ng = (int)plan->group_names.size();
+    *npasses = ng;
+    for (int g = 0; g < capacity; ++g) ms_total[g] = 0.0, launches[g] = 0;
+    if (plan->ev_used) {
+        if (cudaEventSynchronize(plan->ev[plan->ev_used - 1]) != cudaSuccess) return FB_FFT_ERR_CUDA;
+        for (size_t i = 0; i + 1 < plan->ev_used; i += 2) {
+            float ms = 0.f;
+            if (cudaEventElapsedTime(&ms, plan->ev[i], plan->ev[i + 1]) != cudaSuccess) return FB_FFT_ERR_CUDA;
+            const int g = plan->ev_group[i / 2];
+            if (g < capacity) ms_total[g] += ms, launches[g] += 1;
+        }
+    }
+    plan->ev_used = 0;
+    return FB_FFT_OK;
+}
+
+const char* fb_fft_pass_name(fb_fft_plan_t plan, int pass)
+{
+    if (!plan_ok(plan) || pass < 0 || pass >= (int)plan->group_names.size()) return nullptr;
+    return plan->group_names[pass];
+}
+
+long long fb_fft_launch_count(void) { return g_launches.load(std::memory_order_relaxed); }
+
+int fb_fft_twiddles(long long d, long long count, float* host_out)
+{
+    if (d < 1 || count < 0 || (count > 0 && !host_out)) return FB_FFT_ERR_INVALID_ARG;
+    if (count == 0) return FB_FFT_OK;
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) {
+        cudaGetLastError();
+        return FB_FFT_ERR_NO_DEVICE;
+    }
+    float2* buf = nullptr;
+    if (cudaMalloc(&buf, (size_t)count * sizeof(float2)) != cudaSuccess) {
+        cudaGetLastError();
+        return FB_FFT_ERR_ALLOC;
+    }
+    TwiddleJob j{0, count, d, 1, 0, 0, 0};
+    int rc = FB_FFT_OK;
+    if (launch_twiddles(buf, j, nullptr) != cudaSuccess ||
+        cudaMemcpy(host_out, buf, (size_t)count * sizeof(float2), cudaMemcpyDeviceToHost) != cudaSuccess)
+        rc = FB_FFT_ERR_CUDA;
+    cudaFree(buf);
+    return rc;
+}
+
+}  // extern "C"

@@ -1,0 +1,112 @@
+// fb_internal.h -- declarations shared by the library's translation units.
+// Not part of the public ABI (that is include/fb_fft.h).
+#pragma once
+
+#include <cuda.h>
+#include <cuda_runtime.h>
+
+#include <cstddef>
+
+namespace fbfft {
+
+constexpr int kMaxStages = 8;
+constexpr int kElemsPerThread = 16;  // E: complex values one thread holds per stage
+constexpr int kGenericElems = 8;     // E of the generic (run-time schedule) kernel
+
+// Thread-block shapes of the line-pass kernel: tile capacity = threads * E.
+// Power-of-two lines get kernels with compile-time radix schedules (256
+// threads for L <= 4096, 512 threads for 512 <= L <= 4096); other 5-smooth
+// lines use the generic 256-thread kernel that reads its schedule at run time.
+enum LineCfg { kCfg256 = 0, kCfg512 = 1, kNumCfg = 2 };
+constexpr int cfg_threads(int cfg) { return cfg == kCfg256 ? 256 : 512; }
+constexpr long long cfg_capacity(int cfg) { return (long long)cfg_threads(cfg) * kElemsPerThread; }
+constexpr int kGenericThreads = 512;  // generic kernel: 512 x 8 = 4096 values per tile
+constexpr int kMaxLineLog2 = 12;  // 4096
+
+// One kernel launch of the line pass: 1-D DFTs of length L along one axis of a
+// strided view.  Line (o, c) starts at o*so + c*sc; its element n sits n*sn
+// further on (separate strides for input and output).  A CTA takes a tile of
+// T = 2^logT consecutive c at one o.
+struct PassDesc {
+    const float2* in;
+    float2* out;
+    const float2* tw;      // twiddle buffer; stage s table at tw + twoff[s]
+    const float2* ptw_lo;  // four-step post-twiddle, exp(-2 pi i m / ptw_n) for m < 2^ptw_log
+    const float2* ptw_hi;  // exp(-2 pi i (m << ptw_log) / ptw_n)
+    long long in_sn, in_sc, in_so;
+    long long out_sk, out_sc, out_so;
+    long long C;           // lines per outer index o
+    long long tiles_per_o; // ceil(C / T)
+    long long ntiles;      // O * tiles_per_o
+    int L;                 // line length
+    int LS;                // shared-memory line stride (elements, padded)
+    int logT;              // T = 1 << logT lines per tile
+    int nst;               // number of Stockham stages
+    int radix[kMaxStages];
+    int ns[kMaxStages];    // product of the radices before stage s
+    int twoff[kMaxStages]; // element offset of stage s's twiddle table
+    int in_tfast;          // 1: first stage maps threads across lines (input contiguous across c)
+    int out_tfast;         // 1: last stage maps threads across lines (output contiguous across c)
+    int ptw;               // 1: multiply output (c, k) by exp(s 2 pi i c k / ptw_n)
+    int ptw_log;
+    int apply_scale;
+    float scale;
+    int async_io;          // 1: tiles move by TMA (bulk / tensor copies), double-buffered
+    int land_stride;       // elements between the two landing buffers (multiple of 16)
+    int box_rows;          // rows per 3-D TMA box (a divisor of L, <= 256)
+    int* err;              // device error word: 1 = a bounded wait gave up
+    unsigned debug_extra_tx;  // test hook: bytes announced per tile that never arrive
+};
+
+// Kernel argument: the descriptor plus the TMA tensor maps of the c-fast
+// input/output views {C, L, O} (encoded per launch, they hold addresses).
+struct LineArgs {
+    PassDesc d;
+    CUtensorMap tm_in;
+    CUtensorMap tm_out;
+};
+
+// Shared memory (bytes) the line pass needs for a tile of T lines of length L:
+// alignment slack and mbarriers (256 B), one or two dense landing buffers and the
+// padded work buffer.
+inline long long land_stride_elems(int L, int T) { return ((long long)L * T + 15) & ~15LL; }
+inline size_t line_smem_bytes(int L, int T, int nst, bool async)
+{
+    const long long land = land_stride_elems(L, T) * (async ? 2 : 1);
+    const long long LS = (long long)L + (L >> 4) + 1;
+    const long long work = nst <= 1 ? 0 : LS * T;
+    return 256 + (size_t)(land + work) * sizeof(float2);  // alignment slack + mbarriers
+}
+
+// One compiled line-pass kernel: launcher, occupancy query and a name.
+using LineLaunchFn = cudaError_t (*)(const LineArgs&, long long grid, size_t smem, cudaStream_t);
+using LineOccFn = cudaError_t (*)(size_t smem, int* blocks_per_sm);
+struct LineKernel {
+    LineLaunchFn launch;
+    LineOccFn occupancy;
+    const char* name;
+};
+// The kernel for (threads, direction, lg): lg = log2(L) for the compile-time
+// power-of-two schedules, 0 for the generic kernel.  launch == nullptr when
+// that combination is not compiled.
+LineKernel line_kernel(int threads, bool forward, int lg);
+LineKernel line_kernel_p2_256_fwd(int lg);
+LineKernel line_kernel_p2_256_inv(int lg);
+LineKernel line_kernel_p2_512(bool forward, int lg);
+LineKernel line_kernel_generic(bool forward);
+
+// Twiddle table jobs: K0 evaluates exp(-2 pi i m / D) in FP64 and rounds to FP32.
+//   kind 0 (linear): entry i has m = (i * mult) mod D
+//   kind 1 (stage):  entry i = (r-1)*Ns + k has m = r*k, D = Ns*R
+struct TwiddleJob {
+    long long offset;
+    long long count;
+    long long D;
+    long long mult;
+    int kind;
+    int R;
+    int Ns;
+};
+cudaError_t launch_twiddles(float2* tw, const TwiddleJob& job, cudaStream_t stream);
+
+}  // namespace fbfft

@@ -1,0 +1,620 @@
+// fft_device.cuh -- register-level DFT butterflies and the Stockham line pass.
+//
+// A length-L line is transformed by mixed-radix Stockham autosort stages
+// (radices 16, 8, 5, 4, 3, 2).  Stage s with radix R, after Ns = product of
+// the earlier radices, takes butterfly j (0 <= j < L/R) with k = j mod Ns:
+//   v[r]  = a[j + r*L/R] * w_{Ns*R}^{r*k}          (r = 0..R-1)
+//   V     = R-point DFT of v
+//   b[(j-k)*R + k + r*Ns] = V[r]
+// which after the last stage leaves X[k] in natural order (Stockham's
+// self-sorting form of the Cooley-Tukey factorisation).  The first stage reads
+// global memory directly and the last writes it directly; stages in between
+// exchange through shared memory, so a two-stage line (L <= 256) touches shared
+// memory once.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdio>
+
+#include "fb_internal.h"
+
+namespace fbfft {
+
+__host__ __device__ __forceinline__ float2 operator+(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
+__host__ __device__ __forceinline__ float2 operator-(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+__host__ __device__ __forceinline__ float2 operator*(float s, float2 a) { return make_float2(s * a.x, s * a.y); }
+
+__host__ __device__ __forceinline__ float2 cmul(float2 a, float2 b)
+{
+    return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+// a * w for the forward sign, a * conj(w) for the inverse (tables hold exp(-...)).
+template <bool FWD>
+__host__ __device__ __forceinline__ float2 twmul(float2 a, float2 w)
+{
+    return FWD ? make_float2(a.x * w.x - a.y * w.y, a.x * w.y + a.y * w.x)
+               : make_float2(a.x * w.x + a.y * w.y, a.y * w.x - a.x * w.y);
+}
+// z * (s*i), s = -1 forward, +1 inverse.
+template <bool FWD>
+__host__ __device__ __forceinline__ float2 mul_si(float2 z)
+{
+    return FWD ? make_float2(z.y, -z.x) : make_float2(-z.y, z.x);
+}
+// z * (C + s*i*S)  ==  C*z + S*(s*i*z)
+template <bool FWD>
+__host__ __device__ __forceinline__ float2 rot(float2 z, float C, float S)
+{
+    const float2 q = mul_si<FWD>(z);
+    return make_float2(C * z.x + S * q.x, C * z.y + S * q.y);
+}
+
+// Constants: cos/sin of 2*pi*m/16, 2*pi/3, 2*pi/5, 4*pi/5.
+#define FB_C16_1 0.92387953251128675613f  // cos(pi/8)
+#define FB_S16_1 0.38268343236508977173f  // sin(pi/8)
+#define FB_R2    0.70710678118654752440f  // sqrt(2)/2
+#define FB_S3    0.86602540378443864676f  // sin(2pi/3)
+#define FB_C5_1  0.30901699437494742410f  // cos(2pi/5)
+#define FB_C5_2 -0.80901699437494742410f  // cos(4pi/5)
+#define FB_S5_1  0.95105651629515357212f  // sin(2pi/5)
+#define FB_S5_2  0.58778525229247312917f  // sin(4pi/5)
+
+template <bool FWD>
+__host__ __device__ __forceinline__ void dft2(float2& a, float2& b)
+{
+    const float2 t = a;
+    a = t + b;
+    b = t - b;
+}
+
+template <bool FWD>
+__host__ __device__ __forceinline__ void dft4(float2& v0, float2& v1, float2& v2, float2& v3)
+{
+    const float2 t0 = v0 + v2, t1 = v0 - v2, t2 = v1 + v3, t3 = mul_si<FWD>(v1 - v3);
+    v0 = t0 + t2;
+    v2 = t0 - t2;
+    v1 = t1 + t3;
+    v3 = t1 - t3;
+}
+
+template <bool FWD>
+__host__ __device__ __forceinline__ void dft3(float2& a, float2& b, float2& c)
+{
+    const float2 t = b + c;
+    const float2 m = a - 0.5f * t;
+    const float2 d = FB_S3 * mul_si<FWD>(b - c);
+    a = a + t;
+    b = m + d;
+    c = m - d;
+}
+
+template <bool FWD>
+__host__ __device__ __forceinline__ void dft5(float2* v)
+{
+    const float2 t1 = v[1] + v[4], t2 = v[2] + v[3], t3 = v[1] - v[4], t4 = v[2] - v[3];
+    const float2 a1 = make_float2(v[0].x + FB_C5_1 * t1.x + FB_C5_2 * t2.x, v[0].y + FB_C5_1 * t1.y + FB_C5_2 * t2.y);
+    const float2 a2 = make_float2(v[0].x + FB_C5_2 * t1.x + FB_C5_1 * t2.x, v[0].y + FB_C5_2 * t1.y + FB_C5_1 * t2.y);
+    const float2 b1 = mul_si<FWD>(make_float2(FB_S5_1 * t3.x + FB_S5_2 * t4.x, FB_S5_1 * t3.y + FB_S5_2 * t4.y));
+    const float2 b2 = mul_si<FWD>(make_float2(FB_S5_2 * t3.x - FB_S5_1 * t4.x, FB_S5_2 * t3.y - FB_S5_1 * t4.y));
+    v[0] = v[0] + t1 + t2;
+    v[1] = a1 + b1;
+    v[4] = a1 - b1;
+    v[2] = a2 + b2;
+    v[3] = a2 - b2;
+}
+
+// 8 = 2 x 4: even/odd 4-point DFTs, then Y[k] = E[k] +- w8^k O[k].
+template <bool FWD>
+__host__ __device__ __forceinline__ void dft8(float2* v)
+{
+    float2 e0 = v[0], e1 = v[2], e2 = v[4], e3 = v[6];
+    float2 o0 = v[1], o1 = v[3], o2 = v[5], o3 = v[7];
+    dft4<FWD>(e0, e1, e2, e3);
+    dft4<FWD>(o0, o1, o2, o3);
+    o1 = rot<FWD>(o1, FB_R2, FB_R2);
+    o2 = mul_si<FWD>(o2);
+    o3 = rot<FWD>(o3, -FB_R2, FB_R2);
+    v[0] = e0 + o0;
+    v[4] = e0 - o0;
+    v[1] = e1 + o1;
+    v[5] = e1 - o1;
+    v[2] = e2 + o2;
+    v[6] = e2 - o2;
+    v[3] = e3 + o3;
+    v[7] = e3 - o3;
+}
+
+// 16 = 4 x 4: with r = 4*r1 + r2 and k = k1 + 4*k2,
+// w16^{rk} = w4^{r1 k1} w16^{r2 k1} w4^{r2 k2}.
+template <bool FWD>
+__host__ __device__ __forceinline__ void dft16(float2* v)
+{
+#pragma unroll
+    for (int r2 = 0; r2 < 4; ++r2) dft4<FWD>(v[r2], v[4 + r2], v[8 + r2], v[12 + r2]);
+    // v[4*k1 + r2] now holds A[r2][k1]; multiply by w16^{r2*k1}
+    v[5] = rot<FWD>(v[5], FB_C16_1, FB_S16_1);    // (1,1): m=1
+    v[6] = rot<FWD>(v[6], FB_R2, FB_R2);          // k1=1, r2=2: m=2
+    v[7] = rot<FWD>(v[7], FB_S16_1, FB_C16_1);    // k1=1, r2=3: m=3
+    v[9] = rot<FWD>(v[9], FB_R2, FB_R2);          // k1=2, r2=1: m=2
+    v[10] = mul_si<FWD>(v[10]);                   // k1=2, r2=2: m=4
+    v[11] = rot<FWD>(v[11], -FB_R2, FB_R2);       // k1=2, r2=3: m=6
+    v[13] = rot<FWD>(v[13], FB_S16_1, FB_C16_1);  // k1=3, r2=1: m=3
+    v[14] = rot<FWD>(v[14], -FB_R2, FB_R2);       // k1=3, r2=2: m=6
+    v[15] = rot<FWD>(v[15], -FB_C16_1, -FB_S16_1);// k1=3, r2=3: m=9
+#pragma unroll
+    for (int k1 = 0; k1 < 4; ++k1) dft4<FWD>(v[4 * k1], v[4 * k1 + 1], v[4 * k1 + 2], v[4 * k1 + 3]);
+    // v[4*k1 + k2] holds Y[k1 + 4*k2]: transpose the 4x4 index
+    float2 y[16];
+#pragma unroll
+    for (int k1 = 0; k1 < 4; ++k1)
+#pragma unroll
+        for (int k2 = 0; k2 < 4; ++k2) y[k1 + 4 * k2] = v[4 * k1 + k2];
+#pragma unroll
+    for (int i = 0; i < 16; ++i) v[i] = y[i];
+}
+
+template <int R, bool FWD>
+__host__ __device__ __forceinline__ void dft(float2* v)
+{
+    if constexpr (R == 2) dft2<FWD>(v[0], v[1]);
+    else if constexpr (R == 3) dft3<FWD>(v[0], v[1], v[2]);
+    else if constexpr (R == 4) dft4<FWD>(v[0], v[1], v[2], v[3]);
+    else if constexpr (R == 5) dft5<FWD>(v);
+    else if constexpr (R == 8) dft8<FWD>(v);
+    else if constexpr (R == 16) dft16<FWD>(v);
+}
+
+#ifdef __CUDACC__
+
+__host__ __device__ constexpr int ilog2(int x) { return x <= 1 ? 0 : 1 + ilog2(x >> 1); }
+
+// Padded shared-memory index of element i of a line: one gap every 16 values
+// keeps the stride-R writes of early stages free of bank conflicts.
+__device__ __forceinline__ int spad(int i) { return i + (i >> 4); }
+
+// ---------------------------------------------------------------------------
+// TMA (bulk asynchronous copy) and mbarrier primitives, in inline PTX.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ unsigned smem_u32(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(unsigned long long* bar, unsigned count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void fence_mbar_init()
+{
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+// Make this thread's generic-proxy shared-memory writes visible to the TMA engine.
+__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(unsigned long long* bar, unsigned bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(unsigned long long* bar, unsigned parity)
+{
+    unsigned ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+__device__ __forceinline__ unsigned long long global_ns()
+{
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+// Wait for the phase with the given parity; give up after kWaitLimitNs.
+constexpr unsigned long long kWaitLimitNs = 1000000000ULL;
+__device__ __forceinline__ bool mbar_wait_bounded(unsigned long long* bar, unsigned parity)
+{
+    if (mbar_try_wait(bar, parity)) return true;
+    const unsigned long long t0 = global_ns();
+    while (!mbar_try_wait(bar, parity))
+        if (global_ns() - t0 > kWaitLimitNs) return false;
+    return true;
+}
+// global -> shared, contiguous bytes; completion counted on `bar`.
+__device__ __forceinline__ void bulk_load_1d(void* dst, const void* src, unsigned bytes, unsigned long long* bar)
+{
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     smem_u32(dst)),
+                 "l"(src), "r"(bytes), "r"(smem_u32(bar))
+                 : "memory");
+}
+// shared -> global, contiguous bytes; tracked by the issuing thread's bulk group.
+__device__ __forceinline__ void bulk_store_1d(void* dst, const void* src, unsigned bytes)
+{
+    asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;" ::"l"(dst), "r"(smem_u32(src)),
+                 "r"(bytes)
+                 : "memory");
+}
+// 3-D tiled tensor copies (coordinates innermost first).
+__device__ __forceinline__ void tma_load_3d(void* dst, const void* tmap, int x, int y, int z, unsigned long long* bar)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], "
+        "[%5];" ::"r"(smem_u32(dst)),
+        "l"(tmap), "r"(x), "r"(y), "r"(z), "r"(smem_u32(bar))
+        : "memory");
+}
+__device__ __forceinline__ void tma_store_3d(const void* tmap, int x, int y, int z, const void* src)
+{
+    asm volatile("cp.async.bulk.tensor.3d.global.shared::cta.tile.bulk_group [%0, {%1, %2, %3}], [%4];" ::"l"(tmap),
+                 "r"(x), "r"(y), "r"(z), "r"(smem_u32(src))
+                 : "memory");
+}
+__device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void bulk_wait_read_all() { asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory"); }
+__device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
+
+struct TileIdx {
+    long long o, c0;
+    int Tv;
+};
+__device__ __forceinline__ TileIdx tile_index(const PassDesc& d, long long tile)
+{
+    TileIdx ti;
+    ti.o = tile / d.tiles_per_o;
+    ti.c0 = (tile - ti.o * d.tiles_per_o) << d.logT;
+    const long long rem = d.C - ti.c0;
+    const int T = 1 << d.logT;
+    ti.Tv = rem < T ? (int)rem : T;
+    return ti;
+}
+
+// Thread 0: start the TMA loads of one tile into a landing buffer.
+// n-fast tiles are contiguous (line stride == L) and land as [t][n];
+// c-fast tiles land as [n][t] by 3-D boxes of T x box_rows (zero fill past C).
+__device__ __forceinline__ void issue_tile_load(const PassDesc& d, const CUtensorMap* tm_in, long long tile,
+                                                float2* land, unsigned long long* bar)
+{
+    const TileIdx ti = tile_index(d, tile);
+    const int L = d.L, T = 1 << d.logT;
+    if (!d.in_tfast) {
+        const unsigned bytes = (unsigned)(ti.Tv * L) * 8u;
+        mbar_arrive_expect_tx(bar, bytes + d.debug_extra_tx);
+        bulk_load_1d(land, d.in + ti.o * d.in_so + ti.c0 * d.in_sc, bytes, bar);
+    } else {
+        mbar_arrive_expect_tx(bar, (unsigned)(T * L) * 8u + d.debug_extra_tx);
+        for (int n0 = 0; n0 < L; n0 += d.box_rows)
+            tma_load_3d(land + n0 * T, tm_in, (int)ti.c0, n0, (int)ti.o, bar);
+    }
+}
+// Thread 0: start the TMA stores of one finished tile from its buffer.
+__device__ __forceinline__ void issue_tile_store(const PassDesc& d, const CUtensorMap* tm_out, long long tile,
+                                                 const float2* land)
+{
+    const TileIdx ti = tile_index(d, tile);
+    const int L = d.L, T = 1 << d.logT;
+    if (!d.out_tfast) {
+        bulk_store_1d(d.out + ti.o * d.out_so + ti.c0 * d.out_sc, land, (unsigned)(ti.Tv * L) * 8u);
+    } else {
+        for (int k0 = 0; k0 < L; k0 += d.box_rows) tma_store_3d(tm_out, (int)ti.c0, k0, (int)ti.o, land + k0 * T);
+    }
+    bulk_commit();
+}
+
+// Plain-copy fallback (misaligned bases, odd strides): the whole CTA copies.
+template <int THREADS>
+__device__ __forceinline__ void plain_tile_load(const PassDesc& d, const TileIdx& ti, float2* land)
+{
+    const int L = d.L, T = 1 << d.logT;
+    const float2* gin = d.in + ti.o * d.in_so + ti.c0 * d.in_sc;
+    if (!d.in_tfast) {
+        for (int e = threadIdx.x; e < ti.Tv * L; e += THREADS) {
+            const int t = e / L, n = e - t * L;
+            land[e] = gin[(long long)t * d.in_sc + (long long)n * d.in_sn];
+        }
+    } else {
+        for (int e = threadIdx.x; e < T * L; e += THREADS) {
+            const int n = e >> d.logT, t = e & (T - 1);
+            if (t < ti.Tv) land[e] = gin[(long long)n * d.in_sn + t];
+        }
+    }
+}
+template <int THREADS>
+__device__ __forceinline__ void plain_tile_store(const PassDesc& d, const TileIdx& ti, const float2* land)
+{
+    const int L = d.L, T = 1 << d.logT;
+    float2* gout = d.out + ti.o * d.out_so + ti.c0 * d.out_sc;
+    if (!d.out_tfast) {
+        for (int e = threadIdx.x; e < ti.Tv * L; e += THREADS) {
+            const int t = e / L, k = e - t * L;
+            gout[(long long)t * d.out_sc + (long long)k * d.out_sk] = land[e];
+        }
+    } else {
+        for (int e = threadIdx.x; e < T * L; e += THREADS) {
+            const int k = e >> d.logT, t = e & (T - 1);
+            if (t < ti.Tv) gout[(long long)k * d.out_sk + t] = land[e];
+        }
+    }
+}
+
+// One Stockham stage for the whole tile.  Threads cover butterflies (t, j):
+// t-fast mapping puts consecutive threads on consecutive lines (conflict-free
+// on the [n][t] landing layout), j-fast on consecutive j.  Stage 0 reads the
+// landing buffer, the last stage writes the tile's output layout back into it
+// (with the four-step twiddle and the 1/N scale applied), the stages between
+// work in place on the padded work buffer.
+enum StagePos { kPosOnly = 0, kPosFirst = 1, kPosMid = 2, kPosLast = 3 };
+
+template <int R, int THREADS, bool FWD, int POS, int E = kElemsPerThread>
+__device__ __forceinline__ void stage(const PassDesc& d, int Ns, int twoff, float2* land, float2* work, int Tv,
+                                      int c0)
+{
+    constexpr int Q = (E + R - 1) / R;
+    constexpr bool first = POS == kPosOnly || POS == kPosFirst;
+    constexpr bool last = POS == kPosOnly || POS == kPosLast;
+    const bool tfast = (first && d.in_tfast) || (last && d.out_tfast);
+    const int tid = threadIdx.x;
+    const int logT = d.logT;
+    const int T = 1 << logT;
+    const int G = THREADS >> logT;  // threads per line
+    const int L = d.L;
+    const int LR = L / R;
+    int t, jb;
+    if (tfast) {
+        t = tid & (T - 1);
+        jb = tid >> logT;
+    } else {
+        t = tid >> (ilog2(THREADS) - logT);  // tid / G, G a power of two
+        jb = tid & (G - 1);
+    }
+    const bool tok = t < Tv;
+    float2 v[Q][R];
+#pragma unroll
+    for (int q = 0; q < Q; ++q) {
+        const int j = jb + q * G;
+        if (tok && j < LR) {
+            if constexpr (first) {
+                if (d.in_tfast) {
+#pragma unroll
+                    for (int r = 0; r < R; ++r) v[q][r] = land[((j + r * LR) << logT) + t];
+                } else {
+#pragma unroll
+                    for (int r = 0; r < R; ++r) v[q][r] = land[t * L + j + r * LR];
+                }
+            } else {
+                const float2* p = work + t * d.LS;
+#pragma unroll
+                for (int r = 0; r < R; ++r) v[q][r] = p[spad(j + r * LR)];
+            }
+        }
+    }
+    if constexpr (first == last) __syncthreads();  // reads and writes share one buffer
+#pragma unroll
+    for (int q = 0; q < Q; ++q) {
+        const int j = jb + q * G;
+        if (tok && j < LR) {
+            const int k = j % Ns;
+            if (!first && Ns > 1) {
+                const float2* tw = d.tw + twoff + k;
+#pragma unroll
+                for (int r = 1; r < R; ++r) v[q][r] = twmul<FWD>(v[q][r], __ldg(tw + (r - 1) * Ns));
+            }
+            dft<R, FWD>(v[q]);
+            const int base = (j - k) * R + k;
+            if constexpr (!last) {
+                float2* p = work + t * d.LS;
+#pragma unroll
+                for (int r = 0; r < R; ++r) p[spad(base + r * Ns)] = v[q][r];
+            } else {
+                const unsigned c = (unsigned)(c0 + t);
+#pragma unroll
+                for (int r = 0; r < R; ++r) {
+                    const int kk = base + r * Ns;
+                    float2 y = v[q][r];
+                    if (d.ptw) {
+                        const unsigned m = c * (unsigned)kk;  // < N < 2^31
+                        const float2 w = cmul(__ldg(d.ptw_hi + (m >> d.ptw_log)),
+                                              __ldg(d.ptw_lo + (m & ((1u << d.ptw_log) - 1))));
+                        y = twmul<FWD>(y, w);
+                    }
+                    if (d.apply_scale) y = d.scale * y;
+                    if (d.out_tfast)
+                        land[(kk << logT) + t] = y;
+                    else
+                        land[t * L + kk] = y;
+                }
+            }
+        }
+    }
+}
+
+template <int THREADS, bool FWD, int POS, int E>
+__device__ __forceinline__ void run_stage(int R, const PassDesc& d, int Ns, int twoff, float2* land, float2* work,
+                                          int Tv, int c0)
+{
+    switch (R) {
+    case 16: stage<16, THREADS, FWD, POS, E>(d, Ns, twoff, land, work, Tv, c0); break;
+    case 8: stage<8, THREADS, FWD, POS, E>(d, Ns, twoff, land, work, Tv, c0); break;
+    case 5: stage<5, THREADS, FWD, POS, E>(d, Ns, twoff, land, work, Tv, c0); break;
+    case 4: stage<4, THREADS, FWD, POS, E>(d, Ns, twoff, land, work, Tv, c0); break;
+    case 3: stage<3, THREADS, FWD, POS, E>(d, Ns, twoff, land, work, Tv, c0); break;
+    default: stage<2, THREADS, FWD, POS, E>(d, Ns, twoff, land, work, Tv, c0); break;
+    }
+}
+
+// Power-of-two schedules, fixed at compile time: log2 L = 4a + b gives a
+// radix-16 stages followed by one radix-2^b stage when b > 0.
+__host__ __device__ constexpr int pow2_nst(int lg) { return lg / 4 + (lg % 4 ? 1 : 0); }
+__host__ __device__ constexpr int pow2_radix(int lg, int s) { return s < lg / 4 ? 16 : (1 << (lg % 4)); }
+
+template <int THREADS, bool FWD, int LG, int S>
+__device__ __forceinline__ void pow2_stage(const PassDesc& d, float2* land, float2* work, int Tv, int c0)
+{
+    constexpr int NST = pow2_nst(LG);
+    constexpr int R = pow2_radix(LG, S);
+    constexpr int POS = NST == 1 ? kPosOnly : (S == 0 ? kPosFirst : (S == NST - 1 ? kPosLast : kPosMid));
+    stage<R, THREADS, FWD, POS>(d, d.ns[S], d.twoff[S], land, work, Tv, c0);
+}
+template <int THREADS, bool FWD, int LG, int S>
+__device__ __forceinline__ void pow2_rest(const PassDesc& d, float2* land, float2* work, int Tv, int c0, bool async)
+{
+    if constexpr (S < pow2_nst(LG)) {
+        pow2_stage<THREADS, FWD, LG, S>(d, land, work, Tv, c0);
+        if (async && S == pow2_nst(LG) - 1) fence_proxy_async();
+        __syncthreads();
+        pow2_rest<THREADS, FWD, LG, S + 1>(d, land, work, Tv, c0, async);
+    }
+}
+
+// The line pass.  LG > 0: line length 2^LG with a compile-time schedule;
+// LG == 0: any 5-smooth length, stage radices read from the descriptor.
+// Persistent CTAs walk tiles blockIdx.x, +gridDim.x, ...  With TMA on
+// (d.async_io), tile i+1 streams into the second landing buffer while tile i
+// is transformed, and finished tiles leave by TMA stores.
+template <int THREADS, bool FWD, int LG>
+__global__ void __launch_bounds__(THREADS, LG == 0 ? 1 : 512 / THREADS)
+    k_line_fft(const __grid_constant__ LineArgs a)
+{
+    extern __shared__ __align__(128) unsigned char smem_dyn[];
+    // 128-byte aligned base (the size includes 128 bytes of slack for this)
+    unsigned char* smem_raw = smem_dyn + ((128u - (smem_u32(smem_dyn) & 127u)) & 127u);
+    unsigned long long* bar = reinterpret_cast<unsigned long long*>(smem_raw);  // 2 mbarriers
+    float2* land0 = reinterpret_cast<float2*>(smem_raw + 128);
+    const int T = 1 << a.d.logT;
+    const bool async = a.d.async_io != 0;
+    float2* work = land0 + (async ? 2 : 1) * a.d.land_stride;
+    const long long step = gridDim.x;
+    // The descriptor, copied to shared memory once: field reads and the
+    // dynamically indexed stage tables then never touch local memory.
+    __shared__ PassDesc sd;
+    {
+        const int* src = reinterpret_cast<const int*>(&a.d);
+        int* dst = reinterpret_cast<int*>(&sd);
+        for (int w = threadIdx.x; w < (int)(sizeof(PassDesc) / 4); w += THREADS) dst[w] = src[w];
+    }
+    __syncthreads();
+    const PassDesc& d = sd;
+    if (async && threadIdx.x == 0) {
+        mbar_init(&bar[0], 1);
+        mbar_init(&bar[1], 1);
+        fence_mbar_init();
+        if (blockIdx.x < d.ntiles) issue_tile_load(d, &a.tm_in, blockIdx.x, land0, &bar[0]);
+        if (blockIdx.x + step < d.ntiles)
+            issue_tile_load(d, &a.tm_in, blockIdx.x + step, land0 + d.land_stride, &bar[1]);
+    }
+    __syncthreads();
+    int i = 0;
+    for (long long tile = blockIdx.x; tile < d.ntiles; tile += step, ++i) {
+        const TileIdx ti = tile_index(d, tile);
+        const int buf = async ? (i & 1) : 0;
+        float2* land = land0 + buf * d.land_stride;
+        const int c0 = (int)ti.c0;
+        if (async) {
+            const bool bad = !mbar_wait_bounded(&bar[buf], (unsigned)(i >> 1) & 1u);
+            if (__syncthreads_or(bad)) {
+                if (threadIdx.x == 0) {
+                    atomicExch(d.err, 1);
+                    bulk_wait_all();
+                    if (i == 0 && tile + step < d.ntiles) mbar_wait_bounded(&bar[1], 0);
+                }
+                return;
+            }
+        } else {
+            plain_tile_load<THREADS>(d, ti, land);
+            __syncthreads();
+        }
+        // stage 0
+        if constexpr (LG > 0) {
+            pow2_stage<THREADS, FWD, LG, 0>(d, land, work, ti.Tv, c0);
+        } else {
+            if (d.nst == 1)
+                run_stage<THREADS, FWD, kPosOnly, kGenericElems>(d.radix[0], d, 1, 0, land, work, ti.Tv, c0);
+            else
+                run_stage<THREADS, FWD, kPosFirst, kGenericElems>(d.radix[0], d, 1, 0, land, work, ti.Tv, c0);
+        }
+        if (async && d.nst == 1) fence_proxy_async();
+        __syncthreads();
+        // The previous tile's store has had a stage to drain: recycle its
+        // buffer for the next tile's load.
+        if (async && i >= 1 && threadIdx.x == 0 && tile + step < d.ntiles) {
+            bulk_wait_read_all();
+            issue_tile_load(d, &a.tm_in, tile + step, land0 + (buf ^ 1) * d.land_stride, &bar[buf ^ 1]);
+        }
+        // stages 1 .. nst-1
+        if constexpr (LG > 0) {
+            pow2_rest<THREADS, FWD, LG, 1>(d, land, work, ti.Tv, c0, async);
+        } else {
+            for (int s = 1; s < d.nst; ++s) {
+                if (s == d.nst - 1)
+                    run_stage<THREADS, FWD, kPosLast, kGenericElems>(d.radix[s], d, d.ns[s], d.twoff[s], land, work, ti.Tv, c0);
+                else
+                    run_stage<THREADS, FWD, kPosMid, kGenericElems>(d.radix[s], d, d.ns[s], d.twoff[s], land, work, ti.Tv, c0);
+                if (async && s == d.nst - 1) fence_proxy_async();
+                __syncthreads();
+            }
+        }
+        if (async) {
+            if (threadIdx.x == 0) issue_tile_store(d, &a.tm_out, tile, land);
+        } else {
+            plain_tile_store<THREADS>(d, ti, land);
+            __syncthreads();
+        }
+    }
+    if (async && threadIdx.x == 0) bulk_wait_all();
+}
+
+template <int THREADS, bool FWD, int LG>
+cudaError_t set_smem_attr()
+{
+    // The opt-in shared-memory limit is a per-device attribute: set it once
+    // per device for this kernel (a benign race if two threads do it).
+    static unsigned long long done = 0;
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    const unsigned long long bit = 1ULL << (dev & 63);
+    if (!(done & bit)) {
+        e = cudaFuncSetAttribute(k_line_fft<THREADS, FWD, LG>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 227 * 1024);
+        if (e != cudaSuccess) return e;
+        done |= bit;
+    }
+    return cudaSuccess;
+}
+template <int THREADS, bool FWD, int LG>
+cudaError_t launch_k(const LineArgs& a, long long grid, size_t smem, cudaStream_t stream)
+{
+    if (grid <= 0) return cudaSuccess;
+    cudaError_t e = set_smem_attr<THREADS, FWD, LG>();
+    if (e != cudaSuccess) return e;
+    const unsigned g = (unsigned)(grid > 0x7fffffffLL ? 0x7fffffffLL : grid);
+    k_line_fft<THREADS, FWD, LG><<<g, THREADS, smem, stream>>>(a);
+    return cudaGetLastError();
+}
+template <int THREADS, bool FWD, int LG>
+cudaError_t occ_k(size_t smem, int* blocks)
+{
+    cudaError_t e = set_smem_attr<THREADS, FWD, LG>();
+    if (e != cudaSuccess) return e;
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, k_line_fft<THREADS, FWD, LG>, THREADS, smem);
+}
+template <int THREADS, bool FWD, int LG>
+LineKernel kernel_entry()
+{
+    static const char* name = [] {
+        static char buf[64];
+        if (LG > 0)
+            snprintf(buf, sizeof(buf), "k_line_fft<%d,%s,L=%d>", THREADS, FWD ? "fwd" : "inv", 1 << LG);
+        else
+            snprintf(buf, sizeof(buf), "k_line_fft<%d,%s,generic>", THREADS, FWD ? "fwd" : "inv");
+        return (const char*)buf;
+    }();
+    return LineKernel{launch_k<THREADS, FWD, LG>, occ_k<THREADS, FWD, LG>, name};
+}
+
+#endif  // __CUDACC__
+
+}  // namespace fbfft

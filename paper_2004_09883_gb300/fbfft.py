@@ -1,0 +1,242 @@
+"""ctypes binding of ``libfbfft.so`` (the C ABI in ``include/fb_fft.h``).
+
+Argument marshalling only: every transform runs in the library's CUDA kernels.
+Device buffers are torch tensors (complex64, contiguous, on the plan's device);
+host buffers for :meth:`Plan.exec_host` are numpy complex64 arrays.  Importing
+this module raises if the compiled library is missing -- there is no fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libfbfft.so")
+
+FORWARD = -1
+INVERSE = 1
+SCALE_INV_N = 0x1
+MAX_SMEM_LEN = 4096
+MAX_1D_LEN = 4096 * 4096
+
+STATUS = {
+    0: "FB_FFT_OK", -1: "FB_FFT_ERR_INVALID_ARG", -2: "FB_FFT_ERR_UNSUPPORTED_SIZE",
+    -3: "FB_FFT_ERR_ALLOC", -4: "FB_FFT_ERR_CUDA", -5: "FB_FFT_ERR_TIMEOUT",
+    -6: "FB_FFT_ERR_BAD_PLAN", -7: "FB_FFT_ERR_NO_DEVICE",
+}
+
+
+class FFTError(RuntimeError):
+    def __init__(self, status: int, what: str):
+        self.status = status
+        super().__init__(f"{what}: {STATUS.get(status, status)} ({_text(status)})")
+
+
+class Info(ctypes.Structure):
+    _fields_ = [("passes", ctypes.c_int), ("reserved", ctypes.c_int),
+                ("smem_len_max", ctypes.c_longlong), ("scratch_bytes", ctypes.c_longlong),
+                ("twiddle_bytes", ctypes.c_longlong), ("elements", ctypes.c_longlong),
+                ("batch", ctypes.c_longlong)]
+
+
+if not os.path.exists(LIB_PATH):
+    raise ImportError(f"{LIB_PATH} is missing: build it with __graft_entry__.build() "
+                      "(python -m paper_2004_09883_gb300.build)")
+
+lib = ctypes.CDLL(LIB_PATH)
+_vp, _ll, _int = ctypes.c_void_p, ctypes.c_longlong, ctypes.c_int
+_sig = {
+    "fb_fft_plan": (_int, [ctypes.POINTER(_vp), _int, ctypes.POINTER(_ll), _ll, ctypes.c_uint, _vp]),
+    "fb_fft_exec": (_int, [_vp, _vp, _vp, _int]),
+    "fb_fft_exec_host": (_int, [_vp, _vp, _vp, _int]),
+    "fb_fft_check": (_int, [_vp]),
+    "fb_fft_set_stream": (_int, [_vp, _vp]),
+    "fb_fft_destroy": (_int, [_vp]),
+    "fb_fft_status_string": (ctypes.c_char_p, [_int]),
+    "fb_fft_plan_info": (_int, [_vp, ctypes.POINTER(Info)]),
+    "fb_fft_factorize": (_int, [_ll, ctypes.POINTER(_int), _int, ctypes.POINTER(_int)]),
+    "fb_fft_split": (_int, [_ll, ctypes.POINTER(_ll), ctypes.POINTER(_ll)]),
+    "fb_fft_profile": (_int, [_vp, _int]),
+    "fb_fft_profile_read": (_int, [_vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(_ll), _int,
+                                   ctypes.POINTER(_int)]),
+    "fb_fft_pass_name": (ctypes.c_char_p, [_vp, _int]),
+    "fb_fft_launch_count": (_ll, []),
+    "fb_fft_twiddles": (_int, [_ll, _ll, ctypes.POINTER(ctypes.c_float)]),
+    "fb_fft_debug_inject_timeout": (_int, [_vp, _int]),
+}
+for _name, (_res, _args) in _sig.items():
+    _f = getattr(lib, _name)
+    _f.restype = _res
+    _f.argtypes = _args
+
+
+def _text(status: int) -> str:
+    return lib.fb_fft_status_string(int(status)).decode()
+
+
+def _check(rc: int, what: str) -> None:
+    if rc != 0:
+        raise FFTError(rc, what)
+
+
+def factorize(n: int) -> list[int]:
+    """Radix schedule the planner uses for an in-shared-memory line of length n."""
+    buf = (_int * 32)()
+    cnt = _int()
+    _check(lib.fb_fft_factorize(int(n), buf, 32, ctypes.byref(cnt)), "fb_fft_factorize")
+    return list(buf[: cnt.value])
+
+
+def split(n: int) -> tuple[int, int]:
+    """Four-step split n = n1 * n2 of a rank-1 length (n2 == 1: one pass)."""
+    n1, n2 = _ll(), _ll()
+    _check(lib.fb_fft_split(int(n), ctypes.byref(n1), ctypes.byref(n2)), "fb_fft_split")
+    return n1.value, n2.value
+
+
+def launch_count() -> int:
+    return int(lib.fb_fft_launch_count())
+
+
+def twiddles(d: int, count: int) -> np.ndarray:
+    """exp(-2*pi*i*m/d), m = 0..count-1, from the library's FP64 twiddle kernel."""
+    out = np.empty(2 * int(count), dtype=np.float32)
+    _check(lib.fb_fft_twiddles(int(d), int(count), out.ctypes.data_as(ctypes.POINTER(ctypes.c_float))),
+           "fb_fft_twiddles")
+    return out.view(np.complex64)
+
+
+def _stream_handle(stream) -> int:
+    if stream is None:
+        import torch
+        if not torch.cuda.is_available():
+            return 0
+        return torch.cuda.current_stream().cuda_stream
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+class Plan:
+    """A planned complex64 C2C transform: ``dims`` (row-major) x ``batch``."""
+
+    def __init__(self, dims, batch: int = 1, scale_inv_n: bool = False, stream=None):
+        dims = [int(d) for d in (dims if hasattr(dims, "__len__") else [dims])]
+        self.dims = dims
+        self.batch = int(batch)
+        self.flags = SCALE_INV_N if scale_inv_n else 0
+        self.n = int(np.prod(dims))
+        self._h = _vp()
+        cd = (_ll * len(dims))(*dims)
+        self._stream = _stream_handle(stream)
+        _check(lib.fb_fft_plan(ctypes.byref(self._h), len(dims), cd, self.batch, self.flags,
+                               _vp(self._stream)), "fb_fft_plan")
+
+    # -- lifetime -----------------------------------------------------------
+    def close(self) -> None:
+        if self._h:
+            rc = lib.fb_fft_destroy(self._h)
+            self._h = _vp()
+            _check(rc, "fb_fft_destroy")
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    @property
+    def handle(self) -> int:
+        return self._h.value or 0
+
+    # -- execution ----------------------------------------------------------
+    def set_stream(self, stream) -> None:
+        self._stream = _stream_handle(stream)
+        _check(lib.fb_fft_set_stream(self._h, _vp(self._stream)), "fb_fft_set_stream")
+
+    def exec_ptr(self, in_ptr: int, out_ptr: int, direction: int = FORWARD) -> None:
+        """Run on raw device pointers (asynchronous on the plan's stream)."""
+        _check(lib.fb_fft_exec(self._h, _vp(in_ptr), _vp(out_ptr), int(direction)), "fb_fft_exec")
+
+    def exec(self, x, out=None, direction: int = FORWARD):
+        """Transform torch complex64 CUDA tensor ``x`` (batch*prod(dims) values)
+        into ``out`` (new tensor if None; ``out is x`` runs in place)."""
+        import torch
+        if x.dtype != torch.complex64 or not x.is_cuda or not x.is_contiguous():
+            raise ValueError("x must be a contiguous complex64 CUDA tensor")
+        if x.numel() != self.n * self.batch:
+            raise ValueError(f"x has {x.numel()} values, plan expects {self.n * self.batch}")
+        if out is None:
+            out = torch.empty_like(x)
+        elif out.dtype != torch.complex64 or not out.is_contiguous() or out.numel() != x.numel():
+            raise ValueError("out must be a contiguous complex64 tensor like x")
+        s = torch.cuda.current_stream(x.device).cuda_stream
+        if s != self._stream:
+            self.set_stream(s)
+        self.exec_ptr(x.data_ptr(), out.data_ptr(), direction)
+        return out
+
+    def exec_host(self, x: np.ndarray, out: np.ndarray | None = None, direction: int = FORWARD):
+        """Drop-in CPU-array form: host in, host out, synchronous."""
+        x = np.ascontiguousarray(x, dtype=np.complex64)
+        if x.size != self.n * self.batch:
+            raise ValueError("size mismatch")
+        if out is None:
+            out = np.empty_like(x)
+        if out.dtype != np.complex64 or not out.flags.c_contiguous or out.size != x.size:
+            raise ValueError("out must be a contiguous complex64 array like x")
+        _check(lib.fb_fft_exec_host(self._h, _vp(x.ctypes.data), _vp(out.ctypes.data), int(direction)),
+               "fb_fft_exec_host")
+        return out
+
+    def debug_inject_timeout(self, enable: bool = True) -> None:
+        """Test hook: make the plan's bounded device waits run out."""
+        _check(lib.fb_fft_debug_inject_timeout(self._h, 1 if enable else 0), "fb_fft_debug_inject_timeout")
+
+    def check(self) -> None:
+        """Synchronise and raise if a kernel reported a bounded-wait timeout."""
+        _check(lib.fb_fft_check(self._h), "fb_fft_check")
+
+    # -- introspection ------------------------------------------------------
+    def info(self) -> dict:
+        inf = Info()
+        _check(lib.fb_fft_plan_info(self._h, ctypes.byref(inf)), "fb_fft_plan_info")
+        return {f: getattr(inf, f) for f, _ in Info._fields_ if f != "reserved"}
+
+    def pass_names(self) -> list[str]:
+        names = []
+        i = 0
+        while True:
+            nm = lib.fb_fft_pass_name(self._h, i)
+            if not nm:
+                return names
+            names.append(nm.decode())
+            i += 1
+
+    def profile(self, enable: bool = True) -> None:
+        _check(lib.fb_fft_profile(self._h, 1 if enable else 0), "fb_fft_profile")
+
+    def profile_read(self) -> list[tuple[str, float, int]]:
+        """Per pass role: (name, total ms, launches) since the last read."""
+        cap = 16
+        ms = (ctypes.c_double * cap)()
+        cnt = (_ll * cap)()
+        n = _int()
+        _check(lib.fb_fft_profile_read(self._h, ms, cnt, cap, ctypes.byref(n)), "fb_fft_profile_read")
+        names = self.pass_names()
+        return [(names[i], ms[i], cnt[i]) for i in range(min(n.value, cap))]
+
+
+def fft(x, dims, direction: int = FORWARD, scale_inv_n: bool = False, out=None):
+    """One-shot convenience: plan, run, destroy (plans should be reused in hot loops)."""
+    n = int(np.prod(dims))
+    with Plan(dims, x.numel() // n, scale_inv_n=scale_inv_n) as p:
+        return p.exec(x, out, direction)

@@ -1,0 +1,147 @@
+"""Host-side checks of the C ABI library that need no GPU: it builds, loads,
+exports every entry point the header declares, and its planner logic (radix
+schedules, four-step splits, argument validation) behaves as documented."""
+import ctypes
+import os
+import re
+import subprocess
+
+import numpy as np
+import pytest
+
+from paper_2004_09883_gb300 import build as fbbuild
+from paper_2004_09883_gb300 import inputs
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADERS = [os.path.join(ROOT, "include", f) for f in sorted(os.listdir(os.path.join(ROOT, "include")))
+           if f.endswith(".h")]
+
+
+@pytest.fixture(scope="module")
+def fb():
+    fbbuild.build()
+    from paper_2004_09883_gb300 import fbfft
+    return fbfft
+
+
+def declared_functions():
+    names = []
+    for h in HEADERS:
+        text = open(h).read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        names += re.findall(r"^\s*(?:const\s+)?[A-Za-z_][\w\s\*]*?\b(fb_fft_\w+)\s*\(", text, flags=re.M)
+    return sorted(set(names))
+
+
+def test_header_declares_the_core_calls():
+    names = declared_functions()
+    for core in ("fb_fft_plan", "fb_fft_exec", "fb_fft_destroy", "fb_fft_exec_host", "fb_fft_status_string"):
+        assert core in names
+
+
+def test_library_exports_every_declared_symbol(fb):
+    nm = subprocess.run(["nm", "-D", "--defined-only", fb.LIB_PATH], capture_output=True, text=True,
+                        check=True).stdout
+    exported = set(re.findall(r"\bT\s+(fb_fft_\w+)", nm))
+    missing = [n for n in declared_functions() if n not in exported]
+    assert not missing, f"declared but not exported: {missing}"
+    for n in declared_functions():
+        assert hasattr(fb.lib, n)
+
+
+def test_header_compiles_as_plain_c(tmp_path):
+    src = tmp_path / "use.c"
+    src.write_text('#include "fb_fft.h"\nint main(void){ fb_fft_plan_t p = 0; (void)p; '
+                   'return fb_fft_destroy(0); }\n')
+    subprocess.run(["gcc", "-std=c99", "-Wall", "-Werror", "-c", f"-I{ROOT}/include", str(src),
+                    "-o", str(tmp_path / "use.o")], check=True)
+
+
+def test_status_strings(fb):
+    for code in range(-7, 1):
+        assert fb.lib.fb_fft_status_string(code)
+    assert b"unknown" in fb.lib.fb_fft_status_string(-99)
+
+
+@pytest.mark.parametrize("n", inputs.smooth_lengths(1, 4096))
+def test_factorize_every_smooth_length(fb, n):
+    r = fb.factorize(n)
+    assert int(np.prod(r)) == n
+    assert all(x in (2, 3, 4, 5, 8, 16) for x in r)
+    assert len(r) <= 8
+    # 16s lead, at most one other power-of-two radix, then 5s, then 3s
+    p2 = [x for x in r if x in (2, 4, 8)]
+    assert len(p2) <= 1
+    assert r == sorted(r, key=lambda x: {16: 0, 8: 1, 4: 1, 2: 1, 5: 2, 3: 3}[x])
+
+
+@pytest.mark.parametrize("n", [0, -4, 7, 14, 4097 * 2, 8192, 11 * 16])
+def test_factorize_rejects(fb, n):
+    with pytest.raises(fb.FFTError):
+        fb.factorize(n)
+
+
+@pytest.mark.parametrize("n", [4097 * 0 + 4096, 5000, 8192, 65536, 1 << 20, 3 * 5 ** 7, 1 << 22, 1 << 24, 2 * 3 ** 9])
+def test_split(fb, n):
+    n1, n2 = fb.split(n)
+    assert n1 * n2 == n
+    assert n1 <= fb.MAX_SMEM_LEN and n2 <= fb.MAX_SMEM_LEN
+    if n <= fb.MAX_SMEM_LEN:
+        assert (n1, n2) == (n, 1)
+    else:
+        assert n1 <= n2  # the column pass takes the shorter factor
+
+
+@pytest.mark.parametrize("n", [(1 << 24) * 2, 7 * 4096, 4099])
+def test_split_rejects(fb, n):
+    with pytest.raises(fb.FFTError):
+        fb.split(n)
+
+
+def _plan_rc(fb, dims, batch=1, flags=0):
+    h = ctypes.c_void_p()
+    cd = (ctypes.c_longlong * max(1, len(dims)))(*dims)
+    return fb.lib.fb_fft_plan(ctypes.byref(h), len(dims), cd, batch, flags, None), h
+
+
+@pytest.mark.parametrize("dims,batch,flags,rc", [
+    ([], 1, 0, -1),            # rank 0
+    ([4, 4, 4, 4], 1, 0, -1),  # rank 4
+    ([0], 1, 0, -1),           # zero length
+    ([8], -1, 0, -1),          # negative batch
+    ([8], 1, 0x100, -1),       # unknown flag
+    ([14], 1, 0, -2),          # 7 is not a supported prime
+    ([8192, 2], 1, 0, -2),     # axis longer than one pass
+    ([1 << 25], 1, 0, -2),     # longer than the four-step limit
+])
+def test_plan_argument_errors_need_no_device(fb, dims, batch, flags, rc):
+    got, h = _plan_rc(fb, dims, batch, flags)
+    assert got == rc
+    assert not h.value
+
+
+def test_plan_without_device_reports_no_device(fb):
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a device is present")
+    got, h = _plan_rc(fb, [64], 2)
+    assert got == -7
+    assert not h.value
+    out = np.zeros(8, np.float32)
+    assert fb.lib.fb_fft_twiddles(8, 4, out.ctypes.data_as(ctypes.POINTER(ctypes.c_float))) == -7
+
+
+def test_null_plan_handling(fb):
+    assert fb.lib.fb_fft_destroy(None) == 0
+    assert fb.lib.fb_fft_exec(None, None, None, -1) == -6
+    assert fb.lib.fb_fft_exec_host(None, None, None, -1) == -6
+    assert fb.lib.fb_fft_check(None) == -6
+    assert fb.lib.fb_fft_pass_name(None, 0) is None
+    assert fb.lib.fb_fft_plan(None, 1, None, 1, 0, None) == -1
+
+
+def test_launch_counter_starts_at_zero_without_gpu(fb):
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a device is present")
+    assert fb.launch_count() == 0
