@@ -125,6 +125,10 @@ int fb_fft_destroy(fb_fft_plan_t plan);
 /* fb_fft_status_string -- static English text for a status code. */
 const char* fb_fft_status_string(int status);
 
+/* fb_fft_last_error -- the CUDA call that last failed on this host thread and
+ * CUDA's text for it ("" if none); valid until this thread's next failure. */
+const char* fb_fft_last_error(void);
+
 /*
  * Plan description (host-side facts of the schedule).
  *   passes         kernel launches per exec

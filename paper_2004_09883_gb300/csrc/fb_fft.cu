@@ -17,6 +17,7 @@
 #include <atomic>
 #include <cstdint>
 #include <cstdlib>
+#include <cstdio>
 #include <cstring>
 #include <new>
 #include <vector>
@@ -31,6 +32,19 @@ using namespace fbfft;
 namespace {
 
 std::atomic<long long> g_launches{0};
+thread_local char g_last_error[256] = "";
+
+// Record a failed CUDA call (readable through fb_fft_last_error) and map it.
+int cuda_fail(cudaError_t e, const char* what)
+{
+    snprintf(g_last_error, sizeof(g_last_error), "%s: %s (%s)", what, cudaGetErrorString(e), cudaGetErrorName(e));
+    return FB_FFT_ERR_CUDA;
+}
+#define FB_CK(call)                                      \
+    do {                                                 \
+        cudaError_t fb_e_ = (call);                      \
+        if (fb_e_ != cudaSuccess) return cuda_fail(fb_e_, #call); \
+    } while (0)
 constexpr uint32_t kMagic = 0xFBFF7A11u;
 constexpr uint32_t kDead = 0xDEADFBFFu;
 
@@ -354,20 +368,20 @@ int build_plan(fb_fft_plan_s* p)
         p->tw = nullptr;
         return FB_FFT_ERR_ALLOC;
     }
-    for (const TwiddleJob& j : twb.jobs)
-        if (launch_twiddles(p->tw, j, p->stream) != cudaSuccess) return FB_FFT_ERR_CUDA;
+    for (const TwiddleJob& j : twb.jobs) FB_CK(launch_twiddles(p->tw, j, p->stream));
     if (cudaMalloc(&p->err, sizeof(int)) != cudaSuccess) {
         cudaGetLastError();
         p->err = nullptr;
         return FB_FFT_ERR_ALLOC;
     }
-    if (cudaMemsetAsync(p->err, 0, sizeof(int), p->stream) != cudaSuccess) return FB_FFT_ERR_CUDA;
+    FB_CK(cudaMemsetAsync(p->err, 0, sizeof(int), p->stream));
     int sms = 0;
-    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, p->device) != cudaSuccess) return FB_FFT_ERR_CUDA;
+    FB_CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, p->device));
     for (PassPlan& q : p->passes) {
         int occ = 0;
         const LineKernel k = line_kernel(q.threads, true, q.lg);
-        if (k.occupancy(q.smem, &occ) != cudaSuccess || occ < 1) return FB_FFT_ERR_CUDA;
+        FB_CK(k.occupancy(q.smem, &occ));
+        if (occ < 1) return cuda_fail(cudaErrorInvalidConfiguration, k.name);
         q.grid = std::min(q.grid, (long long)sms * occ);
         q.d.err = p->err;
         q.d.tw = p->tw;
@@ -383,7 +397,7 @@ int build_plan(fb_fft_plan_s* p)
             return FB_FFT_ERR_ALLOC;
         }
     }
-    if (cudaStreamSynchronize(p->stream) != cudaSuccess) return FB_FFT_ERR_CUDA;
+    FB_CK(cudaStreamSynchronize(p->stream));
     return FB_FFT_OK;
 }
 
@@ -427,9 +441,7 @@ int exec_device(fb_fft_plan_s* p, const float2* in, float2* out, int direction)
     const bool fwd = direction == FB_FFT_FORWARD;
     const size_t bytes = (size_t)(p->N * p->batch) * sizeof(float2);
     if (p->passes.empty()) {  // every axis has length 1: the DFT is the identity
-        if (bytes && in != out &&
-            cudaMemcpyAsync(out, in, bytes, cudaMemcpyDeviceToDevice, p->stream) != cudaSuccess)
-            return FB_FFT_ERR_CUDA;
+        if (bytes && in != out) FB_CK(cudaMemcpyAsync(out, in, bytes, cudaMemcpyDeviceToDevice, p->stream));
         return FB_FFT_OK;
     }
     const bool scale = !fwd && (p->flags & FB_FFT_SCALE_INV_N);
@@ -463,7 +475,7 @@ int exec_device(fb_fft_plan_s* p, const float2* in, float2* out, int direction)
             if (p->ev_used + 2 > p->ev.size()) {
                 for (int i = 0; i < 64; ++i) {
                     cudaEvent_t e;
-                    if (cudaEventCreate(&e) != cudaSuccess) return FB_FFT_ERR_CUDA;
+                    FB_CK(cudaEventCreate(&e));
                     p->ev.push_back(e);
                 }
                 p->ev_group.resize(p->ev.size() / 2, 0);
@@ -475,7 +487,8 @@ int exec_device(fb_fft_plan_s* p, const float2* in, float2* out, int direction)
             cudaEventRecord(e0, p->stream);
         }
         const LineKernel k = line_kernel(q.threads, fwd, q.lg);
-        if (k.launch(args, q.grid, smem, p->stream) != cudaSuccess) return FB_FFT_ERR_CUDA;
+        const cudaError_t le = k.launch(args, q.grid, smem, p->stream);
+        if (le != cudaSuccess) return cuda_fail(le, k.name);
         g_launches.fetch_add(1, std::memory_order_relaxed);
         if (p->profiling) cudaEventRecord(e1, p->stream);
     }
@@ -485,6 +498,8 @@ int exec_device(fb_fft_plan_s* p, const float2* in, float2* out, int direction)
 }  // namespace
 
 extern "C" {
+
+const char* fb_fft_last_error(void) { return g_last_error; }
 
 const char* fb_fft_status_string(int status)
 {
@@ -582,21 +597,19 @@ int fb_fft_exec_host(fb_fft_plan_t plan, const void* host_in, void* host_out, in
         }
         plan->staging_bytes = bytes;
     }
-    if (cudaMemcpyAsync(plan->staging, host_in, bytes, cudaMemcpyHostToDevice, plan->stream) != cudaSuccess)
-        return FB_FFT_ERR_CUDA;
+    FB_CK(cudaMemcpyAsync(plan->staging, host_in, bytes, cudaMemcpyHostToDevice, plan->stream));
     int rc = exec_device(plan, plan->staging, plan->staging, direction);
     if (rc != FB_FFT_OK) return rc;
-    if (cudaMemcpyAsync(host_out, plan->staging, bytes, cudaMemcpyDeviceToHost, plan->stream) != cudaSuccess)
-        return FB_FFT_ERR_CUDA;
+    FB_CK(cudaMemcpyAsync(host_out, plan->staging, bytes, cudaMemcpyDeviceToHost, plan->stream));
     return fb_fft_check(plan);
 }
 
 int fb_fft_check(fb_fft_plan_t plan)
 {
     if (!plan_ok(plan)) return FB_FFT_ERR_BAD_PLAN;
-    if (cudaStreamSynchronize(plan->stream) != cudaSuccess) return FB_FFT_ERR_CUDA;
+    FB_CK(cudaStreamSynchronize(plan->stream));
     int e = 0;
-    if (cudaMemcpy(&e, plan->err, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) return FB_FFT_ERR_CUDA;
+    FB_CK(cudaMemcpy(&e, plan->err, sizeof(int), cudaMemcpyDeviceToHost));
     if (e) {
         cudaMemset(plan->err, 0, sizeof(int));
         return FB_FFT_ERR_TIMEOUT;
@@ -657,10 +670,10 @@ int fb_fft_profile_read(fb_fft_plan_t plan, double* ms_total, long long* launche
     *npasses = ng;
     for (int g = 0; g < capacity; ++g) ms_total[g] = 0.0, launches[g] = 0;
     if (plan->ev_used) {
-        if (cudaEventSynchronize(plan->ev[plan->ev_used - 1]) != cudaSuccess) return FB_FFT_ERR_CUDA;
+        FB_CK(cudaEventSynchronize(plan->ev[plan->ev_used - 1]));
         for (size_t i = 0; i + 1 < plan->ev_used; i += 2) {
             float ms = 0.f;
-            if (cudaEventElapsedTime(&ms, plan->ev[i], plan->ev[i + 1]) != cudaSuccess) return FB_FFT_ERR_CUDA;
+            FB_CK(cudaEventElapsedTime(&ms, plan->ev[i], plan->ev[i + 1]));
             const int g = plan->ev_group[i / 2];
             if (g < capacity) ms_total[g] += ms, launches[g] += 1;
         }

@@ -483,7 +483,6 @@ __global__ void __launch_bounds__(THREADS, LG == 0 ? 1 : 512 / THREADS)
     unsigned char* smem_raw = smem_dyn + ((128u - (smem_u32(smem_dyn) & 127u)) & 127u);
     unsigned long long* bar = reinterpret_cast<unsigned long long*>(smem_raw);  // 2 mbarriers
     float2* land0 = reinterpret_cast<float2*>(smem_raw + 128);
-    const int T = 1 << a.d.logT;
     const bool async = a.d.async_io != 0;
     float2* work = land0 + (async ? 2 : 1) * a.d.land_stride;
     const long long step = gridDim.x;
@@ -577,8 +576,14 @@ cudaError_t set_smem_attr()
     if (e != cudaSuccess) return e;
     const unsigned long long bit = 1ULL << (dev & 63);
     if (!(done & bit)) {
+        int optin = 0;
+        e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+        if (e != cudaSuccess) return e;
+        cudaFuncAttributes fa;
+        e = cudaFuncGetAttributes(&fa, k_line_fft<THREADS, FWD, LG>);
+        if (e != cudaSuccess) return e;
         e = cudaFuncSetAttribute(k_line_fft<THREADS, FWD, LG>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 227 * 1024);
+                                 optin - (int)fa.sharedSizeBytes);
         if (e != cudaSuccess) return e;
         done |= bit;
     }

@@ -31,7 +31,9 @@ STATUS = {
 class FFTError(RuntimeError):
     def __init__(self, status: int, what: str):
         self.status = status
-        super().__init__(f"{what}: {STATUS.get(status, status)} ({_text(status)})")
+        detail = lib.fb_fft_last_error().decode() if status == -4 else ""
+        super().__init__(f"{what}: {STATUS.get(status, status)} ({_text(status)})"
+                         + (f" [{detail}]" if detail else ""))
 
 
 class Info(ctypes.Structure):
@@ -55,6 +57,7 @@ _sig = {
     "fb_fft_set_stream": (_int, [_vp, _vp]),
     "fb_fft_destroy": (_int, [_vp]),
     "fb_fft_status_string": (ctypes.c_char_p, [_int]),
+    "fb_fft_last_error": (ctypes.c_char_p, []),
     "fb_fft_plan_info": (_int, [_vp, ctypes.POINTER(Info)]),
     "fb_fft_factorize": (_int, [_ll, ctypes.POINTER(_int), _int, ctypes.POINTER(_int)]),
     "fb_fft_split": (_int, [_ll, ctypes.POINTER(_ll), ctypes.POINTER(_ll)]),
