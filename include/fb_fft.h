@@ -149,6 +149,13 @@ typedef struct fb_fft_info {
 int fb_fft_plan_info(fb_fft_plan_t plan, fb_fft_info* info);
 
 /*
+ * fb_fft_plan_query -- run the planner on the host only (no device, no
+ * allocation) and describe the plan fb_fft_plan would build for these
+ * arguments.  Same errors as fb_fft_plan except ALLOC/CUDA/NO_DEVICE.
+ */
+int fb_fft_plan_query(int rank, const long long* dims, long long batch, unsigned flags, fb_fft_info* info);
+
+/*
  * fb_fft_factorize -- the planner's radix schedule for one in-shared-memory
  * line length n (host only, needs no GPU).  Writes the radices (each of
  * 2,3,4,5,8,16, product n) to radices[0..*count).  Errors: INVALID_ARG,

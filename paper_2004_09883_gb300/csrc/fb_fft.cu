@@ -199,9 +199,13 @@ int make_line_pass(PassPlan& p, TwiddleBuilder& twb, long long L, long long O, l
     const bool pow2 = (L & (L - 1)) == 0;
     p.lg = pow2 ? ilog2ll(L) : 0;
     // Strided (c-fast) tiles want 16 lines for 128-byte rows: long power-of-two
-    // lines get the 512-thread kernel to double the tile.
-    p.threads = (pow2 && cfast && L >= 512) ? 512 : 256;
-    const long long cap = (long long)p.threads * kElemsPerThread;
+    // lines get the 512-thread kernel to double the tile.  Other lengths use
+    // the generic kernel's shape.
+    if (pow2)
+        p.threads = (cfast && L >= 512) ? 512 : 256;
+    else
+        p.threads = kGenericThreads;
+    const long long cap = (long long)p.threads * (pow2 ? kElemsPerThread : kGenericElems);
     if (L > cap) return FB_FFT_ERR_UNSUPPORTED_SIZE;
     long long T = pow2floor(cap / L);
     T = std::min<long long>(T, cfast ? 16 : p.threads);
@@ -293,9 +297,9 @@ void free_plan(fb_fft_plan_s* p)
     delete p;
 }
 
-int build_plan(fb_fft_plan_s* p)
+// Host part of planning: the pass list and the twiddle jobs (no device work).
+int schedule_plan(fb_fft_plan_s* p, TwiddleBuilder& twb)
 {
-    TwiddleBuilder twb;
     const long long B = p->batch;
     if (p->rank == 1 && p->N > FB_FFT_MAX_SMEM_LEN) {
         long long N1, N2;
@@ -361,8 +365,16 @@ int build_plan(fb_fft_plan_s* p)
         }
         if (!p->passes.empty()) p->passes.back().last = true;
     }
-    // Twiddle tables: one device buffer, built by the FP64 kernel.
     p->tw_elems = std::max(2LL, twb.total);
+    return FB_FFT_OK;
+}
+
+int build_plan(fb_fft_plan_s* p)
+{
+    TwiddleBuilder twb;
+    int rc = schedule_plan(p, twb);
+    if (rc != FB_FFT_OK) return rc;
+    // Twiddle tables: one device buffer, built by the FP64 kernel.
     if (cudaMalloc(&p->tw, (size_t)p->tw_elems * sizeof(float2)) != cudaSuccess) {
         cudaGetLastError();
         p->tw = nullptr;
@@ -531,11 +543,8 @@ int fb_fft_split(long long n, long long* n1, long long* n2)
     return split_fourstep(n, n1, n2);
 }
 
-int fb_fft_plan(fb_fft_plan_t* plan, int rank, const long long* dims, long long batch, unsigned flags,
-                void* stream)
+static int validate(int rank, const long long* dims, long long batch, unsigned flags, long long* N_out)
 {
-    if (!plan) return FB_FFT_ERR_INVALID_ARG;
-    *plan = nullptr;
     if (rank < 1 || rank > 3 || !dims || batch < 0 || (flags & ~FB_FFT_SCALE_INV_N)) return FB_FFT_ERR_INVALID_ARG;
     long long N = 1;
     for (int d = 0; d < rank; ++d) {
@@ -546,6 +555,44 @@ int fb_fft_plan(fb_fft_plan_t* plan, int rank, const long long* dims, long long 
         N *= dims[d];
     }
     if (batch > 0 && N > (1LL << 58) / batch) return FB_FFT_ERR_UNSUPPORTED_SIZE;
+    *N_out = N;
+    return FB_FFT_OK;
+}
+
+int fb_fft_plan_query(int rank, const long long* dims, long long batch, unsigned flags, fb_fft_info* info)
+{
+    if (!info) return FB_FFT_ERR_INVALID_ARG;
+    long long N = 1;
+    int rc = validate(rank, dims, batch, flags, &N);
+    if (rc != FB_FFT_OK) return rc;
+    fb_fft_plan_s p;
+    p.rank = rank;
+    for (int d = 0; d < rank; ++d) p.dims[d] = dims[d];
+    p.batch = batch;
+    p.flags = flags;
+    p.N = N;
+    TwiddleBuilder twb;
+    rc = schedule_plan(&p, twb);
+    p.magic = kDead;
+    if (rc != FB_FFT_OK) return rc;
+    std::memset(info, 0, sizeof(*info));
+    info->passes = (int)p.passes.size();
+    info->smem_len_max = p.smem_len_max;
+    info->scratch_bytes = (long long)p.scratch_bytes;
+    info->twiddle_bytes = p.tw_elems * (long long)sizeof(float2);
+    info->elements = N;
+    info->batch = batch;
+    return FB_FFT_OK;
+}
+
+int fb_fft_plan(fb_fft_plan_t* plan, int rank, const long long* dims, long long batch, unsigned flags,
+                void* stream)
+{
+    if (!plan) return FB_FFT_ERR_INVALID_ARG;
+    *plan = nullptr;
+    long long N = 1;
+    int rc0 = validate(rank, dims, batch, flags, &N);
+    if (rc0 != FB_FFT_OK) return rc0;
     int ndev = 0;
     if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) {
         cudaGetLastError();

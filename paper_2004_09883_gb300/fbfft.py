@@ -59,6 +59,7 @@ _sig = {
     "fb_fft_status_string": (ctypes.c_char_p, [_int]),
     "fb_fft_last_error": (ctypes.c_char_p, []),
     "fb_fft_plan_info": (_int, [_vp, ctypes.POINTER(Info)]),
+    "fb_fft_plan_query": (_int, [_int, ctypes.POINTER(_ll), _ll, ctypes.c_uint, ctypes.POINTER(Info)]),
     "fb_fft_factorize": (_int, [_ll, ctypes.POINTER(_int), _int, ctypes.POINTER(_int)]),
     "fb_fft_split": (_int, [_ll, ctypes.POINTER(_ll), ctypes.POINTER(_ll)]),
     "fb_fft_profile": (_int, [_vp, _int]),
@@ -97,6 +98,16 @@ def split(n: int) -> tuple[int, int]:
     n1, n2 = _ll(), _ll()
     _check(lib.fb_fft_split(int(n), ctypes.byref(n1), ctypes.byref(n2)), "fb_fft_split")
     return n1.value, n2.value
+
+
+def plan_query(dims, batch: int = 1, scale_inv_n: bool = False) -> dict:
+    """Host-only planner run: what fb_fft_plan would build (no GPU needed)."""
+    dims = [int(d) for d in dims]
+    cd = (_ll * len(dims))(*dims)
+    inf = Info()
+    _check(lib.fb_fft_plan_query(len(dims), cd, int(batch), SCALE_INV_N if scale_inv_n else 0,
+                                 ctypes.byref(inf)), "fb_fft_plan_query")
+    return {f: getattr(inf, f) for f, _ in Info._fields_ if f != "reserved"}
 
 
 def launch_count() -> int:

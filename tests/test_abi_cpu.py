@@ -145,3 +145,35 @@ def test_launch_counter_starts_at_zero_without_gpu(fb):
     if torch.cuda.is_available():
         pytest.skip("a device is present")
     assert fb.launch_count() == 0
+
+
+GPU_TEST_SHAPES = (
+    [([n], 37) for n in [2 ** k for k in range(1, 13)]]
+    + [([n], 37) for n in [3, 5, 6, 9, 10, 12, 15, 25, 27, 30, 45, 60, 81, 96, 100, 125, 243, 360, 375, 625,
+                           729, 1000, 1536, 2187, 2400, 3125, 3645, 4000]]
+    + [([n], b) for n, b in [(8192, 3), (65536, 2), (3 * 5 ** 7, 1), (1 << 20, 2), (6000, 5), (2 * 3 ** 9, 1),
+                             (1 << 22, 1), (1 << 16, 70), (1 << 20, 32), (1 << 14, 3)]]
+    + [(d, b) for d, b in [([16, 12], 3), ([256, 256], 2), ([512, 512], 1), ([100, 30], 4), ([8, 8, 8], 5),
+                           ([30, 20, 12], 2), ([128, 128, 128], 1), ([6, 250, 18], 1), ([3, 5, 4096], 1),
+                           ([4096, 2, 3], 1), ([256, 256, 128], 1), ([32, 32, 16], 2), ([60, 45], 2),
+                           ([64, 48], 3), ([64, 64, 32], 2), ([1, 64], 2), ([64, 1], 2), ([1, 1, 1], 7)]]
+)
+
+
+@pytest.mark.parametrize("dims,batch", GPU_TEST_SHAPES)
+def test_planner_accepts_every_tested_shape(fb, dims, batch):
+    info = fb.plan_query(dims, batch, scale_inv_n=True)
+    assert info["elements"] == int(np.prod(dims))
+    n = info["elements"]
+    nontrivial = [d for d in dims if d > 1]
+    if len(dims) == 1 and n > fb.MAX_SMEM_LEN:
+        assert info["passes"] % 2 == 0 and info["scratch_bytes"] > 0
+    else:
+        assert info["passes"] == len(nontrivial)
+        assert info["scratch_bytes"] == 0
+
+
+@pytest.mark.parametrize("n", inputs.smooth_lengths(4097, 1 << 24)[::7])
+def test_planner_accepts_long_1d(fb, n):
+    info = fb.plan_query([n], 2)
+    assert info["passes"] == 2 and info["scratch_bytes"] >= 8 * n
