@@ -175,5 +175,11 @@ def test_planner_accepts_every_tested_shape(fb, dims, batch):
 
 @pytest.mark.parametrize("n", inputs.smooth_lengths(4097, 1 << 24)[::7])
 def test_planner_accepts_long_1d(fb, n):
+    # plannable exactly when n = n1 * n2 with both factors <= 4096
+    splittable = any(n % d == 0 and n // d <= fb.MAX_SMEM_LEN for d in range(1, fb.MAX_SMEM_LEN + 1))
+    if not splittable:
+        with pytest.raises(fb.FFTError):
+            fb.plan_query([n], 2)
+        return
     info = fb.plan_query([n], 2)
     assert info["passes"] % 2 == 0 and info["passes"] >= 2 and info["scratch_bytes"] >= 8 * n

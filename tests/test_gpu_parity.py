@@ -59,13 +59,19 @@ def test_twiddles_round_to_nearest(fb, d):
     count = min(d, 4096)
     got = fb.twiddles(d, count)
     want = np.array([oracle.twiddle(m, d) for m in range(count)]).astype(np.complex64)
-    ulp_re = np.abs(got.real.view(np.int32).astype(np.int64) - want.real.view(np.int32).astype(np.int64))
-    ulp_im = np.abs(got.imag.view(np.int32).astype(np.int64) - want.imag.view(np.int32).astype(np.int64))
-    # sign-magnitude ints: only compare same-sign values bitwise, others by value
-    same = (np.sign(got.real) == np.sign(want.real)) & (np.sign(got.imag) == np.sign(want.imag))
     assert np.all(np.abs(got - want) <= 2 * np.finfo(np.float32).eps)
-    assert np.all(np.maximum(ulp_re, ulp_im)[same] <= 1)
-    assert np.mean((got == want)) > 0.99
+    for g, w in ((got.real, want.real), (got.imag, want.imag)):
+        # Where the exact value is 0 (e.g. sin(pi)) the GPU's sincospi returns
+        # 0 while the oracle's long-double sinl(pi_L) is ~1e-19: compare those
+        # by value; elsewhere the float32 results must be within 1 ulp and
+        # nearly always identical (round to nearest of an FP64 evaluation).
+        big = np.abs(w) > 1e-12
+        assert np.all(np.abs(g[~big]) <= 1e-12)
+        gi = g[big].view(np.int32).astype(np.int64)
+        wi = w[big].view(np.int32).astype(np.int64)
+        assert np.all(np.sign(g[big]) == np.sign(w[big]))
+        assert np.all(np.abs(gi - wi) <= 1)
+        assert np.mean(gi == wi) > 0.99
 
 
 # --------------------------------------------------------------------------
