@@ -282,13 +282,13 @@ def run_gpu(args, wl: dict) -> None:
             dist.barrier()
         torch.cuda.synchronize(dev)
 
-    clocks = ClockSampler(local) if rank == 0 else None
+    clocks = ClockSampler(local) if rank == 0 and not args.quick else None
     for i in range(args.warmup):
         step(i)
     # pre-roll: untimed extra warm-up so the clock samples see a loaded GPU
     t_pre = time.time()
     i = 0
-    while time.time() - t_pre < 1.0:
+    while not args.quick and time.time() - t_pre < 1.0:
         step(i)
         i += 1
         if i % 64 == 0:
@@ -319,7 +319,8 @@ def run_gpu(args, wl: dict) -> None:
 
     # end to end through the drop-in host-array call: every step copies the
     # input host->device and the result device->host inside the call
-    if True:  # scoped block
+    e2e = None
+    if not args.quick:
         hbuf = [torch.from_numpy(h.reshape(-1)).pin_memory() for h in host_inputs[:2]]
         hres = [torch.empty_like(hbuf[0]).pin_memory() for _ in range(2)]
         e2e_steps = max(3, min(args.steps, 20))
@@ -345,7 +346,7 @@ def run_gpu(args, wl: dict) -> None:
         io = 8 * n * batch * execs
         e2e = {"value": round(world * bytes_step / (e2e_ms / 1e3) / 1e9, 3), "unit": "GB/s",
                "h2d_bytes_per_step": io, "d2h_bytes_per_step": io, "ms_per_step": e2e_ms,
-               "path": "fb_fft_exec_host (pinned host arrays), forward then inverse"}
+               "path": "fb_fft_exec_host (pinned host arrays)" + (", forward then inverse" if wl["inverse"] else ", forward")}
 
     if rank == 0:
         peaks = load_peaks()
@@ -355,7 +356,10 @@ def run_gpu(args, wl: dict) -> None:
         roofline = None
         if dom and dom[2] > 0:
             per_launch_ms = dom[1] / dom[2]
-            launch_bytes = 2 * 8.0 * n * batch  # one read + one write of the array
+            # one read + one write of what one launch covers (four-step passes
+            # run once per batch chunk, so a launch covers batch / chunks items)
+            launches_per_exec = dom[2] / (args.steps * execs)
+            launch_bytes = 2 * 8.0 * n * batch / launches_per_exec
             achieved = launch_bytes / (per_launch_ms / 1e3) / 1e9
             tr = load_traffic(wl["name"])
             roofline = {"bound": "hbm", "achieved": round(achieved, 2), "peak": peaks["hbm_gbs"],
@@ -366,10 +370,12 @@ def run_gpu(args, wl: dict) -> None:
                         "peak_source": f"{peaks['source']} (MEASURED_PEAKS.json hbm_gbs, burst copy)"
                         if peaks["source"] == "measured" else "fallback 6.8 TB/s"}
         threads = len(os.sched_getaffinity(0))
-        cb = oracle_sample(wl, budget_s=float(args.cpu_budget), threads=threads)
-        cpu_baseline = {"value": round(cb["value"], 4), "unit": "GB/s", "cores": threads, "kind": "oracle",
-                        "sample": f"{cb['steps']} full step(s) of {wl['name']} by the FP64 oracle in "
-                                  f"{cb['seconds']:.1f} s on {cpu_model()}"}
+        cpu_baseline = None
+        if not args.quick:
+            cb = oracle_sample(wl, budget_s=float(args.cpu_budget), threads=threads)
+            cpu_baseline = {"value": round(cb["value"], 4), "unit": "GB/s", "cores": threads, "kind": "oracle",
+                            "sample": f"{cb['steps']} full step(s) of {wl['name']} by the FP64 oracle in "
+                                      f"{cb['seconds']:.1f} s on {cpu_model()}"}
         line = {
             "metric": METRIC, "value": round(value, 3), "unit": "GB/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": round(ms, 5), "higher_is_better": True, "scaling": "weak",
@@ -404,6 +410,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="3d", choices=sorted(WORKLOADS))
     ap.add_argument("--cpu-budget", default=10.0, type=float, help="seconds of oracle time for cpu_baseline")
+    ap.add_argument("--quick", action="store_true",
+                    help="timed loop only (no pre-roll, e2e or CPU baseline): for profiler runs")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
