@@ -26,6 +26,7 @@
 
 #include "fb_fft.h"
 #include "fb_internal.h"
+#include "fft_p2.cuh"
 
 using namespace fbfft;
 
@@ -65,7 +66,8 @@ constexpr size_t kMaxSmemBytes = 227 * 1024;
 struct PassPlan {
     PassDesc d;
     int threads;  // CTA size of the chosen kernel
-    int lg;       // log2(L) for a compile-time power-of-two schedule, 0 = generic kernel
+    int lg;       // log2(L) for a compile-time power-of-two kernel, 0 = generic kernel
+    int io;       // IoMode of the power-of-two kernel
     long long grid;
     size_t smem;
     bool async_ok;  // tiles can move by TMA (given 16-byte aligned buffer bases)
@@ -179,7 +181,7 @@ struct TwiddleBuilder {
 // Fill a line pass: L-point DFTs over lines (o, c); strides in elements.
 int make_line_pass(PassPlan& p, TwiddleBuilder& twb, long long L, long long O, long long C,
                    long long in_sn, long long in_sc, long long in_so, long long out_sk, long long out_sc,
-                   long long out_so, bool in_tfast, bool out_tfast)
+                   long long out_so, bool in_tfast, bool out_tfast, bool ptw)
 {
     std::memset(&p, 0, sizeof(p));
     PassDesc& d = p.d;
@@ -198,19 +200,26 @@ int make_line_pass(PassPlan& p, TwiddleBuilder& twb, long long L, long long O, l
     const bool cfast = in_tfast || out_tfast;
     const bool pow2 = (L & (L - 1)) == 0;
     p.lg = pow2 ? ilog2ll(L) : 0;
-    // Strided (c-fast) tiles want 16 lines for 128-byte rows: long power-of-two
-    // lines get the 512-thread kernel to double the tile.  Other lengths use
-    // the generic kernel's shape.
-    if (pow2)
+    long long T = 1, land = 0;
+    if (pow2) {
+        // Compile-time kernels: strided tiles want 16 lines for 128-byte rows,
+        // so long lines on a strided side take the 512-thread kernel.
+        if (in_tfast && !out_tfast) return FB_FFT_ERR_UNSUPPORTED_SIZE;  // never planned
+        p.io = ptw ? kIoCCP : (in_tfast ? kIoCC : (out_tfast ? kIoNC : kIoNN));
         p.threads = (cfast && L >= 512) ? 512 : 256;
-    else
+        if (!line_kernel_p2(p.threads, true, p.lg, p.io).fn) return FB_FFT_ERR_UNSUPPORTED_SIZE;
+        T = p2_tile_lines(p.threads, p.lg, p.io);
+        land = p2_land_elems(p.threads, p.lg, p.io);
+    } else {
+        p.io = -1;
         p.threads = kGenericThreads;
-    const long long cap = (long long)p.threads * (pow2 ? kElemsPerThread : kGenericElems);
-    if (L > cap) return FB_FFT_ERR_UNSUPPORTED_SIZE;
-    long long T = pow2floor(cap / L);
-    T = std::min<long long>(T, cfast ? 16 : p.threads);
-    T = std::max<long long>(1, std::min(T, pow2ceil(C)));
-    if (!line_kernel(p.threads, true, p.lg).launch) return FB_FFT_ERR_UNSUPPORTED_SIZE;
+        const long long cap = (long long)p.threads * kGenericElems;
+        if (L > cap) return FB_FFT_ERR_UNSUPPORTED_SIZE;
+        T = pow2floor(cap / L);
+        T = std::min<long long>(T, cfast ? 16 : p.threads);
+        T = std::max<long long>(1, std::min(T, pow2ceil(C)));
+        land = land_stride_elems((int)L, (int)T);
+    }
 
     d.L = (int)L;
     d.LS = (int)(L + (L >> 4) + 1);
@@ -241,11 +250,12 @@ int make_line_pass(PassPlan& p, TwiddleBuilder& twb, long long L, long long O, l
             if (L % b == 0 && (b * T * 8) % 128 == 0) br = b;
     if (br == 0 && (in_tfast || out_tfast)) p.async_ok = false;
     d.box_rows = br > 0 ? br : 1;
-    d.land_stride = (int)land_stride_elems((int)L, (int)T);
-    p.smem = line_smem_bytes((int)L, (int)T, nst, p.async_ok);
+    d.land_stride = (int)land;
+    d.ptw = ptw ? 1 : 0;
+    p.smem = line_smem_bytes(d.land_stride, (int)L, (int)T, nst, p.async_ok);
     if (p.smem > kMaxSmemBytes) {
         p.async_ok = false;
-        p.smem = line_smem_bytes((int)L, (int)T, nst, false);
+        p.smem = line_smem_bytes(d.land_stride, (int)L, (int)T, nst, false);
     }
     if (p.smem > kMaxSmemBytes) return FB_FFT_ERR_UNSUPPORTED_SIZE;
     p.grid = d.ntiles;  // capped to the resident CTA count when the plan is built
@@ -317,9 +327,8 @@ int schedule_plan(fb_fft_plan_s* p, TwiddleBuilder& twb)
         for (long long b0 = 0; b0 < B; b0 += chunk) {
             const long long nb = std::min(chunk, B - b0);
             PassPlan a, r;
-            rc = make_line_pass(a, twb, N1, nb, N2, N2, 1, N, N2, 1, N, true, true);
+            rc = make_line_pass(a, twb, N1, nb, N2, N2, 1, N, N2, 1, N, true, true, true);
             if (rc != FB_FFT_OK) return rc;
-            a.d.ptw = 1;
             a.d.ptw_log = plog;
             a.src = kBufIn, a.src_off = b0 * N;
             a.dst = kBufScratch, a.dst_off = 0;
@@ -327,7 +336,7 @@ int schedule_plan(fb_fft_plan_s* p, TwiddleBuilder& twb)
             // stash table offsets in the pointer fields until exec binds them
             a.d.ptw_lo = reinterpret_cast<const float2*>(lo_off);
             a.d.ptw_hi = reinterpret_cast<const float2*>(hi_off);
-            rc = make_line_pass(r, twb, N2, nb, N1, 1, N2, N, N1, 1, N, false, true);
+            rc = make_line_pass(r, twb, N2, nb, N1, 1, N2, N, N1, 1, N, false, true, false);
             if (rc != FB_FFT_OK) return rc;
             r.src = kBufScratch, r.src_off = 0;
             r.dst = kBufOut, r.dst_off = b0 * N;
@@ -351,9 +360,9 @@ int schedule_plan(fb_fft_plan_s* p, TwiddleBuilder& twb)
             PassPlan q;
             int rc;
             if (S == 1)
-                rc = make_line_pass(q, twb, L, 1, B * Opre, 1, L, 0, 1, L, 0, false, false);
+                rc = make_line_pass(q, twb, L, 1, B * Opre, 1, L, 0, 1, L, 0, false, false, false);
             else
-                rc = make_line_pass(q, twb, L, B * Opre, S, S, 1, L * S, S, 1, L * S, true, true);
+                rc = make_line_pass(q, twb, L, B * Opre, S, S, 1, L * S, S, 1, L * S, true, true, false);
             if (rc != FB_FFT_OK) return rc;
             q.src = first ? kBufIn : kBufOut;
             q.dst = kBufOut;
@@ -391,9 +400,9 @@ int build_plan(fb_fft_plan_s* p)
     FB_CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, p->device));
     for (PassPlan& q : p->passes) {
         int occ = 0;
-        const LineKernel k = line_kernel(q.threads, true, q.lg);
-        FB_CK(k.occupancy(q.smem, &occ));
-        if (occ < 1) return cuda_fail(cudaErrorInvalidConfiguration, k.name);
+        const LineKernel k = q.lg ? line_kernel_p2(q.threads, true, q.lg, q.io) : line_kernel_generic(true);
+        FB_CK(line_occupancy(k, q.smem, &occ));
+        if (occ < 1) return cuda_fail(cudaErrorInvalidConfiguration, "line pass occupancy");
         q.grid = std::min(q.grid, (long long)sms * occ);
         q.d.err = p->err;
         q.d.tw = p->tw;
@@ -477,7 +486,7 @@ int exec_device(fb_fft_plan_s* p, const float2* in, float2* out, int direction)
                 d.async_io = 0;
         }
         if (p->debug_timeout && d.async_io) d.debug_extra_tx = 16;
-        const size_t smem = line_smem_bytes(d.L, 1 << d.logT, d.nst, d.async_io != 0);
+        const size_t smem = line_smem_bytes(d.land_stride, d.L, 1 << d.logT, d.nst, d.async_io != 0);
         if (q.last && scale) {
             d.apply_scale = 1;
             d.scale = (float)(1.0 / (double)p->N);
@@ -498,9 +507,13 @@ int exec_device(fb_fft_plan_s* p, const float2* in, float2* out, int direction)
             p->ev_used += 2;
             cudaEventRecord(e0, p->stream);
         }
-        const LineKernel k = line_kernel(q.threads, fwd, q.lg);
-        const cudaError_t le = k.launch(args, q.grid, smem, p->stream);
-        if (le != cudaSuccess) return cuda_fail(le, k.name);
+        const LineKernel k = q.lg ? line_kernel_p2(q.threads, fwd, q.lg, q.io) : line_kernel_generic(fwd);
+        const cudaError_t le = line_launch(k, args, q.grid, smem, p->stream);
+        if (le != cudaSuccess) {
+            char nm[64];
+            line_kernel_name(k, nm, sizeof(nm));
+            return cuda_fail(le, nm);
+        }
         g_launches.fetch_add(1, std::memory_order_relaxed);
         if (p->profiling) cudaEventRecord(e1, p->stream);
     }

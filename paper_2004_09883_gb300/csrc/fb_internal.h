@@ -70,30 +70,30 @@ struct LineArgs {
 // alignment slack and mbarriers (256 B), one or two dense landing buffers and the
 // padded work buffer.
 inline long long land_stride_elems(int L, int T) { return ((long long)L * T + 15) & ~15LL; }
-inline size_t line_smem_bytes(int L, int T, int nst, bool async)
+inline size_t line_smem_bytes(long long land_elems, int L, int T, int nst, bool async)
 {
-    const long long land = land_stride_elems(L, T) * (async ? 2 : 1);
+    const long long land = land_elems * (async ? 2 : 1);
     const long long LS = (long long)L + (L >> 4) + 1;
     const long long work = nst <= 1 ? 0 : LS * T;
     return 256 + (size_t)(land + work) * sizeof(float2);  // alignment slack + mbarriers
 }
 
-// One compiled line-pass kernel: launcher, occupancy query and a name.
-using LineLaunchFn = cudaError_t (*)(const LineArgs&, long long grid, size_t smem, cudaStream_t);
-using LineOccFn = cudaError_t (*)(size_t smem, int* blocks_per_sm);
+// One compiled line-pass kernel.  lg = log2(L) for the compile-time
+// power-of-two kernels (io = their IoMode), 0 for the generic kernel (io = -1).
 struct LineKernel {
-    LineLaunchFn launch;
-    LineOccFn occupancy;
-    const char* name;
+    void (*fn)(LineArgs);
+    int threads;
+    bool fwd;
+    int lg;
+    int io;
 };
-// The kernel for (threads, direction, lg): lg = log2(L) for the compile-time
-// power-of-two schedules, 0 for the generic kernel.  launch == nullptr when
-// that combination is not compiled.
-LineKernel line_kernel(int threads, bool forward, int lg);
-LineKernel line_kernel_p2_256_fwd(int lg);
-LineKernel line_kernel_p2_256_inv(int lg);
-LineKernel line_kernel_p2_512(bool forward, int lg);
+// The kernel for a pass; fn == nullptr when that combination is not compiled.
+LineKernel line_kernel_p2(int threads, bool forward, int lg, int io);
 LineKernel line_kernel_generic(bool forward);
+// Launch / occupancy / name of a table entry (shared-memory opt-in handled inside).
+cudaError_t line_launch(const LineKernel& k, const LineArgs& a, long long grid, size_t smem, cudaStream_t stream);
+cudaError_t line_occupancy(const LineKernel& k, size_t smem, int* blocks_per_sm);
+void line_kernel_name(const LineKernel& k, char* buf, size_t n);
 
 // Twiddle table jobs: K0 evaluates exp(-2 pi i m / D) in FP64 and rounds to FP32.
 //   kind 0 (linear): entry i has m = (i * mult) mod D

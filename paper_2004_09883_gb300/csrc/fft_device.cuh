@@ -450,33 +450,12 @@ __device__ __forceinline__ void run_stage(int R, const PassDesc& d, int Ns, int 
 __host__ __device__ constexpr int pow2_nst(int lg) { return lg / 4 + (lg % 4 ? 1 : 0); }
 __host__ __device__ constexpr int pow2_radix(int lg, int s) { return s < lg / 4 ? 16 : (1 << (lg % 4)); }
 
-template <int THREADS, bool FWD, int LG, int S>
-__device__ __forceinline__ void pow2_stage(const PassDesc& d, float2* land, float2* work, int Tv, int c0)
-{
-    constexpr int NST = pow2_nst(LG);
-    constexpr int R = pow2_radix(LG, S);
-    constexpr int POS = NST == 1 ? kPosOnly : (S == 0 ? kPosFirst : (S == NST - 1 ? kPosLast : kPosMid));
-    stage<R, THREADS, FWD, POS>(d, d.ns[S], d.twoff[S], land, work, Tv, c0);
-}
-template <int THREADS, bool FWD, int LG, int S>
-__device__ __forceinline__ void pow2_rest(const PassDesc& d, float2* land, float2* work, int Tv, int c0, bool async)
-{
-    if constexpr (S < pow2_nst(LG)) {
-        pow2_stage<THREADS, FWD, LG, S>(d, land, work, Tv, c0);
-        if (async && S == pow2_nst(LG) - 1) fence_proxy_async();
-        __syncthreads();
-        pow2_rest<THREADS, FWD, LG, S + 1>(d, land, work, Tv, c0, async);
-    }
-}
-
-// The line pass.  LG > 0: line length 2^LG with a compile-time schedule;
-// LG == 0: any 5-smooth length, stage radices read from the descriptor.
-// Persistent CTAs walk tiles blockIdx.x, +gridDim.x, ...  With TMA on
-// (d.async_io), tile i+1 streams into the second landing buffer while tile i
-// is transformed, and finished tiles leave by TMA stores.
-template <int THREADS, bool FWD, int LG>
-__global__ void __launch_bounds__(THREADS, LG == 0 ? 1 : 512 / THREADS)
-    k_line_fft(const __grid_constant__ LineArgs a)
+// The generic line pass: any 5-smooth L <= 4096, stage radices read from the
+// descriptor at run time.  Persistent CTAs walk tiles blockIdx.x, +gridDim.x,
+// ...; with TMA on (d.async_io), tile i+1 streams into the second landing
+// buffer while tile i is transformed, and finished tiles leave by TMA stores.
+template <int THREADS, bool FWD>
+__global__ void __launch_bounds__(THREADS, 1) k_fft_generic(const __grid_constant__ LineArgs a)
 {
     extern __shared__ __align__(128) unsigned char smem_dyn[];
     // 128-byte aligned base (the size includes 128 bytes of slack for this)
@@ -525,15 +504,10 @@ __global__ void __launch_bounds__(THREADS, LG == 0 ? 1 : 512 / THREADS)
             plain_tile_load<THREADS>(d, ti, land);
             __syncthreads();
         }
-        // stage 0
-        if constexpr (LG > 0) {
-            pow2_stage<THREADS, FWD, LG, 0>(d, land, work, ti.Tv, c0);
-        } else {
-            if (d.nst == 1)
-                run_stage<THREADS, FWD, kPosOnly, kGenericElems>(d.radix[0], d, 1, 0, land, work, ti.Tv, c0);
-            else
-                run_stage<THREADS, FWD, kPosFirst, kGenericElems>(d.radix[0], d, 1, 0, land, work, ti.Tv, c0);
-        }
+        if (d.nst == 1)
+            run_stage<THREADS, FWD, kPosOnly, kGenericElems>(d.radix[0], d, 1, 0, land, work, ti.Tv, c0);
+        else
+            run_stage<THREADS, FWD, kPosFirst, kGenericElems>(d.radix[0], d, 1, 0, land, work, ti.Tv, c0);
         if (async && d.nst == 1) fence_proxy_async();
         __syncthreads();
         // The previous tile's store has had a stage to drain: recycle its
@@ -542,18 +516,15 @@ __global__ void __launch_bounds__(THREADS, LG == 0 ? 1 : 512 / THREADS)
             bulk_wait_read_all();
             issue_tile_load(d, &a.tm_in, tile + step, land0 + (buf ^ 1) * d.land_stride, &bar[buf ^ 1]);
         }
-        // stages 1 .. nst-1
-        if constexpr (LG > 0) {
-            pow2_rest<THREADS, FWD, LG, 1>(d, land, work, ti.Tv, c0, async);
-        } else {
-            for (int s = 1; s < d.nst; ++s) {
-                if (s == d.nst - 1)
-                    run_stage<THREADS, FWD, kPosLast, kGenericElems>(d.radix[s], d, d.ns[s], d.twoff[s], land, work, ti.Tv, c0);
-                else
-                    run_stage<THREADS, FWD, kPosMid, kGenericElems>(d.radix[s], d, d.ns[s], d.twoff[s], land, work, ti.Tv, c0);
-                if (async && s == d.nst - 1) fence_proxy_async();
-                __syncthreads();
-            }
+        for (int s = 1; s < d.nst; ++s) {
+            if (s == d.nst - 1)
+                run_stage<THREADS, FWD, kPosLast, kGenericElems>(d.radix[s], d, d.ns[s], d.twoff[s], land, work,
+                                                                 ti.Tv, c0);
+            else
+                run_stage<THREADS, FWD, kPosMid, kGenericElems>(d.radix[s], d, d.ns[s], d.twoff[s], land, work,
+                                                                ti.Tv, c0);
+            if (async && s == d.nst - 1) fence_proxy_async();
+            __syncthreads();
         }
         if (async) {
             if (threadIdx.x == 0) issue_tile_store(d, &a.tm_out, tile, land);
@@ -565,59 +536,23 @@ __global__ void __launch_bounds__(THREADS, LG == 0 ? 1 : 512 / THREADS)
     if (async && threadIdx.x == 0) bulk_wait_all();
 }
 
-template <int THREADS, bool FWD, int LG>
-cudaError_t set_smem_attr()
+// A kernel's table entry: its pointer, CTA size and a printable name.
+template <int THREADS>
+LineKernel make_entry(void (*fn)(LineArgs), bool fwd, int lg, int io)
 {
-    // The opt-in shared-memory limit is a per-device attribute: set it once
-    // per device for this kernel (a benign race if two threads do it).
-    static unsigned long long done = 0;
-    int dev = 0;
-    cudaError_t e = cudaGetDevice(&dev);
-    if (e != cudaSuccess) return e;
-    const unsigned long long bit = 1ULL << (dev & 63);
-    if (!(done & bit)) {
-        int optin = 0;
-        e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-        if (e != cudaSuccess) return e;
-        cudaFuncAttributes fa;
-        e = cudaFuncGetAttributes(&fa, k_line_fft<THREADS, FWD, LG>);
-        if (e != cudaSuccess) return e;
-        e = cudaFuncSetAttribute(k_line_fft<THREADS, FWD, LG>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 optin - (int)fa.sharedSizeBytes);
-        if (e != cudaSuccess) return e;
-        done |= bit;
-    }
-    return cudaSuccess;
+    LineKernel k;
+    k.fn = fn;
+    k.threads = THREADS;
+    k.fwd = fwd;
+    k.lg = lg;
+    k.io = io;
+    return k;
 }
-template <int THREADS, bool FWD, int LG>
-cudaError_t launch_k(const LineArgs& a, long long grid, size_t smem, cudaStream_t stream)
+
+template <int THREADS, bool FWD>
+LineKernel generic_entry()
 {
-    if (grid <= 0) return cudaSuccess;
-    cudaError_t e = set_smem_attr<THREADS, FWD, LG>();
-    if (e != cudaSuccess) return e;
-    const unsigned g = (unsigned)(grid > 0x7fffffffLL ? 0x7fffffffLL : grid);
-    k_line_fft<THREADS, FWD, LG><<<g, THREADS, smem, stream>>>(a);
-    return cudaGetLastError();
-}
-template <int THREADS, bool FWD, int LG>
-cudaError_t occ_k(size_t smem, int* blocks)
-{
-    cudaError_t e = set_smem_attr<THREADS, FWD, LG>();
-    if (e != cudaSuccess) return e;
-    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, k_line_fft<THREADS, FWD, LG>, THREADS, smem);
-}
-template <int THREADS, bool FWD, int LG>
-LineKernel kernel_entry()
-{
-    static const char* name = [] {
-        static char buf[64];
-        if (LG > 0)
-            snprintf(buf, sizeof(buf), "k_line_fft<%d,%s,L=%d>", THREADS, FWD ? "fwd" : "inv", 1 << LG);
-        else
-            snprintf(buf, sizeof(buf), "k_line_fft<%d,%s,generic>", THREADS, FWD ? "fwd" : "inv");
-        return (const char*)buf;
-    }();
-    return LineKernel{launch_k<THREADS, FWD, LG>, occ_k<THREADS, FWD, LG>, name};
+    return make_entry<THREADS>(k_fft_generic<THREADS, FWD>, FWD, 0, -1);
 }
 
 #endif  // __CUDACC__

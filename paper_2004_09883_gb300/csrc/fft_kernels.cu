@@ -1,20 +1,93 @@
-// fft_kernels.cu -- the generic line-pass kernel and the kernel dispatch table.
-#include "fft_device.cuh"
+// fft_kernels.cu -- the generic line-pass kernel, the kernel table and the
+// launch path shared by all line-pass kernels.
+#include <mutex>
+#include <unordered_map>
+
+#include "fft_p2.cuh"
 
 namespace fbfft {
 
+LineKernel line_kernel_p2_256_fwd_a(int lg, int io);
+LineKernel line_kernel_p2_256_fwd_b(int lg, int io);
+LineKernel line_kernel_p2_256_inv_a(int lg, int io);
+LineKernel line_kernel_p2_256_inv_b(int lg, int io);
+LineKernel line_kernel_p2_512_fwd_a(int lg, int io);
+LineKernel line_kernel_p2_512_fwd_b(int lg, int io);
+LineKernel line_kernel_p2_512_inv_a(int lg, int io);
+LineKernel line_kernel_p2_512_inv_b(int lg, int io);
+
 LineKernel line_kernel_generic(bool forward)
 {
-    return forward ? kernel_entry<kGenericThreads, true, 0>() : kernel_entry<kGenericThreads, false, 0>();
+    return forward ? generic_entry<kGenericThreads, true>() : generic_entry<kGenericThreads, false>();
 }
 
-LineKernel line_kernel(int threads, bool forward, int lg)
+LineKernel line_kernel_p2(int threads, bool forward, int lg, int io)
 {
-    if (lg == 0) return threads == kGenericThreads ? line_kernel_generic(forward) : LineKernel{nullptr, nullptr, nullptr};
-    if (lg < 0 || lg > kMaxLineLog2) return LineKernel{nullptr, nullptr, nullptr};
-    if (threads == 256) return forward ? line_kernel_p2_256_fwd(lg) : line_kernel_p2_256_inv(lg);
-    if (threads == 512) return line_kernel_p2_512(forward, lg);
-    return LineKernel{nullptr, nullptr, nullptr};
+    const LineKernel none{nullptr, 0, false, 0, 0};
+    if (lg < 1 || lg > kMaxLineLog2 || io < kIoNN || io > kIoCCP) return none;
+    const bool a = io == kIoNN || io == kIoCC;
+    if (threads == 256)
+        return forward ? (a ? line_kernel_p2_256_fwd_a(lg, io) : line_kernel_p2_256_fwd_b(lg, io))
+                       : (a ? line_kernel_p2_256_inv_a(lg, io) : line_kernel_p2_256_inv_b(lg, io));
+    if (threads == 512)
+        return forward ? (a ? line_kernel_p2_512_fwd_a(lg, io) : line_kernel_p2_512_fwd_b(lg, io))
+                       : (a ? line_kernel_p2_512_inv_a(lg, io) : line_kernel_p2_512_inv_b(lg, io));
+    return none;
+}
+
+namespace {
+// The opt-in dynamic shared-memory limit is a per-device function attribute:
+// set it once per (kernel, device).
+cudaError_t ensure_smem_attr(const LineKernel& k)
+{
+    static std::mutex mu;
+    static std::unordered_map<const void*, unsigned long long> done;
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    const unsigned long long bit = 1ULL << (dev & 63);
+    std::lock_guard<std::mutex> g(mu);
+    unsigned long long& mask = done[(const void*)k.fn];
+    if (mask & bit) return cudaSuccess;
+    int optin = 0;
+    e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    if (e != cudaSuccess) return e;
+    cudaFuncAttributes fa;
+    e = cudaFuncGetAttributes(&fa, (const void*)k.fn);
+    if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute((const void*)k.fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             optin - (int)fa.sharedSizeBytes);
+    if (e != cudaSuccess) return e;
+    mask |= bit;
+    return cudaSuccess;
+}
+}  // namespace
+
+cudaError_t line_launch(const LineKernel& k, const LineArgs& a, long long grid, size_t smem, cudaStream_t stream)
+{
+    if (grid <= 0) return cudaSuccess;
+    cudaError_t e = ensure_smem_attr(k);
+    if (e != cudaSuccess) return e;
+    const unsigned g = (unsigned)(grid > 0x7fffffffLL ? 0x7fffffffLL : grid);
+    k.fn<<<g, k.threads, smem, stream>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t line_occupancy(const LineKernel& k, size_t smem, int* blocks_per_sm)
+{
+    cudaError_t e = ensure_smem_attr(k);
+    if (e != cudaSuccess) return e;
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, (const void*)k.fn, k.threads, smem);
+}
+
+void line_kernel_name(const LineKernel& k, char* buf, size_t n)
+{
+    static const char* io_names[4] = {"NN", "CC", "NC", "CCP"};
+    if (k.lg > 0)
+        snprintf(buf, n, "k_fft_p2<%d,%s,L=%d,%s>", k.threads, k.fwd ? "fwd" : "inv", 1 << k.lg,
+                 (k.io >= 0 && k.io < 4) ? io_names[k.io] : "?");
+    else
+        snprintf(buf, n, "k_fft_generic<%d,%s>", k.threads, k.fwd ? "fwd" : "inv");
 }
 
 }  // namespace fbfft

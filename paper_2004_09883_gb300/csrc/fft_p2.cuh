@@ -1,0 +1,329 @@
+// fft_p2.cuh -- the line pass for power-of-two lines, specialised at compile
+// time on the line length (L = 2^LG), the CTA size and the in/out layout.
+//
+// Everything that shapes the index arithmetic is a template constant: the
+// radix schedule (16, 16, ..., then one of 8/4/2), Ns of every stage, lines per
+// tile T, the shared-memory strides and which side is strided.  What remains
+// at run time is the tile walk (pointers, strides, counts), the twiddle table
+// base and the optional 1/N scale.
+#pragma once
+
+#include "fft_device.cuh"
+
+namespace fbfft {
+
+// In/out layouts of a pass.  N = lines contiguous in memory (a tile is T whole
+// lines), C = lines adjacent in memory (a tile is T columns x L rows).
+enum IoMode {
+    kIoNN = 0,   // contiguous in and out: 1-D lines, last axis of multi-D
+    kIoCC = 1,   // strided in and out: the other axes of multi-D
+    kIoNC = 2,   // contiguous in, strided out: four-step rows (transposed store)
+    kIoCCP = 3,  // strided in and out, output times exp(s 2 pi i c k / N): four-step columns
+};
+
+__host__ __device__ constexpr int p2_min(int a, int b) { return a < b ? a : b; }
+__host__ __device__ constexpr int p2_max(int a, int b) { return a > b ? a : b; }
+__host__ __device__ constexpr bool io_in_strided(int io) { return io == kIoCC || io == kIoCCP; }
+__host__ __device__ constexpr bool io_out_strided(int io) { return io != kIoNN; }
+// Lines per tile: 16 (128-byte rows) when a side is strided, else as many
+// whole lines as the tile holds (at most one per thread).
+__host__ __device__ constexpr int p2_tile_lines(int threads, int lg, int io)
+{
+    return (io_in_strided(io) || io_out_strided(io)) ? p2_min(16, threads * kElemsPerThread >> lg)
+                                                     : p2_min(threads, threads * kElemsPerThread >> lg);
+}
+// Row padding of contiguous landing layouts: when one warp spans several
+// lines, a gap of G/2 values (G = threads per line) spreads them over the banks.
+__host__ __device__ constexpr int p2_row_pad(int threads, int lg, int io, bool out_side)
+{
+    const int T = p2_tile_lines(threads, lg, io);
+    const int G = threads / T;
+    const bool strided = out_side ? io_out_strided(io) : io_in_strided(io);
+    return (!strided && G < 32) ? p2_max(2, G / 2) : 0;
+}
+// Elements of one landing buffer (input layout, then reused for the output layout).
+__host__ __device__ constexpr int p2_land_elems(int threads, int lg, int io)
+{
+    const int T = p2_tile_lines(threads, lg, io);
+    const int L = 1 << lg;
+    const int in_e = io_in_strided(io) ? L * T : (L + p2_row_pad(threads, lg, io, false)) * T;
+    const int out_e = io_out_strided(io) ? L * T : (L + p2_row_pad(threads, lg, io, true)) * T;
+    return (p2_max(in_e, out_e) + 15) & ~15;
+}
+
+template <int THREADS, int LG, int IO>
+struct P2 {
+    static constexpr int L = 1 << LG;
+    static constexpr bool IN_T = io_in_strided(IO);
+    static constexpr bool OUT_T = io_out_strided(IO);
+    static constexpr bool PTW = IO == kIoCCP;
+    static constexpr int T = p2_tile_lines(THREADS, LG, IO);
+    static constexpr int LOGT = ilog2(T);
+    static constexpr int G = THREADS / T;
+    static constexpr int NST = pow2_nst(LG);
+    static constexpr int LS = L + L / 16 + 1;   // padded work-buffer line stride
+    static constexpr int LLS = L + p2_row_pad(THREADS, LG, IO, false);  // landing line stride (contiguous in)
+    static constexpr int OLS = L + p2_row_pad(THREADS, LG, IO, true);   // landing line stride (contiguous out)
+    static constexpr int LAND = p2_land_elems(THREADS, LG, IO);
+    static constexpr int BR = L < 256 ? L : 256;  // rows per 3-D TMA box
+    static_assert(T * L <= THREADS * kElemsPerThread, "tile exceeds the CTA's registers");
+    static_assert(T >= 1 && G >= 1, "bad tile shape");
+};
+
+// One Stockham stage (stage S of the compile-time schedule) over the tile.
+template <int THREADS, bool FWD, int LG, int IO, int S>
+__device__ __forceinline__ void p2_stage(const PassDesc& d, float2* land, float2* work, int Tv, int c0)
+{
+    using C = P2<THREADS, LG, IO>;
+    constexpr int L = C::L, T = C::T, G = C::G;
+    constexpr int R = pow2_radix(LG, S);
+    constexpr int NS = 1 << (4 * S);  // every earlier stage is radix 16
+    constexpr int LR = L / R;
+    constexpr int Q = (kElemsPerThread + R - 1) / R;
+    constexpr bool first = S == 0;
+    constexpr bool last = S == C::NST - 1;
+    constexpr bool tfast = (first && C::IN_T) || (last && C::OUT_T);
+    const int tid = threadIdx.x;
+    const int t = tfast ? (tid & (T - 1)) : (tid / G);
+    const int jb = tfast ? (tid >> C::LOGT) : (tid & (G - 1));
+    const bool tok = t < Tv;
+    float2 v[Q][R];
+#pragma unroll
+    for (int q = 0; q < Q; ++q) {
+        if (q * G >= LR) break;  // compile-time: no butterflies left for this slot
+        const int j = jb + q * G;
+        if (tok && ((q + 1) * G <= LR || j < LR)) {
+            if constexpr (first) {
+#pragma unroll
+                for (int r = 0; r < R; ++r)
+                    v[q][r] = C::IN_T ? land[(j + r * LR) * T + t] : land[t * C::LLS + j + r * LR];
+            } else {
+                const float2* p = work + t * C::LS;
+#pragma unroll
+                for (int r = 0; r < R; ++r) v[q][r] = p[spad(j + r * LR)];
+            }
+        }
+    }
+    if constexpr (first == last) __syncthreads();  // reads and writes share the landing buffer
+#pragma unroll
+    for (int q = 0; q < Q; ++q) {
+        if (q * G >= LR) break;
+        const int j = jb + q * G;
+        if (tok && ((q + 1) * G <= LR || j < LR)) {
+            const int k = j & (NS - 1);
+            if constexpr (NS > 1) {
+                const float2* tw = d.tw + d.twoff[S] + k;
+#pragma unroll
+                for (int r = 1; r < R; ++r) v[q][r] = twmul<FWD>(v[q][r], __ldg(tw + (r - 1) * NS));
+            }
+            dft<R, FWD>(v[q]);
+            if constexpr (!last) {
+                float2* p = work + t * C::LS;
+                const int base = (j - k) * R + k;
+#pragma unroll
+                for (int r = 0; r < R; ++r) p[spad(base + r * NS)] = v[q][r];
+            } else {
+                // last stage: NS = L / R, so k == j and output index kk = j + r * LR
+#pragma unroll
+                for (int r = 0; r < R; ++r) {
+                    const int kk = j + r * LR;
+                    float2 y = v[q][r];
+                    if constexpr (C::PTW) {
+                        const unsigned m = (unsigned)(c0 + t) * (unsigned)kk;  // < N < 2^31
+                        const float2 w = cmul(__ldg(d.ptw_hi + (m >> d.ptw_log)),
+                                              __ldg(d.ptw_lo + (m & ((1u << d.ptw_log) - 1))));
+                        y = twmul<FWD>(y, w);
+                    }
+                    if (d.apply_scale) y = d.scale * y;
+                    if constexpr (C::OUT_T)
+                        land[kk * T + t] = y;
+                    else
+                        land[t * C::OLS + kk] = y;
+                }
+            }
+        }
+    }
+}
+
+template <int THREADS, bool FWD, int LG, int IO, int S>
+__device__ __forceinline__ void p2_stages_from(const PassDesc& d, float2* land, float2* work, int Tv, int c0,
+                                               bool async)
+{
+    using C = P2<THREADS, LG, IO>;
+    if constexpr (S < C::NST) {
+        p2_stage<THREADS, FWD, LG, IO, S>(d, land, work, Tv, c0);
+        if constexpr (S == C::NST - 1)
+            if (async) fence_proxy_async();
+        __syncthreads();
+        p2_stages_from<THREADS, FWD, LG, IO, S + 1>(d, land, work, Tv, c0, async);
+    }
+}
+
+__device__ __forceinline__ TileIdx p2_tile_index(const PassDesc& d, long long tile, int logT, int T)
+{
+    TileIdx ti;
+    ti.o = tile / d.tiles_per_o;
+    ti.c0 = (tile - ti.o * d.tiles_per_o) << logT;
+    const long long rem = d.C - ti.c0;
+    ti.Tv = rem < T ? (int)rem : T;
+    return ti;
+}
+
+// Warp 0 (all lanes): start the TMA loads of one tile.
+template <int THREADS, int LG, int IO>
+__device__ __forceinline__ void p2_issue_load(const PassDesc& d, const CUtensorMap* tm, long long tile,
+                                              float2* land, unsigned long long* bar, int lane)
+{
+    using C = P2<THREADS, LG, IO>;
+    const TileIdx ti = p2_tile_index(d, tile, C::LOGT, C::T);
+    if constexpr (!C::IN_T) {
+        const float2* src = d.in + ti.o * d.in_so + ti.c0 * C::L;  // lines are contiguous
+        const unsigned bytes = (unsigned)(ti.Tv * C::L) * 8u;
+        if (lane == 0) mbar_arrive_expect_tx(bar, bytes + d.debug_extra_tx);
+        __syncwarp();
+        if constexpr (C::LLS == C::L) {
+            if (lane == 0) bulk_load_1d(land, src, bytes, bar);
+        } else {
+            for (int t = lane; t < ti.Tv; t += 32) bulk_load_1d(land + t * C::LLS, src + t * C::L, C::L * 8u, bar);
+        }
+    } else {
+        if (lane == 0) {
+            mbar_arrive_expect_tx(bar, (unsigned)(C::T * C::L) * 8u + d.debug_extra_tx);
+            for (int n0 = 0; n0 < C::L; n0 += C::BR)
+                tma_load_3d(land + n0 * C::T, tm, (int)ti.c0, n0, (int)ti.o, bar);
+        }
+    }
+}
+// Warp 0 (all lanes): start the TMA stores of one finished tile.
+template <int THREADS, int LG, int IO>
+__device__ __forceinline__ void p2_issue_store(const PassDesc& d, const CUtensorMap* tm, long long tile,
+                                               const float2* land, int lane)
+{
+    using C = P2<THREADS, LG, IO>;
+    const TileIdx ti = p2_tile_index(d, tile, C::LOGT, C::T);
+    if constexpr (!C::OUT_T) {
+        float2* dst = d.out + ti.o * d.out_so + ti.c0 * C::L;
+        if constexpr (C::OLS == C::L) {
+            if (lane == 0) bulk_store_1d(dst, land, (unsigned)(ti.Tv * C::L) * 8u);
+        } else {
+            for (int t = lane; t < ti.Tv; t += 32) bulk_store_1d(dst + t * C::L, land + t * C::OLS, C::L * 8u);
+        }
+    } else {
+        if (lane == 0)
+            for (int k0 = 0; k0 < C::L; k0 += C::BR) tma_store_3d(tm, (int)ti.c0, k0, (int)ti.o, land + k0 * C::T);
+    }
+    bulk_commit();
+}
+
+// Plain-copy fallback (misaligned bases, odd strides).
+template <int THREADS, int LG, int IO>
+__device__ __forceinline__ void p2_plain_load(const PassDesc& d, const TileIdx& ti, float2* land)
+{
+    using C = P2<THREADS, LG, IO>;
+    const float2* gin = d.in + ti.o * d.in_so + ti.c0 * d.in_sc;
+    if constexpr (!C::IN_T) {
+        for (int e = threadIdx.x; e < ti.Tv * C::L; e += THREADS) {
+            const int t = e >> LG, n = e & (C::L - 1);
+            land[t * C::LLS + n] = gin[(long long)t * d.in_sc + (long long)n * d.in_sn];
+        }
+    } else {
+        for (int e = threadIdx.x; e < C::T * C::L; e += THREADS) {
+            const int n = e >> C::LOGT, t = e & (C::T - 1);
+            if (t < ti.Tv) land[e] = gin[(long long)n * d.in_sn + t];
+        }
+    }
+}
+template <int THREADS, int LG, int IO>
+__device__ __forceinline__ void p2_plain_store(const PassDesc& d, const TileIdx& ti, const float2* land)
+{
+    using C = P2<THREADS, LG, IO>;
+    float2* gout = d.out + ti.o * d.out_so + ti.c0 * d.out_sc;
+    if constexpr (!C::OUT_T) {
+        for (int e = threadIdx.x; e < ti.Tv * C::L; e += THREADS) {
+            const int t = e >> LG, k = e & (C::L - 1);
+            gout[(long long)t * d.out_sc + (long long)k * d.out_sk] = land[t * C::OLS + k];
+        }
+    } else {
+        for (int e = threadIdx.x; e < C::T * C::L; e += THREADS) {
+            const int k = e >> C::LOGT, t = e & (C::T - 1);
+            if (t < ti.Tv) gout[(long long)k * d.out_sk + t] = land[e];
+        }
+    }
+}
+
+// The power-of-two line pass.  Persistent CTAs walk tiles blockIdx.x,
+// +gridDim.x, ...; with TMA on, tile i+1 streams into the second landing
+// buffer while tile i is transformed, and finished tiles leave by TMA stores.
+template <int THREADS, bool FWD, int LG, int IO>
+__global__ void __launch_bounds__(THREADS, 512 / THREADS) k_fft_p2(const __grid_constant__ LineArgs a)
+{
+    using C = P2<THREADS, LG, IO>;
+    const PassDesc& d = a.d;
+    extern __shared__ __align__(128) unsigned char smem_dyn[];
+    unsigned char* smem_raw = smem_dyn + ((128u - (smem_u32(smem_dyn) & 127u)) & 127u);
+    unsigned long long* bar = reinterpret_cast<unsigned long long*>(smem_raw);
+    float2* land0 = reinterpret_cast<float2*>(smem_raw + 128);
+    const bool async = d.async_io != 0;
+    float2* work = land0 + (async ? 2 : 1) * C::LAND;
+    const long long step = gridDim.x;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (async && threadIdx.x == 0) {
+        mbar_init(&bar[0], 1);
+        mbar_init(&bar[1], 1);
+        fence_mbar_init();
+    }
+    __syncthreads();
+    if (async && warp == 0) {
+        if (blockIdx.x < d.ntiles) p2_issue_load<THREADS, LG, IO>(d, &a.tm_in, blockIdx.x, land0, &bar[0], lane);
+        if (blockIdx.x + step < d.ntiles)
+            p2_issue_load<THREADS, LG, IO>(d, &a.tm_in, blockIdx.x + step, land0 + C::LAND, &bar[1], lane);
+    }
+    int i = 0;
+    for (long long tile = blockIdx.x; tile < d.ntiles; tile += step, ++i) {
+        const TileIdx ti = p2_tile_index(d, tile, C::LOGT, C::T);
+        const int buf = async ? (i & 1) : 0;
+        float2* land = land0 + buf * C::LAND;
+        const int c0 = (int)ti.c0;
+        if (async) {
+            const bool bad = !mbar_wait_bounded(&bar[buf], (unsigned)(i >> 1) & 1u);
+            if (__syncthreads_or(bad)) {
+                if (warp == 0) {
+                    if (lane == 0) atomicExch(d.err, 1);
+                    bulk_wait_all();
+                    if (lane == 0 && i == 0 && tile + step < d.ntiles) mbar_wait_bounded(&bar[1], 0);
+                }
+                return;
+            }
+        } else {
+            p2_plain_load<THREADS, LG, IO>(d, ti, land);
+            __syncthreads();
+        }
+        p2_stage<THREADS, FWD, LG, IO, 0>(d, land, work, ti.Tv, c0);
+        if constexpr (C::NST == 1)
+            if (async) fence_proxy_async();
+        __syncthreads();
+        // The previous tile's store has had a stage to drain: recycle its
+        // buffer for the next tile's load.
+        if (async && i >= 1 && warp == 0 && tile + step < d.ntiles) {
+            bulk_wait_read_all();
+            __syncwarp();
+            p2_issue_load<THREADS, LG, IO>(d, &a.tm_in, tile + step, land0 + (buf ^ 1) * C::LAND, &bar[buf ^ 1], lane);
+        }
+        p2_stages_from<THREADS, FWD, LG, IO, 1>(d, land, work, ti.Tv, c0, async);
+        if (async) {
+            if (warp == 0) p2_issue_store<THREADS, LG, IO>(d, &a.tm_out, tile, land, lane);
+        } else {
+            p2_plain_store<THREADS, LG, IO>(d, ti, land);
+            __syncthreads();
+        }
+    }
+    if (async && warp == 0) bulk_wait_all();
+}
+
+template <int THREADS, bool FWD, int LG, int IO>
+LineKernel p2_entry()
+{
+    return make_entry<THREADS>(k_fft_p2<THREADS, FWD, LG, IO>, FWD, LG, IO);
+}
+
+}  // namespace fbfft
