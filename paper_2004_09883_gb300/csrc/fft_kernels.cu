@@ -84,7 +84,7 @@ void line_kernel_name(const LineKernel& k, char* buf, size_t n)
 {
     static const char* io_names[4] = {"NN", "CC", "NC", "CCP"};
     if (k.lg > 0)
-        snprintf(buf, n, "k_fft_p2<%d,%s,L=%d,%s>", k.threads, k.fwd ? "fwd" : "inv", 1 << k.lg,
+        snprintf(buf, n, "k_fft_p2<%d,%s,L=%d,%s>", k.threads - 32, k.fwd ? "fwd" : "inv", 1 << k.lg,
                  (k.io >= 0 && k.io < 4) ? io_names[k.io] : "?");
     else
         snprintf(buf, n, "k_fft_generic<%d,%s>", k.threads, k.fwd ? "fwd" : "inv");

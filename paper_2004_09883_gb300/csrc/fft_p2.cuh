@@ -61,7 +61,12 @@ struct P2 {
     static constexpr int LOGT = ilog2(T);
     static constexpr int G = THREADS / T;
     static constexpr int NST = pow2_nst(LG);
-    static constexpr int LS = L + L / 16 + 1;   // padded work-buffer line stride
+    // Padded work-buffer line stride.  Strided modes read/write it across
+    // lines (consecutive threads on consecutive lines): an odd stride.  The
+    // contiguous mode with G < 16 threads per line puts 16/G lines in one
+    // half-warp: a stride of G (mod 16) values puts them on disjoint banks.
+    static constexpr int LS0 = L + L / 16;
+    static constexpr int LS = (IO == kIoNN && G < 16) ? LS0 + ((G - LS0 % 16) % 16 + 16) % 16 : LS0 + 1;
     static constexpr int LLS = L + p2_row_pad(THREADS, LG, IO, false);  // landing line stride (contiguous in)
     static constexpr int OLS = L + p2_row_pad(THREADS, LG, IO, true);   // landing line stride (contiguous out)
     static constexpr int LAND = p2_land_elems(THREADS, LG, IO);
@@ -69,6 +74,33 @@ struct P2 {
     static_assert(T * L <= THREADS * kElemsPerThread, "tile exceeds the CTA's registers");
     static_assert(T >= 1 && G >= 1, "bad tile shape");
 };
+
+// Barrier among the compute warps only (named barrier 1; the producer warp
+// never joins it).
+template <int THREADS>
+__device__ __forceinline__ void compute_sync()
+{
+    asm volatile("bar.sync 1, %0;" ::"n"(THREADS) : "memory");
+}
+// Same, returning whether any compute thread passed `pred`.
+template <int THREADS>
+__device__ __forceinline__ bool compute_sync_or(bool pred)
+{
+    unsigned r;
+    asm volatile(
+        "{\n\t.reg .pred p, q;\n\t"
+        "setp.ne.u32 p, %1, 0;\n\t"
+        "bar.red.or.pred q, 1, %2, p;\n\t"
+        "selp.u32 %0, 1, 0, q;\n\t}"
+        : "=r"(r)
+        : "r"((unsigned)pred), "n"(THREADS)
+        : "memory");
+    return r != 0;
+}
+__device__ __forceinline__ void mbar_arrive(unsigned long long* bar)
+{
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
 
 // One Stockham stage (stage S of the compile-time schedule) over the tile.
 template <int THREADS, bool FWD, int LG, int IO, int S>
@@ -104,7 +136,7 @@ __device__ __forceinline__ void p2_stage(const PassDesc& d, float2* land, float2
             }
         }
     }
-    if constexpr (first == last) __syncthreads();  // reads and writes share the landing buffer
+    if constexpr (first == last) compute_sync<THREADS>();  // reads and writes share the landing buffer
 #pragma unroll
     for (int q = 0; q < Q; ++q) {
         if (q * G >= LR) break;
@@ -153,8 +185,8 @@ __device__ __forceinline__ void p2_stages_from(const PassDesc& d, float2* land, 
     if constexpr (S < C::NST) {
         p2_stage<THREADS, FWD, LG, IO, S>(d, land, work, Tv, c0);
         if constexpr (S == C::NST - 1)
-            if (async) fence_proxy_async();
-        __syncthreads();
+            if (async) fence_proxy_async();  // output tile -> visible to the TMA store
+        compute_sync<THREADS>();              // (last stage: the work buffer is free again)
         p2_stages_from<THREADS, FWD, LG, IO, S + 1>(d, land, work, Tv, c0, async);
     }
 }
@@ -251,33 +283,68 @@ __device__ __forceinline__ void p2_plain_store(const PassDesc& d, const TileIdx&
     }
 }
 
-// The power-of-two line pass.  Persistent CTAs walk tiles blockIdx.x,
-// +gridDim.x, ...; with TMA on, tile i+1 streams into the second landing
-// buffer while tile i is transformed, and finished tiles leave by TMA stores.
+// The power-of-two line pass.  THREADS compute threads plus one producer
+// warp.  Persistent CTAs walk tiles blockIdx.x, +gridDim.x, ...  With TMA on
+// (d.async_io) the producer warp owns every copy: it loads tile i into landing
+// buffer i%2 (mbarrier full[i%2], counted in bytes), and once the compute
+// warps release a buffer (mbarrier empty[i%2]) it stores the finished tile and
+// reloads the buffer with tile i+2.  Compute warps only wait for `full` and
+// synchronise among themselves on a named barrier, so copy bookkeeping never
+// stalls them.  Every wait is bounded.
 template <int THREADS, bool FWD, int LG, int IO>
-__global__ void __launch_bounds__(THREADS, 512 / THREADS) k_fft_p2(const __grid_constant__ LineArgs a)
+__global__ void __launch_bounds__(THREADS + 32) __maxnreg__(THREADS == 256 ? 112 : 120) k_fft_p2(const __grid_constant__ LineArgs a)
 {
     using C = P2<THREADS, LG, IO>;
     const PassDesc& d = a.d;
     extern __shared__ __align__(128) unsigned char smem_dyn[];
     unsigned char* smem_raw = smem_dyn + ((128u - (smem_u32(smem_dyn) & 127u)) & 127u);
-    unsigned long long* bar = reinterpret_cast<unsigned long long*>(smem_raw);
+    unsigned long long* full = reinterpret_cast<unsigned long long*>(smem_raw);        // [2]
+    unsigned long long* empty = reinterpret_cast<unsigned long long*>(smem_raw) + 2;   // [2]
     float2* land0 = reinterpret_cast<float2*>(smem_raw + 128);
     const bool async = d.async_io != 0;
     float2* work = land0 + (async ? 2 : 1) * C::LAND;
     const long long step = gridDim.x;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    constexpr int kProducer = THREADS / 32;
     if (async && threadIdx.x == 0) {
-        mbar_init(&bar[0], 1);
-        mbar_init(&bar[1], 1);
+        mbar_init(&full[0], 1);
+        mbar_init(&full[1], 1);
+        mbar_init(&empty[0], THREADS);
+        mbar_init(&empty[1], THREADS);
         fence_mbar_init();
     }
     __syncthreads();
-    if (async && warp == 0) {
-        if (blockIdx.x < d.ntiles) p2_issue_load<THREADS, LG, IO>(d, &a.tm_in, blockIdx.x, land0, &bar[0], lane);
-        if (blockIdx.x + step < d.ntiles)
-            p2_issue_load<THREADS, LG, IO>(d, &a.tm_in, blockIdx.x + step, land0 + C::LAND, &bar[1], lane);
+
+    if (warp == kProducer) {
+        if (!async) return;
+        // ---- producer warp ----
+        bool ok = true;
+        int i = 0;
+        long long tile = blockIdx.x;
+        for (; tile < d.ntiles; tile += step, ++i) {
+            const int b = i & 1;
+            if (i >= 2) {  // buffer b still holds tile i-2: wait until it is computed, store it
+                ok = mbar_wait_bounded(&empty[b], (unsigned)((i - 2) >> 1) & 1u);
+                if (!ok) break;
+                p2_issue_store<THREADS, LG, IO>(d, &a.tm_out, tile - 2 * step, land0 + b * C::LAND, lane);
+                bulk_wait_read_all();  // the store has read the buffer
+                __syncwarp();
+            }
+            p2_issue_load<THREADS, LG, IO>(d, &a.tm_in, tile, land0 + b * C::LAND, &full[b], lane);
+        }
+        // drain: store the last (up to two) tiles once computed
+        for (int k = (i >= 2 ? i - 2 : 0); ok && k < i; ++k) {
+            const int b = k & 1;
+            ok = mbar_wait_bounded(&empty[b], (unsigned)(k >> 1) & 1u);
+            if (ok) p2_issue_store<THREADS, LG, IO>(d, &a.tm_out, blockIdx.x + (long long)k * step,
+                                                    land0 + b * C::LAND, lane);
+        }
+        if (!ok && lane == 0) atomicExch(d.err, 1);
+        bulk_wait_all();
+        return;
     }
+
+    // ---- compute warps ----
     int i = 0;
     for (long long tile = blockIdx.x; tile < d.ntiles; tile += step, ++i) {
         const TileIdx ti = p2_tile_index(d, tile, C::LOGT, C::T);
@@ -285,45 +352,38 @@ __global__ void __launch_bounds__(THREADS, 512 / THREADS) k_fft_p2(const __grid_
         float2* land = land0 + buf * C::LAND;
         const int c0 = (int)ti.c0;
         if (async) {
-            const bool bad = !mbar_wait_bounded(&bar[buf], (unsigned)(i >> 1) & 1u);
-            if (__syncthreads_or(bad)) {
-                if (warp == 0) {
-                    if (lane == 0) atomicExch(d.err, 1);
-                    bulk_wait_all();
-                    if (lane == 0 && i == 0 && tile + step < d.ntiles) mbar_wait_bounded(&bar[1], 0);
-                }
-                return;
+            const bool bad = !mbar_wait_bounded(&full[buf], (unsigned)(i >> 1) & 1u);
+            if (compute_sync_or<THREADS>(bad)) {
+                if (threadIdx.x == 0) atomicExch(d.err, 1);
+                return;  // the producer's own bounded waits end it
             }
         } else {
             p2_plain_load<THREADS, LG, IO>(d, ti, land);
-            __syncthreads();
+            compute_sync<THREADS>();
         }
         p2_stage<THREADS, FWD, LG, IO, 0>(d, land, work, ti.Tv, c0);
-        if constexpr (C::NST == 1)
+        if constexpr (C::NST == 1) {
             if (async) fence_proxy_async();
-        __syncthreads();
-        // The previous tile's store has had a stage to drain: recycle its
-        // buffer for the next tile's load.
-        if (async && i >= 1 && warp == 0 && tile + step < d.ntiles) {
-            bulk_wait_read_all();
-            __syncwarp();
-            p2_issue_load<THREADS, LG, IO>(d, &a.tm_in, tile + step, land0 + (buf ^ 1) * C::LAND, &bar[buf ^ 1], lane);
+        } else {
+            compute_sync<THREADS>();
         }
         p2_stages_from<THREADS, FWD, LG, IO, 1>(d, land, work, ti.Tv, c0, async);
         if (async) {
-            if (warp == 0) p2_issue_store<THREADS, LG, IO>(d, &a.tm_out, tile, land, lane);
+            mbar_arrive(&empty[buf]);  // after this thread's proxy fence
         } else {
+            compute_sync<THREADS>();
             p2_plain_store<THREADS, LG, IO>(d, ti, land);
-            __syncthreads();
+            compute_sync<THREADS>();
         }
     }
-    if (async && warp == 0) bulk_wait_all();
 }
 
 template <int THREADS, bool FWD, int LG, int IO>
 LineKernel p2_entry()
 {
-    return make_entry<THREADS>(k_fft_p2<THREADS, FWD, LG, IO>, FWD, LG, IO);
+    LineKernel k = make_entry<THREADS>(k_fft_p2<THREADS, FWD, LG, IO>, FWD, LG, IO);
+    k.threads = THREADS + 32;  // compute warps + the producer warp
+    return k;
 }
 
 }  // namespace fbfft
