@@ -104,8 +104,9 @@ int ilog2ll(long long x)
     return l;
 }
 
-// Radix schedule of an in-shared-memory line: 16s first, then the leftover
-// power of two (8, 4 or 2), then 5s, then 3s.
+// Radix schedule of an in-shared-memory line: the leftover power of two
+// (8, 4 or 2) first, then 16s, then 5s, then 3s.  For powers of two this is
+// the schedule the compile-time kernels use (pow2_radix).
 int factorize(long long n, int* r, int cap)
 {
     if (n < 1) return FB_FFT_ERR_INVALID_ARG;
@@ -117,10 +118,10 @@ int factorize(long long n, int* r, int cap)
     };
     int a = 0;
     while (n % 2 == 0) n /= 2, ++a;
-    while (a >= 4) push(16), a -= 4;
-    if (a == 3) push(8);
-    if (a == 2) push(4);
-    if (a == 1) push(2);
+    if (a % 4 == 3) push(8);
+    if (a % 4 == 2) push(4);
+    if (a % 4 == 1) push(2);
+    for (; a >= 4; a -= 4) push(16);
     while (n % 5 == 0) n /= 5, push(5);
     while (n % 3 == 0) n /= 3, push(3);
     return c;

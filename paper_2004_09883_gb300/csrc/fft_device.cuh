@@ -445,10 +445,17 @@ __device__ __forceinline__ void run_stage(int R, const PassDesc& d, int Ns, int 
     }
 }
 
-// Power-of-two schedules, fixed at compile time: log2 L = 4a + b gives a
-// radix-16 stages followed by one radix-2^b stage when b > 0.
+// Power-of-two schedules, fixed at compile time: log2 L = 4a + b gives one
+// radix-2^b stage first when b > 0 (stage 0 multiplies by no twiddles, so the
+// small radix's extra butterflies per thread cost least there), then a
+// radix-16 stages.
 __host__ __device__ constexpr int pow2_nst(int lg) { return lg / 4 + (lg % 4 ? 1 : 0); }
-__host__ __device__ constexpr int pow2_radix(int lg, int s) { return s < lg / 4 ? 16 : (1 << (lg % 4)); }
+__host__ __device__ constexpr int pow2_radix(int lg, int s) { return (lg % 4 && s == 0) ? (1 << (lg % 4)) : 16; }
+// Ns before stage s (the product of the earlier radices).
+__host__ __device__ constexpr int pow2_ns(int lg, int s)
+{
+    return s == 0 ? 1 : (lg % 4 ? (1 << (lg % 4)) : 16) * (1 << (4 * (s - 1)));
+}
 
 // The generic line pass: any 5-smooth L <= 4096, stage radices read from the
 // descriptor at run time.  Persistent CTAs walk tiles blockIdx.x, +gridDim.x,

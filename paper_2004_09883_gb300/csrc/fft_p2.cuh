@@ -109,7 +109,7 @@ __device__ __forceinline__ void p2_stage(const PassDesc& d, float2* land, float2
     using C = P2<THREADS, LG, IO>;
     constexpr int L = C::L, T = C::T, G = C::G;
     constexpr int R = pow2_radix(LG, S);
-    constexpr int NS = 1 << (4 * S);  // every earlier stage is radix 16
+    constexpr int NS = pow2_ns(LG, S);
     constexpr int LR = L / R;
     constexpr int Q = (kElemsPerThread + R - 1) / R;
     constexpr bool first = S == 0;
@@ -292,7 +292,7 @@ __device__ __forceinline__ void p2_plain_store(const PassDesc& d, const TileIdx&
 // synchronise among themselves on a named barrier, so copy bookkeeping never
 // stalls them.  Every wait is bounded.
 template <int THREADS, bool FWD, int LG, int IO>
-__global__ void __launch_bounds__(THREADS + 32) __maxnreg__(THREADS == 256 ? 112 : 120) k_fft_p2(const __grid_constant__ LineArgs a)
+__global__ void __maxnreg__(96) k_fft_p2(const __grid_constant__ LineArgs a)
 {
     using C = P2<THREADS, LG, IO>;
     const PassDesc& d = a.d;

@@ -69,10 +69,10 @@ def test_factorize_every_smooth_length(fb, n):
     assert int(np.prod(r)) == n
     assert all(x in (2, 3, 4, 5, 8, 16) for x in r)
     assert len(r) <= 8
-    # 16s lead, at most one other power-of-two radix, then 5s, then 3s
+    # at most one of 8/4/2, leading; then 16s, then 5s, then 3s
     p2 = [x for x in r if x in (2, 4, 8)]
     assert len(p2) <= 1
-    assert r == sorted(r, key=lambda x: {16: 0, 8: 1, 4: 1, 2: 1, 5: 2, 3: 3}[x])
+    assert r == sorted(r, key=lambda x: {8: 0, 4: 0, 2: 0, 16: 1, 5: 2, 3: 3}[x])
 
 
 @pytest.mark.parametrize("n", [0, -4, 7, 14, 4097 * 2, 8192, 11 * 16])
