@@ -195,6 +195,34 @@ long long fb_fft_launch_count(void);
  */
 int fb_fft_twiddles(long long d, long long count, float* host_out);
 
+/*
+ * fb_fft_exec_1d_noalloc -- batched 1-D transform that allocates nothing.
+ * The paper has no counterpart: this serves callers that cannot call
+ * cudaMalloc (code running while a CUDA graph is being captured, real-time
+ * or signal-context code that must stay out of allocators, embedders whose
+ * device memory belongs to another allocator), for whom fb_fft_plan's
+ * device-resident twiddle tables and scratch are not an option.
+ *   in, out    device pointers, batch*n complex64 values each, 8-byte aligned;
+ *              out == in runs in place, partial overlap is INVALID_ARG.
+ *   n          5-smooth length, 1 <= n <= 4194304 (2^22) and splittable as the
+ *              plan API's four-step (fb_fft_split); larger n is
+ *              FB_FFT_ERR_UNSUPPORTED_SIZE.
+ *   batch      >= 0 transforms back to back (any count: they run in chunks).
+ *   direction  FB_FFT_FORWARD / FB_FFT_INVERSE;  flags 0 or FB_FFT_SCALE_INV_N.
+ *   stream     cudaStream_t (NULL = legacy default stream).
+ * Asynchronous on `stream`.  Twiddle tables and the four-step intermediate
+ * live in one file-scope device array of the library (32 MiB + 256 KiB + 256
+ * bytes, held by every GPU that loads the library until the process exits).
+ * The first call on each device looks up that array's device address
+ * (cudaGetSymbolAddress), so make it before any stream capture.  Every call
+ * reuses and overwrites the array: calls that overlap on the GPU race, so
+ * serialise them (one stream, or events).  A device-side wait that times out
+ * is recorded in the array but not reported by this call.
+ * Errors: INVALID_ARG, UNSUPPORTED_SIZE, CUDA.
+ */
+int fb_fft_exec_1d_noalloc(const void* in, void* out, long long n, long long batch, int direction,
+                           unsigned flags, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -69,6 +69,7 @@ _sig = {
     "fb_fft_launch_count": (_ll, []),
     "fb_fft_twiddles": (_int, [_ll, _ll, ctypes.POINTER(ctypes.c_float)]),
     "fb_fft_debug_inject_timeout": (_int, [_vp, _int]),
+    "fb_fft_exec_1d_noalloc": (_int, [_vp, _vp, _ll, _ll, _int, ctypes.c_uint, _vp]),
 }
 for _name, (_res, _args) in _sig.items():
     _f = getattr(lib, _name)
@@ -247,6 +248,17 @@ class Plan:
         _check(lib.fb_fft_profile_read(self._h, ms, cnt, cap, ctypes.byref(n)), "fb_fft_profile_read")
         names = self.pass_names()
         return [(names[i], ms[i], cnt[i]) for i in range(min(n.value, cap))]
+
+
+def exec_1d_noalloc(x, out, n: int, batch: int, direction: int = FORWARD, scale_inv_n: bool = False):
+    """Batched 1-D transform through fb_fft_exec_1d_noalloc: no plan, no
+    device allocation (the library's static workspace is used), on the
+    current torch stream.  ``x`` and ``out`` are complex64 CUDA tensors."""
+    import torch
+    s = torch.cuda.current_stream(x.device).cuda_stream
+    _check(lib.fb_fft_exec_1d_noalloc(_vp(x.data_ptr()), _vp(out.data_ptr()), int(n), int(batch), int(direction),
+                                      SCALE_INV_N if scale_inv_n else 0, _vp(s)), "fb_fft_exec_1d_noalloc")
+    return out
 
 
 def fft(x, dims, direction: int = FORWARD, scale_inv_n: bool = False, out=None):
