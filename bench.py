@@ -9,7 +9,7 @@ beside it.  Four input/output buffer pairs (512 MiB) rotate between steps so
 the working set exceeds the 126 MB L2.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
-                  [--workload 3d|1d4096|1d2p20]
+                  [--workload 3d|1d4096|1d4096L|1d2p20]
 
 Under torchrun each rank runs its own replica (independent transforms, no
 collective on the data path); rank 0 prints one JSON line.  --impl reference
@@ -40,6 +40,8 @@ WORKLOADS = {
                seed=inputs.seed_for(inputs.WORKLOAD_3D_256x256x128), dist="normal", inverse=True),
     "1d4096": dict(name="1d_c2c_4096_batch64_fwd", dims=[4096], batch=64,
                    seed=inputs.seed_for(inputs.WORKLOAD_1D_4096x64), dist="uniform", inverse=False),
+    "1d4096L": dict(name="1d_c2c_4096_batch16384_fwd", dims=[4096], batch=16384,
+                    seed=inputs.seed_for(inputs.WORKLOAD_1D_4096x64), dist="uniform", inverse=False),
     "1d2p20": dict(name="1d_c2c_2p20_batch32_fwd", dims=[1 << 20], batch=32,
                    seed=inputs.seed_for(inputs.WORKLOAD_1D_2P20x32), dist="normal", inverse=False),
 }
@@ -140,6 +142,31 @@ def dist_setup():
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     return world, rank, local
+
+
+# ---------------------------------------------------------------------------
+# Multi-rank host logic (replicas: each rank transforms its own inputs; no
+# collective touches the data path, only the timing reduction below)
+# ---------------------------------------------------------------------------
+def replica_rep(rank: int, r: int) -> int:
+    """Seed repeat index of buffer r on `rank`: distinct data on every rank."""
+    return rank * 16 + r
+
+
+def max_over_ranks(x: float, dist, device) -> float:
+    """Largest value of x over all ranks (per-step times: the job is as slow
+    as its slowest rank).  dist None = single process."""
+    if dist is None:
+        return float(x)
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(world: int, units_per_rank_step: float, ms_per_step: float) -> float:
+    """Units all ranks processed per second, from the slowest rank's step time."""
+    return world * units_per_rank_step / (ms_per_step / 1e3)
 
 
 def make_input(wl: dict, rep: int) -> np.ndarray:
@@ -265,7 +292,7 @@ def run_gpu(args, wl: dict) -> None:
     nbuf = max(2, int(math.ceil(512 * 2 ** 20 / (2 * 8 * n * batch))))
     nbuf = min(nbuf, 8)
     stream = torch.cuda.current_stream(dev)
-    host_inputs = [make_input(wl, rank * 16 + r) for r in range(nbuf)]
+    host_inputs = [make_input(wl, replica_rep(rank, r)) for r in range(nbuf)]
     xin = [torch.from_numpy(h.reshape(-1)).to(dev) for h in host_inputs]
     xout = [torch.empty_like(xin[0]) for _ in range(nbuf)]
     plan = fbfft.Plan(dims, batch, scale_inv_n=wl["inverse"], stream=stream)
@@ -309,10 +336,7 @@ def run_gpu(args, wl: dict) -> None:
     passes = plan.profile_read()
     plan.profile(False)
     plan.check()
-    if dist is not None:
-        t = torch.tensor([ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(ms, dist, dev)
     clk = clocks.summary(wall0, wall1) if clocks else None
     if clocks:
         clocks.stop()
@@ -339,18 +363,15 @@ def run_gpu(args, wl: dict) -> None:
             e2e_step(i)
         barrier()
         e2e_ms = (time.perf_counter() - t0) / e2e_steps * 1e3
-        if dist is not None:
-            t = torch.tensor([e2e_ms], device=dev)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            e2e_ms = float(t.item())
+        e2e_ms = max_over_ranks(e2e_ms, dist, dev)
         io = 8 * n * batch * execs
-        e2e = {"value": round(world * bytes_step / (e2e_ms / 1e3) / 1e9, 3), "unit": "GB/s",
+        e2e = {"value": round(whole_job_rate(world, bytes_step, e2e_ms) / 1e9, 3), "unit": "GB/s",
                "h2d_bytes_per_step": io, "d2h_bytes_per_step": io, "ms_per_step": e2e_ms,
                "path": "fb_fft_exec_host (pinned host arrays)" + (", forward then inverse" if wl["inverse"] else ", forward")}
 
     if rank == 0:
         peaks = load_peaks()
-        value = world * bytes_step / (ms / 1e3) / 1e9
+        value = whole_job_rate(world, bytes_step, ms) / 1e9
         # dominant kernel: the pass role with the largest measured time
         dom = max(passes, key=lambda r: r[1]) if passes else None
         roofline = None
@@ -384,7 +405,7 @@ def run_gpu(args, wl: dict) -> None:
                        "l2": f"{nbuf} rotating input/output buffer pairs "
                              f"({nbuf * 2 * 8 * n * batch / 2 ** 20:.0f} MiB) > 126 MB L2",
                        "parallelism": "replicas" if world > 1 else "single GPU"},
-            "gflops": round(world * flops_step / (ms / 1e3) / 1e9, 2),
+            "gflops": round(whole_job_rate(world, flops_step, ms) / 1e9, 2),
             "hbm_frac_effective": round(value / world / peaks["hbm_gbs"], 4),
             "roofline": roofline,
             "cpu_baseline": cpu_baseline,
