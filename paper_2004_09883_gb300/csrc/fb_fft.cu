@@ -104,9 +104,9 @@ int ilog2ll(long long x)
     return l;
 }
 
-// Radix schedule of an in-shared-memory line: the leftover power of two
-// (8, 4 or 2) first, then 16s, then 5s, then 3s.  For powers of two this is
-// the schedule the compile-time kernels use (pow2_radix).
+// Radix schedule of an in-shared-memory line: the power-of-two part as the
+// compile-time kernels order it (pow2_radix: 16s, with the leftover 8/4/2
+// last when that makes two stages, first otherwise), then 5s, then 3s.
 int factorize(long long n, int* r, int cap)
 {
     if (n < 1) return FB_FFT_ERR_INVALID_ARG;
@@ -118,10 +118,7 @@ int factorize(long long n, int* r, int cap)
     };
     int a = 0;
     while (n % 2 == 0) n /= 2, ++a;
-    if (a % 4 == 3) push(8);
-    if (a % 4 == 2) push(4);
-    if (a % 4 == 1) push(2);
-    for (; a >= 4; a -= 4) push(16);
+    for (int s = 0; s < pow2_nst(a); ++s) push(pow2_radix(a, s));
     while (n % 5 == 0) n /= 5, push(5);
     while (n % 3 == 0) n /= 3, push(3);
     return c;
@@ -211,6 +208,7 @@ int make_line_pass(PassPlan& p, TwiddleBuilder& twb, long long L, long long O, l
         if (!line_kernel_p2(p.threads, true, p.lg, p.io).fn) return FB_FFT_ERR_UNSUPPORTED_SIZE;
         T = p2_tile_lines(p.threads, p.lg, p.io);
         land = p2_land_elems(p.threads, p.lg, p.io);
+        d.tws = p2_smem_twiddles(p.lg);
     } else {
         p.io = -1;
         p.threads = kGenericThreads;
@@ -253,10 +251,10 @@ int make_line_pass(PassPlan& p, TwiddleBuilder& twb, long long L, long long O, l
     d.box_rows = br > 0 ? br : 1;
     d.land_stride = (int)land;
     d.ptw = ptw ? 1 : 0;
-    p.smem = line_smem_bytes(d.land_stride, (int)L, (int)T, nst, p.async_ok);
+    p.smem = line_smem_bytes(d.land_stride, (int)L, (int)T, nst, p.async_ok, d.tws);
     if (p.smem > kMaxSmemBytes) {
         p.async_ok = false;
-        p.smem = line_smem_bytes(d.land_stride, (int)L, (int)T, nst, false);
+        p.smem = line_smem_bytes(d.land_stride, (int)L, (int)T, nst, false, d.tws);
     }
     if (p.smem > kMaxSmemBytes) return FB_FFT_ERR_UNSUPPORTED_SIZE;
     p.grid = d.ntiles;  // capped to the resident CTA count when the plan is built
@@ -487,7 +485,7 @@ int exec_device(fb_fft_plan_s* p, const float2* in, float2* out, int direction)
                 d.async_io = 0;
         }
         if (p->debug_timeout && d.async_io) d.debug_extra_tx = 16;
-        const size_t smem = line_smem_bytes(d.land_stride, d.L, 1 << d.logT, d.nst, d.async_io != 0);
+        const size_t smem = line_smem_bytes(d.land_stride, d.L, 1 << d.logT, d.nst, d.async_io != 0, d.tws);
         if (q.last && scale) {
             d.apply_scale = 1;
             d.scale = (float)(1.0 / (double)p->N);

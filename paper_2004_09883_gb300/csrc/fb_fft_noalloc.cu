@@ -128,6 +128,7 @@ int fill_pass(Pass& p, StackTwiddles& tw, long long L, long long O, long long C,
         p.k[0] = line_kernel_p2(threads, false, lg, io);
         T = p2_tile_lines(threads, lg, io);
         land = p2_land_elems(threads, lg, io);
+        d.tws = p2_smem_twiddles(lg);
     } else {
         threads = kGenericThreads;
         p.k[1] = line_kernel_generic(true);
@@ -168,10 +169,10 @@ int fill_pass(Pass& p, StackTwiddles& tw, long long L, long long O, long long C,
     p.async_ok = in_ok && out_ok && br > 0;
     d.box_rows = br > 0 ? br : 1;
     d.land_stride = (int)land;
-    p.smem = line_smem_bytes(land, (int)L, (int)T, nst, p.async_ok);
+    p.smem = line_smem_bytes(land, (int)L, (int)T, nst, p.async_ok, d.tws);
     if (p.smem > 227 * 1024) {
         p.async_ok = false;
-        p.smem = line_smem_bytes(land, (int)L, (int)T, nst, false);
+        p.smem = line_smem_bytes(land, (int)L, (int)T, nst, false, d.tws);
     }
     if (p.smem > 227 * 1024) return FB_FFT_ERR_UNSUPPORTED_SIZE;
     p.grid = d.ntiles;
@@ -229,7 +230,7 @@ int launch(const Pass& p, const float2* in, float2* out, const float2* tw, int* 
         if (p.d.in_tfast && encode(&a.tm_in, in, p.d, O, p.d.in_sn, p.d.in_so) != 0) a.d.async_io = 0;
         if (p.d.out_tfast && encode(&a.tm_out, out, p.d, O, p.d.out_sk, p.d.out_so) != 0) a.d.async_io = 0;
     }
-    const size_t smem = line_smem_bytes(p.d.land_stride, p.d.L, 1 << p.d.logT, p.d.nst, a.d.async_io != 0);
+    const size_t smem = line_smem_bytes(p.d.land_stride, p.d.L, 1 << p.d.logT, p.d.nst, a.d.async_io != 0, p.d.tws);
     const LineKernel& k = p.k[fwd ? 1 : 0];
     int occ = 0;
     if (line_occupancy(k, smem, &occ) != cudaSuccess || occ < 1) return FB_FFT_ERR_CUDA;

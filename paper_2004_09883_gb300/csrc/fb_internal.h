@@ -56,6 +56,7 @@ struct PassDesc {
     int box_rows;          // rows per 3-D TMA box (a divisor of L, <= 256)
     int* err;              // device error word: 1 = a bounded wait gave up
     unsigned debug_extra_tx;  // test hook: bytes announced per tile that never arrive
+    int tws;               // stage-twiddle entries the kernel copies to shared memory
 };
 
 // Kernel argument: the descriptor plus the TMA tensor maps of the c-fast
@@ -70,12 +71,12 @@ struct LineArgs {
 // alignment slack and mbarriers (256 B), one or two dense landing buffers and the
 // padded work buffer.
 inline long long land_stride_elems(int L, int T) { return ((long long)L * T + 15) & ~15LL; }
-inline size_t line_smem_bytes(long long land_elems, int L, int T, int nst, bool async)
+inline size_t line_smem_bytes(long long land_elems, int L, int T, int nst, bool async, int tws = 0)
 {
     const long long land = land_elems * (async ? 2 : 1);
-    const long long LS = (long long)L + (L >> 4) + 1;
+    const long long LS = (long long)L + (L >> 4) + 16;  // bound on every mode's work-row stride
     const long long work = nst <= 1 ? 0 : LS * T;
-    return 256 + (size_t)(land + work) * sizeof(float2);  // alignment slack + mbarriers
+    return 256 + (size_t)(land + work + tws) * sizeof(float2);  // alignment slack + mbarriers
 }
 
 // One compiled line-pass kernel.  lg = log2(L) for the compile-time

@@ -445,16 +445,24 @@ __device__ __forceinline__ void run_stage(int R, const PassDesc& d, int Ns, int 
     }
 }
 
-// Power-of-two schedules, fixed at compile time: log2 L = 4a + b gives one
-// radix-2^b stage first when b > 0 (stage 0 multiplies by no twiddles, so the
-// small radix's extra butterflies per thread cost least there), then a
-// radix-16 stages.
+// Power-of-two schedules, fixed at compile time.  log2 L = 4a + b: a radix-16
+// stages and, when b > 0, one radix-2^b stage.  Two-stage schedules run the
+// radix-16 stage first (every shared-memory phase then touches G consecutive
+// values per line, which the row padding keeps conflict free); longer ones run
+// the small radix first, where stage 0's lack of twiddles offsets its extra
+// butterflies per thread.
 __host__ __device__ constexpr int pow2_nst(int lg) { return lg / 4 + (lg % 4 ? 1 : 0); }
-__host__ __device__ constexpr int pow2_radix(int lg, int s) { return (lg % 4 && s == 0) ? (1 << (lg % 4)) : 16; }
+__host__ __device__ constexpr bool pow2_rem_first(int lg) { return (lg % 4) != 0 && pow2_nst(lg) >= 3; }
+__host__ __device__ constexpr int pow2_radix(int lg, int s)
+{
+    return (lg % 4) == 0 ? 16
+                         : (pow2_rem_first(lg) ? (s == 0 ? (1 << (lg % 4)) : 16)
+                                               : (s == pow2_nst(lg) - 1 ? (1 << (lg % 4)) : 16));
+}
 // Ns before stage s (the product of the earlier radices).
 __host__ __device__ constexpr int pow2_ns(int lg, int s)
 {
-    return s == 0 ? 1 : (lg % 4 ? (1 << (lg % 4)) : 16) * (1 << (4 * (s - 1)));
+    return s == 0 ? 1 : pow2_radix(lg, s - 1) * pow2_ns(lg, s - 1);
 }
 
 // The generic line pass: any 5-smooth L <= 4096, stage radices read from the

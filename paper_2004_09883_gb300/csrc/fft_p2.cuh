@@ -32,14 +32,24 @@ __host__ __device__ constexpr int p2_tile_lines(int threads, int lg, int io)
     return (io_in_strided(io) || io_out_strided(io)) ? p2_min(16, threads * kElemsPerThread >> lg)
                                                      : p2_min(threads, threads * kElemsPerThread >> lg);
 }
-// Row padding of contiguous landing layouts: when one warp spans several
-// lines, a gap of G/2 values (G = threads per line) spreads them over the banks.
+// Row padding of contiguous landing layouts: with G < 16 threads per line a
+// half-warp touches 16/G lines at G consecutive values each; rows G values
+// apart (mod 16) put those lines on disjoint banks.  (Even, so every row stays
+// 16-byte aligned for its bulk copy.)
 __host__ __device__ constexpr int p2_row_pad(int threads, int lg, int io, bool out_side)
 {
     const int T = p2_tile_lines(threads, lg, io);
     const int G = threads / T;
     const bool strided = out_side ? io_out_strided(io) : io_in_strided(io);
-    return (!strided && G < 32) ? p2_max(2, G / 2) : 0;
+    return (!strided && G < 16) ? (G >= 2 ? G : 2) : 0;
+}
+// Stage twiddle tables (stages 1..NST-1) small enough to copy into shared
+// memory once per CTA: their total entry count, or 0 when they stay in global.
+__host__ __device__ constexpr int p2_smem_twiddles(int lg)
+{
+    int total = 0;
+    for (int s = 1; s < pow2_nst(lg); ++s) total += pow2_ns(lg, s) * (pow2_radix(lg, s) - 1);
+    return total <= 1024 ? total : 0;
 }
 // Elements of one landing buffer (input layout, then reused for the output layout).
 __host__ __device__ constexpr int p2_land_elems(int threads, int lg, int io)
@@ -71,6 +81,7 @@ struct P2 {
     static constexpr int OLS = L + p2_row_pad(THREADS, LG, IO, true);   // landing line stride (contiguous out)
     static constexpr int LAND = p2_land_elems(THREADS, LG, IO);
     static constexpr int BR = L < 256 ? L : 256;  // rows per 3-D TMA box
+    static constexpr int TWS = p2_smem_twiddles(LG);  // twiddle entries kept in shared memory (0: global)
     static_assert(T * L <= THREADS * kElemsPerThread, "tile exceeds the CTA's registers");
     static_assert(T >= 1 && G >= 1, "bad tile shape");
 };
@@ -102,9 +113,16 @@ __device__ __forceinline__ void mbar_arrive(unsigned long long* bar)
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
 }
 
+// Offset of stage s's table inside the shared-memory twiddle copy.
+__host__ __device__ constexpr int p2_tws_off(int lg, int s)
+{
+    return s <= 1 ? 0 : p2_tws_off(lg, s - 1) + pow2_ns(lg, s - 1) * (pow2_radix(lg, s - 1) - 1);
+}
+
 // One Stockham stage (stage S of the compile-time schedule) over the tile.
 template <int THREADS, bool FWD, int LG, int IO, int S>
-__device__ __forceinline__ void p2_stage(const PassDesc& d, float2* land, float2* work, int Tv, int c0)
+__device__ __forceinline__ void p2_stage(const PassDesc& d, float2* land, float2* work, int Tv, int c0,
+                                         const float2* tws)
 {
     using C = P2<THREADS, LG, IO>;
     constexpr int L = C::L, T = C::T, G = C::G;
@@ -144,9 +162,15 @@ __device__ __forceinline__ void p2_stage(const PassDesc& d, float2* land, float2
         if (tok && ((q + 1) * G <= LR || j < LR)) {
             const int k = j & (NS - 1);
             if constexpr (NS > 1) {
-                const float2* tw = d.tw + d.twoff[S] + k;
+                if constexpr (C::TWS > 0) {
+                    const float2* tw = tws + p2_tws_off(LG, S) + k;
 #pragma unroll
-                for (int r = 1; r < R; ++r) v[q][r] = twmul<FWD>(v[q][r], __ldg(tw + (r - 1) * NS));
+                    for (int r = 1; r < R; ++r) v[q][r] = twmul<FWD>(v[q][r], tw[(r - 1) * NS]);
+                } else {
+                    const float2* tw = d.tw + d.twoff[S] + k;
+#pragma unroll
+                    for (int r = 1; r < R; ++r) v[q][r] = twmul<FWD>(v[q][r], __ldg(tw + (r - 1) * NS));
+                }
             }
             dft<R, FWD>(v[q]);
             if constexpr (!last) {
@@ -179,15 +203,27 @@ __device__ __forceinline__ void p2_stage(const PassDesc& d, float2* land, float2
 
 template <int THREADS, bool FWD, int LG, int IO, int S>
 __device__ __forceinline__ void p2_stages_from(const PassDesc& d, float2* land, float2* work, int Tv, int c0,
-                                               bool async)
+                                               bool async, const float2* tws)
 {
     using C = P2<THREADS, LG, IO>;
     if constexpr (S < C::NST) {
-        p2_stage<THREADS, FWD, LG, IO, S>(d, land, work, Tv, c0);
+        p2_stage<THREADS, FWD, LG, IO, S>(d, land, work, Tv, c0, tws);
         if constexpr (S == C::NST - 1)
             if (async) fence_proxy_async();  // output tile -> visible to the TMA store
         compute_sync<THREADS>();              // (last stage: the work buffer is free again)
-        p2_stages_from<THREADS, FWD, LG, IO, S + 1>(d, land, work, Tv, c0, async);
+        p2_stages_from<THREADS, FWD, LG, IO, S + 1>(d, land, work, Tv, c0, async, tws);
+    }
+}
+
+// Compute threads: copy the stage twiddle tables into shared memory.
+template <int THREADS, int LG, int S>
+__device__ __forceinline__ void p2_copy_twiddles(const PassDesc& d, float2* tws)
+{
+    if constexpr (S < pow2_nst(LG)) {
+        constexpr int n = pow2_ns(LG, S) * (pow2_radix(LG, S) - 1);
+        const float2* src = d.tw + d.twoff[S];
+        for (int e = threadIdx.x; e < n; e += THREADS) tws[p2_tws_off(LG, S) + e] = __ldg(src + e);
+        p2_copy_twiddles<THREADS, LG, S + 1>(d, tws);
     }
 }
 
@@ -303,6 +339,8 @@ __global__ void __maxnreg__(96) k_fft_p2(const __grid_constant__ LineArgs a)
     float2* land0 = reinterpret_cast<float2*>(smem_raw + 128);
     const bool async = d.async_io != 0;
     float2* work = land0 + (async ? 2 : 1) * C::LAND;
+    // stage twiddles (when small) follow the work buffer
+    float2* tws = work + (C::NST > 1 ? C::T * C::LS : 0);
     const long long step = gridDim.x;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     constexpr int kProducer = THREADS / 32;
@@ -345,6 +383,10 @@ __global__ void __maxnreg__(96) k_fft_p2(const __grid_constant__ LineArgs a)
     }
 
     // ---- compute warps ----
+    if constexpr (C::TWS > 0) {
+        p2_copy_twiddles<THREADS, LG, 1>(d, tws);
+        compute_sync<THREADS>();
+    }
     int i = 0;
     for (long long tile = blockIdx.x; tile < d.ntiles; tile += step, ++i) {
         const TileIdx ti = p2_tile_index(d, tile, C::LOGT, C::T);
@@ -361,13 +403,13 @@ __global__ void __maxnreg__(96) k_fft_p2(const __grid_constant__ LineArgs a)
             p2_plain_load<THREADS, LG, IO>(d, ti, land);
             compute_sync<THREADS>();
         }
-        p2_stage<THREADS, FWD, LG, IO, 0>(d, land, work, ti.Tv, c0);
+        p2_stage<THREADS, FWD, LG, IO, 0>(d, land, work, ti.Tv, c0, tws);
         if constexpr (C::NST == 1) {
             if (async) fence_proxy_async();
         } else {
             compute_sync<THREADS>();
         }
-        p2_stages_from<THREADS, FWD, LG, IO, 1>(d, land, work, ti.Tv, c0, async);
+        p2_stages_from<THREADS, FWD, LG, IO, 1>(d, land, work, ti.Tv, c0, async, tws);
         if (async) {
             mbar_arrive(&empty[buf]);  // after this thread's proxy fence
         } else {

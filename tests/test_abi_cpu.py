@@ -69,10 +69,15 @@ def test_factorize_every_smooth_length(fb, n):
     assert int(np.prod(r)) == n
     assert all(x in (2, 3, 4, 5, 8, 16) for x in r)
     assert len(r) <= 8
-    # at most one of 8/4/2, leading; then 16s, then 5s, then 3s
+    # power-of-two radices (16s and at most one 8/4/2) before 5s before 3s
     p2 = [x for x in r if x in (2, 4, 8)]
     assert len(p2) <= 1
-    assert r == sorted(r, key=lambda x: {8: 0, 4: 0, 2: 0, 16: 1, 5: 2, 3: 3}[x])
+    assert r == sorted(r, key=lambda x: {8: 0, 4: 0, 2: 0, 16: 0, 5: 2, 3: 3}[x])
+    pw = [x for x in r if x in (2, 4, 8, 16)]
+    if p2 and len(pw) == 2:
+        assert pw == [16, p2[0]]       # two stages: radix 16 first
+    elif p2:
+        assert pw[0] == p2[0]          # three or more: the small radix first
 
 
 @pytest.mark.parametrize("n", [0, -4, 7, 14, 4097 * 2, 8192, 11 * 16])
