@@ -262,19 +262,6 @@ __device__ __forceinline__ void p2_issue_load(const PassDesc& d, const CUtensorM
         }
     }
 }
-// Producer lane 0: pull a later tile into L2 ahead of its load.
-template <int THREADS, int LG, int IO>
-__device__ __forceinline__ void p2_prefetch(const PassDesc& d, const CUtensorMap* tm, long long tile)
-{
-    using C = P2<THREADS, LG, IO>;
-    const TileIdx ti = p2_tile_index(d, tile, C::LOGT, C::T);
-    if constexpr (!C::IN_T) {
-        bulk_prefetch_l2(d.in + ti.o * d.in_so + ti.c0 * C::L, (unsigned)(ti.Tv * C::L) * 8u);
-    } else {
-        for (int n0 = 0; n0 < C::L; n0 += C::BR) tma_prefetch_3d(tm, (int)ti.c0, n0, (int)ti.o);
-    }
-}
-
 // Warp 0 (all lanes): start the TMA stores of one finished tile.
 template <int THREADS, int LG, int IO>
 __device__ __forceinline__ void p2_issue_store(const PassDesc& d, const CUtensorMap* tm, long long tile,
@@ -372,11 +359,8 @@ __global__ void __maxnreg__(96) k_fft_p2(const __grid_constant__ LineArgs a)
         bool ok = true;
         int i = 0;
         long long tile = blockIdx.x;
-        if (lane == 0 && tile + 2 * step < d.ntiles) p2_prefetch<THREADS, LG, IO>(d, &a.tm_in, tile + 2 * step);
         for (; tile < d.ntiles; tile += step, ++i) {
             const int b = i & 1;
-            // keep the tile two loads ahead in flight towards L2
-            if (lane == 0 && tile + 3 * step < d.ntiles) p2_prefetch<THREADS, LG, IO>(d, &a.tm_in, tile + 3 * step);
             if (i >= 2) {  // buffer b still holds tile i-2: wait until it is computed, store it
                 ok = mbar_wait_bounded(&empty[b], (unsigned)((i - 2) >> 1) & 1u);
                 if (!ok) break;
