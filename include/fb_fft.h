@@ -76,6 +76,34 @@ int fb_fft_plan(fb_fft_plan_t* plan, int rank, const long long* dims, long long 
                 unsigned flags, void* stream);
 
 /*
+ * Batched uneven lengths (the paper's block offload applied to many calls at
+ * once, Sec. 3.4 C-1 / Sec. 3.3: one replaced block serving a workload of
+ * transforms of different sizes).
+ *
+ * fb_fft_many_layout -- the packed layout such a plan expects: transform i
+ * (length lengths[i]) starts at element offsets[i] = sum over j < i of
+ * lengths[j] rounded up to even (every transform 16-byte aligned).  Writes
+ * offsets (if not NULL) and returns the total element count, or -1 on bad
+ * arguments.  Host only.
+ *
+ * fb_fft_plan_many -- plan `count` 1-D transforms of the given 5-smooth
+ * lengths (each <= FB_FFT_MAX_1D_LEN) laid out as above; fb_fft_exec /
+ * fb_fft_exec_host then take buffers of fb_fft_many_layout(...) elements.
+ * Transforms of one length run as one pass through an offset table (long
+ * ones as a four-step pair); different lengths run concurrently on
+ * plan-owned side streams, and each exec is replayed as one CUDA graph
+ * launch (captured on the first exec with a given in/out/direction).
+ * FB_FFT_SCALE_INV_N scales each inverse result by 1/its length.
+ * Errors: as fb_fft_plan.
+ *
+ * fb_fft_set_graph -- 0 launches the passes directly instead of through the
+ * graph (same results; used to compare the two).
+ */
+long long fb_fft_many_layout(int count, const long long* lengths, long long* offsets);
+int fb_fft_plan_many(fb_fft_plan_t* plan, int count, const long long* lengths, unsigned flags, void* stream);
+int fb_fft_set_graph(fb_fft_plan_t plan, int enable);
+
+/*
  * fb_fft_exec -- run the transform on device buffers (Sec. 3.3 / Sec. 5.1(a):
  * the Fourier transform block itself).
  *   in        device pointer to batch*prod(dims) complex64 values, 8-byte aligned.

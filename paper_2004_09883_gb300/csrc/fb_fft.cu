@@ -60,6 +60,17 @@ long long fourstep_chunk_bytes()
     return v;
 }
 
+// Side streams of a batched-uneven plan (independent length groups overlap).
+int many_streams()
+{
+    static int v = [] {
+        const char* s = std::getenv("FB_FFT_MANY_STREAMS");
+        const int n = s ? std::atoi(s) : 0;
+        return n >= 1 && n <= 32 ? n : 4;
+    }();
+    return v;
+}
+
 enum BufKind { kBufIn = 0, kBufOut = 1, kBufScratch = 2 };
 constexpr size_t kMaxSmemBytes = 227 * 1024;
 
@@ -75,6 +86,10 @@ struct PassPlan {
     long long src_off, dst_off;  // element offsets into the source / destination buffer
     int group;                   // profiling group (the pass's role in the schedule)
     bool last;                   // last pass of its data: gets the 1/N scale
+    long long scale_n = 0;       // transform length the 1/N scale refers to (0: the plan's N)
+    int slot = 0;                // batched-uneven plans: side stream the pass runs on
+    long long off_in_idx = -1;   // batched-uneven plans: index of the pass's offset
+    long long off_out_idx = -1;  // tables in the plan's device offset buffer
 };
 
 bool is_smooth(long long n)
@@ -283,6 +298,23 @@ struct fb_fft_plan_s {
     int* err = nullptr;  // device error word written by bounded waits
     long long smem_len_max = 0;
     bool debug_timeout = false;  // test hook: make every TMA wait run out
+    // batched uneven lengths (fb_fft_plan_many)
+    bool many = false;
+    long long total = 0;                 // elements of the packed layout
+    std::vector<long long> lengths, offsets;
+    long long* d_off = nullptr;          // device offset tables of all passes
+    std::vector<long long> h_off;        // host copy, uploaded once
+    int nslots = 1;
+    std::vector<cudaStream_t> side;      // side streams (slots)
+    std::vector<cudaEvent_t> fork_join;  // [0] fork, [1 + s] join of slot s
+    bool use_graph = true;
+    struct GraphEntry {
+        const void* in;
+        void* out;
+        int dir;
+        cudaGraphExec_t exec;
+    };
+    std::vector<GraphEntry> graphs;
     // profiling
     bool profiling = false;
     std::vector<cudaEvent_t> ev;  // pairs
@@ -301,14 +333,119 @@ void free_plan(fb_fft_plan_s* p)
     if (p->scratch) cudaFree(p->scratch);
     if (p->staging) cudaFree(p->staging);
     if (p->err) cudaFree(p->err);
+    if (p->d_off) cudaFree(p->d_off);
+    for (auto& g : p->graphs) cudaGraphExecDestroy(g.exec);
+    for (cudaStream_t st : p->side) cudaStreamDestroy(st);
+    for (cudaEvent_t e : p->fork_join) cudaEventDestroy(e);
     for (cudaEvent_t e : p->ev) cudaEventDestroy(e);
     p->magic = kDead;
     delete p;
 }
 
+// Packed layout of a batch of uneven 1-D transforms: transform i starts at
+// offsets[i] = sum over j < i of lengths[j] rounded up to even, so every
+// transform starts 16-byte aligned (a TMA requirement).
+long long many_layout(int count, const long long* lengths, long long* offsets)
+{
+    long long off = 0;
+    for (int i = 0; i < count; ++i) {
+        if (offsets) offsets[i] = off;
+        off += (lengths[i] + 1) & ~1LL;
+    }
+    return off;
+}
+
+// Batched uneven lengths: one pass (or one four-step pair per L2-sized
+// chunk) per distinct length, each covering all transforms of that length
+// through an offset table.  Single-pass groups are spread over side streams
+// 1..nslots-1; four-step groups share the scratch and run in order on slot 0.
+int schedule_many(fb_fft_plan_s* p, TwiddleBuilder& twb)
+{
+    std::vector<std::pair<long long, std::vector<long long>>> groups;  // (L, transform indices)
+    {
+        std::vector<long long> order(p->lengths.size());
+        for (size_t i = 0; i < order.size(); ++i) order[i] = (long long)i;
+        std::stable_sort(order.begin(), order.end(),
+                         [&](long long a, long long b) { return p->lengths[a] > p->lengths[b]; });
+        for (long long i : order) {
+            if (groups.empty() || groups.back().first != p->lengths[i]) groups.push_back({p->lengths[i], {}});
+            groups.back().second.push_back(i);
+        }
+    }
+    p->group_names = {"many.single_pass", "many.fourstep.columns", "many.fourstep.rows"};
+    long long scratch_need = 0;
+    int rr = 0;
+    for (auto& g : groups) {
+        const long long L = g.first;
+        const std::vector<long long>& idx = g.second;
+        const bool pow2 = (L & (L - 1)) == 0;
+        auto push_offsets = [&](size_t b0, size_t nb) {
+            const long long at = (long long)p->h_off.size();
+            for (size_t k = b0; k < b0 + nb; ++k) p->h_off.push_back(p->offsets[idx[k]]);
+            return at;
+        };
+        if (L <= FB_FFT_MAX_SMEM_LEN) {
+            PassPlan q;
+            int rc = make_line_pass(q, twb, L, 1, (long long)idx.size(), 1, L, 0, 1, L, 0, false, false, false);
+            if (rc != FB_FFT_OK) return rc;
+            q.off_in_idx = q.off_out_idx = push_offsets(0, idx.size());
+            if (!pow2) q.async_ok = false;  // the generic kernel copies offset-table tiles itself
+            q.src = kBufIn, q.dst = kBufOut;
+            q.group = 0;
+            q.last = true;
+            q.scale_n = L;
+            q.slot = p->nslots > 1 ? 1 + (rr++ % (p->nslots - 1)) : 0;
+            p->passes.push_back(q);
+            p->smem_len_max = std::max(p->smem_len_max, L);
+            continue;
+        }
+        long long N1, N2;
+        int rc = split_fourstep(L, &N1, &N2);
+        if (rc != FB_FFT_OK) return rc;
+        const int plog = (ilog2ll(L) + 1) / 2;
+        const long long lo_cnt = 1LL << plog, hi_cnt = (L + lo_cnt - 1) >> plog;
+        const long long lo_off = twb.add_linear(lo_cnt, L, 1);
+        const long long hi_off = twb.add_linear(hi_cnt, L, lo_cnt);
+        const long long cnt = (long long)idx.size();
+        const long long chunk = std::max(1LL, std::min(cnt, fourstep_chunk_bytes() / (L * 8)));
+        scratch_need = std::max(scratch_need, chunk * L);
+        for (long long b0 = 0; b0 < cnt; b0 += chunk) {
+            const long long nb = std::min(chunk, cnt - b0);
+            const long long at = push_offsets((size_t)b0, (size_t)nb);
+            PassPlan a, r;
+            rc = make_line_pass(a, twb, N1, nb, N2, N2, 1, L, N2, 1, L, true, true, true);
+            if (rc != FB_FFT_OK) return rc;
+            a.d.ptw_log = plog;
+            a.d.ptw_lo = reinterpret_cast<const float2*>(lo_off);
+            a.d.ptw_hi = reinterpret_cast<const float2*>(hi_off);
+            a.off_in_idx = at;
+            if ((N1 & (N1 - 1)) != 0) a.async_ok = false;
+            a.src = kBufIn, a.dst = kBufScratch;
+            a.group = 1;
+            a.slot = 0;
+            rc = make_line_pass(r, twb, N2, nb, N1, 1, N2, L, N1, 1, L, false, true, false);
+            if (rc != FB_FFT_OK) return rc;
+            r.off_out_idx = at;
+            if ((N2 & (N2 - 1)) != 0) r.async_ok = false;
+            r.src = kBufScratch, r.dst = kBufOut;
+            r.group = 2;
+            r.last = true;
+            r.scale_n = L;
+            r.slot = 0;
+            p->passes.push_back(a);
+            p->passes.push_back(r);
+        }
+        p->smem_len_max = std::max(p->smem_len_max, std::max(N1, N2));
+    }
+    p->scratch_bytes = (size_t)scratch_need * sizeof(float2);
+    p->tw_elems = std::max(2LL, twb.total);
+    return FB_FFT_OK;
+}
+
 // Host part of planning: the pass list and the twiddle jobs (no device work).
 int schedule_plan(fb_fft_plan_s* p, TwiddleBuilder& twb)
 {
+    if (p->many) return schedule_many(p, twb);
     const long long B = p->batch;
     if (p->rank == 1 && p->N > FB_FFT_MAX_SMEM_LEN) {
         long long N1, N2;
@@ -417,6 +554,31 @@ int build_plan(fb_fft_plan_s* p)
             return FB_FFT_ERR_ALLOC;
         }
     }
+    if (p->many) {
+        if (!p->h_off.empty()) {
+            if (cudaMalloc(&p->d_off, p->h_off.size() * sizeof(long long)) != cudaSuccess) {
+                cudaGetLastError();
+                p->d_off = nullptr;
+                return FB_FFT_ERR_ALLOC;
+            }
+            FB_CK(cudaMemcpyAsync(p->d_off, p->h_off.data(), p->h_off.size() * sizeof(long long),
+                                  cudaMemcpyHostToDevice, p->stream));
+        }
+        for (PassPlan& q : p->passes) {
+            if (q.off_in_idx >= 0) q.d.off_in = p->d_off + q.off_in_idx;
+            if (q.off_out_idx >= 0) q.d.off_out = p->d_off + q.off_out_idx;
+        }
+        for (int sl = 0; sl < p->nslots; ++sl) {
+            cudaStream_t st;
+            FB_CK(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
+            p->side.push_back(st);
+        }
+        for (int e = 0; e <= p->nslots; ++e) {
+            cudaEvent_t ev;
+            FB_CK(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+            p->fork_join.push_back(ev);
+        }
+    }
     FB_CK(cudaStreamSynchronize(p->stream));
     return FB_FFT_OK;
 }
@@ -456,65 +618,130 @@ int encode_view(CUtensorMap* tm, const float2* base, long long C, long long L, l
     return r == CUDA_SUCCESS ? 0 : -1;
 }
 
+// Launch one pass of a plan on `stream` (profiling events, when on, go on
+// the same stream).
+int launch_pass(fb_fft_plan_s* p, const PassPlan& q, const float2* in, float2* out, bool fwd, cudaStream_t stream,
+                bool count)
+{
+    LineArgs args;
+    std::memset(&args, 0, sizeof(args));
+    args.d = q.d;
+    PassDesc& d = args.d;
+    const float2* src = q.src == kBufIn ? in : (q.src == kBufOut ? out : p->scratch);
+    float2* dst = q.dst == kBufOut ? out : p->scratch;
+    d.in = src + q.src_off;
+    d.out = dst + q.dst_off;
+    d.async_io = 0;
+    if (q.async_ok && (((uintptr_t)d.in | (uintptr_t)d.out) & 15) == 0) {
+        d.async_io = 1;
+        const long long O = d.ntiles / d.tiles_per_o;
+        if (d.in_tfast && !d.off_in &&
+            encode_view(&args.tm_in, d.in, d.C, d.L, O, d.in_sn, d.in_so, 1 << d.logT, d.box_rows) != 0)
+            d.async_io = 0;
+        if (d.out_tfast && !d.off_out &&
+            encode_view(&args.tm_out, d.out, d.C, d.L, O, d.out_sk, d.out_so, 1 << d.logT, d.box_rows) != 0)
+            d.async_io = 0;
+    }
+    if (p->debug_timeout && d.async_io) d.debug_extra_tx = 16;
+    const size_t smem = line_smem_bytes(d.land_stride, d.L, 1 << d.logT, d.nst, d.async_io != 0, d.tws);
+    if (q.last && !fwd && (p->flags & FB_FFT_SCALE_INV_N)) {
+        d.apply_scale = 1;
+        d.scale = (float)(1.0 / (double)(q.scale_n ? q.scale_n : p->N));
+    }
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (p->profiling) {
+        if (p->ev_used + 2 > p->ev.size()) {
+            for (int i = 0; i < 64; ++i) {
+                cudaEvent_t e;
+                FB_CK(cudaEventCreate(&e));
+                p->ev.push_back(e);
+            }
+            p->ev_group.resize(p->ev.size() / 2, 0);
+        }
+        e0 = p->ev[p->ev_used];
+        e1 = p->ev[p->ev_used + 1];
+        p->ev_group[p->ev_used / 2] = q.group;
+        p->ev_used += 2;
+        cudaEventRecord(e0, stream);
+    }
+    const LineKernel k = q.lg ? line_kernel_p2(q.threads, fwd, q.lg, q.io) : line_kernel_generic(fwd);
+    const cudaError_t le = line_launch(k, args, q.grid, smem, stream);
+    if (le != cudaSuccess) {
+        char nm[64];
+        line_kernel_name(k, nm, sizeof(nm));
+        return cuda_fail(le, nm);
+    }
+    if (count) g_launches.fetch_add(1, std::memory_order_relaxed);
+    if (p->profiling) cudaEventRecord(e1, stream);
+    return FB_FFT_OK;
+}
+
+// Batched uneven plan: fork the side streams off the plan's stream, run each
+// pass on its slot, join back.
+int launch_many(fb_fft_plan_s* p, const float2* in, float2* out, bool fwd, bool count)
+{
+    FB_CK(cudaEventRecord(p->fork_join[0], p->stream));
+    for (int sl = 0; sl < p->nslots; ++sl) FB_CK(cudaStreamWaitEvent(p->side[sl], p->fork_join[0], 0));
+    for (const PassPlan& q : p->passes) {
+        const int rc = launch_pass(p, q, in, out, fwd, p->side[q.slot], count);
+        if (rc != FB_FFT_OK) return rc;
+    }
+    for (int sl = 0; sl < p->nslots; ++sl) {
+        FB_CK(cudaEventRecord(p->fork_join[1 + sl], p->side[sl]));
+        FB_CK(cudaStreamWaitEvent(p->stream, p->fork_join[1 + sl], 0));
+    }
+    return FB_FFT_OK;
+}
+
+// Batched uneven plan, replayed as one CUDA graph per (in, out, direction):
+// the first exec with a new triple captures the fork/join launch sequence.
+int exec_many(fb_fft_plan_s* p, const float2* in, float2* out, int direction)
+{
+    const bool fwd = direction == FB_FFT_FORWARD;
+    if (!p->use_graph || p->profiling) return launch_many(p, in, out, fwd, true);
+    for (auto& g : p->graphs)
+        if (g.in == in && g.out == out && g.dir == direction) {
+            FB_CK(cudaGraphLaunch(g.exec, p->stream));
+            g_launches.fetch_add((long long)p->passes.size(), std::memory_order_relaxed);
+            return FB_FFT_OK;
+        }
+    FB_CK(cudaStreamBeginCapture(p->stream, cudaStreamCaptureModeThreadLocal));
+    const int rc = launch_many(p, in, out, fwd, false);
+    cudaGraph_t graph = nullptr;
+    const cudaError_t ce = cudaStreamEndCapture(p->stream, &graph);
+    if (rc != FB_FFT_OK) {
+        if (graph) cudaGraphDestroy(graph);
+        return rc;
+    }
+    if (ce != cudaSuccess) return cuda_fail(ce, "cudaStreamEndCapture");
+    cudaGraphExec_t exec = nullptr;
+    const cudaError_t ie = cudaGraphInstantiate(&exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (ie != cudaSuccess) return cuda_fail(ie, "cudaGraphInstantiate");
+    if (p->graphs.size() >= 8) {  // keep the most recent few
+        cudaGraphExecDestroy(p->graphs.front().exec);
+        p->graphs.erase(p->graphs.begin());
+    }
+    p->graphs.push_back({in, out, direction, exec});
+    FB_CK(cudaGraphLaunch(exec, p->stream));
+    g_launches.fetch_add((long long)p->passes.size(), std::memory_order_relaxed);
+    return FB_FFT_OK;
+}
+
+long long plan_elems(const fb_fft_plan_s* p) { return p->many ? p->total : p->N * p->batch; }
+
 int exec_device(fb_fft_plan_s* p, const float2* in, float2* out, int direction)
 {
+    if (p->many) return exec_many(p, in, out, direction);
     const bool fwd = direction == FB_FFT_FORWARD;
     const size_t bytes = (size_t)(p->N * p->batch) * sizeof(float2);
     if (p->passes.empty()) {  // every axis has length 1: the DFT is the identity
         if (bytes && in != out) FB_CK(cudaMemcpyAsync(out, in, bytes, cudaMemcpyDeviceToDevice, p->stream));
         return FB_FFT_OK;
     }
-    const bool scale = !fwd && (p->flags & FB_FFT_SCALE_INV_N);
     for (const PassPlan& q : p->passes) {
-        LineArgs args;
-        std::memset(&args, 0, sizeof(args));
-        args.d = q.d;
-        PassDesc& d = args.d;
-        const float2* src = q.src == kBufIn ? in : (q.src == kBufOut ? out : p->scratch);
-        float2* dst = q.dst == kBufOut ? out : p->scratch;
-        d.in = src + q.src_off;
-        d.out = dst + q.dst_off;
-        d.async_io = 0;
-        if (q.async_ok && (((uintptr_t)d.in | (uintptr_t)d.out) & 15) == 0) {
-            d.async_io = 1;
-            const long long O = d.ntiles / d.tiles_per_o;
-            if (d.in_tfast && encode_view(&args.tm_in, d.in, d.C, d.L, O, d.in_sn, d.in_so, 1 << d.logT, d.box_rows) != 0)
-                d.async_io = 0;
-            if (d.out_tfast &&
-                encode_view(&args.tm_out, d.out, d.C, d.L, O, d.out_sk, d.out_so, 1 << d.logT, d.box_rows) != 0)
-                d.async_io = 0;
-        }
-        if (p->debug_timeout && d.async_io) d.debug_extra_tx = 16;
-        const size_t smem = line_smem_bytes(d.land_stride, d.L, 1 << d.logT, d.nst, d.async_io != 0, d.tws);
-        if (q.last && scale) {
-            d.apply_scale = 1;
-            d.scale = (float)(1.0 / (double)p->N);
-        }
-        cudaEvent_t e0 = nullptr, e1 = nullptr;
-        if (p->profiling) {
-            if (p->ev_used + 2 > p->ev.size()) {
-                for (int i = 0; i < 64; ++i) {
-                    cudaEvent_t e;
-                    FB_CK(cudaEventCreate(&e));
-                    p->ev.push_back(e);
-                }
-                p->ev_group.resize(p->ev.size() / 2, 0);
-            }
-            e0 = p->ev[p->ev_used];
-            e1 = p->ev[p->ev_used + 1];
-            p->ev_group[p->ev_used / 2] = q.group;
-            p->ev_used += 2;
-            cudaEventRecord(e0, p->stream);
-        }
-        const LineKernel k = q.lg ? line_kernel_p2(q.threads, fwd, q.lg, q.io) : line_kernel_generic(fwd);
-        const cudaError_t le = line_launch(k, args, q.grid, smem, p->stream);
-        if (le != cudaSuccess) {
-            char nm[64];
-            line_kernel_name(k, nm, sizeof(nm));
-            return cuda_fail(le, nm);
-        }
-        g_launches.fetch_add(1, std::memory_order_relaxed);
-        if (p->profiling) cudaEventRecord(e1, p->stream);
+        const int rc = launch_pass(p, q, in, out, fwd, p->stream, true);
+        if (rc != FB_FFT_OK) return rc;
     }
     return FB_FFT_OK;
 }
@@ -628,6 +855,59 @@ int fb_fft_plan(fb_fft_plan_t* plan, int rank, const long long* dims, long long 
     return FB_FFT_OK;
 }
 
+long long fb_fft_many_layout(int count, const long long* lengths, long long* offsets)
+{
+    if (count < 0 || (count > 0 && !lengths)) return -1;
+    for (int i = 0; i < count; ++i)
+        if (lengths[i] < 1) return -1;
+    return many_layout(count, lengths, offsets);
+}
+
+int fb_fft_plan_many(fb_fft_plan_t* plan, int count, const long long* lengths, unsigned flags, void* stream)
+{
+    if (!plan) return FB_FFT_ERR_INVALID_ARG;
+    *plan = nullptr;
+    if (count < 0 || (count > 0 && !lengths) || (flags & ~FB_FFT_SCALE_INV_N)) return FB_FFT_ERR_INVALID_ARG;
+    for (int i = 0; i < count; ++i) {
+        if (lengths[i] < 1) return FB_FFT_ERR_INVALID_ARG;
+        long long n1, n2;
+        const int rc = split_fourstep(lengths[i], &n1, &n2);
+        if (rc != FB_FFT_OK) return rc;
+    }
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) {
+        cudaGetLastError();
+        return FB_FFT_ERR_NO_DEVICE;
+    }
+    fb_fft_plan_s* p = new (std::nothrow) fb_fft_plan_s();
+    if (!p) return FB_FFT_ERR_ALLOC;
+    cudaGetDevice(&p->device);
+    p->many = true;
+    p->rank = 1;
+    p->batch = count;
+    p->flags = flags;
+    p->stream = (cudaStream_t)stream;
+    p->lengths.assign(lengths, lengths + count);
+    p->offsets.resize(count);
+    p->total = many_layout(count, lengths, p->offsets.data());
+    p->N = 0;
+    p->nslots = many_streams();
+    int rc = build_plan(p);
+    if (rc != FB_FFT_OK) {
+        free_plan(p);
+        return rc;
+    }
+    *plan = p;
+    return FB_FFT_OK;
+}
+
+int fb_fft_set_graph(fb_fft_plan_t plan, int enable)
+{
+    if (!plan_ok(plan)) return FB_FFT_ERR_BAD_PLAN;
+    plan->use_graph = enable != 0;
+    return FB_FFT_OK;
+}
+
 int fb_fft_exec(fb_fft_plan_t plan, const void* in, void* out, int direction)
 {
     if (!plan_ok(plan)) return FB_FFT_ERR_BAD_PLAN;
@@ -635,7 +915,7 @@ int fb_fft_exec(fb_fft_plan_t plan, const void* in, void* out, int direction)
     if (plan->batch == 0) return FB_FFT_OK;
     if (!in || !out) return FB_FFT_ERR_INVALID_ARG;
     if (((uintptr_t)in | (uintptr_t)out) & 7) return FB_FFT_ERR_INVALID_ARG;
-    const uintptr_t bytes = (uintptr_t)(plan->N * plan->batch) * sizeof(float2);
+    const uintptr_t bytes = (uintptr_t)plan_elems(plan) * sizeof(float2);
     const uintptr_t a = (uintptr_t)in, b = (uintptr_t)out;
     if (a != b && a < b + bytes && b < a + bytes) return FB_FFT_ERR_INVALID_ARG;
     return exec_device(plan, (const float2*)in, (float2*)out, direction);
@@ -647,7 +927,7 @@ int fb_fft_exec_host(fb_fft_plan_t plan, const void* host_in, void* host_out, in
     if (direction != FB_FFT_FORWARD && direction != FB_FFT_INVERSE) return FB_FFT_ERR_INVALID_ARG;
     if (plan->batch == 0) return FB_FFT_OK;
     if (!host_in || !host_out) return FB_FFT_ERR_INVALID_ARG;
-    const size_t bytes = (size_t)(plan->N * plan->batch) * sizeof(float2);
+    const size_t bytes = (size_t)plan_elems(plan) * sizeof(float2);
     if (!plan->staging) {
         if (cudaMalloc(&plan->staging, bytes) != cudaSuccess) {
             cudaGetLastError();
@@ -708,7 +988,7 @@ int fb_fft_plan_info(fb_fft_plan_t plan, fb_fft_info* info)
     info->smem_len_max = plan->smem_len_max;
     info->scratch_bytes = (long long)plan->scratch_bytes;
     info->twiddle_bytes = plan->tw_elems * (long long)sizeof(float2);
-    info->elements = plan->N;
+    info->elements = plan->many ? plan->total : plan->N;
     info->batch = plan->batch;
     return FB_FFT_OK;
 }

@@ -57,6 +57,11 @@ struct PassDesc {
     int* err;              // device error word: 1 = a bounded wait gave up
     unsigned debug_extra_tx;  // test hook: bytes announced per tile that never arrive
     int tws;               // stage-twiddle entries the kernel copies to shared memory
+    // Batched uneven lengths: element offset of each transform's start in
+    // in / out (device arrays, or null for the regular strides above).
+    // Contiguous layouts index them by line, strided ones by outer index.
+    const long long* off_in;
+    const long long* off_out;
 };
 
 // Kernel argument: the descriptor plus the TMA tensor maps of the c-fast

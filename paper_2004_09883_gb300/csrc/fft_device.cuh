@@ -272,6 +272,29 @@ __device__ __forceinline__ TileIdx tile_index(const PassDesc& d, long long tile)
     return ti;
 }
 
+// Global base of the input / output a tile reads or writes.  With an offset
+// table (batched uneven lengths), transform x starts at off[x]: x is the line
+// for contiguous layouts, the outer index o for strided ones.
+__device__ __forceinline__ const float2* tile_in_base(const PassDesc& d, const TileIdx& ti, bool strided)
+{
+    if (d.off_in) return d.in + (strided ? d.off_in[ti.o] + ti.c0 : 0);
+    return d.in + ti.o * d.in_so + ti.c0 * d.in_sc;
+}
+__device__ __forceinline__ float2* tile_out_base(const PassDesc& d, const TileIdx& ti, bool strided)
+{
+    if (d.off_out) return d.out + (strided ? d.off_out[ti.o] + ti.c0 : 0);
+    return d.out + ti.o * d.out_so + ti.c0 * d.out_sc;
+}
+// Start of line t of a contiguous-layout tile.
+__device__ __forceinline__ const float2* line_in(const PassDesc& d, const TileIdx& ti, const float2* base, int t)
+{
+    return d.off_in ? d.in + d.off_in[ti.c0 + t] : base + (long long)t * d.in_sc;
+}
+__device__ __forceinline__ float2* line_out(const PassDesc& d, const TileIdx& ti, float2* base, int t)
+{
+    return d.off_out ? d.out + d.off_out[ti.c0 + t] : base + (long long)t * d.out_sc;
+}
+
 // Thread 0: start the TMA loads of one tile into a landing buffer.
 // n-fast tiles are contiguous (line stride == L) and land as [t][n];
 // c-fast tiles land as [n][t] by 3-D boxes of T x box_rows (zero fill past C).
@@ -309,11 +332,11 @@ template <int THREADS>
 __device__ __forceinline__ void plain_tile_load(const PassDesc& d, const TileIdx& ti, float2* land)
 {
     const int L = d.L, T = 1 << d.logT;
-    const float2* gin = d.in + ti.o * d.in_so + ti.c0 * d.in_sc;
+    const float2* gin = tile_in_base(d, ti, d.in_tfast != 0);
     if (!d.in_tfast) {
         for (int e = threadIdx.x; e < ti.Tv * L; e += THREADS) {
             const int t = e / L, n = e - t * L;
-            land[e] = gin[(long long)t * d.in_sc + (long long)n * d.in_sn];
+            land[e] = line_in(d, ti, gin, t)[(long long)n * d.in_sn];
         }
     } else {
         for (int e = threadIdx.x; e < T * L; e += THREADS) {
@@ -326,11 +349,11 @@ template <int THREADS>
 __device__ __forceinline__ void plain_tile_store(const PassDesc& d, const TileIdx& ti, const float2* land)
 {
     const int L = d.L, T = 1 << d.logT;
-    float2* gout = d.out + ti.o * d.out_so + ti.c0 * d.out_sc;
+    float2* gout = tile_out_base(d, ti, d.out_tfast != 0);
     if (!d.out_tfast) {
         for (int e = threadIdx.x; e < ti.Tv * L; e += THREADS) {
             const int t = e / L, k = e - t * L;
-            gout[(long long)t * d.out_sc + (long long)k * d.out_sk] = land[e];
+            line_out(d, ti, gout, t)[(long long)k * d.out_sk] = land[e];
         }
     } else {
         for (int e = threadIdx.x; e < T * L; e += THREADS) {

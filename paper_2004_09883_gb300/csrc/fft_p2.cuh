@@ -237,48 +237,57 @@ __device__ __forceinline__ TileIdx p2_tile_index(const PassDesc& d, long long ti
     return ti;
 }
 
-// Warp 0 (all lanes): start the TMA loads of one tile.
+// Producer warp (all lanes): start the TMA loads of one tile.
 template <int THREADS, int LG, int IO>
 __device__ __forceinline__ void p2_issue_load(const PassDesc& d, const CUtensorMap* tm, long long tile,
                                               float2* land, unsigned long long* bar, int lane)
 {
     using C = P2<THREADS, LG, IO>;
     const TileIdx ti = p2_tile_index(d, tile, C::LOGT, C::T);
+    const float2* src = tile_in_base(d, ti, C::IN_T);
     if constexpr (!C::IN_T) {
-        const float2* src = d.in + ti.o * d.in_so + ti.c0 * C::L;  // lines are contiguous
         const unsigned bytes = (unsigned)(ti.Tv * C::L) * 8u;
         if (lane == 0) mbar_arrive_expect_tx(bar, bytes + d.debug_extra_tx);
         __syncwarp();
-        if constexpr (C::LLS == C::L) {
+        if (C::LLS == C::L && !d.off_in) {
             if (lane == 0) bulk_load_1d(land, src, bytes, bar);
         } else {
-            for (int t = lane; t < ti.Tv; t += 32) bulk_load_1d(land + t * C::LLS, src + t * C::L, C::L * 8u, bar);
+            for (int t = lane; t < ti.Tv; t += 32) bulk_load_1d(land + t * C::LLS, line_in(d, ti, src, t), C::L * 8u, bar);
         }
-    } else {
+    } else if (!d.off_in) {
         if (lane == 0) {
             mbar_arrive_expect_tx(bar, (unsigned)(C::T * C::L) * 8u + d.debug_extra_tx);
             for (int n0 = 0; n0 < C::L; n0 += C::BR)
                 tma_load_3d(land + n0 * C::T, tm, (int)ti.c0, n0, (int)ti.o, bar);
         }
+    } else {
+        // irregular transform bases: one bulk copy per row of Tv columns
+        if (lane == 0) mbar_arrive_expect_tx(bar, (unsigned)(ti.Tv * C::L) * 8u + d.debug_extra_tx);
+        __syncwarp();
+        for (int n = lane; n < C::L; n += 32)
+            bulk_load_1d(land + n * C::T, src + (long long)n * d.in_sn, (unsigned)ti.Tv * 8u, bar);
     }
 }
-// Warp 0 (all lanes): start the TMA stores of one finished tile.
+// Producer warp (all lanes): start the TMA stores of one finished tile.
 template <int THREADS, int LG, int IO>
 __device__ __forceinline__ void p2_issue_store(const PassDesc& d, const CUtensorMap* tm, long long tile,
                                                const float2* land, int lane)
 {
     using C = P2<THREADS, LG, IO>;
     const TileIdx ti = p2_tile_index(d, tile, C::LOGT, C::T);
+    float2* dst = tile_out_base(d, ti, C::OUT_T);
     if constexpr (!C::OUT_T) {
-        float2* dst = d.out + ti.o * d.out_so + ti.c0 * C::L;
-        if constexpr (C::OLS == C::L) {
+        if (C::OLS == C::L && !d.off_out) {
             if (lane == 0) bulk_store_1d(dst, land, (unsigned)(ti.Tv * C::L) * 8u);
         } else {
-            for (int t = lane; t < ti.Tv; t += 32) bulk_store_1d(dst + t * C::L, land + t * C::OLS, C::L * 8u);
+            for (int t = lane; t < ti.Tv; t += 32) bulk_store_1d(line_out(d, ti, dst, t), land + t * C::OLS, C::L * 8u);
         }
-    } else {
+    } else if (!d.off_out) {
         if (lane == 0)
             for (int k0 = 0; k0 < C::L; k0 += C::BR) tma_store_3d(tm, (int)ti.c0, k0, (int)ti.o, land + k0 * C::T);
+    } else {
+        for (int k = lane; k < C::L; k += 32)
+            bulk_store_1d(dst + (long long)k * d.out_sk, land + k * C::T, (unsigned)ti.Tv * 8u);
     }
     bulk_commit();
 }
@@ -288,11 +297,11 @@ template <int THREADS, int LG, int IO>
 __device__ __forceinline__ void p2_plain_load(const PassDesc& d, const TileIdx& ti, float2* land)
 {
     using C = P2<THREADS, LG, IO>;
-    const float2* gin = d.in + ti.o * d.in_so + ti.c0 * d.in_sc;
+    const float2* gin = tile_in_base(d, ti, C::IN_T);
     if constexpr (!C::IN_T) {
         for (int e = threadIdx.x; e < ti.Tv * C::L; e += THREADS) {
             const int t = e >> LG, n = e & (C::L - 1);
-            land[t * C::LLS + n] = gin[(long long)t * d.in_sc + (long long)n * d.in_sn];
+            land[t * C::LLS + n] = line_in(d, ti, gin, t)[(long long)n * d.in_sn];
         }
     } else {
         for (int e = threadIdx.x; e < C::T * C::L; e += THREADS) {
@@ -305,11 +314,11 @@ template <int THREADS, int LG, int IO>
 __device__ __forceinline__ void p2_plain_store(const PassDesc& d, const TileIdx& ti, const float2* land)
 {
     using C = P2<THREADS, LG, IO>;
-    float2* gout = d.out + ti.o * d.out_so + ti.c0 * d.out_sc;
+    float2* gout = tile_out_base(d, ti, C::OUT_T);
     if constexpr (!C::OUT_T) {
         for (int e = threadIdx.x; e < ti.Tv * C::L; e += THREADS) {
             const int t = e >> LG, k = e & (C::L - 1);
-            gout[(long long)t * d.out_sc + (long long)k * d.out_sk] = land[t * C::OLS + k];
+            line_out(d, ti, gout, t)[(long long)k * d.out_sk] = land[t * C::OLS + k];
         }
     } else {
         for (int e = threadIdx.x; e < C::T * C::L; e += THREADS) {

@@ -70,6 +70,9 @@ _sig = {
     "fb_fft_twiddles": (_int, [_ll, _ll, ctypes.POINTER(ctypes.c_float)]),
     "fb_fft_debug_inject_timeout": (_int, [_vp, _int]),
     "fb_fft_exec_1d_noalloc": (_int, [_vp, _vp, _ll, _ll, _int, ctypes.c_uint, _vp]),
+    "fb_fft_many_layout": (_ll, [_int, ctypes.POINTER(_ll), ctypes.POINTER(_ll)]),
+    "fb_fft_plan_many": (_int, [ctypes.POINTER(_vp), _int, ctypes.POINTER(_ll), ctypes.c_uint, _vp]),
+    "fb_fft_set_graph": (_int, [_vp, _int]),
 }
 for _name, (_res, _args) in _sig.items():
     _f = getattr(lib, _name)
@@ -109,6 +112,17 @@ def plan_query(dims, batch: int = 1, scale_inv_n: bool = False) -> dict:
     _check(lib.fb_fft_plan_query(len(dims), cd, int(batch), SCALE_INV_N if scale_inv_n else 0,
                                  ctypes.byref(inf)), "fb_fft_plan_query")
     return {f: getattr(inf, f) for f, _ in Info._fields_ if f != "reserved"}
+
+
+def many_layout(lengths) -> tuple[np.ndarray, int]:
+    """(offsets, total) of the packed layout of a batch of uneven transforms."""
+    lens = np.ascontiguousarray(np.asarray(lengths, dtype=np.int64))
+    offs = np.empty_like(lens)
+    total = lib.fb_fft_many_layout(len(lens), lens.ctypes.data_as(ctypes.POINTER(_ll)),
+                                   offs.ctypes.data_as(ctypes.POINTER(_ll)))
+    if total < 0:
+        raise ValueError("bad lengths")
+    return offs, int(total)
 
 
 def launch_count() -> int:
@@ -248,6 +262,59 @@ class Plan:
         _check(lib.fb_fft_profile_read(self._h, ms, cnt, cap, ctypes.byref(n)), "fb_fft_profile_read")
         names = self.pass_names()
         return [(names[i], ms[i], cnt[i]) for i in range(min(n.value, cap))]
+
+
+class PlanMany(Plan):
+    """Batched 1-D transforms of uneven lengths in the packed layout of
+    :func:`many_layout` (one graph launch per exec)."""
+
+    def __init__(self, lengths, scale_inv_n: bool = False, stream=None):
+        lens = np.ascontiguousarray(np.asarray(lengths, dtype=np.int64))
+        self.lengths = lens
+        self.offsets, self.total = many_layout(lens)
+        self.dims = None
+        self.batch = len(lens)
+        self.flags = SCALE_INV_N if scale_inv_n else 0
+        self._h = _vp()
+        self._stream = _stream_handle(stream)
+        _check(lib.fb_fft_plan_many(ctypes.byref(self._h), len(lens), lens.ctypes.data_as(ctypes.POINTER(_ll)),
+                                    self.flags, _vp(self._stream)), "fb_fft_plan_many")
+        self.n = self.total  # exec() checks numel == n * batch
+        self.batch_for_size = 1
+
+    def exec(self, x, out=None, direction: int = FORWARD):
+        import torch
+        if x.dtype != torch.complex64 or not x.is_cuda or not x.is_contiguous() or x.numel() != self.total:
+            raise ValueError(f"x must be a contiguous complex64 CUDA tensor of {self.total} values")
+        if out is None:
+            out = torch.empty_like(x)
+        s = torch.cuda.current_stream(x.device).cuda_stream
+        if s != self._stream:
+            self.set_stream(s)
+        self.exec_ptr(x.data_ptr(), out.data_ptr(), direction)
+        return out
+
+    def exec_host(self, x, out=None, direction: int = FORWARD):
+        x = np.ascontiguousarray(x, dtype=np.complex64)
+        if x.size != self.total:
+            raise ValueError("size mismatch")
+        out = np.empty_like(x) if out is None else out
+        _check(lib.fb_fft_exec_host(self._h, _vp(x.ctypes.data), _vp(out.ctypes.data), int(direction)),
+               "fb_fft_exec_host")
+        return out
+
+    def set_graph(self, enable: bool) -> None:
+        _check(lib.fb_fft_set_graph(self._h, 1 if enable else 0), "fb_fft_set_graph")
+
+    def pack(self, items) -> np.ndarray:
+        """Host helper: pack a list of 1-D arrays into the plan's layout."""
+        buf = np.zeros(self.total, dtype=np.complex64)
+        for o, a in zip(self.offsets, items):
+            buf[o:o + len(a)] = a
+        return buf
+
+    def unpack(self, buf):
+        return [np.asarray(buf[o:o + n]) for o, n in zip(self.offsets, self.lengths)]
 
 
 def exec_1d_noalloc(x, out, n: int, batch: int, direction: int = FORWARD, scale_inv_n: bool = False):

@@ -188,3 +188,16 @@ def test_planner_accepts_long_1d(fb, n):
         return
     info = fb.plan_query([n], 2)
     assert info["passes"] % 2 == 0 and info["passes"] >= 2 and info["scratch_bytes"] >= 8 * n
+
+
+def test_many_layout_is_packed_and_16_byte_aligned(fb):
+    lens = [3, 4, 5, 8, 1, 64, 75]
+    offs, total = fb.many_layout(lens)
+    assert offs[0] == 0
+    for i in range(1, len(lens)):
+        assert offs[i] == offs[i - 1] + lens[i - 1] + (lens[i - 1] & 1)
+        assert offs[i] % 2 == 0
+    assert total == offs[-1] + lens[-1] + (lens[-1] & 1)
+    assert fb.many_layout([])[1] == 0
+    with pytest.raises(ValueError):
+        fb.many_layout([4, 0])

@@ -1,0 +1,87 @@
+"""Batched uneven lengths (fb_fft_plan_many) against the FP64 oracle: every
+transform of a packed batch, graph replay vs direct launches, repeats,
+in place, inverse with 1/N, host arrays."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2004_09883_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+
+def tol(n: int) -> float:
+    return 2e-6 * math.log2(n) if n > 1 else 1e-7
+
+
+def _batch(lengths, seed):
+    return [inputs.uniform_c64((int(n),), seed + i) for i, n in enumerate(lengths)]
+
+
+def _check(plan, xs, ys, direction, scale=False):
+    for x, y, n in zip(xs, ys, plan.lengths):
+        ref = oracle.fft(x.astype(np.complex128), [int(n)], direction, scale)
+        err = oracle.rel_l2(y.reshape(1, -1), ref.reshape(1, -1))[0]
+        assert err <= tol(int(n)), f"n={n}: rel L2 {err:.3e}"
+
+
+LENGTHS = ([64, 4096, 100, 75, 4096, 6000, 64, 1 << 16, 81, 2, 3125, 8192, 65536, 4096, 1000, 45000, 4, 96]
+           + list(inputs.uneven_lengths(40, 64, 65536, inputs.seed_for(inputs.WORKLOAD_UNEVEN_4096))))
+
+
+@pytest.mark.parametrize("graph", [True, False])
+def test_many_matches_oracle(fb, graph):
+    import torch
+    xs = _batch(LENGTHS, 900)
+    with fb.PlanMany(LENGTHS) as p:
+        p.set_graph(graph)
+        d = torch.from_numpy(p.pack(xs)).cuda()
+        out = p.exec(d, None, -1)
+        out2 = p.exec(d, None, -1)  # second exec replays the cached graph
+        p.check()
+        ys = p.unpack(out.cpu().numpy())
+        assert torch.equal(out, out2)
+    _check(p, xs, ys, -1)
+
+
+def test_many_graph_equals_direct_and_inverse_scaled(fb):
+    import torch
+    xs = _batch(LENGTHS, 901)
+    with fb.PlanMany(LENGTHS, scale_inv_n=True) as p:
+        d = torch.from_numpy(p.pack(xs)).cuda()
+        p.set_graph(True)
+        g = p.exec(d, None, 1)
+        p.set_graph(False)
+        direct = p.exec(d, None, 1)
+        p.check()
+        assert torch.equal(g, direct)
+        ys = p.unpack(g.cpu().numpy())
+    _check(p, xs, ys, 1, scale=True)
+
+
+def test_many_in_place_and_host_arrays(fb):
+    import torch
+    lens = [4096] * 7 + [128] * 33 + [65536, 1 << 20, 3 * 5 ** 6]
+    xs = _batch(lens, 902)
+    with fb.PlanMany(lens) as p:
+        packed = p.pack(xs)
+        d = torch.from_numpy(packed).cuda()
+        p.exec(d, d, -1)
+        p.check()
+        dev = p.unpack(d.cpu().numpy())
+        host = p.unpack(p.exec_host(packed, None, -1))
+    _check(p, xs, dev, -1)
+    for a, b in zip(dev, host):
+        assert np.array_equal(a, b)
+
+
+def test_many_single_transform_and_empty(fb):
+    import torch
+    with fb.PlanMany([]) as p:
+        assert p.total == 0
+    with fb.PlanMany([12]) as p:
+        x = inputs.uniform_c64((12,), 3)
+        y = p.exec(torch.from_numpy(p.pack([x])).cuda(), None, -1)
+        _check(p, [x], p.unpack(y.cpu().numpy()), -1)
