@@ -9,7 +9,7 @@ beside it.  Four input/output buffer pairs (512 MiB) rotate between steps so
 the working set exceeds the 126 MB L2.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
-                  [--workload 3d|1d4096|1d4096L|1d2p20]
+                  [--workload 3d|1d4096|1d4096L|1d2p20|uneven]
 
 Under torchrun each rank runs its own replica (independent transforms, no
 collective on the data path); rank 0 prints one JSON line.  --impl reference
@@ -42,6 +42,9 @@ WORKLOADS = {
                    seed=inputs.seed_for(inputs.WORKLOAD_1D_4096x64), dist="uniform", inverse=False),
     "1d4096L": dict(name="1d_c2c_4096_batch16384_fwd", dims=[4096], batch=16384,
                     seed=inputs.seed_for(inputs.WORKLOAD_1D_4096x64), dist="uniform", inverse=False),
+    "uneven": dict(name="1d_c2c_uneven_4096_lengths_64_to_65536_fwd", dims=None, batch=4096,
+                   seed=inputs.seed_for(inputs.WORKLOAD_UNEVEN_4096), dist="uniform", inverse=False,
+                   lengths=(4096, 64, 65536)),
     "1d2p20": dict(name="1d_c2c_2p20_batch32_fwd", dims=[1 << 20], batch=32,
                    seed=inputs.seed_for(inputs.WORKLOAD_1D_2P20x32), dist="normal", inverse=False),
 }
@@ -205,6 +208,24 @@ def oracle_sample(wl: dict, budget_s: float, threads: int) -> dict:
     return {"value": bytes_step * reps / t_total / 1e9, "seconds": t_total, "steps": reps}
 
 
+def oracle_uneven_sample(wl: dict, budget_s: float, threads: int) -> dict:
+    """Time the oracle on the uneven workload's transforms, in order, until
+    the budget is spent (at least one); GB/s over the transforms done."""
+    import oracle
+
+    lens = uneven_lengths(wl)
+    done_bytes, t_total, k = 0.0, 0.0, 0
+    while k < len(lens) and (k == 0 or t_total < budget_s):
+        n = int(lens[k])
+        x = inputs.uniform_c64((n,), wl["seed"] + k).astype(np.complex128)
+        t = time.perf_counter()
+        oracle.fft(x, [n], -1, False, threads)
+        t_total += time.perf_counter() - t
+        done_bytes += 2 * 8.0 * n
+        k += 1
+    return {"value": done_bytes / t_total / 1e9, "seconds": t_total, "transforms": k}
+
+
 def cpu_model() -> str:
     try:
         with open("/proc/cpuinfo") as f:
@@ -221,6 +242,24 @@ def run_reference(args, wl: dict) -> None:
     if rank != 0:
         return
     threads = len(os.sched_getaffinity(0))
+    if wl.get("lengths"):  # uneven batch: each step a bounded sample of its transforms
+        per_step = max(0.5, 150.0 / max(1, args.steps + args.warmup))
+        for _ in range(args.warmup):
+            oracle_uneven_sample(wl, per_step, threads)
+        runs = [oracle_uneven_sample(wl, per_step, threads) for _ in range(args.steps)]
+        secs = sum(r["seconds"] for r in runs)
+        value = sum(r["value"] * r["seconds"] for r in runs) / secs
+        desc = (f"first {runs[0]['transforms']} of {wl['batch']} transforms of {wl['name']} per step, FP64 oracle, "
+                f"{threads} threads on {cpu_model()}")
+        line = {"impl": "reference", "metric": METRIC, "value": round(value, 4), "unit": "GB/s", "n_gpus": world,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": secs / args.steps * 1e3,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+                "data": "synthetic", "config": {"workload": wl["name"], "parallelism": "host threads"},
+                "cpu_baseline": {"value": round(value, 4), "unit": "GB/s", "cores": threads, "kind": "oracle",
+                                 "sample": desc},
+                "e2e": {"value": round(value, 4), "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+        print(json.dumps(line), flush=True)
+        return
     bytes_step, flops_step, _ = algorithmic(wl)
     # one step = one forward(+inverse) of the workload by the oracle; for long
     # runs each step is a bounded sample: a share of the batch items (the
@@ -423,6 +462,114 @@ def run_gpu(args, wl: dict) -> None:
         dist.destroy_process_group()
 
 
+def uneven_lengths(wl: dict) -> np.ndarray:
+    count, lo, hi = wl["lengths"]
+    return inputs.uneven_lengths(count, lo, hi, wl["seed"])
+
+
+def run_gpu_many(args, wl: dict) -> None:
+    """Batched uneven 1-D lengths: one graph launch per step (fb_fft_plan_many)
+    against the plain per-call path (one fb_fft_exec per transform, plans
+    cached per length) on the same buffers."""
+    import torch
+
+    world, rank, local = dist_setup()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+    from paper_2004_09883_gb300 import build as fbbuild
+    fbbuild.build()
+    from paper_2004_09883_gb300 import fbfft
+
+    lens = uneven_lengths(wl)
+    stream = torch.cuda.current_stream(dev)
+    plan = fbfft.PlanMany(lens, stream=stream)
+    total = plan.total
+    nbuf = 2
+    xin = [torch.from_numpy(inputs.uniform_c64((total,), wl["seed"] + 1000 * replica_rep(rank, r))).to(dev)
+           for r in range(nbuf)]
+    xout = [torch.empty_like(xin[0]) for _ in range(nbuf)]
+    bytes_step = float(sum(2 * 8 * int(n) for n in lens))
+    flops_step = float(sum(5 * int(n) * math.log2(int(n)) for n in lens))
+
+    def barrier():
+        torch.cuda.synchronize(dev)
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize(dev)
+
+    def timed(step, steps):
+        for i in range(args.warmup):
+            step(i)
+        barrier()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        l0 = fbfft.launch_count()
+        e0.record(stream)
+        for i in range(steps):
+            step(i)
+        e1.record(stream)
+        barrier()
+        return max_over_ranks(e0.elapsed_time(e1) / steps, dist, dev), fbfft.launch_count() - l0
+
+    def batched(i):
+        plan.exec_ptr(xin[i % nbuf].data_ptr(), xout[i % nbuf].data_ptr(), fbfft.FORWARD)
+
+    clocks = ClockSampler(local) if rank == 0 and not args.quick else None
+    wall0 = time.time()
+    ms, launches = timed(batched, args.steps)
+    wall1 = time.time()
+    plan.check()
+    # the plain per-call path: one exec per transform on the same data
+    plans = {}
+    for n in sorted(set(int(x) for x in lens)):
+        plans[n] = fbfft.Plan([n], 1, stream=stream)
+    offs = plan.offsets
+
+    def per_call(i):
+        a, b = xin[i % nbuf].data_ptr(), xout[i % nbuf].data_ptr()
+        for n, o in zip(lens, offs):
+            plans[int(n)].exec_ptr(a + 8 * int(o), b + 8 * int(o), fbfft.FORWARD)
+
+    plain_steps = max(3, min(args.steps, 20))
+    ms_plain, _ = timed(per_call, plain_steps)
+    clk = clocks.summary(wall0, wall1) if clocks else None
+    if clocks:
+        clocks.stop()
+    if rank == 0:
+        peaks = load_peaks()
+        value = whole_job_rate(world, bytes_step, ms) / 1e9
+        line = {
+            "metric": METRIC, "value": round(value, 3), "unit": "GB/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": round(ms, 5), "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": wl["name"], "transforms": len(lens), "distinct_lengths": len(plans),
+                       "elements": int(sum(int(n) for n in lens)), "l2": "2 rotating buffer pairs of "
+                       f"{total * 8 / 2 ** 20:.0f} MiB each > 126 MB L2", "parallelism": "replicas" if world > 1
+                       else "single GPU", "path": "fb_fft_plan_many, one CUDA graph launch per step"},
+            "gflops": round(whole_job_rate(world, flops_step, ms) / 1e9, 2),
+            "hbm_frac_effective": round(value / world / peaks["hbm_gbs"], 4),
+            "plain_per_call": {"value": round(whole_job_rate(world, bytes_step, ms_plain) / 1e9, 3), "unit": "GB/s",
+                               "ms_per_step": round(ms_plain, 4), "execs_per_step": len(lens)},
+            "speedup_vs_plain_per_call": round(ms_plain / ms, 3),
+            "cpu_baseline": None if args.quick else (lambda cb: {
+                "value": round(cb["value"], 4), "unit": "GB/s", "cores": len(os.sched_getaffinity(0)),
+                "kind": "oracle", "sample": f"first {cb['transforms']} transforms of the workload by the FP64 "
+                                            f"oracle in {cb['seconds']:.1f} s on {cpu_model()}"})(
+                oracle_uneven_sample(wl, float(args.cpu_budget), len(os.sched_getaffinity(0)))),
+            "gpu_launches": int(launches), "clocks": clk, "kernel_hash": kernel_hash(),
+        }
+        print(json.dumps(line), flush=True)
+    for p in plans.values():
+        p.close()
+    plan.close()
+    if dist is not None:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -439,6 +586,8 @@ def main():
     wl = WORKLOADS[args.workload]
     if args.impl == "reference":
         run_reference(args, wl)
+    elif wl.get("lengths"):
+        run_gpu_many(args, wl)
     else:
         run_gpu(args, wl)
 
