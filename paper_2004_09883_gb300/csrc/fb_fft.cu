@@ -39,6 +39,7 @@ thread_local char g_last_error[256] = "";
 int cuda_fail(cudaError_t e, const char* what)
 {
     snprintf(g_last_error, sizeof(g_last_error), "%s: %s (%s)", what, cudaGetErrorString(e), cudaGetErrorName(e));
+    cudaGetLastError();  // clear a non-sticky error so later launch checks do not see it
     return FB_FFT_ERR_CUDA;
 }
 #define FB_CK(call)                                      \
@@ -306,6 +307,7 @@ struct fb_fft_plan_s {
     std::vector<long long> h_off;        // host copy, uploaded once
     int nslots = 1;
     std::vector<cudaStream_t> side;      // side streams (slots)
+    cudaStream_t capture = nullptr;      // where graphs are captured (the caller's may be uncapturable)
     std::vector<cudaEvent_t> fork_join;  // [0] fork, [1 + s] join of slot s
     bool use_graph = true;
     struct GraphEntry {
@@ -336,6 +338,7 @@ void free_plan(fb_fft_plan_s* p)
     if (p->d_off) cudaFree(p->d_off);
     for (auto& g : p->graphs) cudaGraphExecDestroy(g.exec);
     for (cudaStream_t st : p->side) cudaStreamDestroy(st);
+    if (p->capture) cudaStreamDestroy(p->capture);
     for (cudaEvent_t e : p->fork_join) cudaEventDestroy(e);
     for (cudaEvent_t e : p->ev) cudaEventDestroy(e);
     p->magic = kDead;
@@ -573,6 +576,7 @@ int build_plan(fb_fft_plan_s* p)
             FB_CK(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
             p->side.push_back(st);
         }
+        FB_CK(cudaStreamCreateWithFlags(&p->capture, cudaStreamNonBlocking));
         for (int e = 0; e <= p->nslots; ++e) {
             cudaEvent_t ev;
             FB_CK(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
@@ -676,11 +680,11 @@ int launch_pass(fb_fft_plan_s* p, const PassPlan& q, const float2* in, float2* o
     return FB_FFT_OK;
 }
 
-// Batched uneven plan: fork the side streams off the plan's stream, run each
-// pass on its slot, join back.
-int launch_many(fb_fft_plan_s* p, const float2* in, float2* out, bool fwd, bool count)
+// Batched uneven plan: fork the side streams off `origin`, run each pass on
+// its slot, join back into `origin`.
+int launch_many(fb_fft_plan_s* p, cudaStream_t origin, const float2* in, float2* out, bool fwd, bool count)
 {
-    FB_CK(cudaEventRecord(p->fork_join[0], p->stream));
+    FB_CK(cudaEventRecord(p->fork_join[0], origin));
     for (int sl = 0; sl < p->nslots; ++sl) FB_CK(cudaStreamWaitEvent(p->side[sl], p->fork_join[0], 0));
     for (const PassPlan& q : p->passes) {
         const int rc = launch_pass(p, q, in, out, fwd, p->side[q.slot], count);
@@ -688,7 +692,7 @@ int launch_many(fb_fft_plan_s* p, const float2* in, float2* out, bool fwd, bool 
     }
     for (int sl = 0; sl < p->nslots; ++sl) {
         FB_CK(cudaEventRecord(p->fork_join[1 + sl], p->side[sl]));
-        FB_CK(cudaStreamWaitEvent(p->stream, p->fork_join[1 + sl], 0));
+        FB_CK(cudaStreamWaitEvent(origin, p->fork_join[1 + sl], 0));
     }
     return FB_FFT_OK;
 }
@@ -698,17 +702,19 @@ int launch_many(fb_fft_plan_s* p, const float2* in, float2* out, bool fwd, bool 
 int exec_many(fb_fft_plan_s* p, const float2* in, float2* out, int direction)
 {
     const bool fwd = direction == FB_FFT_FORWARD;
-    if (!p->use_graph || p->profiling) return launch_many(p, in, out, fwd, true);
+    if (!p->use_graph || p->profiling) return launch_many(p, p->stream, in, out, fwd, true);
     for (auto& g : p->graphs)
         if (g.in == in && g.out == out && g.dir == direction) {
             FB_CK(cudaGraphLaunch(g.exec, p->stream));
             g_launches.fetch_add((long long)p->passes.size(), std::memory_order_relaxed);
             return FB_FFT_OK;
         }
-    FB_CK(cudaStreamBeginCapture(p->stream, cudaStreamCaptureModeThreadLocal));
-    const int rc = launch_many(p, in, out, fwd, false);
+    // capture on the plan's own stream (the caller's may be the legacy
+    // default stream, which cannot be captured), launch on the caller's
+    FB_CK(cudaStreamBeginCapture(p->capture, cudaStreamCaptureModeThreadLocal));
+    const int rc = launch_many(p, p->capture, in, out, fwd, false);
     cudaGraph_t graph = nullptr;
-    const cudaError_t ce = cudaStreamEndCapture(p->stream, &graph);
+    const cudaError_t ce = cudaStreamEndCapture(p->capture, &graph);
     if (rc != FB_FFT_OK) {
         if (graph) cudaGraphDestroy(graph);
         return rc;
@@ -1045,9 +1051,9 @@ int fb_fft_twiddles(long long d, long long count, float* host_out)
     }
     TwiddleJob j{0, count, d, 1, 0, 0, 0};
     int rc = FB_FFT_OK;
-    if (launch_twiddles(buf, j, nullptr) != cudaSuccess ||
-        cudaMemcpy(host_out, buf, (size_t)count * sizeof(float2), cudaMemcpyDeviceToHost) != cudaSuccess)
-        rc = FB_FFT_ERR_CUDA;
+    cudaError_t e = launch_twiddles(buf, j, nullptr);
+    if (e == cudaSuccess) e = cudaMemcpy(host_out, buf, (size_t)count * sizeof(float2), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) rc = cuda_fail(e, "fb_fft_twiddles");
     cudaFree(buf);
     return rc;
 }
