@@ -53,6 +53,8 @@ def build(force: bool = False, verbose: bool = False, extra: list[str] | None = 
     os.makedirs(BUILD, exist_ok=True)
     cc = nvcc()
     extra = list(extra or [])
+    if os.environ.get("FB_FFT_SELFCHECK"):  # diagnostic build: kernels validate every copy
+        extra.append("-DFB_FFT_SELFCHECK")
 
     def compile_one(src: str) -> str:
         obj = os.path.join(BUILD, os.path.basename(src)[:-3] + ".o")

@@ -529,12 +529,12 @@ int build_plan(fb_fft_plan_s* p)
         return FB_FFT_ERR_ALLOC;
     }
     for (const TwiddleJob& j : twb.jobs) FB_CK(launch_twiddles(p->tw, j, p->stream));
-    if (cudaMalloc(&p->err, sizeof(int)) != cudaSuccess) {
+    if (cudaMalloc(&p->err, 16 * sizeof(int)) != cudaSuccess) {
         cudaGetLastError();
         p->err = nullptr;
         return FB_FFT_ERR_ALLOC;
     }
-    FB_CK(cudaMemsetAsync(p->err, 0, sizeof(int), p->stream));
+    FB_CK(cudaMemsetAsync(p->err, 0, 16 * sizeof(int), p->stream));
     int sms = 0;
     FB_CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, p->device));
     for (PassPlan& q : p->passes) {
@@ -953,10 +953,13 @@ int fb_fft_check(fb_fft_plan_t plan)
 {
     if (!plan_ok(plan)) return FB_FFT_ERR_BAD_PLAN;
     FB_CK(cudaStreamSynchronize(plan->stream));
-    int e = 0;
-    FB_CK(cudaMemcpy(&e, plan->err, sizeof(int), cudaMemcpyDeviceToHost));
-    if (e) {
-        cudaMemset(plan->err, 0, sizeof(int));
+    int e[4] = {0, 0, 0, 0};
+    FB_CK(cudaMemcpy(e, plan->err, sizeof(e), cudaMemcpyDeviceToHost));
+    if (e[0]) {
+        if (e[0] == 2)
+            snprintf(g_last_error, sizeof(g_last_error), "self-check: copy kind %d at address ...%08x, %d bytes", e[1],
+                     (unsigned)e[2], e[3]);
+        cudaMemset(plan->err, 0, 16 * sizeof(int));
         return FB_FFT_ERR_TIMEOUT;
     }
     return FB_FFT_OK;

@@ -178,6 +178,28 @@ __device__ __forceinline__ int spad(int i) { return i + (i >> 4); }
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ unsigned smem_u32(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
 
+// Self-check build (FB_FFT_SELFCHECK): every copy validates its addresses and
+// size first; a violation is recorded in err[1..3] (kind, address, bytes),
+// err[0] is set and the copy is skipped (its wait then times out cleanly).
+#ifdef FB_FFT_SELFCHECK
+__device__ __forceinline__ bool selfcheck_bad(int* err, int kind, const void* g, const void* s, unsigned bytes,
+                                              unsigned galign, unsigned salign)
+{
+    const bool bad = ((unsigned long long)g % galign) != 0 || (s && (smem_u32(s) % salign) != 0) ||
+                     (bytes % 16) != 0 || bytes == 0;
+    if (bad && atomicCAS(err + 1, 0, kind) == 0) {
+        err[2] = (int)((unsigned long long)g & 0x7fffffff);
+        err[3] = (int)bytes;
+        atomicExch(err, 2);
+    }
+    return bad;
+}
+#define FB_SELFCHECK(err, kind, g, s, bytes, ga, sa) \
+    if (selfcheck_bad(err, kind, g, s, bytes, ga, sa)) return
+#else
+#define FB_SELFCHECK(err, kind, g, s, bytes, ga, sa) (void)0
+#endif
+
 __device__ __forceinline__ void mbar_init(unsigned long long* bar, unsigned count)
 {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
@@ -224,31 +246,38 @@ __device__ __forceinline__ bool mbar_wait_bounded(unsigned long long* bar, unsig
     return true;
 }
 // global -> shared, contiguous bytes; completion counted on `bar`.
-__device__ __forceinline__ void bulk_load_1d(void* dst, const void* src, unsigned bytes, unsigned long long* bar)
+__device__ __forceinline__ void bulk_load_1d(void* dst, const void* src, unsigned bytes, unsigned long long* bar,
+                                             int* err = nullptr)
 {
+    if (err) FB_SELFCHECK(err, 11, src, dst, bytes, 16, 16);
     asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
                      smem_u32(dst)),
                  "l"(src), "r"(bytes), "r"(smem_u32(bar))
                  : "memory");
 }
 // shared -> global, contiguous bytes; tracked by the issuing thread's bulk group.
-__device__ __forceinline__ void bulk_store_1d(void* dst, const void* src, unsigned bytes)
+__device__ __forceinline__ void bulk_store_1d(void* dst, const void* src, unsigned bytes, int* err = nullptr)
 {
+    if (err) FB_SELFCHECK(err, 12, dst, src, bytes, 16, 16);
     asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;" ::"l"(dst), "r"(smem_u32(src)),
                  "r"(bytes)
                  : "memory");
 }
 // 3-D tiled tensor copies (coordinates innermost first).
-__device__ __forceinline__ void tma_load_3d(void* dst, const void* tmap, int x, int y, int z, unsigned long long* bar)
+__device__ __forceinline__ void tma_load_3d(void* dst, const void* tmap, int x, int y, int z, unsigned long long* bar,
+                                            int* err = nullptr)
 {
+    if (err) FB_SELFCHECK(err, 13, tmap, dst, 16u, 64, 128);
     asm volatile(
         "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], "
         "[%5];" ::"r"(smem_u32(dst)),
         "l"(tmap), "r"(x), "r"(y), "r"(z), "r"(smem_u32(bar))
         : "memory");
 }
-__device__ __forceinline__ void tma_store_3d(const void* tmap, int x, int y, int z, const void* src)
+__device__ __forceinline__ void tma_store_3d(const void* tmap, int x, int y, int z, const void* src,
+                                             int* err = nullptr)
 {
+    if (err) FB_SELFCHECK(err, 14, tmap, src, 16u, 64, 128);
     asm volatile("cp.async.bulk.tensor.3d.global.shared::cta.tile.bulk_group [%0, {%1, %2, %3}], [%4];" ::"l"(tmap),
                  "r"(x), "r"(y), "r"(z), "r"(smem_u32(src))
                  : "memory");
@@ -261,6 +290,8 @@ struct TileIdx {
     long long o, c0;
     int Tv;
 };
+
+
 __device__ __forceinline__ TileIdx tile_index(const PassDesc& d, long long tile)
 {
     TileIdx ti;
@@ -306,11 +337,11 @@ __device__ __forceinline__ void issue_tile_load(const PassDesc& d, const CUtenso
     if (!d.in_tfast) {
         const unsigned bytes = (unsigned)(ti.Tv * L) * 8u;
         mbar_arrive_expect_tx(bar, bytes + d.debug_extra_tx);
-        bulk_load_1d(land, d.in + ti.o * d.in_so + ti.c0 * d.in_sc, bytes, bar);
+        bulk_load_1d(land, d.in + ti.o * d.in_so + ti.c0 * d.in_sc, bytes, bar, d.err);
     } else {
         mbar_arrive_expect_tx(bar, (unsigned)(T * L) * 8u + d.debug_extra_tx);
         for (int n0 = 0; n0 < L; n0 += d.box_rows)
-            tma_load_3d(land + n0 * T, tm_in, (int)ti.c0, n0, (int)ti.o, bar);
+            tma_load_3d(land + n0 * T, tm_in, (int)ti.c0, n0, (int)ti.o, bar, d.err);
     }
 }
 // Thread 0: start the TMA stores of one finished tile from its buffer.
@@ -320,9 +351,9 @@ __device__ __forceinline__ void issue_tile_store(const PassDesc& d, const CUtens
     const TileIdx ti = tile_index(d, tile);
     const int L = d.L, T = 1 << d.logT;
     if (!d.out_tfast) {
-        bulk_store_1d(d.out + ti.o * d.out_so + ti.c0 * d.out_sc, land, (unsigned)(ti.Tv * L) * 8u);
+        bulk_store_1d(d.out + ti.o * d.out_so + ti.c0 * d.out_sc, land, (unsigned)(ti.Tv * L) * 8u, d.err);
     } else {
-        for (int k0 = 0; k0 < L; k0 += d.box_rows) tma_store_3d(tm_out, (int)ti.c0, k0, (int)ti.o, land + k0 * T);
+        for (int k0 = 0; k0 < L; k0 += d.box_rows) tma_store_3d(tm_out, (int)ti.c0, k0, (int)ti.o, land + k0 * T, d.err);
     }
     bulk_commit();
 }

@@ -250,22 +250,23 @@ __device__ __forceinline__ void p2_issue_load(const PassDesc& d, const CUtensorM
         if (lane == 0) mbar_arrive_expect_tx(bar, bytes + d.debug_extra_tx);
         __syncwarp();
         if (C::LLS == C::L && !d.off_in) {
-            if (lane == 0) bulk_load_1d(land, src, bytes, bar);
+            if (lane == 0) bulk_load_1d(land, src, bytes, bar, d.err);
         } else {
-            for (int t = lane; t < ti.Tv; t += 32) bulk_load_1d(land + t * C::LLS, line_in(d, ti, src, t), C::L * 8u, bar);
+            for (int t = lane; t < ti.Tv; t += 32)
+                bulk_load_1d(land + t * C::LLS, line_in(d, ti, src, t), C::L * 8u, bar, d.err);
         }
     } else if (!d.off_in) {
         if (lane == 0) {
             mbar_arrive_expect_tx(bar, (unsigned)(C::T * C::L) * 8u + d.debug_extra_tx);
             for (int n0 = 0; n0 < C::L; n0 += C::BR)
-                tma_load_3d(land + n0 * C::T, tm, (int)ti.c0, n0, (int)ti.o, bar);
+                tma_load_3d(land + n0 * C::T, tm, (int)ti.c0, n0, (int)ti.o, bar, d.err);
         }
     } else {
         // irregular transform bases: one bulk copy per row of Tv columns
         if (lane == 0) mbar_arrive_expect_tx(bar, (unsigned)(ti.Tv * C::L) * 8u + d.debug_extra_tx);
         __syncwarp();
         for (int n = lane; n < C::L; n += 32)
-            bulk_load_1d(land + n * C::T, src + (long long)n * d.in_sn, (unsigned)ti.Tv * 8u, bar);
+            bulk_load_1d(land + n * C::T, src + (long long)n * d.in_sn, (unsigned)ti.Tv * 8u, bar, d.err);
     }
 }
 // Producer warp (all lanes): start the TMA stores of one finished tile.
@@ -278,16 +279,18 @@ __device__ __forceinline__ void p2_issue_store(const PassDesc& d, const CUtensor
     float2* dst = tile_out_base(d, ti, C::OUT_T);
     if constexpr (!C::OUT_T) {
         if (C::OLS == C::L && !d.off_out) {
-            if (lane == 0) bulk_store_1d(dst, land, (unsigned)(ti.Tv * C::L) * 8u);
+            if (lane == 0) bulk_store_1d(dst, land, (unsigned)(ti.Tv * C::L) * 8u, d.err);
         } else {
-            for (int t = lane; t < ti.Tv; t += 32) bulk_store_1d(line_out(d, ti, dst, t), land + t * C::OLS, C::L * 8u);
+            for (int t = lane; t < ti.Tv; t += 32)
+                bulk_store_1d(line_out(d, ti, dst, t), land + t * C::OLS, C::L * 8u, d.err);
         }
     } else if (!d.off_out) {
         if (lane == 0)
-            for (int k0 = 0; k0 < C::L; k0 += C::BR) tma_store_3d(tm, (int)ti.c0, k0, (int)ti.o, land + k0 * C::T);
+            for (int k0 = 0; k0 < C::L; k0 += C::BR)
+                tma_store_3d(tm, (int)ti.c0, k0, (int)ti.o, land + k0 * C::T, d.err);
     } else {
         for (int k = lane; k < C::L; k += 32)
-            bulk_store_1d(dst + (long long)k * d.out_sk, land + k * C::T, (unsigned)ti.Tv * 8u);
+            bulk_store_1d(dst + (long long)k * d.out_sk, land + k * C::T, (unsigned)ti.Tv * 8u, d.err);
     }
     bulk_commit();
 }
