@@ -183,6 +183,9 @@ int fb_fft_plan_info(fb_fft_plan_t plan, fb_fft_info* info);
  */
 int fb_fft_plan_query(int rank, const long long* dims, long long batch, unsigned flags, fb_fft_info* info);
 
+/* fb_fft_plan_many_query -- the same for fb_fft_plan_many (host only). */
+int fb_fft_plan_many_query(int count, const long long* lengths, unsigned flags, fb_fft_info* info);
+
 /*
  * fb_fft_factorize -- the planner's radix schedule for one in-shared-memory
  * line length n (host only, needs no GPU).  Writes the radices (each of

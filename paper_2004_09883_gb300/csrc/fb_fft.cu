@@ -197,7 +197,7 @@ int make_line_pass(PassPlan& p, TwiddleBuilder& twb, long long L, long long O, l
                    long long in_sn, long long in_sc, long long in_so, long long out_sk, long long out_sc,
                    long long out_so, bool in_tfast, bool out_tfast, bool ptw)
 {
-    std::memset(&p, 0, sizeof(p));
+    p = PassPlan{};  // zero descriptor, default member values (no offset tables)
     PassDesc& d = p.d;
     int nst = factorize(L, d.radix, kMaxStages);
     if (nst < 0) return nst;
@@ -445,10 +445,35 @@ int schedule_many(fb_fft_plan_s* p, TwiddleBuilder& twb)
     return FB_FFT_OK;
 }
 
+// Invariants of a schedule, checked on the host before anything launches:
+// offset tables only on the caller's buffers (never on the scratch), table
+// ranges inside the offset buffer, slots inside the plan's side streams.
+int check_schedule(const fb_fft_plan_s* p)
+{
+    const long long nofs = (long long)p->h_off.size();
+    for (const PassPlan& q : p->passes) {
+        const long long O = q.d.tiles_per_o ? q.d.ntiles / q.d.tiles_per_o : 0;
+        if (q.off_in_idx >= 0) {
+            const long long need = q.d.in_tfast ? O : q.d.C;  // strided: per outer index, contiguous: per line
+            if (q.src != kBufIn || q.off_in_idx + need > nofs) return FB_FFT_ERR_INVALID_ARG;
+        }
+        if (q.off_out_idx >= 0) {
+            const long long need = q.d.out_tfast ? O : q.d.C;
+            if (q.dst != kBufOut || q.off_out_idx + need > nofs) return FB_FFT_ERR_INVALID_ARG;
+        }
+        if (!p->many && (q.off_in_idx >= 0 || q.off_out_idx >= 0)) return FB_FFT_ERR_INVALID_ARG;
+        if (q.slot < 0 || q.slot >= p->nslots) return FB_FFT_ERR_INVALID_ARG;
+    }
+    return FB_FFT_OK;
+}
+
 // Host part of planning: the pass list and the twiddle jobs (no device work).
 int schedule_plan(fb_fft_plan_s* p, TwiddleBuilder& twb)
 {
-    if (p->many) return schedule_many(p, twb);
+    if (p->many) {
+        const int rc = schedule_many(p, twb);
+        return rc != FB_FFT_OK ? rc : check_schedule(p);
+    }
     const long long B = p->batch;
     if (p->rank == 1 && p->N > FB_FFT_MAX_SMEM_LEN) {
         long long N1, N2;
@@ -514,7 +539,7 @@ int schedule_plan(fb_fft_plan_s* p, TwiddleBuilder& twb)
         if (!p->passes.empty()) p->passes.back().last = true;
     }
     p->tw_elems = std::max(2LL, twb.total);
-    return FB_FFT_OK;
+    return check_schedule(p);
 }
 
 int build_plan(fb_fft_plan_s* p)
@@ -904,6 +929,38 @@ int fb_fft_plan_many(fb_fft_plan_t* plan, int count, const long long* lengths, u
         return rc;
     }
     *plan = p;
+    return FB_FFT_OK;
+}
+
+int fb_fft_plan_many_query(int count, const long long* lengths, unsigned flags, fb_fft_info* info)
+{
+    if (!info || count < 0 || (count > 0 && !lengths) || (flags & ~FB_FFT_SCALE_INV_N)) return FB_FFT_ERR_INVALID_ARG;
+    for (int i = 0; i < count; ++i) {
+        if (lengths[i] < 1) return FB_FFT_ERR_INVALID_ARG;
+        long long n1, n2;
+        const int rc = split_fourstep(lengths[i], &n1, &n2);
+        if (rc != FB_FFT_OK) return rc;
+    }
+    fb_fft_plan_s p;
+    p.many = true;
+    p.rank = 1;
+    p.batch = count;
+    p.flags = flags;
+    p.lengths.assign(lengths, lengths + count);
+    p.offsets.resize(count);
+    p.total = many_layout(count, lengths, p.offsets.data());
+    p.nslots = many_streams();
+    TwiddleBuilder twb;
+    const int rc = schedule_plan(&p, twb);
+    p.magic = kDead;
+    if (rc != FB_FFT_OK) return rc;
+    std::memset(info, 0, sizeof(*info));
+    info->passes = (int)p.passes.size();
+    info->smem_len_max = p.smem_len_max;
+    info->scratch_bytes = (long long)p.scratch_bytes;
+    info->twiddle_bytes = p.tw_elems * (long long)sizeof(float2);
+    info->elements = p.total;
+    info->batch = count;
     return FB_FFT_OK;
 }
 

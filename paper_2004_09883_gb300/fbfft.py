@@ -73,6 +73,7 @@ _sig = {
     "fb_fft_many_layout": (_ll, [_int, ctypes.POINTER(_ll), ctypes.POINTER(_ll)]),
     "fb_fft_plan_many": (_int, [ctypes.POINTER(_vp), _int, ctypes.POINTER(_ll), ctypes.c_uint, _vp]),
     "fb_fft_set_graph": (_int, [_vp, _int]),
+    "fb_fft_plan_many_query": (_int, [_int, ctypes.POINTER(_ll), ctypes.c_uint, ctypes.POINTER(Info)]),
 }
 for _name, (_res, _args) in _sig.items():
     _f = getattr(lib, _name)
@@ -123,6 +124,15 @@ def many_layout(lengths) -> tuple[np.ndarray, int]:
     if total < 0:
         raise ValueError("bad lengths")
     return offs, int(total)
+
+
+def plan_many_query(lengths, scale_inv_n: bool = False) -> dict:
+    """Host-only planner run for a batched uneven plan (no GPU needed)."""
+    lens = np.ascontiguousarray(np.asarray(lengths, dtype=np.int64))
+    inf = Info()
+    _check(lib.fb_fft_plan_many_query(len(lens), lens.ctypes.data_as(ctypes.POINTER(_ll)),
+                                      SCALE_INV_N if scale_inv_n else 0, ctypes.byref(inf)), "fb_fft_plan_many_query")
+    return {f: getattr(inf, f) for f, _ in Info._fields_ if f != "reserved"}
 
 
 def launch_count() -> int:

@@ -201,3 +201,15 @@ def test_many_layout_is_packed_and_16_byte_aligned(fb):
     assert fb.many_layout([])[1] == 0
     with pytest.raises(ValueError):
         fb.many_layout([4, 0])
+
+
+@pytest.mark.parametrize("seed", [0, 1, 2])
+def test_many_planner_schedules_pass_host_checks(fb, seed):
+    lens = list(inputs.uneven_lengths(300, 64, 65536, inputs.seed_for(inputs.WORKLOAD_UNEVEN_4096, seed)))
+    lens += [2, 3, 4096, 4096, 65536, 1 << 20, 6000, 45000, 75]
+    info = fb.plan_many_query(lens)
+    offs, total = fb.many_layout(lens)
+    assert info["elements"] == total and info["batch"] == len(lens)
+    distinct_small = len({n for n in lens if n <= fb.MAX_SMEM_LEN})
+    assert info["passes"] >= distinct_small + 2 * len({n for n in lens if n > fb.MAX_SMEM_LEN})
+    assert info["scratch_bytes"] >= 8 * max(lens)
