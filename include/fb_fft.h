@@ -104,6 +104,40 @@ int fb_fft_plan_many(fb_fft_plan_t* plan, int count, const long long* lengths, u
 int fb_fft_set_graph(fb_fft_plan_t plan, int enable);
 
 /*
+ * Tuning knobs of a batched uneven plan (all 0 = the defaults):
+ *   streams            side streams the length groups spread over (1..32; default 4)
+ *   use_graph          1/0: replay one CUDA graph per exec (default) / launch directly;
+ *                      any other value = default
+ *   chunk_bytes        four-step intermediate per chunk of a length group (default 32 MiB)
+ *   odd_radices_first  lengths with factors 3/5 (generic kernel): 1 runs the 5s and 3s
+ *                      before the power-of-two radices
+ *   max_lines          generic kernel: at most this many lines per tile (0 = no extra cap)
+ */
+typedef struct fb_fft_many_opts {
+    int streams;
+    int use_graph;
+    long long chunk_bytes;
+    int odd_radices_first;
+    int max_lines;
+} fb_fft_many_opts;
+int fb_fft_plan_many_ex(fb_fft_plan_t* plan, int count, const long long* lengths, unsigned flags, void* stream,
+                        const fb_fft_many_opts* opts);
+
+/*
+ * fb_fft_autotune_many -- the project's autotuner for batched uneven plans
+ * (the paper's verification step, Sec. 3.4 / Sec. 4.2: measure candidate
+ * offload patterns in the target environment, keep the fastest).  Plans,
+ * runs and times (CUDA events, `reps` execs after two warm-ups) candidate
+ * knob settings by coordinate descent -- streams, chunk_bytes,
+ * odd_radices_first, max_lines -- on the caller's device buffers `in`/`out`
+ * (layout of fb_fft_many_layout; `out` is overwritten) in `direction`,
+ * and writes the fastest settings to *best and their time per exec (ms)
+ * to *best_ms.  Synchronous.  Errors: as fb_fft_plan_many / fb_fft_exec.
+ */
+int fb_fft_autotune_many(int count, const long long* lengths, unsigned flags, const void* in, void* out,
+                         int direction, void* stream, int reps, fb_fft_many_opts* best, float* best_ms);
+
+/*
  * fb_fft_exec -- run the transform on device buffers (Sec. 3.3 / Sec. 5.1(a):
  * the Fourier transform block itself).
  *   in        device pointer to batch*prod(dims) complex64 values, 8-byte aligned.

@@ -123,7 +123,7 @@ int ilog2ll(long long x)
 // Radix schedule of an in-shared-memory line: the power-of-two part as the
 // compile-time kernels order it (pow2_radix: 16s, with the leftover 8/4/2
 // last when that makes two stages, first otherwise), then 5s, then 3s.
-int factorize(long long n, int* r, int cap)
+int factorize(long long n, int* r, int cap, bool odd_first = false)
 {
     if (n < 1) return FB_FFT_ERR_INVALID_ARG;
     if (!is_smooth(n) || n > FB_FFT_MAX_SMEM_LEN) return FB_FFT_ERR_UNSUPPORTED_SIZE;
@@ -134,6 +134,12 @@ int factorize(long long n, int* r, int cap)
     };
     int a = 0;
     while (n % 2 == 0) n /= 2, ++a;
+    if (odd_first && n > 1) {  // only ever asked for lengths with a factor 3 or 5
+        while (n % 5 == 0) n /= 5, push(5);
+        while (n % 3 == 0) n /= 3, push(3);
+        for (int s = 0; s < pow2_nst(a); ++s) push(pow2_radix(a, s));
+        return c;
+    }
     for (int s = 0; s < pow2_nst(a); ++s) push(pow2_radix(a, s));
     while (n % 5 == 0) n /= 5, push(5);
     while (n % 3 == 0) n /= 3, push(3);
@@ -195,11 +201,13 @@ struct TwiddleBuilder {
 // Fill a line pass: L-point DFTs over lines (o, c); strides in elements.
 int make_line_pass(PassPlan& p, TwiddleBuilder& twb, long long L, long long O, long long C,
                    long long in_sn, long long in_sc, long long in_so, long long out_sk, long long out_sc,
-                   long long out_so, bool in_tfast, bool out_tfast, bool ptw)
+                   long long out_so, bool in_tfast, bool out_tfast, bool ptw, bool odd_first = false,
+                   int max_lines = 0)
 {
     p = PassPlan{};  // zero descriptor, default member values (no offset tables)
     PassDesc& d = p.d;
-    int nst = factorize(L, d.radix, kMaxStages);
+    const bool pow2_len = (L & (L - 1)) == 0;
+    int nst = factorize(L, d.radix, kMaxStages, odd_first && !pow2_len);
     if (nst < 0) return nst;
     if (nst > kMaxStages) return FB_FFT_ERR_UNSUPPORTED_SIZE;
     d.nst = nst;
@@ -232,6 +240,7 @@ int make_line_pass(PassPlan& p, TwiddleBuilder& twb, long long L, long long O, l
         if (L > cap) return FB_FFT_ERR_UNSUPPORTED_SIZE;
         T = pow2floor(cap / L);
         T = std::min<long long>(T, cfast ? 16 : p.threads);
+        if (max_lines > 0) T = std::min<long long>(T, pow2floor(max_lines));
         T = std::max<long long>(1, std::min(T, pow2ceil(C)));
         land = land_stride_elems((int)L, (int)T);
     }
@@ -310,6 +319,9 @@ struct fb_fft_plan_s {
     cudaStream_t capture = nullptr;      // where graphs are captured (the caller's may be uncapturable)
     std::vector<cudaEvent_t> fork_join;  // [0] fork, [1 + s] join of slot s
     bool use_graph = true;
+    long long chunk_bytes = 0;   // 0: fourstep_chunk_bytes()
+    bool odd_first = false;
+    int max_lines = 0;
     struct GraphEntry {
         const void* in;
         void* out;
@@ -389,7 +401,8 @@ int schedule_many(fb_fft_plan_s* p, TwiddleBuilder& twb)
         };
         if (L <= FB_FFT_MAX_SMEM_LEN) {
             PassPlan q;
-            int rc = make_line_pass(q, twb, L, 1, (long long)idx.size(), 1, L, 0, 1, L, 0, false, false, false);
+            int rc = make_line_pass(q, twb, L, 1, (long long)idx.size(), 1, L, 0, 1, L, 0, false, false, false,
+                                    p->odd_first, p->max_lines);
             if (rc != FB_FFT_OK) return rc;
             q.off_in_idx = q.off_out_idx = push_offsets(0, idx.size());
             if (!pow2) q.async_ok = false;  // the generic kernel copies offset-table tiles itself
@@ -410,13 +423,14 @@ int schedule_many(fb_fft_plan_s* p, TwiddleBuilder& twb)
         const long long lo_off = twb.add_linear(lo_cnt, L, 1);
         const long long hi_off = twb.add_linear(hi_cnt, L, lo_cnt);
         const long long cnt = (long long)idx.size();
-        const long long chunk = std::max(1LL, std::min(cnt, fourstep_chunk_bytes() / (L * 8)));
+        const long long cbytes = p->chunk_bytes > 0 ? p->chunk_bytes : fourstep_chunk_bytes();
+        const long long chunk = std::max(1LL, std::min(cnt, cbytes / (L * 8)));
         scratch_need = std::max(scratch_need, chunk * L);
         for (long long b0 = 0; b0 < cnt; b0 += chunk) {
             const long long nb = std::min(chunk, cnt - b0);
             const long long at = push_offsets((size_t)b0, (size_t)nb);
             PassPlan a, r;
-            rc = make_line_pass(a, twb, N1, nb, N2, N2, 1, L, N2, 1, L, true, true, true);
+            rc = make_line_pass(a, twb, N1, nb, N2, N2, 1, L, N2, 1, L, true, true, true, p->odd_first, p->max_lines);
             if (rc != FB_FFT_OK) return rc;
             a.d.ptw_log = plog;
             a.d.ptw_lo = reinterpret_cast<const float2*>(lo_off);
@@ -426,7 +440,8 @@ int schedule_many(fb_fft_plan_s* p, TwiddleBuilder& twb)
             a.src = kBufIn, a.dst = kBufScratch;
             a.group = 1;
             a.slot = 0;
-            rc = make_line_pass(r, twb, N2, nb, N1, 1, N2, L, N1, 1, L, false, true, false);
+            rc = make_line_pass(r, twb, N2, nb, N1, 1, N2, L, N1, 1, L, false, true, false, p->odd_first,
+                                p->max_lines);
             if (rc != FB_FFT_OK) return rc;
             r.off_out_idx = at;
             if ((N2 & (N2 - 1)) != 0) r.async_ok = false;
@@ -894,11 +909,14 @@ long long fb_fft_many_layout(int count, const long long* lengths, long long* off
     return many_layout(count, lengths, offsets);
 }
 
-int fb_fft_plan_many(fb_fft_plan_t* plan, int count, const long long* lengths, unsigned flags, void* stream)
+int fb_fft_plan_many_ex(fb_fft_plan_t* plan, int count, const long long* lengths, unsigned flags, void* stream,
+                        const fb_fft_many_opts* opts)
 {
     if (!plan) return FB_FFT_ERR_INVALID_ARG;
     *plan = nullptr;
     if (count < 0 || (count > 0 && !lengths) || (flags & ~FB_FFT_SCALE_INV_N)) return FB_FFT_ERR_INVALID_ARG;
+    if (opts && (opts->streams < 0 || opts->streams > 32 || opts->chunk_bytes < 0 || opts->max_lines < 0))
+        return FB_FFT_ERR_INVALID_ARG;
     for (int i = 0; i < count; ++i) {
         if (lengths[i] < 1) return FB_FFT_ERR_INVALID_ARG;
         long long n1, n2;
@@ -922,13 +940,97 @@ int fb_fft_plan_many(fb_fft_plan_t* plan, int count, const long long* lengths, u
     p->offsets.resize(count);
     p->total = many_layout(count, lengths, p->offsets.data());
     p->N = 0;
-    p->nslots = many_streams();
+    p->nslots = (opts && opts->streams > 0) ? opts->streams : many_streams();
+    if (opts) {
+        if (opts->use_graph == 0 || opts->use_graph == 1) p->use_graph = opts->use_graph == 1;
+        p->chunk_bytes = opts->chunk_bytes;
+        p->odd_first = opts->odd_radices_first != 0;
+        p->max_lines = opts->max_lines;
+    }
     int rc = build_plan(p);
     if (rc != FB_FFT_OK) {
         free_plan(p);
         return rc;
     }
     *plan = p;
+    return FB_FFT_OK;
+}
+
+int fb_fft_plan_many(fb_fft_plan_t* plan, int count, const long long* lengths, unsigned flags, void* stream)
+{
+    return fb_fft_plan_many_ex(plan, count, lengths, flags, stream, nullptr);
+}
+
+int fb_fft_autotune_many(int count, const long long* lengths, unsigned flags, const void* in, void* out,
+                         int direction, void* stream, int reps, fb_fft_many_opts* best, float* best_ms)
+{
+    if (!best || !best_ms || reps < 1 || !in || !out) return FB_FFT_ERR_INVALID_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    cudaEvent_t e0, e1;
+    FB_CK(cudaEventCreate(&e0));
+    if (cudaEventCreate(&e1) != cudaSuccess) {
+        cudaEventDestroy(e0);
+        return cuda_fail(cudaErrorUnknown, "cudaEventCreate");
+    }
+    auto measure = [&](const fb_fft_many_opts& o, float* ms) -> int {
+        fb_fft_plan_t pl = nullptr;
+        int rc = fb_fft_plan_many_ex(&pl, count, lengths, flags, stream, &o);
+        if (rc != FB_FFT_OK) return rc;
+        for (int w = 0; w < 2 && rc == FB_FFT_OK; ++w) rc = fb_fft_exec(pl, in, out, direction);
+        if (rc == FB_FFT_OK && cudaEventRecord(e0, st) != cudaSuccess) rc = FB_FFT_ERR_CUDA;
+        for (int r = 0; r < reps && rc == FB_FFT_OK; ++r) rc = fb_fft_exec(pl, in, out, direction);
+        if (rc == FB_FFT_OK && (cudaEventRecord(e1, st) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess))
+            rc = FB_FFT_ERR_CUDA;
+        float t = 0.f;
+        if (rc == FB_FFT_OK && cudaEventElapsedTime(&t, e0, e1) != cudaSuccess) rc = FB_FFT_ERR_CUDA;
+        if (rc == FB_FFT_OK) rc = fb_fft_check(pl);
+        fb_fft_destroy(pl);
+        *ms = t / reps;
+        return rc;
+    };
+    fb_fft_many_opts cur{4, 1, 32LL << 20, 0, 0};
+    float cur_ms = 0.f;
+    int rc = measure(cur, &cur_ms);
+    // coordinate descent, one knob at a time
+    const int streams[] = {1, 2, 8, 16, 32};
+    const long long chunks[] = {8LL << 20, 16LL << 20, 64LL << 20, 128LL << 20};
+    const int lines[] = {4, 16, 64};
+    for (int v : streams) {
+        if (rc != FB_FFT_OK) break;
+        fb_fft_many_opts o = cur;
+        o.streams = v;
+        float ms;
+        rc = measure(o, &ms);
+        if (rc == FB_FFT_OK && ms < cur_ms) cur = o, cur_ms = ms;
+    }
+    for (long long v : chunks) {
+        if (rc != FB_FFT_OK) break;
+        fb_fft_many_opts o = cur;
+        o.chunk_bytes = v;
+        float ms;
+        rc = measure(o, &ms);
+        if (rc == FB_FFT_OK && ms < cur_ms) cur = o, cur_ms = ms;
+    }
+    if (rc == FB_FFT_OK) {
+        fb_fft_many_opts o = cur;
+        o.odd_radices_first = 1;
+        float ms;
+        rc = measure(o, &ms);
+        if (rc == FB_FFT_OK && ms < cur_ms) cur = o, cur_ms = ms;
+    }
+    for (int v : lines) {
+        if (rc != FB_FFT_OK) break;
+        fb_fft_many_opts o = cur;
+        o.max_lines = v;
+        float ms;
+        rc = measure(o, &ms);
+        if (rc == FB_FFT_OK && ms < cur_ms) cur = o, cur_ms = ms;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (rc != FB_FFT_OK) return rc;
+    *best = cur;
+    *best_ms = cur_ms;
     return FB_FFT_OK;
 }
 

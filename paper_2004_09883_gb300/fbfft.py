@@ -43,6 +43,15 @@ class Info(ctypes.Structure):
                 ("batch", ctypes.c_longlong)]
 
 
+class ManyOpts(ctypes.Structure):
+    """Knobs of a batched uneven plan (0 = default)."""
+    _fields_ = [("streams", ctypes.c_int), ("use_graph", ctypes.c_int), ("chunk_bytes", ctypes.c_longlong),
+                ("odd_radices_first", ctypes.c_int), ("max_lines", ctypes.c_int)]
+
+    def as_dict(self) -> dict:
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
 if not os.path.exists(LIB_PATH):
     raise ImportError(f"{LIB_PATH} is missing: build it with __graft_entry__.build() "
                       "(python -m paper_2004_09883_gb300.build)")
@@ -74,6 +83,10 @@ _sig = {
     "fb_fft_plan_many": (_int, [ctypes.POINTER(_vp), _int, ctypes.POINTER(_ll), ctypes.c_uint, _vp]),
     "fb_fft_set_graph": (_int, [_vp, _int]),
     "fb_fft_plan_many_query": (_int, [_int, ctypes.POINTER(_ll), ctypes.c_uint, ctypes.POINTER(Info)]),
+    "fb_fft_plan_many_ex": (_int, [ctypes.POINTER(_vp), _int, ctypes.POINTER(_ll), ctypes.c_uint, _vp,
+                                   ctypes.POINTER(ManyOpts)]),
+    "fb_fft_autotune_many": (_int, [_int, ctypes.POINTER(_ll), ctypes.c_uint, _vp, _vp, _int, _vp, _int,
+                                    ctypes.POINTER(ManyOpts), ctypes.POINTER(ctypes.c_float)]),
 }
 for _name, (_res, _args) in _sig.items():
     _f = getattr(lib, _name)
@@ -278,7 +291,7 @@ class PlanMany(Plan):
     """Batched 1-D transforms of uneven lengths in the packed layout of
     :func:`many_layout` (one graph launch per exec)."""
 
-    def __init__(self, lengths, scale_inv_n: bool = False, stream=None):
+    def __init__(self, lengths, scale_inv_n: bool = False, stream=None, opts: "ManyOpts | dict | None" = None):
         lens = np.ascontiguousarray(np.asarray(lengths, dtype=np.int64))
         self.lengths = lens
         self.offsets, self.total = many_layout(lens)
@@ -287,8 +300,12 @@ class PlanMany(Plan):
         self.flags = SCALE_INV_N if scale_inv_n else 0
         self._h = _vp()
         self._stream = _stream_handle(stream)
-        _check(lib.fb_fft_plan_many(ctypes.byref(self._h), len(lens), lens.ctypes.data_as(ctypes.POINTER(_ll)),
-                                    self.flags, _vp(self._stream)), "fb_fft_plan_many")
+        if isinstance(opts, dict):
+            opts = ManyOpts(**opts)
+        self.opts = opts
+        _check(lib.fb_fft_plan_many_ex(ctypes.byref(self._h), len(lens), lens.ctypes.data_as(ctypes.POINTER(_ll)),
+                                       self.flags, _vp(self._stream), ctypes.byref(opts) if opts else None),
+               "fb_fft_plan_many_ex")
         self.n = self.total  # exec() checks numel == n * batch
         self.batch_for_size = 1
 
@@ -325,6 +342,21 @@ class PlanMany(Plan):
 
     def unpack(self, buf):
         return [np.asarray(buf[o:o + n]) for o, n in zip(self.offsets, self.lengths)]
+
+
+def autotune_many(lengths, x, out, direction: int = FORWARD, scale_inv_n: bool = False, reps: int = 5):
+    """Run the library's autotuner on device buffers x/out (packed layout);
+    returns (ManyOpts, ms per exec).  `out` is overwritten."""
+    import torch
+    lens = np.ascontiguousarray(np.asarray(lengths, dtype=np.int64))
+    best = ManyOpts()
+    ms = ctypes.c_float()
+    s = torch.cuda.current_stream(x.device).cuda_stream
+    _check(lib.fb_fft_autotune_many(len(lens), lens.ctypes.data_as(ctypes.POINTER(_ll)),
+                                    SCALE_INV_N if scale_inv_n else 0, _vp(x.data_ptr()), _vp(out.data_ptr()),
+                                    int(direction), _vp(s), int(reps), ctypes.byref(best), ctypes.byref(ms)),
+           "fb_fft_autotune_many")
+    return best, ms.value
 
 
 def exec_1d_noalloc(x, out, n: int, batch: int, direction: int = FORWARD, scale_inv_n: bool = False):

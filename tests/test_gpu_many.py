@@ -85,3 +85,33 @@ def test_many_single_transform_and_empty(fb):
         x = inputs.uniform_c64((12,), 3)
         y = p.exec(torch.from_numpy(p.pack([x])).cuda(), None, -1)
         _check(p, [x], p.unpack(y.cpu().numpy()), -1)
+
+
+@pytest.mark.parametrize("opts", [dict(streams=1, use_graph=0, chunk_bytes=8 << 20, odd_radices_first=1, max_lines=4),
+                                  dict(streams=16, use_graph=1, chunk_bytes=1 << 20, odd_radices_first=0, max_lines=16)])
+def test_many_knobs_keep_results(fb, opts):
+    import torch
+    xs = _batch(LENGTHS, 903)
+    with fb.PlanMany(LENGTHS, opts=opts) as p:
+        out = p.exec(torch.from_numpy(p.pack(xs)).cuda(), None, -1)
+        p.check()
+        ys = p.unpack(out.cpu().numpy())
+    _check(p, xs, ys, -1)
+
+
+def test_autotuner_returns_a_working_setting(fb):
+    import torch
+    lens = LENGTHS[:30]
+    xs = _batch(lens, 904)
+    offs, total = fb.many_layout(lens)
+    buf = np.zeros(total, np.complex64)
+    for o, x in zip(offs, xs):
+        buf[o:o + len(x)] = x
+    d = torch.from_numpy(buf).cuda()
+    out = torch.empty_like(d)
+    best, ms = fb.autotune_many(lens, d, out, -1, reps=2)
+    assert ms > 0 and 1 <= best.streams <= 32 and best.chunk_bytes > 0
+    with fb.PlanMany(lens, opts=best) as p:
+        y = p.exec(d, None, -1)
+        p.check()
+        _check(p, xs, p.unpack(y.cpu().numpy()), -1)
