@@ -405,6 +405,7 @@ int schedule_many(fb_fft_plan_s* p, TwiddleBuilder& twb)
                                     p->odd_first, p->max_lines);
             if (rc != FB_FFT_OK) return rc;
             q.off_in_idx = q.off_out_idx = push_offsets(0, idx.size());
+            if (!pow2) q.async_ok = false;  // the generic kernel copies offset-table tiles itself
             q.src = kBufIn, q.dst = kBufOut;
             q.group = 0;
             q.last = true;
@@ -435,7 +436,7 @@ int schedule_many(fb_fft_plan_s* p, TwiddleBuilder& twb)
             a.d.ptw_lo = reinterpret_cast<const float2*>(lo_off);
             a.d.ptw_hi = reinterpret_cast<const float2*>(hi_off);
             a.off_in_idx = at;
-            if (N2 % 2) a.async_ok = false;  // per-row copies of a ragged tile need an even width
+            if ((N1 & (N1 - 1)) != 0) a.async_ok = false;
             a.src = kBufIn, a.dst = kBufScratch;
             a.group = 1;
             a.slot = 0;
@@ -443,7 +444,7 @@ int schedule_many(fb_fft_plan_s* p, TwiddleBuilder& twb)
                                 p->max_lines);
             if (rc != FB_FFT_OK) return rc;
             r.off_out_idx = at;
-            if (N1 % 2) r.async_ok = false;
+            if ((N2 & (N2 - 1)) != 0) r.async_ok = false;
             r.src = kBufScratch, r.dst = kBufOut;
             r.group = 2;
             r.last = true;

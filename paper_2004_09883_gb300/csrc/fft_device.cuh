@@ -327,29 +327,21 @@ __device__ __forceinline__ float2* line_out(const PassDesc& d, const TileIdx& ti
 }
 
 // Thread 0: start the TMA loads of one tile into a landing buffer.
-// n-fast tiles land as [t][n], c-fast tiles as [n][t] by 3-D boxes of
-// T x box_rows (zero fill past C).  With offset tables (batched uneven
-// lengths) lines / rows are copied one bulk copy each.
+// n-fast tiles are contiguous (line stride == L) and land as [t][n];
+// c-fast tiles land as [n][t] by 3-D boxes of T x box_rows (zero fill past C).
 __device__ __forceinline__ void issue_tile_load(const PassDesc& d, const CUtensorMap* tm_in, long long tile,
                                                 float2* land, unsigned long long* bar)
 {
     const TileIdx ti = tile_index(d, tile);
     const int L = d.L, T = 1 << d.logT;
-    const float2* src = tile_in_base(d, ti, d.in_tfast != 0);
     if (!d.in_tfast) {
         const unsigned bytes = (unsigned)(ti.Tv * L) * 8u;
         mbar_arrive_expect_tx(bar, bytes + d.debug_extra_tx);
-        if (!d.off_in)
-            bulk_load_1d(land, src, bytes, bar, d.err);
-        else
-            for (int t = 0; t < ti.Tv; ++t) bulk_load_1d(land + t * L, line_in(d, ti, src, t), L * 8u, bar, d.err);
-    } else if (!d.off_in) {
+        bulk_load_1d(land, d.in + ti.o * d.in_so + ti.c0 * d.in_sc, bytes, bar, d.err);
+    } else {
         mbar_arrive_expect_tx(bar, (unsigned)(T * L) * 8u + d.debug_extra_tx);
         for (int n0 = 0; n0 < L; n0 += d.box_rows)
             tma_load_3d(land + n0 * T, tm_in, (int)ti.c0, n0, (int)ti.o, bar, d.err);
-    } else {
-        mbar_arrive_expect_tx(bar, (unsigned)(ti.Tv * L) * 8u + d.debug_extra_tx);
-        for (int n = 0; n < L; ++n) bulk_load_1d(land + n * T, src + (long long)n * d.in_sn, (unsigned)ti.Tv * 8u, bar, d.err);
     }
 }
 // Thread 0: start the TMA stores of one finished tile from its buffer.
@@ -358,16 +350,10 @@ __device__ __forceinline__ void issue_tile_store(const PassDesc& d, const CUtens
 {
     const TileIdx ti = tile_index(d, tile);
     const int L = d.L, T = 1 << d.logT;
-    float2* dst = tile_out_base(d, ti, d.out_tfast != 0);
     if (!d.out_tfast) {
-        if (!d.off_out)
-            bulk_store_1d(dst, land, (unsigned)(ti.Tv * L) * 8u, d.err);
-        else
-            for (int t = 0; t < ti.Tv; ++t) bulk_store_1d(line_out(d, ti, dst, t), land + t * L, L * 8u, d.err);
-    } else if (!d.off_out) {
-        for (int k0 = 0; k0 < L; k0 += d.box_rows) tma_store_3d(tm_out, (int)ti.c0, k0, (int)ti.o, land + k0 * T, d.err);
+        bulk_store_1d(d.out + ti.o * d.out_so + ti.c0 * d.out_sc, land, (unsigned)(ti.Tv * L) * 8u, d.err);
     } else {
-        for (int k = 0; k < L; ++k) bulk_store_1d(dst + (long long)k * d.out_sk, land + k * T, (unsigned)ti.Tv * 8u, d.err);
+        for (int k0 = 0; k0 < L; k0 += d.box_rows) tma_store_3d(tm_out, (int)ti.c0, k0, (int)ti.o, land + k0 * T, d.err);
     }
     bulk_commit();
 }
