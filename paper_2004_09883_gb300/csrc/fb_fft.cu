@@ -80,6 +80,7 @@ struct PassPlan {
     int threads;  // CTA size of the chosen kernel
     int lg;       // log2(L) for a compile-time power-of-two kernel, 0 = generic kernel
     int io;       // IoMode of the power-of-two kernel
+    int kind;     // 0 power-of-two kernel, 1 generic kernel, 2 mixed kernel (lg = log2 of the 2-factor)
     long long grid;
     size_t smem;
     bool async_ok;  // tiles can move by TMA (given 16-byte aligned buffer bases)
@@ -198,6 +199,14 @@ struct TwiddleBuilder {
     }
 };
 
+// The compiled kernel a pass runs in one direction.
+LineKernel pass_kernel(const PassPlan& q, bool fwd)
+{
+    if (q.kind == 2) return line_kernel_mixed(fwd, q.lg);
+    if (q.kind == 1) return line_kernel_generic(fwd);
+    return line_kernel_p2(q.threads, fwd, q.lg, q.io);
+}
+
 // Fill a line pass: L-point DFTs over lines (o, c); strides in elements.
 int make_line_pass(PassPlan& p, TwiddleBuilder& twb, long long L, long long O, long long C,
                    long long in_sn, long long in_sc, long long in_so, long long out_sk, long long out_sc,
@@ -207,7 +216,8 @@ int make_line_pass(PassPlan& p, TwiddleBuilder& twb, long long L, long long O, l
     p = PassPlan{};  // zero descriptor, default member values (no offset tables)
     PassDesc& d = p.d;
     const bool pow2_len = (L & (L - 1)) == 0;
-    int nst = factorize(L, d.radix, kMaxStages, odd_first && !pow2_len);
+    const bool mixed_len = !pow2_len && L <= kMixedMaxLen;  // mixed kernels fix the radix order
+    int nst = factorize(L, d.radix, kMaxStages, odd_first && !pow2_len && !mixed_len);
     if (nst < 0) return nst;
     if (nst > kMaxStages) return FB_FFT_ERR_UNSUPPORTED_SIZE;
     d.nst = nst;
@@ -235,14 +245,19 @@ int make_line_pass(PassPlan& p, TwiddleBuilder& twb, long long L, long long O, l
         d.tws = p2_smem_twiddles(p.lg);
     } else {
         p.io = -1;
-        p.threads = kGenericThreads;
-        const long long cap = (long long)p.threads * kGenericElems;
+        int a2 = 0;
+        while (((L >> a2) & 1) == 0) ++a2;
+        p.kind = mixed_len ? 2 : 1;
+        p.lg = mixed_len ? a2 : 0;
+        p.threads = mixed_len ? kMixedThreads : kGenericThreads;
+        const long long cap = (long long)p.threads * (mixed_len ? kMixedElems : kGenericElems);
         if (L > cap) return FB_FFT_ERR_UNSUPPORTED_SIZE;
         T = pow2floor(cap / L);
         T = std::min<long long>(T, cfast ? 16 : p.threads);
         if (max_lines > 0) T = std::min<long long>(T, pow2floor(max_lines));
         T = std::max<long long>(1, std::min(T, pow2ceil(C)));
         land = land_stride_elems((int)L, (int)T);
+        if (!pass_kernel(p, true).fn) return FB_FFT_ERR_UNSUPPORTED_SIZE;
     }
 
     d.L = (int)L;
@@ -579,7 +594,7 @@ int build_plan(fb_fft_plan_s* p)
     FB_CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, p->device));
     for (PassPlan& q : p->passes) {
         int occ = 0;
-        const LineKernel k = q.lg ? line_kernel_p2(q.threads, true, q.lg, q.io) : line_kernel_generic(true);
+        const LineKernel k = pass_kernel(q, true);
         FB_CK(line_occupancy(k, q.smem, &occ));
         if (occ < 1) return cuda_fail(cudaErrorInvalidConfiguration, "line pass occupancy");
         q.grid = std::min(q.grid, (long long)sms * occ);
@@ -708,7 +723,7 @@ int launch_pass(fb_fft_plan_s* p, const PassPlan& q, const float2* in, float2* o
         p->ev_used += 2;
         cudaEventRecord(e0, stream);
     }
-    const LineKernel k = q.lg ? line_kernel_p2(q.threads, fwd, q.lg, q.io) : line_kernel_generic(fwd);
+    const LineKernel k = pass_kernel(q, fwd);
     const cudaError_t le = line_launch(k, args, q.grid, smem, stream);
     if (le != cudaSuccess) {
         char nm[64];

@@ -130,10 +130,13 @@ int fill_pass(Pass& p, StackTwiddles& tw, long long L, long long O, long long C,
         land = p2_land_elems(threads, lg, io);
         d.tws = p2_smem_twiddles(lg);
     } else {
-        threads = kGenericThreads;
-        p.k[1] = line_kernel_generic(true);
-        p.k[0] = line_kernel_generic(false);
-        const long long cap = (long long)threads * kGenericElems;
+        const bool mixed = L <= kMixedMaxLen;
+        int a2 = 0;
+        while (((L >> a2) & 1) == 0) ++a2;
+        threads = mixed ? kMixedThreads : kGenericThreads;
+        p.k[1] = mixed ? line_kernel_mixed(true, a2) : line_kernel_generic(true);
+        p.k[0] = mixed ? line_kernel_mixed(false, a2) : line_kernel_generic(false);
+        const long long cap = (long long)threads * (mixed ? kMixedElems : kGenericElems);
         T = 1;
         while (T * 2 * L <= cap && T * 2 <= (cfast ? 16 : threads)) T *= 2;
         long long cpow = 1;

@@ -21,6 +21,11 @@ enum LineCfg { kCfg256 = 0, kCfg512 = 1, kNumCfg = 2 };
 constexpr int cfg_threads(int cfg) { return cfg == kCfg256 ? 256 : 512; }
 constexpr long long cfg_capacity(int cfg) { return (long long)cfg_threads(cfg) * kElemsPerThread; }
 constexpr int kGenericThreads = 512;  // generic kernel: 512 x 8 = 4096 values per tile
+// Mixed kernels (power-of-two radices at compile time, then 5s and 3s):
+// 256 threads x 8 values, lines up to 2048 with a factor 3 or 5.
+constexpr int kMixedThreads = 256;
+constexpr int kMixedElems = 8;
+constexpr int kMixedMaxLen = kMixedThreads * kMixedElems;
 constexpr int kMaxLineLog2 = 12;  // 4096
 
 // One kernel launch of the line pass: 1-D DFTs of length L along one axis of a
@@ -84,18 +89,21 @@ inline size_t line_smem_bytes(long long land_elems, int L, int T, int nst, bool 
     return 256 + (size_t)(land + work + tws) * sizeof(float2);  // alignment slack + mbarriers
 }
 
-// One compiled line-pass kernel.  lg = log2(L) for the compile-time
-// power-of-two kernels (io = their IoMode), 0 for the generic kernel (io = -1).
+// One compiled line-pass kernel.  kind 0: compile-time power-of-two kernel
+// (lg = log2 L, io = its IoMode); 1: generic kernel; 2: mixed kernel
+// (lg = log2 of L's power-of-two factor).
 struct LineKernel {
     void (*fn)(LineArgs);
     int threads;
     bool fwd;
     int lg;
     int io;
+    int kind = 0;
 };
 // The kernel for a pass; fn == nullptr when that combination is not compiled.
 LineKernel line_kernel_p2(int threads, bool forward, int lg, int io);
 LineKernel line_kernel_generic(bool forward);
+LineKernel line_kernel_mixed(bool forward, int lg2);
 // Launch / occupancy / name of a table entry (shared-memory opt-in handled inside).
 cudaError_t line_launch(const LineKernel& k, const LineArgs& a, long long grid, size_t smem, cudaStream_t stream);
 cudaError_t line_occupancy(const LineKernel& k, size_t smem, int* blocks_per_sm);

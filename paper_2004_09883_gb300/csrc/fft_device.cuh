@@ -605,6 +605,117 @@ __global__ void __launch_bounds__(THREADS, 1) k_fft_generic(const __grid_constan
     if (async && threadIdx.x == 0) bulk_wait_all();
 }
 
+// Run-time dispatch over the odd radices only (5, 3).
+template <int THREADS, bool FWD, int POS, int E>
+__device__ __forceinline__ void run_odd_stage(int R, const PassDesc& d, int Ns, int twoff, float2* land, float2* work,
+                                              int Tv, int c0)
+{
+    if (R == 5)
+        stage<5, THREADS, FWD, POS, E>(d, Ns, twoff, land, work, Tv, c0);
+    else
+        stage<3, THREADS, FWD, POS, E>(d, Ns, twoff, land, work, Tv, c0);
+}
+// Compile-time power-of-two prefix of a mixed schedule (stage S < pow2_nst(LG2)).
+template <int THREADS, bool FWD, int LG2, int S, int E>
+__device__ __forceinline__ void mixed_p2_stages(const PassDesc& d, float2* land, float2* work, int Tv, int c0)
+{
+    if constexpr (S < pow2_nst(LG2)) {
+        constexpr int R = pow2_radix(LG2, S);
+        if constexpr (S == 0)
+            stage<R, THREADS, FWD, kPosFirst, E>(d, 1, 0, land, work, Tv, c0);
+        else
+            stage<R, THREADS, FWD, kPosMid, E>(d, d.ns[S], d.twoff[S], land, work, Tv, c0);
+        __syncthreads();
+        mixed_p2_stages<THREADS, FWD, LG2, S + 1, E>(d, land, work, Tv, c0);
+    }
+}
+
+// The mixed line pass: L = 2^LG2 * 3^b * 5^c with b + c >= 1.  Stages: the
+// power-of-two radices (compile time), then the 5s, then the 3s (run time).
+// Same tile walk and TMA pipeline as the generic kernel.
+template <int THREADS, bool FWD, int LG2>
+__global__ void __launch_bounds__(THREADS, 1) k_fft_mixed(const __grid_constant__ LineArgs a)
+{
+    extern __shared__ __align__(128) unsigned char smem_dyn[];
+    unsigned char* smem_raw = smem_dyn + ((128u - (smem_u32(smem_dyn) & 127u)) & 127u);
+    unsigned long long* bar = reinterpret_cast<unsigned long long*>(smem_raw);
+    float2* land0 = reinterpret_cast<float2*>(smem_raw + 128);
+    const bool async = a.d.async_io != 0;
+    float2* work = land0 + (async ? 2 : 1) * a.d.land_stride;
+    const long long step = gridDim.x;
+    __shared__ PassDesc sd;
+    {
+        const int* src = reinterpret_cast<const int*>(&a.d);
+        int* dst = reinterpret_cast<int*>(&sd);
+        for (int w = threadIdx.x; w < (int)(sizeof(PassDesc) / 4); w += THREADS) dst[w] = src[w];
+    }
+    __syncthreads();
+    const PassDesc& d = sd;
+    constexpr int E = kMixedElems;
+    constexpr int NP2 = pow2_nst(LG2);
+    if (async && threadIdx.x == 0) {
+        mbar_init(&bar[0], 1);
+        mbar_init(&bar[1], 1);
+        fence_mbar_init();
+        if (blockIdx.x < d.ntiles) issue_tile_load(d, &a.tm_in, blockIdx.x, land0, &bar[0]);
+        if (blockIdx.x + step < d.ntiles)
+            issue_tile_load(d, &a.tm_in, blockIdx.x + step, land0 + d.land_stride, &bar[1]);
+    }
+    __syncthreads();
+    int i = 0;
+    for (long long tile = blockIdx.x; tile < d.ntiles; tile += step, ++i) {
+        const TileIdx ti = tile_index(d, tile);
+        const int buf = async ? (i & 1) : 0;
+        float2* land = land0 + buf * d.land_stride;
+        const int c0 = (int)ti.c0;
+        if (async) {
+            const bool bad = !mbar_wait_bounded(&bar[buf], (unsigned)(i >> 1) & 1u);
+            if (__syncthreads_or(bad)) {
+                if (threadIdx.x == 0) {
+                    atomicExch(d.err, 1);
+                    bulk_wait_all();
+                    if (i == 0 && tile + step < d.ntiles) mbar_wait_bounded(&bar[1], 0);
+                }
+                return;
+            }
+        } else {
+            plain_tile_load<THREADS>(d, ti, land);
+            __syncthreads();
+        }
+        int s0 = NP2;
+        if constexpr (NP2 > 0) {
+            mixed_p2_stages<THREADS, FWD, LG2, 0, E>(d, land, work, ti.Tv, c0);
+        } else {
+            if (d.nst == 1)
+                run_odd_stage<THREADS, FWD, kPosOnly, E>(d.radix[0], d, 1, 0, land, work, ti.Tv, c0);
+            else
+                run_odd_stage<THREADS, FWD, kPosFirst, E>(d.radix[0], d, 1, 0, land, work, ti.Tv, c0);
+            if (async && d.nst == 1) fence_proxy_async();
+            __syncthreads();
+            s0 = 1;
+        }
+        if (async && i >= 1 && threadIdx.x == 0 && tile + step < d.ntiles) {
+            bulk_wait_read_all();
+            issue_tile_load(d, &a.tm_in, tile + step, land0 + (buf ^ 1) * d.land_stride, &bar[buf ^ 1]);
+        }
+        for (int s = s0; s < d.nst; ++s) {
+            if (s == d.nst - 1)
+                run_odd_stage<THREADS, FWD, kPosLast, E>(d.radix[s], d, d.ns[s], d.twoff[s], land, work, ti.Tv, c0);
+            else
+                run_odd_stage<THREADS, FWD, kPosMid, E>(d.radix[s], d, d.ns[s], d.twoff[s], land, work, ti.Tv, c0);
+            if (async && s == d.nst - 1) fence_proxy_async();
+            __syncthreads();
+        }
+        if (async) {
+            if (threadIdx.x == 0) issue_tile_store(d, &a.tm_out, tile, land);
+        } else {
+            plain_tile_store<THREADS>(d, ti, land);
+            __syncthreads();
+        }
+    }
+    if (async && threadIdx.x == 0) bulk_wait_all();
+}
+
 // A kernel's table entry: its pointer, CTA size and a printable name.
 template <int THREADS>
 LineKernel make_entry(void (*fn)(LineArgs), bool fwd, int lg, int io)
@@ -621,7 +732,16 @@ LineKernel make_entry(void (*fn)(LineArgs), bool fwd, int lg, int io)
 template <int THREADS, bool FWD>
 LineKernel generic_entry()
 {
-    return make_entry<THREADS>(k_fft_generic<THREADS, FWD>, FWD, 0, -1);
+    LineKernel k = make_entry<THREADS>(k_fft_generic<THREADS, FWD>, FWD, 0, -1);
+    k.kind = 1;
+    return k;
+}
+template <bool FWD, int LG2>
+LineKernel mixed_entry()
+{
+    LineKernel k = make_entry<kMixedThreads>(k_fft_mixed<kMixedThreads, FWD, LG2>, FWD, LG2, -1);
+    k.kind = 2;
+    return k;
 }
 
 #endif  // __CUDACC__

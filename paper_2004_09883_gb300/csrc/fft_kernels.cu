@@ -83,7 +83,9 @@ cudaError_t line_occupancy(const LineKernel& k, size_t smem, int* blocks_per_sm)
 void line_kernel_name(const LineKernel& k, char* buf, size_t n)
 {
     static const char* io_names[4] = {"NN", "CC", "NC", "CCP"};
-    if (k.lg > 0)
+    if (k.kind == 2)
+        snprintf(buf, n, "k_fft_mixed<%d,%s,2^%d>", k.threads, k.fwd ? "fwd" : "inv", k.lg);
+    else if (k.kind == 0)
         snprintf(buf, n, "k_fft_p2<%d,%s,L=%d,%s>", k.threads - 32, k.fwd ? "fwd" : "inv", 1 << k.lg,
                  (k.io >= 0 && k.io < 4) ? io_names[k.io] : "?");
     else
