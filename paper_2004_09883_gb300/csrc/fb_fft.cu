@@ -388,7 +388,8 @@ long long many_layout(int count, const long long* lengths, long long* offsets)
 // Batched uneven lengths: one pass (or one four-step pair per L2-sized
 // chunk) per distinct length, each covering all transforms of that length
 // through an offset table.  Single-pass groups are spread over side streams
-// 1..nslots-1; four-step groups share the scratch and run in order on slot 0.
+// 1..nslots-1, four-step groups over all slots, each slot with its own
+// scratch region.
 int schedule_many(fb_fft_plan_s* p, TwiddleBuilder& twb)
 {
     std::vector<std::pair<long long, std::vector<long long>>> groups;  // (L, transform indices)
@@ -403,8 +404,10 @@ int schedule_many(fb_fft_plan_s* p, TwiddleBuilder& twb)
         }
     }
     p->group_names = {"many.single_pass", "many.fourstep.columns", "many.fourstep.rows"};
-    long long scratch_need = 0;
-    int rr = 0;
+    // every slot owns a scratch region, so four-step groups on different
+    // slots overlap; groups on one slot reuse its region in turn
+    std::vector<long long> slot_need(p->nslots, 0);
+    int rr = 0, rr4 = 0;
     for (auto& g : groups) {
         const long long L = g.first;
         const std::vector<long long>& idx = g.second;
@@ -440,7 +443,8 @@ int schedule_many(fb_fft_plan_s* p, TwiddleBuilder& twb)
         const long long cnt = (long long)idx.size();
         const long long cbytes = p->chunk_bytes > 0 ? p->chunk_bytes : fourstep_chunk_bytes();
         const long long chunk = std::max(1LL, std::min(cnt, cbytes / (L * 8)));
-        scratch_need = std::max(scratch_need, chunk * L);
+        const int slot = rr4++ % p->nslots;
+        slot_need[slot] = std::max(slot_need[slot], chunk * L);
         for (long long b0 = 0; b0 < cnt; b0 += chunk) {
             const long long nb = std::min(chunk, cnt - b0);
             const long long at = push_offsets((size_t)b0, (size_t)nb);
@@ -454,7 +458,7 @@ int schedule_many(fb_fft_plan_s* p, TwiddleBuilder& twb)
             if ((N1 & (N1 - 1)) != 0) a.async_ok = false;
             a.src = kBufIn, a.dst = kBufScratch;
             a.group = 1;
-            a.slot = 0;
+            a.slot = slot;
             rc = make_line_pass(r, twb, N2, nb, N1, 1, N2, L, N1, 1, L, false, true, false, p->odd_first,
                                 p->max_lines);
             if (rc != FB_FFT_OK) return rc;
@@ -464,11 +468,22 @@ int schedule_many(fb_fft_plan_s* p, TwiddleBuilder& twb)
             r.group = 2;
             r.last = true;
             r.scale_n = L;
-            r.slot = 0;
+            r.slot = slot;
             p->passes.push_back(a);
             p->passes.push_back(r);
         }
         p->smem_len_max = std::max(p->smem_len_max, std::max(N1, N2));
+    }
+    // scratch regions: slot s starts after the regions of slots < s
+    std::vector<long long> region(p->nslots, 0);
+    long long scratch_need = 0;
+    for (int sl = 0; sl < p->nslots; ++sl) {
+        region[sl] = scratch_need;
+        scratch_need += (slot_need[sl] + 31) & ~31LL;  // keep regions 256-byte aligned
+    }
+    for (PassPlan& q : p->passes) {
+        if (q.dst == kBufScratch) q.dst_off = region[q.slot];
+        if (q.src == kBufScratch) q.src_off = region[q.slot];
     }
     p->scratch_bytes = (size_t)scratch_need * sizeof(float2);
     p->tw_elems = std::max(2LL, twb.total);
@@ -492,6 +507,11 @@ int check_schedule(const fb_fft_plan_s* p)
             if (q.dst != kBufOut || q.off_out_idx + need > nofs) return FB_FFT_ERR_INVALID_ARG;
         }
         if (!p->many && (q.off_in_idx >= 0 || q.off_out_idx >= 0)) return FB_FFT_ERR_INVALID_ARG;
+        // a four-step pass's scratch window (O transforms of L*C values) lies inside the scratch
+        const long long scratch_elems = (long long)(p->scratch_bytes / sizeof(float2));
+        const long long window = O * (long long)q.d.L * q.d.C;
+        if (q.dst == kBufScratch && q.dst_off + window > scratch_elems) return FB_FFT_ERR_INVALID_ARG;
+        if (q.src == kBufScratch && q.src_off + window > scratch_elems) return FB_FFT_ERR_INVALID_ARG;
         if (q.slot < 0 || q.slot >= p->nslots) return FB_FFT_ERR_INVALID_ARG;
     }
     return FB_FFT_OK;
