@@ -177,6 +177,23 @@ int fb_fft_check(fb_fft_plan_t plan);
  */
 int fb_fft_debug_inject_timeout(fb_fft_plan_t plan, int enable);
 
+/*
+ * fb_fft_offload_decide -- the paper's verification step for one function
+ * block (Sec. 3.4 / Sec. 4.2: each replaceable block is measured offloaded
+ * and not offloaded in the verification environment, and offloaded only if
+ * that is faster).  Times `reps` calls of the caller's own CPU routine
+ * cpu(ctx, host_in, host_out, direction) against `reps` calls of
+ * fb_fft_exec_host(plan, host_in, host_out, direction) (host->device copy,
+ * transform, device->host copy), after one untimed call of each, with a
+ * monotonic host clock; writes the mean times per call and *use_gpu = 1 when
+ * the device path is faster.  host_out is overwritten.  The library never
+ * runs a CPU transform of its own: `cpu` is the caller's block.
+ * Errors: BAD_PLAN, INVALID_ARG, and those of fb_fft_exec_host.
+ */
+typedef void (*fb_fft_cpu_block)(void* ctx, const void* host_in, void* host_out, int direction);
+int fb_fft_offload_decide(fb_fft_plan_t plan, fb_fft_cpu_block cpu, void* ctx, const void* host_in, void* host_out,
+                          int direction, int reps, int* use_gpu, double* cpu_ms, double* gpu_ms);
+
 /* fb_fft_set_stream -- change the stream later execs launch on. */
 int fb_fft_set_stream(fb_fft_plan_t plan, void* stream);
 

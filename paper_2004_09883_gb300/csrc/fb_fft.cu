@@ -15,6 +15,7 @@
 
 #include <algorithm>
 #include <atomic>
+#include <chrono>
 #include <cstdint>
 #include <cstdlib>
 #include <cstdio>
@@ -1163,6 +1164,28 @@ int fb_fft_debug_inject_timeout(fb_fft_plan_t plan, int enable)
 {
     if (!plan_ok(plan)) return FB_FFT_ERR_BAD_PLAN;
     plan->debug_timeout = enable != 0;
+    return FB_FFT_OK;
+}
+
+int fb_fft_offload_decide(fb_fft_plan_t plan, fb_fft_cpu_block cpu, void* ctx, const void* host_in, void* host_out,
+                          int direction, int reps, int* use_gpu, double* cpu_ms, double* gpu_ms)
+{
+    if (!plan_ok(plan)) return FB_FFT_ERR_BAD_PLAN;
+    if (!cpu || !host_in || !host_out || reps < 1 || !use_gpu || !cpu_ms || !gpu_ms) return FB_FFT_ERR_INVALID_ARG;
+    if (direction != FB_FFT_FORWARD && direction != FB_FFT_INVERSE) return FB_FFT_ERR_INVALID_ARG;
+    using clk = std::chrono::steady_clock;
+    cpu(ctx, host_in, host_out, direction);  // untimed first call of each side
+    int rc = fb_fft_exec_host(plan, host_in, host_out, direction);
+    if (rc != FB_FFT_OK) return rc;
+    auto t0 = clk::now();
+    for (int r = 0; r < reps; ++r) cpu(ctx, host_in, host_out, direction);
+    auto t1 = clk::now();
+    for (int r = 0; r < reps && rc == FB_FFT_OK; ++r) rc = fb_fft_exec_host(plan, host_in, host_out, direction);
+    auto t2 = clk::now();
+    if (rc != FB_FFT_OK) return rc;
+    *cpu_ms = std::chrono::duration<double, std::milli>(t1 - t0).count() / reps;
+    *gpu_ms = std::chrono::duration<double, std::milli>(t2 - t1).count() / reps;
+    *use_gpu = *gpu_ms < *cpu_ms ? 1 : 0;
     return FB_FFT_OK;
 }
 

@@ -52,6 +52,9 @@ class ManyOpts(ctypes.Structure):
         return {f: getattr(self, f) for f, _ in self._fields_}
 
 
+CPU_BLOCK = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int)
+
+
 if not os.path.exists(LIB_PATH):
     raise ImportError(f"{LIB_PATH} is missing: build it with __graft_entry__.build() "
                       "(python -m paper_2004_09883_gb300.build)")
@@ -82,6 +85,8 @@ _sig = {
     "fb_fft_many_layout": (_ll, [_int, ctypes.POINTER(_ll), ctypes.POINTER(_ll)]),
     "fb_fft_plan_many": (_int, [ctypes.POINTER(_vp), _int, ctypes.POINTER(_ll), ctypes.c_uint, _vp]),
     "fb_fft_set_graph": (_int, [_vp, _int]),
+    "fb_fft_offload_decide": (_int, [_vp, CPU_BLOCK, _vp, _vp, _vp, _int, _int, ctypes.POINTER(_int),
+                                     ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]),
     "fb_fft_plan_many_query": (_int, [_int, ctypes.POINTER(_ll), ctypes.c_uint, ctypes.POINTER(Info)]),
     "fb_fft_plan_many_ex": (_int, [ctypes.POINTER(_vp), _int, ctypes.POINTER(_ll), ctypes.c_uint, _vp,
                                    ctypes.POINTER(ManyOpts)]),
@@ -248,6 +253,26 @@ class Plan:
         _check(lib.fb_fft_exec_host(self._h, _vp(x.ctypes.data), _vp(out.ctypes.data), int(direction)),
                "fb_fft_exec_host")
         return out
+
+    def offload_decide(self, cpu_block, x: np.ndarray, direction: int = FORWARD, reps: int = 3) -> dict:
+        """Time the caller's CPU routine ``cpu_block(x_in, x_out, direction)``
+        (numpy complex64 arrays) against this plan's host-array GPU call and
+        say which is faster (the verification step)."""
+        x = np.ascontiguousarray(x, dtype=np.complex64)
+        out = np.empty_like(x)
+        n = x.size
+
+        def tramp(_ctx, src, dst, d):
+            a = np.ctypeslib.as_array(ctypes.cast(src, ctypes.POINTER(ctypes.c_float)), shape=(2 * n,))
+            b = np.ctypeslib.as_array(ctypes.cast(dst, ctypes.POINTER(ctypes.c_float)), shape=(2 * n,))
+            cpu_block(a.view(np.complex64), b.view(np.complex64), d)
+
+        cb = CPU_BLOCK(tramp)
+        use, cms, gms = _int(), ctypes.c_double(), ctypes.c_double()
+        _check(lib.fb_fft_offload_decide(self._h, cb, None, _vp(x.ctypes.data), _vp(out.ctypes.data), int(direction),
+                                         int(reps), ctypes.byref(use), ctypes.byref(cms), ctypes.byref(gms)),
+               "fb_fft_offload_decide")
+        return {"use_gpu": bool(use.value), "cpu_ms": cms.value, "gpu_ms": gms.value}
 
     def debug_inject_timeout(self, enable: bool = True) -> None:
         """Test hook: make the plan's bounded device waits run out."""
