@@ -9,7 +9,7 @@ beside it.  Four input/output buffer pairs (512 MiB) rotate between steps so
 the working set exceeds the 126 MB L2.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
-                  [--workload 3d|1d4096|1d4096L|1d2p20|uneven]
+                  [--workload 3d|1d4096|1d4096L|1d2p20|uneven|serving]
 
 Under torchrun each rank runs its own replica (independent transforms, no
 collective on the data path); rank 0 prints one JSON line.  --impl reference
@@ -47,6 +47,10 @@ WORKLOADS = {
                    lengths=(4096, 64, 65536)),
     "1d2p20": dict(name="1d_c2c_2p20_batch32_fwd", dims=[1 << 20], batch=32,
                    seed=inputs.seed_for(inputs.WORKLOAD_1D_2P20x32), dist="normal", inverse=False),
+    "serving": dict(name="serving_mix_2000_requests_1d_2d_3d_poisson", dims=None, batch=1,
+                    seed=inputs.seed_for(inputs.WORKLOAD_SERVING), dist="uniform", inverse=False,
+                    serving=dict(requests=2000, host_requests=600, slots=8, hbm_cap=40 * 10 ** 9,
+                                 fractions=[0.1, 0.25, 0.5, 0.75, 0.9, 1.1])),
 }
 KERNEL_SOURCES = ["paper_2004_09883_gb300/csrc/fft_device.cuh", "paper_2004_09883_gb300/csrc/fb_internal.h",
                   "paper_2004_09883_gb300/csrc/fb_fft.cu"]
@@ -208,18 +212,27 @@ def oracle_sample(wl: dict, budget_s: float, threads: int) -> dict:
     return {"value": bytes_step * reps / t_total / 1e9, "seconds": t_total, "steps": reps}
 
 
+def workload_shapes(wl: dict) -> list[tuple]:
+    """Transform shapes of a many-transform workload, in order."""
+    if wl.get("serving"):
+        from paper_2004_09883_gb300 import serving
+        return serving.request_mix(wl["serving"]["requests"], wl["seed"])
+    return [(int(n),) for n in uneven_lengths(wl)]
+
+
 def oracle_uneven_sample(wl: dict, budget_s: float, threads: int) -> dict:
-    """Time the oracle on the uneven workload's transforms, in order, until
-    the budget is spent (at least one); GB/s over the transforms done."""
+    """Time the oracle on a many-transform workload's transforms, in order,
+    until the budget is spent (at least one); GB/s over the transforms done."""
     import oracle
 
-    lens = uneven_lengths(wl)
+    shapes = workload_shapes(wl)
     done_bytes, t_total, k = 0.0, 0.0, 0
-    while k < len(lens) and (k == 0 or t_total < budget_s):
-        n = int(lens[k])
+    while k < len(shapes) and (k == 0 or t_total < budget_s):
+        dims = list(shapes[k])
+        n = int(np.prod(dims))
         x = inputs.uniform_c64((n,), wl["seed"] + k).astype(np.complex128)
         t = time.perf_counter()
-        oracle.fft(x, [n], -1, False, threads)
+        oracle.fft(x, dims, -1, False, threads)
         t_total += time.perf_counter() - t
         done_bytes += 2 * 8.0 * n
         k += 1
@@ -242,14 +255,15 @@ def run_reference(args, wl: dict) -> None:
     if rank != 0:
         return
     threads = len(os.sched_getaffinity(0))
-    if wl.get("lengths"):  # uneven batch: each step a bounded sample of its transforms
+    if wl.get("lengths") or wl.get("serving"):  # many transforms: each step a bounded sample of them
         per_step = max(0.5, 150.0 / max(1, args.steps + args.warmup))
         for _ in range(args.warmup):
             oracle_uneven_sample(wl, per_step, threads)
         runs = [oracle_uneven_sample(wl, per_step, threads) for _ in range(args.steps)]
         secs = sum(r["seconds"] for r in runs)
         value = sum(r["value"] * r["seconds"] for r in runs) / secs
-        desc = (f"first {runs[0]['transforms']} of {wl['batch']} transforms of {wl['name']} per step, FP64 oracle, "
+        total = len(workload_shapes(wl))
+        desc = (f"first {runs[0]['transforms']} of {total} transforms of {wl['name']} per step, FP64 oracle, "
                 f"{threads} threads on {cpu_model()}")
         line = {"impl": "reference", "metric": METRIC, "value": round(value, 4), "unit": "GB/s", "n_gpus": world,
                 "steps": args.steps, "warmup": args.warmup, "ms_per_step": secs / args.steps * 1e3,
@@ -580,6 +594,125 @@ def run_gpu_many(args, wl: dict) -> None:
         dist.destroy_process_group()
 
 
+def run_gpu_serving(args, wl: dict) -> None:
+    """Request server against the plain per-call path on one arrival trace:
+    saturation throughput (all requests queued at t=0), then Poisson arrivals
+    at fractions of the plain path's saturation rate, p50/p99 latency of both.
+    Device-resident requests (inputs already in HBM, latency = arrival ->
+    completion seen by the host), plus a host-array variant (pinned host
+    buffers, copies through the server's staging)."""
+    import torch
+
+    world, rank, local = dist_setup()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+    from paper_2004_09883_gb300 import build as fbbuild
+    fbbuild.build()
+    from paper_2004_09883_gb300 import fbfft, serving
+
+    cfg = wl["serving"]
+    seed = wl["seed"] + 1000 * replica_rep(rank, 0)
+    shapes = serving.request_mix(cfg["requests"], seed)
+    w = serving.Workload(shapes, seed)
+    hshapes = shapes[:cfg["host_requests"]]
+    wh = serving.Workload(hshapes, seed, host=True)
+    srv = fbfft.Server(slots=cfg["slots"], hbm_cap_bytes=cfg["hbm_cap"])
+    for s in set(shapes):
+        srv.prepare(list(s))
+    plans = serving.plain_plans(w)
+    zero, zero_h = np.zeros(len(shapes)), np.zeros(len(hshapes))
+    for _ in range(args.warmup):  # untimed passes: plans, staging, allocator, caches
+        serving.run_served(srv, w, zero)
+        serving.run_plain(plans, w, zero)
+    serving.run_served(srv, wh, zero_h, host_io=True)
+    serving.run_plain(plans, wh, zero_h, host_io=True)
+
+    def barrier():
+        torch.cuda.synchronize(dev)
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize(dev)
+
+    clocks = ClockSampler(local) if rank == 0 else None
+    barrier()
+    wall0 = time.time()
+    l0 = fbfft.launch_count()
+    sat = [serving.run_served(srv, w, zero) for _ in range(args.steps)]
+    launches = (fbfft.launch_count() - l0) // max(1, args.steps)
+    wall1 = time.time()
+    sat_plain = [serving.run_plain(plans, w, zero) for _ in range(max(1, min(args.steps, 3)))]
+    barrier()
+    best = max(sat, key=lambda r: r["throughput_req_s"])
+    best_plain = max(sat_plain, key=lambda r: r["throughput_req_s"])
+    rate_plain = best_plain["throughput_req_s"]
+    sweep = []
+    for k, f in enumerate(cfg["fractions"]):
+        arr = serving.poisson_arrivals(len(shapes), f * rate_plain, seed + 17 + k)
+        a = serving.run_served(srv, w, arr)
+        b = serving.run_plain(plans, w, arr)
+        sweep.append({"rate_frac_of_plain_saturation": f, "rate_req_s": round(f * rate_plain, 1),
+                      "served": {q: round(a[q], 4) for q in ("p50_ms", "p99_ms", "throughput_req_s")},
+                      "plain": {q: round(b[q], 4) for q in ("p50_ms", "p99_ms", "throughput_req_s")}})
+    host_sat = serving.run_served(srv, wh, zero_h, host_io=True)
+    host_plain = serving.run_plain(plans, wh, zero_h, host_io=True)
+    arr = serving.poisson_arrivals(len(hshapes), 0.5 * host_plain["throughput_req_s"], seed + 99)
+    host_half = serving.run_served(srv, wh, arr, host_io=True)
+    host_half_plain = serving.run_plain(plans, wh, arr, host_io=True)
+    st = srv.stats()
+    clk = clocks.summary(wall0, wall1) if clocks else None
+    if clocks:
+        clocks.stop()
+    value = max_over_ranks(best["throughput_gbs"], dist, dev)
+    if rank == 0:
+        nb = w.bytes_moved()
+        kinds = {1: 0, 2: 0, 3: 0}
+        for s in shapes:
+            kinds[len(s)] += 1
+        line = {
+            "metric": METRIC, "value": round(value * world, 3), "unit": "GB/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": round(best["wall_s"] * 1e3, 3), "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": wl["name"], "requests": len(shapes), "rank_mix": kinds,
+                       "distinct_shapes": len(set(shapes)), "elements": int(sum(w.n)),
+                       "slots": cfg["slots"], "hbm_cap_bytes": cfg["hbm_cap"],
+                       "step": "one replay of the whole request list, all arriving at t=0",
+                       "l2": f"{nb / 2 / 2 ** 30:.1f} GiB of distinct inputs per step > 126 MB L2",
+                       "parallelism": "replicas" if world > 1 else "single GPU"},
+            "saturation": {"served_req_s": round(best["throughput_req_s"], 1),
+                           "plain_req_s": round(rate_plain, 1),
+                           "served_gbs": round(best["throughput_gbs"], 2),
+                           "plain_gbs": round(best_plain["throughput_gbs"], 2),
+                           "speedup_vs_plain": round(best["throughput_req_s"] / rate_plain, 3)},
+            "sweep_device_resident": sweep,
+            "host_arrays": {"requests": len(hshapes),
+                            "saturation_req_s": {"served": round(host_sat["throughput_req_s"], 1),
+                                                 "plain": round(host_plain["throughput_req_s"], 1)},
+                            "half_plain_rate": {"served_p50_ms": round(host_half["p50_ms"], 4),
+                                                "served_p99_ms": round(host_half["p99_ms"], 4),
+                                                "plain_p50_ms": round(host_half_plain["p50_ms"], 4),
+                                                "plain_p99_ms": round(host_half_plain["p99_ms"], 4)}},
+            "server_stats": {k: st[k] for k in ("plans", "plan_builds", "arena_peak", "max_in_flight")},
+            "gpu_launches": int(launches), "clocks": clk, "kernel_hash": kernel_hash(),
+            "cpu_baseline": (lambda cb: {
+                "value": round(cb["value"], 4), "unit": "GB/s", "cores": len(os.sched_getaffinity(0)),
+                "kind": "oracle", "sample": f"first {cb['transforms']} requests of the mix by the FP64 oracle, "
+                                            f"one after another, in {cb['seconds']:.1f} s on {cpu_model()}"})(
+                oracle_uneven_sample(wl, float(args.cpu_budget), len(os.sched_getaffinity(0)))),
+        }
+        print(json.dumps(line), flush=True)
+    srv.close()
+    for p in plans.values():
+        p.close()
+    if dist is not None:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -598,6 +731,8 @@ def main():
         run_reference(args, wl)
     elif wl.get("lengths"):
         run_gpu_many(args, wl)
+    elif wl.get("serving"):
+        run_gpu_serving(args, wl)
     else:
         run_gpu(args, wl)
 

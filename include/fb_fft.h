@@ -40,7 +40,9 @@ typedef enum fb_fft_status {
     FB_FFT_ERR_CUDA = -4,             /* a CUDA runtime call or kernel launch failed */
     FB_FFT_ERR_TIMEOUT = -5,          /* a bounded device-side wait gave up */
     FB_FFT_ERR_BAD_PLAN = -6,         /* null or destroyed plan handle */
-    FB_FFT_ERR_NO_DEVICE = -7         /* no CUDA device is visible */
+    FB_FFT_ERR_NO_DEVICE = -7,        /* no CUDA device is visible */
+    FB_FFT_ERR_CANCELLED = -8,        /* a server request was cancelled before it ran */
+    FB_FFT_ERR_OVER_BUDGET = -9       /* a server request can never fit the device-memory budget */
 } fb_fft_status;
 
 /* Exponent sign of the transform kernel exp(s*2*pi*i*n*k/N). */
@@ -276,6 +278,112 @@ long long fb_fft_launch_count(void);
  * Errors: INVALID_ARG, ALLOC, CUDA, NO_DEVICE.
  */
 int fb_fft_twiddles(long long d, long long count, float* host_out);
+
+/*
+ * Serving: continuous batching of offload calls.
+ *
+ * The paper replaces a function block of an application that keeps running
+ * in its production environment (Sec. 3.1, Sec. 5.1(c)); when many callers
+ * offload transforms of mixed shapes to one GPU, calling fb_fft_plan/exec per
+ * call serialises them.  A server keeps plans resident (one per shape, shared
+ * by all slots: twiddle tables are read-only) and runs each admitted request
+ * on one of `slots` CUDA streams, so the copies and kernels of requests that
+ * arrive while others run overlap on the device.  A request is admitted, in
+ * arrival (FIFO) order, as soon as a slot is free and its device bytes fit in
+ * the server's memory budget: an arena of `hbm_cap_bytes` reserved once at
+ * creation, from which each request takes its four-step scratch and, for
+ * host-array requests, one staging buffer; both return to the arena when the
+ * request completes.  Completion is observed with a CUDA event per slot; every
+ * submit and poll first retires finished requests and admits waiting ones,
+ * with no batch barrier.  Nothing blocks except poll with wait != 0 and drain.
+ *
+ * Not thread-safe: one host thread drives a server.  The device current at
+ * fb_fft_server_create must be current on every later call.
+ */
+typedef struct fb_fft_server_s* fb_fft_server_t;
+
+/* One finished request.  Times are seconds on the server's monotonic clock
+ * (fb_fft_server_clock): t_submit at fb_fft_server_submit, t_admit when it
+ * went to a slot, t_done when a submit/poll/drain saw its completion event. */
+typedef struct fb_fft_server_done {
+    long long tag;     /* the caller's tag from submit */
+    int status;        /* FB_FFT_OK, FB_FFT_ERR_CANCELLED, _TIMEOUT or _CUDA */
+    int slot;          /* stream slot it ran on, -1 if it never ran */
+    double t_submit, t_admit, t_done;
+} fb_fft_server_done;
+
+typedef struct fb_fft_server_stats {
+    long long submitted, completed, rejected, cancelled;
+    long long pending, in_flight;          /* now */
+    long long plans, plan_builds, plan_bytes; /* resident plans, plans built, their device bytes */
+    long long arena_bytes, arena_in_use, arena_peak;
+    long long max_in_flight;               /* most requests on slots at once */
+    int slots;
+    int reserved;
+} fb_fft_server_stats;
+
+/*
+ * fb_fft_server_create
+ *   srv            out: new handle, owned by the caller until fb_fft_server_destroy.
+ *   slots          1..64 concurrent requests (one CUDA stream each).
+ *   hbm_cap_bytes  >= 0: device bytes the server may hold for requests (one
+ *                  cudaMalloc at creation; 0 admits only requests that need
+ *                  no scratch and no staging).
+ *   max_plans      >= 1: resident plans kept; the least recently used idle
+ *                  plan is freed beyond that.
+ * Errors: INVALID_ARG, ALLOC, CUDA, NO_DEVICE.
+ */
+int fb_fft_server_create(fb_fft_server_t* srv, int slots, long long hbm_cap_bytes, int max_plans);
+
+/*
+ * fb_fft_server_submit -- queue one transform (rank, dims, batch, flags as
+ * fb_fft_plan; direction as fb_fft_exec).
+ *   in, out   host_io == 0: device pointers (8-byte aligned, equal or not
+ *             overlapping), owned by the caller and untouched by the caller
+ *             until the request is reported done.
+ *             host_io != 0: host pointers (pinned memory gives asynchronous
+ *             copies; in == out is allowed); the server copies through an
+ *             arena staging buffer.
+ *   tag       caller's identifier, reported back by poll.
+ * A plan for a new shape is built here, synchronously (charged to this call;
+ * create plans ahead with fb_fft_server_prepare).  Returns OK when queued;
+ * OVER_BUDGET when the request needs more than the whole arena; the plan
+ * errors (INVALID_ARG, UNSUPPORTED_SIZE, ALLOC, CUDA) otherwise.  A rejected
+ * request is counted in stats.rejected and never reported by poll.
+ */
+int fb_fft_server_submit(fb_fft_server_t srv, int rank, const long long* dims, long long batch, unsigned flags,
+                         int direction, const void* in, void* out, int host_io, long long tag);
+
+/* fb_fft_server_prepare -- build (or touch) the resident plan of a shape now. */
+int fb_fft_server_prepare(fb_fft_server_t srv, int rank, const long long* dims, long long batch, unsigned flags);
+
+/*
+ * fb_fft_server_poll -- retire finished requests, admit waiting ones, then
+ * move up to `capacity` finished requests (oldest first) into done[] and set
+ * *n_done.  wait != 0 and nothing finished yet: block until the oldest request
+ * on a slot completes (returns at once when nothing is queued or running).
+ * Errors: INVALID_ARG, CUDA.
+ */
+int fb_fft_server_poll(fb_fft_server_t srv, int wait, fb_fft_server_done* done, int capacity, int* n_done);
+
+/* fb_fft_server_drain -- block until nothing is queued or running; finished
+ * requests stay available to poll. */
+int fb_fft_server_drain(fb_fft_server_t srv);
+
+/* fb_fft_server_cancel -- drop a queued (not yet admitted) request; poll then
+ * reports it with FB_FFT_ERR_CANCELLED.  A request already on a slot cannot be
+ * cancelled: INVALID_ARG, as for an unknown tag. */
+int fb_fft_server_cancel(fb_fft_server_t srv, long long tag);
+
+/* fb_fft_server_clock -- seconds since the server was created (the clock of
+ * fb_fft_server_done), or -1 for a bad handle. */
+double fb_fft_server_clock(fb_fft_server_t srv);
+
+int fb_fft_server_stats_get(fb_fft_server_t srv, fb_fft_server_stats* stats);
+
+/* fb_fft_server_destroy -- wait for running requests, drop queued ones, free
+ * plans, arena and streams; NULL is a no-op. */
+int fb_fft_server_destroy(fb_fft_server_t srv);
 
 /*
  * fb_fft_exec_1d_noalloc -- batched 1-D transform that allocates nothing.

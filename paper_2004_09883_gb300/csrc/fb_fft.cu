@@ -26,6 +26,7 @@
 #include <cudaTypedefs.h>
 
 #include "fb_fft.h"
+#include "fb_host.h"
 #include "fb_internal.h"
 #include "fft_p2.cuh"
 
@@ -319,6 +320,7 @@ struct fb_fft_plan_s {
     long long tw_elems = 0;
     float2* scratch = nullptr;
     size_t scratch_bytes = 0;
+    bool ext_scratch = false;  // scratch supplied per exec (server plans)
     float2* staging = nullptr;
     size_t staging_bytes = 0;
     int* err = nullptr;  // device error word written by bounded waits
@@ -626,7 +628,7 @@ int build_plan(fb_fft_plan_s* p)
             q.d.ptw_hi = p->tw + reinterpret_cast<long long>(q.d.ptw_hi);
         }
     }
-    if (p->scratch_bytes) {
+    if (p->scratch_bytes && !p->ext_scratch) {
         if (cudaMalloc(&p->scratch, p->scratch_bytes) != cudaSuccess) {
             cudaGetLastError();
             p->scratch = nullptr;
@@ -701,14 +703,15 @@ int encode_view(CUtensorMap* tm, const float2* base, long long C, long long L, l
 // Launch one pass of a plan on `stream` (profiling events, when on, go on
 // the same stream).
 int launch_pass(fb_fft_plan_s* p, const PassPlan& q, const float2* in, float2* out, bool fwd, cudaStream_t stream,
-                bool count)
+                bool count, float2* scratch, int* err)
 {
     LineArgs args;
     std::memset(&args, 0, sizeof(args));
     args.d = q.d;
     PassDesc& d = args.d;
-    const float2* src = q.src == kBufIn ? in : (q.src == kBufOut ? out : p->scratch);
-    float2* dst = q.dst == kBufOut ? out : p->scratch;
+    const float2* src = q.src == kBufIn ? in : (q.src == kBufOut ? out : scratch);
+    float2* dst = q.dst == kBufOut ? out : scratch;
+    if (err) d.err = err;
     d.in = src + q.src_off;
     d.out = dst + q.dst_off;
     d.async_io = 0;
@@ -763,7 +766,7 @@ int launch_many(fb_fft_plan_s* p, cudaStream_t origin, const float2* in, float2*
     FB_CK(cudaEventRecord(p->fork_join[0], origin));
     for (int sl = 0; sl < p->nslots; ++sl) FB_CK(cudaStreamWaitEvent(p->side[sl], p->fork_join[0], 0));
     for (const PassPlan& q : p->passes) {
-        const int rc = launch_pass(p, q, in, out, fwd, p->side[q.slot], count);
+        const int rc = launch_pass(p, q, in, out, fwd, p->side[q.slot], count, p->scratch, nullptr);
         if (rc != FB_FFT_OK) return rc;
     }
     for (int sl = 0; sl < p->nslots; ++sl) {
@@ -812,23 +815,115 @@ int exec_many(fb_fft_plan_s* p, const float2* in, float2* out, int direction)
 
 long long plan_elems(const fb_fft_plan_s* p) { return p->many ? p->total : p->N * p->batch; }
 
-int exec_device(fb_fft_plan_s* p, const float2* in, float2* out, int direction)
+int validate(int rank, const long long* dims, long long batch, unsigned flags, long long* N_out)
 {
-    if (p->many) return exec_many(p, in, out, direction);
+    if (rank < 1 || rank > 3 || !dims || batch < 0 || (flags & ~FB_FFT_SCALE_INV_N)) return FB_FFT_ERR_INVALID_ARG;
+    long long N = 1;
+    for (int d = 0; d < rank; ++d) {
+        if (dims[d] < 1) return FB_FFT_ERR_INVALID_ARG;
+        if (!is_smooth(dims[d])) return FB_FFT_ERR_UNSUPPORTED_SIZE;
+        if (rank > 1 && dims[d] > FB_FFT_MAX_SMEM_LEN) return FB_FFT_ERR_UNSUPPORTED_SIZE;
+        if (rank == 1 && dims[d] > FB_FFT_MAX_1D_LEN) return FB_FFT_ERR_UNSUPPORTED_SIZE;
+        N *= dims[d];
+    }
+    if (batch > 0 && N > (1LL << 58) / batch) return FB_FFT_ERR_UNSUPPORTED_SIZE;
+    *N_out = N;
+    return FB_FFT_OK;
+}
+
+// A regular plan's passes on `stream`, with the four-step intermediate in
+// `scratch` and device-wait errors recorded in `err` (nullptr: the plan's).
+int exec_lines(fb_fft_plan_s* p, const float2* in, float2* out, int direction, cudaStream_t stream, float2* scratch,
+               int* err)
+{
     const bool fwd = direction == FB_FFT_FORWARD;
     const size_t bytes = (size_t)(p->N * p->batch) * sizeof(float2);
     if (p->passes.empty()) {  // every axis has length 1: the DFT is the identity
-        if (bytes && in != out) FB_CK(cudaMemcpyAsync(out, in, bytes, cudaMemcpyDeviceToDevice, p->stream));
+        if (bytes && in != out) FB_CK(cudaMemcpyAsync(out, in, bytes, cudaMemcpyDeviceToDevice, stream));
         return FB_FFT_OK;
     }
     for (const PassPlan& q : p->passes) {
-        const int rc = launch_pass(p, q, in, out, fwd, p->stream, true);
+        const int rc = launch_pass(p, q, in, out, fwd, stream, true, scratch, err);
         if (rc != FB_FFT_OK) return rc;
     }
     return FB_FFT_OK;
 }
 
+int exec_device(fb_fft_plan_s* p, const float2* in, float2* out, int direction)
+{
+    if (p->many) return exec_many(p, in, out, direction);
+    return exec_lines(p, in, out, direction, p->stream, p->scratch, nullptr);
+}
+
+// Plan construction shared by fb_fft_plan and the server; ext_scratch plans
+// allocate no scratch (the caller passes one to exec_lines).
+int plan_new(fb_fft_plan_s** out, int rank, const long long* dims, long long batch, unsigned flags,
+             cudaStream_t stream, bool ext_scratch)
+{
+    *out = nullptr;
+    long long N = 1;
+    int rc0 = validate(rank, dims, batch, flags, &N);
+    if (rc0 != FB_FFT_OK) return rc0;
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) {
+        cudaGetLastError();
+        return FB_FFT_ERR_NO_DEVICE;
+    }
+    fb_fft_plan_s* p = new (std::nothrow) fb_fft_plan_s();
+    if (!p) return FB_FFT_ERR_ALLOC;
+    cudaGetDevice(&p->device);
+    p->rank = rank;
+    for (int d = 0; d < rank; ++d) p->dims[d] = dims[d];
+    p->batch = batch;
+    p->flags = flags;
+    p->stream = stream;
+    p->N = N;
+    p->ext_scratch = ext_scratch;
+    int rc = build_plan(p);
+    if (rc != FB_FFT_OK) {
+        free_plan(p);
+        return rc;
+    }
+    *out = p;
+    return FB_FFT_OK;
+}
+
 }  // namespace
+
+namespace fbfft {
+namespace host {
+
+int plan_create(fb_fft_plan_t* out, int rank, const long long* dims, long long batch, unsigned flags,
+                cudaStream_t build_stream, bool ext_scratch)
+{
+    if (!out) return FB_FFT_ERR_INVALID_ARG;
+    return plan_new(out, rank, dims, batch, flags, build_stream, ext_scratch);
+}
+
+long long plan_scratch_bytes(fb_fft_plan_t p) { return (long long)p->scratch_bytes; }
+
+long long plan_table_bytes(fb_fft_plan_t p) { return p->tw_elems * (long long)sizeof(float2) + 16 * sizeof(int); }
+
+long long plan_io_bytes(fb_fft_plan_t p) { return plan_elems(p) * (long long)sizeof(float2); }
+
+int plan_exec_on(fb_fft_plan_t p, const void* in, void* out, int direction, cudaStream_t stream, void* scratch,
+                 int* err)
+{
+    if (!plan_ok(p) || p->many) return FB_FFT_ERR_BAD_PLAN;
+    if (p->scratch_bytes && !scratch && p->ext_scratch) return FB_FFT_ERR_INVALID_ARG;
+    float2* s = p->ext_scratch ? (float2*)scratch : p->scratch;
+    return exec_lines(p, (const float2*)in, (float2*)out, direction, stream, s, err);
+}
+
+void plan_free(fb_fft_plan_t p)
+{
+    if (plan_ok(p)) free_plan(p);
+}
+
+int fail(cudaError_t e, const char* what) { return cuda_fail(e, what); }
+
+}  // namespace host
+}  // namespace fbfft
 
 extern "C" {
 
@@ -845,6 +940,8 @@ const char* fb_fft_status_string(int status)
     case FB_FFT_ERR_TIMEOUT: return "device wait timed out";
     case FB_FFT_ERR_BAD_PLAN: return "bad plan handle";
     case FB_FFT_ERR_NO_DEVICE: return "no CUDA device";
+    case FB_FFT_ERR_CANCELLED: return "request cancelled";
+    case FB_FFT_ERR_OVER_BUDGET: return "request exceeds the server's device-memory budget";
     default: return "unknown status";
     }
 }
@@ -862,22 +959,6 @@ int fb_fft_split(long long n, long long* n1, long long* n2)
 {
     if (!n1 || !n2) return FB_FFT_ERR_INVALID_ARG;
     return split_fourstep(n, n1, n2);
-}
-
-static int validate(int rank, const long long* dims, long long batch, unsigned flags, long long* N_out)
-{
-    if (rank < 1 || rank > 3 || !dims || batch < 0 || (flags & ~FB_FFT_SCALE_INV_N)) return FB_FFT_ERR_INVALID_ARG;
-    long long N = 1;
-    for (int d = 0; d < rank; ++d) {
-        if (dims[d] < 1) return FB_FFT_ERR_INVALID_ARG;
-        if (!is_smooth(dims[d])) return FB_FFT_ERR_UNSUPPORTED_SIZE;
-        if (rank > 1 && dims[d] > FB_FFT_MAX_SMEM_LEN) return FB_FFT_ERR_UNSUPPORTED_SIZE;
-        if (rank == 1 && dims[d] > FB_FFT_MAX_1D_LEN) return FB_FFT_ERR_UNSUPPORTED_SIZE;
-        N *= dims[d];
-    }
-    if (batch > 0 && N > (1LL << 58) / batch) return FB_FFT_ERR_UNSUPPORTED_SIZE;
-    *N_out = N;
-    return FB_FFT_OK;
 }
 
 int fb_fft_plan_query(int rank, const long long* dims, long long batch, unsigned flags, fb_fft_info* info)
@@ -910,31 +991,7 @@ int fb_fft_plan(fb_fft_plan_t* plan, int rank, const long long* dims, long long 
                 void* stream)
 {
     if (!plan) return FB_FFT_ERR_INVALID_ARG;
-    *plan = nullptr;
-    long long N = 1;
-    int rc0 = validate(rank, dims, batch, flags, &N);
-    if (rc0 != FB_FFT_OK) return rc0;
-    int ndev = 0;
-    if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) {
-        cudaGetLastError();
-        return FB_FFT_ERR_NO_DEVICE;
-    }
-    fb_fft_plan_s* p = new (std::nothrow) fb_fft_plan_s();
-    if (!p) return FB_FFT_ERR_ALLOC;
-    cudaGetDevice(&p->device);
-    p->rank = rank;
-    for (int d = 0; d < rank; ++d) p->dims[d] = dims[d];
-    p->batch = batch;
-    p->flags = flags;
-    p->stream = (cudaStream_t)stream;
-    p->N = N;
-    int rc = build_plan(p);
-    if (rc != FB_FFT_OK) {
-        free_plan(p);
-        return rc;
-    }
-    *plan = p;
-    return FB_FFT_OK;
+    return plan_new(plan, rank, dims, batch, flags, (cudaStream_t)stream, false);
 }
 
 long long fb_fft_many_layout(int count, const long long* lengths, long long* offsets)

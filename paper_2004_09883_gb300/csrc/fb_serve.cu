@@ -1,0 +1,529 @@
+// fb_serve.cu -- request server of the FFT function block: continuous
+// batching of offload calls over a fixed set of stream slots, admission by a
+// device-memory budget, resident plans (C ABI in include/fb_fft.h).
+//
+// Life of a request:
+//   submit   resolve the resident plan of its shape (build on a miss), size
+//            its device needs (four-step scratch + staging for host arrays),
+//            reject it when that exceeds the whole arena, else queue it (FIFO).
+//   admit    the FIFO head goes to the first free slot once the arena can
+//            hold its needs: staging copy in, plan passes, staging copy out,
+//            all on the slot's stream, then a completion event.
+//   retire   a slot whose event has completed returns its arena block, reads
+//            its bounded-wait error word and appends the request to the done
+//            list; the slot is free for the next admission at once.
+// Every submit / poll / drain runs retire-then-admit, so requests arriving
+// while others are on the GPU start as soon as a slot and memory free up.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <chrono>
+#include <cstdint>
+#include <cstring>
+#include <deque>
+#include <map>
+#include <new>
+#include <vector>
+
+#include "fb_fft.h"
+#include "fb_host.h"
+
+using namespace fbfft;
+
+namespace {
+
+constexpr uint32_t kServerMagic = 0x5E2FFB01u;
+constexpr long long kArenaAlign = 256;
+
+#define SV_CK(call)                                                       \
+    do {                                                                  \
+        cudaError_t sv_e_ = (call);                                       \
+        if (sv_e_ != cudaSuccess) return host::fail(sv_e_, #call);        \
+    } while (0)
+
+// First-fit allocator over one device region; blocks are 256-byte aligned and
+// free neighbours coalesce, so the budget is the region and nothing else.
+struct Arena {
+    char* base = nullptr;
+    long long cap = 0, used = 0, peak = 0;
+    std::map<long long, long long> free_;  // offset -> size
+
+    void reset(long long c)
+    {
+        cap = c;
+        free_.clear();
+        if (c > 0) free_[0] = c;
+    }
+    long long alloc(long long n)  // offset, or -1
+    {
+        n = (n + kArenaAlign - 1) / kArenaAlign * kArenaAlign;
+        for (auto it = free_.begin(); it != free_.end(); ++it) {
+            if (it->second < n) continue;
+            const long long off = it->first, rest = it->second - n;
+            free_.erase(it);
+            if (rest) free_[off + n] = rest;
+            used += n;
+            peak = std::max(peak, used);
+            return off;
+        }
+        return -1;
+    }
+    void release(long long off, long long n)
+    {
+        n = (n + kArenaAlign - 1) / kArenaAlign * kArenaAlign;
+        used -= n;
+        auto it = free_.emplace(off, n).first;
+        auto nx = std::next(it);
+        if (nx != free_.end() && it->first + it->second == nx->first) {
+            it->second += nx->second;
+            free_.erase(nx);
+        }
+        if (it != free_.begin()) {
+            auto pv = std::prev(it);
+            if (pv->first + pv->second == it->first) {
+                pv->second += it->second;
+                free_.erase(it);
+            }
+        }
+    }
+};
+
+struct ShapeKey {
+    int rank;
+    long long d0, d1, d2, batch;
+    unsigned flags;
+    bool operator<(const ShapeKey& o) const
+    {
+        if (rank != o.rank) return rank < o.rank;
+        if (d0 != o.d0) return d0 < o.d0;
+        if (d1 != o.d1) return d1 < o.d1;
+        if (d2 != o.d2) return d2 < o.d2;
+        if (batch != o.batch) return batch < o.batch;
+        return flags < o.flags;
+    }
+};
+
+struct PlanEntry {
+    fb_fft_plan_t plan = nullptr;
+    long long scratch = 0, io = 0, table = 0;
+    long long last_use = 0;
+    int users = 0;  // queued + running requests holding it
+};
+
+struct Req {
+    long long tag = 0;
+    PlanEntry* pe = nullptr;
+    int direction = FB_FFT_FORWARD;
+    const void* in = nullptr;
+    void* out = nullptr;
+    bool host_io = false;
+    long long need = 0;  // arena bytes
+    double t_submit = 0, t_admit = 0;
+};
+
+struct Slot {
+    cudaStream_t stream = nullptr;
+    cudaEvent_t done = nullptr;
+    int* err_dev = nullptr;   // int[16] bounded-wait error word of this slot's launches
+    int* err_host = nullptr;  // pinned copy, refreshed at the end of every request
+    bool busy = false;
+    Req r;
+    long long off = -1;  // arena block
+    long long seq = 0;   // admission order
+};
+
+}  // namespace
+
+struct fb_fft_server_s {
+    uint32_t magic = kServerMagic;
+    int device = 0;
+    int max_plans = 1;
+    std::chrono::steady_clock::time_point t0;
+    cudaStream_t build = nullptr;  // plans are built here
+    Arena arena;
+    std::vector<Slot> slots;
+    std::map<ShapeKey, PlanEntry> plans;
+    std::deque<Req> pending;
+    std::deque<fb_fft_server_done> done;
+    long long use_clock = 0, seq = 0;
+    fb_fft_server_stats st{};
+};
+
+namespace {
+
+bool server_ok(fb_fft_server_t s) { return s && s->magic == kServerMagic; }
+
+double now_s(const fb_fft_server_s* s)
+{
+    return std::chrono::duration<double>(std::chrono::steady_clock::now() - s->t0).count();
+}
+
+void evict_idle(fb_fft_server_s* s)
+{
+    while ((int)s->plans.size() > s->max_plans) {
+        auto victim = s->plans.end();
+        for (auto it = s->plans.begin(); it != s->plans.end(); ++it)
+            if (it->second.users == 0 && (victim == s->plans.end() || it->second.last_use < victim->second.last_use))
+                victim = it;
+        if (victim == s->plans.end()) return;  // every plan is in use
+        s->st.plan_bytes -= victim->second.table;
+        host::plan_free(victim->second.plan);
+        s->plans.erase(victim);
+    }
+}
+
+int get_plan(fb_fft_server_s* s, int rank, const long long* dims, long long batch, unsigned flags, PlanEntry** out)
+{
+    if (rank < 1 || rank > 3 || !dims) return FB_FFT_ERR_INVALID_ARG;
+    ShapeKey k{rank, dims[0], rank > 1 ? dims[1] : 1, rank > 2 ? dims[2] : 1, batch, flags};
+    auto it = s->plans.find(k);
+    if (it == s->plans.end()) {
+        PlanEntry e;
+        int rc = host::plan_create(&e.plan, rank, dims, batch, flags, s->build, true);
+        if (rc != FB_FFT_OK) return rc;
+        e.scratch = host::plan_scratch_bytes(e.plan);
+        e.io = host::plan_io_bytes(e.plan);
+        e.table = host::plan_table_bytes(e.plan);
+        s->st.plan_builds++;
+        s->st.plan_bytes += e.table;
+        it = s->plans.emplace(k, e).first;
+    }
+    it->second.last_use = ++s->use_clock;
+    *out = &it->second;
+    return FB_FFT_OK;
+}
+
+long long request_need(const PlanEntry* pe, bool host_io)
+{
+    auto up = [](long long n) { return (n + kArenaAlign - 1) / kArenaAlign * kArenaAlign; };
+    return up(pe->scratch) + (host_io ? up(pe->io) : 0);
+}
+
+void finish(fb_fft_server_s* s, Slot& sl, int slot_index, int status)
+{
+    fb_fft_server_done d;
+    d.tag = sl.r.tag;
+    d.status = status;
+    d.slot = slot_index;
+    d.t_submit = sl.r.t_submit;
+    d.t_admit = sl.r.t_admit;
+    d.t_done = now_s(s);
+    s->done.push_back(d);
+    if (sl.off >= 0) s->arena.release(sl.off, sl.r.need);
+    sl.off = -1;
+    sl.r.pe->users--;
+    sl.busy = false;
+    s->st.completed++;
+    s->st.in_flight--;
+}
+
+// Retire every slot whose completion event has fired.
+int retire(fb_fft_server_s* s)
+{
+    for (int i = 0; i < (int)s->slots.size(); ++i) {
+        Slot& sl = s->slots[i];
+        if (!sl.busy) continue;
+        const cudaError_t q = cudaEventQuery(sl.done);
+        if (q == cudaErrorNotReady) {
+            cudaGetLastError();
+            continue;
+        }
+        int status = FB_FFT_OK;
+        if (q != cudaSuccess) {
+            status = host::fail(q, "request completion");
+        } else if (sl.err_host[0] != 0) {
+            status = FB_FFT_ERR_TIMEOUT;
+            std::memset(sl.err_host, 0, 16 * sizeof(int));
+            const cudaError_t e = cudaMemsetAsync(sl.err_dev, 0, 16 * sizeof(int), sl.stream);
+            if (e != cudaSuccess) status = host::fail(e, "cudaMemsetAsync");
+        }
+        finish(s, sl, i, status);
+    }
+    return FB_FFT_OK;
+}
+
+// Put request r on slot sl: copies and passes on the slot's stream, then its event.
+int start(fb_fft_server_s* s, Slot& sl, const Req& r, long long off)
+{
+    char* block = off >= 0 ? s->arena.base + off : nullptr;
+    const long long scr_bytes = (r.pe->scratch + kArenaAlign - 1) / kArenaAlign * kArenaAlign;
+    void* scratch = r.pe->scratch ? block : nullptr;
+    const void* in = r.in;
+    void* out = r.out;
+    if (r.host_io) {
+        void* stage = block + scr_bytes;
+        SV_CK(cudaMemcpyAsync(stage, r.in, (size_t)r.pe->io, cudaMemcpyHostToDevice, sl.stream));
+        in = stage;
+        out = stage;
+    }
+    int rc = host::plan_exec_on(r.pe->plan, in, out, r.direction, sl.stream, scratch, sl.err_dev);
+    if (rc != FB_FFT_OK) return rc;
+    if (r.host_io) SV_CK(cudaMemcpyAsync(r.out, out, (size_t)r.pe->io, cudaMemcpyDeviceToHost, sl.stream));
+    SV_CK(cudaMemcpyAsync(sl.err_host, sl.err_dev, sizeof(int), cudaMemcpyDeviceToHost, sl.stream));
+    SV_CK(cudaEventRecord(sl.done, sl.stream));
+    return FB_FFT_OK;
+}
+
+// Admit FIFO heads while a slot is free and the arena holds the head's needs.
+int admit(fb_fft_server_s* s)
+{
+    while (!s->pending.empty()) {
+        int free_slot = -1;
+        for (int i = 0; i < (int)s->slots.size(); ++i)
+            if (!s->slots[i].busy) {
+                free_slot = i;
+                break;
+            }
+        if (free_slot < 0) return FB_FFT_OK;
+        Req& r = s->pending.front();
+        long long off = -1;
+        if (r.need > 0) {
+            off = s->arena.alloc(r.need);
+            if (off < 0) return FB_FFT_OK;  // wait for memory (FIFO: no overtaking)
+        }
+        Slot& sl = s->slots[free_slot];
+        sl.r = r;
+        sl.r.t_admit = now_s(s);
+        sl.off = off;
+        sl.busy = true;
+        sl.seq = ++s->seq;
+        s->pending.pop_front();
+        s->st.pending--;
+        s->st.in_flight++;
+        s->st.max_in_flight = std::max(s->st.max_in_flight, s->st.in_flight);
+        const int rc = start(s, sl, sl.r, off);
+        if (rc != FB_FFT_OK) {
+            // nothing usable was queued behind a failed launch: report it done with the error
+            cudaStreamSynchronize(sl.stream);
+            cudaGetLastError();
+            finish(s, sl, free_slot, rc);
+        }
+    }
+    return FB_FFT_OK;
+}
+
+int pump(fb_fft_server_s* s)
+{
+    int rc = retire(s);
+    if (rc != FB_FFT_OK) return rc;
+    return admit(s);
+}
+
+// Block on the earliest-admitted running request.
+int wait_oldest(fb_fft_server_s* s)
+{
+    Slot* oldest = nullptr;
+    for (Slot& sl : s->slots)
+        if (sl.busy && (!oldest || sl.seq < oldest->seq)) oldest = &sl;
+    if (!oldest) return FB_FFT_OK;
+    const cudaError_t e = cudaEventSynchronize(oldest->done);
+    if (e != cudaSuccess) cudaGetLastError();  // retire() reports it per request
+    return FB_FFT_OK;
+}
+
+void free_server(fb_fft_server_s* s)
+{
+    for (Slot& sl : s->slots) {
+        if (sl.stream) cudaStreamSynchronize(sl.stream);
+        if (sl.done) cudaEventDestroy(sl.done);
+        if (sl.stream) cudaStreamDestroy(sl.stream);
+        if (sl.err_host) cudaFreeHost(sl.err_host);
+        if (sl.err_dev) cudaFree(sl.err_dev);
+    }
+    for (auto& kv : s->plans) host::plan_free(kv.second.plan);
+    if (s->arena.base) cudaFree(s->arena.base);
+    if (s->build) cudaStreamDestroy(s->build);
+    s->magic = 0;
+    delete s;
+}
+
+}  // namespace
+
+extern "C" {
+
+int fb_fft_server_create(fb_fft_server_t* srv, int slots, long long hbm_cap_bytes, int max_plans)
+{
+    if (!srv) return FB_FFT_ERR_INVALID_ARG;
+    *srv = nullptr;
+    if (slots < 1 || slots > 64 || hbm_cap_bytes < 0 || max_plans < 1) return FB_FFT_ERR_INVALID_ARG;
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) {
+        cudaGetLastError();
+        return FB_FFT_ERR_NO_DEVICE;
+    }
+    fb_fft_server_s* s = new (std::nothrow) fb_fft_server_s();
+    if (!s) return FB_FFT_ERR_ALLOC;
+    s->t0 = std::chrono::steady_clock::now();
+    cudaGetDevice(&s->device);
+    s->max_plans = max_plans;
+    s->slots.resize(slots);
+    s->st.slots = slots;
+    int rc = FB_FFT_OK;
+    auto ck = [&](cudaError_t e, const char* what) {
+        if (e != cudaSuccess && rc == FB_FFT_OK) rc = host::fail(e, what);
+    };
+    ck(cudaStreamCreateWithFlags(&s->build, cudaStreamNonBlocking), "cudaStreamCreate");
+    for (Slot& sl : s->slots) {
+        if (rc != FB_FFT_OK) break;
+        ck(cudaStreamCreateWithFlags(&sl.stream, cudaStreamNonBlocking), "cudaStreamCreate");
+        ck(cudaEventCreateWithFlags(&sl.done, cudaEventDisableTiming), "cudaEventCreate");
+        ck(cudaHostAlloc((void**)&sl.err_host, 16 * sizeof(int), cudaHostAllocDefault), "cudaHostAlloc");
+        ck(cudaMalloc((void**)&sl.err_dev, 16 * sizeof(int)), "cudaMalloc");
+        if (rc == FB_FFT_OK) {
+            std::memset(sl.err_host, 0, 16 * sizeof(int));
+            ck(cudaMemset(sl.err_dev, 0, 16 * sizeof(int)), "cudaMemset");
+        }
+    }
+    if (rc == FB_FFT_OK && hbm_cap_bytes > 0) {
+        const long long cap = hbm_cap_bytes / kArenaAlign * kArenaAlign;
+        if (cudaMalloc((void**)&s->arena.base, (size_t)cap) != cudaSuccess) {
+            cudaGetLastError();
+            s->arena.base = nullptr;
+            rc = FB_FFT_ERR_ALLOC;
+        } else {
+            s->arena.reset(cap);
+        }
+    }
+    if (rc != FB_FFT_OK) {
+        free_server(s);
+        return rc;
+    }
+    s->st.arena_bytes = s->arena.cap;
+    *srv = s;
+    return FB_FFT_OK;
+}
+
+int fb_fft_server_prepare(fb_fft_server_t srv, int rank, const long long* dims, long long batch, unsigned flags)
+{
+    if (!server_ok(srv)) return FB_FFT_ERR_BAD_PLAN;
+    PlanEntry* pe = nullptr;
+    const int rc = get_plan(srv, rank, dims, batch, flags, &pe);
+    if (rc == FB_FFT_OK) evict_idle(srv);
+    return rc;
+}
+
+int fb_fft_server_submit(fb_fft_server_t srv, int rank, const long long* dims, long long batch, unsigned flags,
+                         int direction, const void* in, void* out, int host_io, long long tag)
+{
+    if (!server_ok(srv)) return FB_FFT_ERR_BAD_PLAN;
+    fb_fft_server_s* s = srv;
+    if (direction != FB_FFT_FORWARD && direction != FB_FFT_INVERSE) {
+        s->st.rejected++;
+        return FB_FFT_ERR_INVALID_ARG;
+    }
+    PlanEntry* pe = nullptr;
+    int rc = get_plan(s, rank, dims, batch, flags, &pe);
+    if (rc == FB_FFT_OK && pe->io > 0) {
+        if (!in || !out) rc = FB_FFT_ERR_INVALID_ARG;
+        const uintptr_t a = (uintptr_t)in, b = (uintptr_t)out, n = (uintptr_t)pe->io;
+        if (!host_io && ((a | b) & 7)) rc = FB_FFT_ERR_INVALID_ARG;
+        if (!host_io && a != b && a < b + n && b < a + n) rc = FB_FFT_ERR_INVALID_ARG;
+    }
+    Req r;
+    if (rc == FB_FFT_OK) {
+        r.need = request_need(pe, host_io != 0);
+        if (r.need > s->arena.cap) rc = FB_FFT_ERR_OVER_BUDGET;
+    }
+    if (rc != FB_FFT_OK) {
+        s->st.rejected++;
+        evict_idle(s);
+        return rc;
+    }
+    r.tag = tag;
+    r.pe = pe;
+    r.direction = direction;
+    r.in = in;
+    r.out = out;
+    r.host_io = host_io != 0;
+    r.t_submit = now_s(s);
+    pe->users++;
+    s->pending.push_back(r);
+    s->st.submitted++;
+    s->st.pending++;
+    evict_idle(s);
+    return pump(s);
+}
+
+int fb_fft_server_poll(fb_fft_server_t srv, int wait, fb_fft_server_done* done, int capacity, int* n_done)
+{
+    if (!server_ok(srv)) return FB_FFT_ERR_BAD_PLAN;
+    if (!n_done || capacity < 0 || (capacity > 0 && !done)) return FB_FFT_ERR_INVALID_ARG;
+    fb_fft_server_s* s = srv;
+    int rc = pump(s);
+    if (rc != FB_FFT_OK) return rc;
+    if (wait && s->done.empty() && s->st.in_flight > 0) {
+        wait_oldest(s);
+        rc = pump(s);
+        if (rc != FB_FFT_OK) return rc;
+    }
+    int n = 0;
+    while (n < capacity && !s->done.empty()) {
+        done[n++] = s->done.front();
+        s->done.pop_front();
+    }
+    *n_done = n;
+    return FB_FFT_OK;
+}
+
+int fb_fft_server_drain(fb_fft_server_t srv)
+{
+    if (!server_ok(srv)) return FB_FFT_ERR_BAD_PLAN;
+    fb_fft_server_s* s = srv;
+    for (;;) {
+        int rc = pump(s);
+        if (rc != FB_FFT_OK) return rc;
+        if (s->st.in_flight == 0) {
+            if (s->pending.empty()) return FB_FFT_OK;
+            // a queued head that cannot be admitted with every slot idle never will be
+            return FB_FFT_ERR_OVER_BUDGET;
+        }
+        wait_oldest(s);
+    }
+}
+
+int fb_fft_server_cancel(fb_fft_server_t srv, long long tag)
+{
+    if (!server_ok(srv)) return FB_FFT_ERR_BAD_PLAN;
+    fb_fft_server_s* s = srv;
+    for (auto it = s->pending.begin(); it != s->pending.end(); ++it) {
+        if (it->tag != tag) continue;
+        fb_fft_server_done d;
+        d.tag = tag;
+        d.status = FB_FFT_ERR_CANCELLED;
+        d.slot = -1;
+        d.t_submit = it->t_submit;
+        d.t_admit = -1.0;
+        d.t_done = now_s(s);
+        it->pe->users--;
+        s->pending.erase(it);
+        s->done.push_back(d);
+        s->st.pending--;
+        s->st.cancelled++;
+        return pump(s);
+    }
+    return FB_FFT_ERR_INVALID_ARG;
+}
+
+double fb_fft_server_clock(fb_fft_server_t srv) { return server_ok(srv) ? now_s(srv) : -1.0; }
+
+int fb_fft_server_stats_get(fb_fft_server_t srv, fb_fft_server_stats* stats)
+{
+    if (!server_ok(srv)) return FB_FFT_ERR_BAD_PLAN;
+    if (!stats) return FB_FFT_ERR_INVALID_ARG;
+    fb_fft_server_s* s = srv;
+    s->st.plans = (long long)s->plans.size();
+    s->st.arena_in_use = s->arena.used;
+    s->st.arena_peak = s->arena.peak;
+    *stats = s->st;
+    return FB_FFT_OK;
+}
+
+int fb_fft_server_destroy(fb_fft_server_t srv)
+{
+    if (!srv) return FB_FFT_OK;
+    if (!server_ok(srv)) return FB_FFT_ERR_BAD_PLAN;
+    free_server(srv);
+    return FB_FFT_OK;
+}
+
+}  // extern "C"

@@ -24,7 +24,8 @@ MAX_1D_LEN = 4096 * 4096
 STATUS = {
     0: "FB_FFT_OK", -1: "FB_FFT_ERR_INVALID_ARG", -2: "FB_FFT_ERR_UNSUPPORTED_SIZE",
     -3: "FB_FFT_ERR_ALLOC", -4: "FB_FFT_ERR_CUDA", -5: "FB_FFT_ERR_TIMEOUT",
-    -6: "FB_FFT_ERR_BAD_PLAN", -7: "FB_FFT_ERR_NO_DEVICE",
+    -6: "FB_FFT_ERR_BAD_PLAN", -7: "FB_FFT_ERR_NO_DEVICE", -8: "FB_FFT_ERR_CANCELLED",
+    -9: "FB_FFT_ERR_OVER_BUDGET",
 }
 
 
@@ -50,6 +51,21 @@ class ManyOpts(ctypes.Structure):
 
     def as_dict(self) -> dict:
         return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+class ServerDone(ctypes.Structure):
+    _fields_ = [("tag", ctypes.c_longlong), ("status", ctypes.c_int), ("slot", ctypes.c_int),
+                ("t_submit", ctypes.c_double), ("t_admit", ctypes.c_double), ("t_done", ctypes.c_double)]
+
+
+class ServerStats(ctypes.Structure):
+    _fields_ = [(f, ctypes.c_longlong) for f in (
+        "submitted", "completed", "rejected", "cancelled", "pending", "in_flight", "plans", "plan_builds",
+        "plan_bytes", "arena_bytes", "arena_in_use", "arena_peak", "max_in_flight")] + [
+        ("slots", ctypes.c_int), ("reserved", ctypes.c_int)]
+
+    def as_dict(self) -> dict:
+        return {f: getattr(self, f) for f, _ in self._fields_ if f != "reserved"}
 
 
 CPU_BLOCK = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int)
@@ -87,6 +103,15 @@ _sig = {
     "fb_fft_set_graph": (_int, [_vp, _int]),
     "fb_fft_offload_decide": (_int, [_vp, CPU_BLOCK, _vp, _vp, _vp, _int, _int, ctypes.POINTER(_int),
                                      ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]),
+    "fb_fft_server_create": (_int, [ctypes.POINTER(_vp), _int, _ll, _int]),
+    "fb_fft_server_submit": (_int, [_vp, _int, ctypes.POINTER(_ll), _ll, ctypes.c_uint, _int, _vp, _vp, _int, _ll]),
+    "fb_fft_server_prepare": (_int, [_vp, _int, ctypes.POINTER(_ll), _ll, ctypes.c_uint]),
+    "fb_fft_server_poll": (_int, [_vp, _int, ctypes.POINTER(ServerDone), _int, ctypes.POINTER(_int)]),
+    "fb_fft_server_drain": (_int, [_vp]),
+    "fb_fft_server_cancel": (_int, [_vp, _ll]),
+    "fb_fft_server_clock": (ctypes.c_double, [_vp]),
+    "fb_fft_server_stats_get": (_int, [_vp, ctypes.POINTER(ServerStats)]),
+    "fb_fft_server_destroy": (_int, [_vp]),
     "fb_fft_plan_many_query": (_int, [_int, ctypes.POINTER(_ll), ctypes.c_uint, ctypes.POINTER(Info)]),
     "fb_fft_plan_many_ex": (_int, [ctypes.POINTER(_vp), _int, ctypes.POINTER(_ll), ctypes.c_uint, _vp,
                                    ctypes.POINTER(ManyOpts)]),
@@ -400,3 +425,79 @@ def fft(x, dims, direction: int = FORWARD, scale_inv_n: bool = False, out=None):
     n = int(np.prod(dims))
     with Plan(dims, x.numel() // n, scale_inv_n=scale_inv_n) as p:
         return p.exec(x, out, direction)
+
+
+class Server:
+    """Continuous-batching request server (``fb_fft_server_*``): ``slots``
+    concurrent requests, ``hbm_cap_bytes`` of device memory for their scratch
+    and staging, resident plans (at most ``max_plans``)."""
+
+    def __init__(self, slots: int = 8, hbm_cap_bytes: int = 40 * 10**9, max_plans: int = 4096):
+        self._h = _vp()
+        _check(lib.fb_fft_server_create(ctypes.byref(self._h), int(slots), int(hbm_cap_bytes), int(max_plans)),
+               "fb_fft_server_create")
+        self._buf = (ServerDone * 256)()
+
+    def close(self) -> None:
+        if self._h:
+            rc = lib.fb_fft_server_destroy(self._h)
+            self._h = _vp()
+            _check(rc, "fb_fft_server_destroy")
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    @staticmethod
+    def _dims(dims):
+        dims = [int(d) for d in (dims if hasattr(dims, "__len__") else [dims])]
+        return len(dims), (_ll * len(dims))(*dims)
+
+    def prepare(self, dims, batch: int = 1, scale_inv_n: bool = False) -> None:
+        r, cd = self._dims(dims)
+        _check(lib.fb_fft_server_prepare(self._h, r, cd, int(batch), SCALE_INV_N if scale_inv_n else 0),
+               "fb_fft_server_prepare")
+
+    def submit_ptr(self, dims, in_ptr: int, out_ptr: int, tag: int, direction: int = FORWARD, batch: int = 1,
+                   scale_inv_n: bool = False, host_io: bool = False) -> None:
+        """Queue one transform on raw pointers (device, or host when host_io)."""
+        r, cd = self._dims(dims)
+        _check(lib.fb_fft_server_submit(self._h, r, cd, int(batch), SCALE_INV_N if scale_inv_n else 0,
+                                        int(direction), _vp(in_ptr), _vp(out_ptr), 1 if host_io else 0, int(tag)),
+               "fb_fft_server_submit")
+
+    def poll(self, wait: bool = False) -> list[tuple]:
+        """Finished requests as (tag, status, slot, t_submit, t_admit, t_done)."""
+        out = []
+        while True:
+            n = _int(0)
+            _check(lib.fb_fft_server_poll(self._h, 1 if wait else 0, self._buf, len(self._buf), ctypes.byref(n)),
+                   "fb_fft_server_poll")
+            for i in range(n.value):
+                d = self._buf[i]
+                out.append((d.tag, d.status, d.slot, d.t_submit, d.t_admit, d.t_done))
+            if n.value < len(self._buf):
+                return out
+            wait = False
+
+    def drain(self) -> None:
+        _check(lib.fb_fft_server_drain(self._h), "fb_fft_server_drain")
+
+    def cancel(self, tag: int) -> None:
+        _check(lib.fb_fft_server_cancel(self._h, int(tag)), "fb_fft_server_cancel")
+
+    def clock(self) -> float:
+        return lib.fb_fft_server_clock(self._h)
+
+    def stats(self) -> dict:
+        st = ServerStats()
+        _check(lib.fb_fft_server_stats_get(self._h, ctypes.byref(st)), "fb_fft_server_stats_get")
+        return st.as_dict()

@@ -58,7 +58,7 @@ def test_header_compiles_as_plain_c(tmp_path):
 
 
 def test_status_strings(fb):
-    for code in range(-7, 1):
+    for code in range(-9, 1):
         assert fb.lib.fb_fft_status_string(code)
     assert b"unknown" in fb.lib.fb_fft_status_string(-99)
 
@@ -143,6 +143,47 @@ def test_null_plan_handling(fb):
     assert fb.lib.fb_fft_check(None) == -6
     assert fb.lib.fb_fft_pass_name(None, 0) is None
     assert fb.lib.fb_fft_plan(None, 1, None, 1, 0, None) == -1
+
+
+def test_struct_layouts_match_the_binding(fb, tmp_path):
+    """Sizes and field offsets of the ABI structs, from a C compile of the
+    header, equal those of the ctypes mirrors."""
+    structs = {"fb_fft_info": fb.Info, "fb_fft_many_opts": fb.ManyOpts, "fb_fft_server_done": fb.ServerDone,
+               "fb_fft_server_stats": fb.ServerStats}
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "fb_fft.h"', 'int main(void){']
+    for cname, py in structs.items():
+        lines.append(f'printf("{cname} size %zu\\n", sizeof({cname}));')
+        for f, _ in py._fields_:
+            lines.append(f'printf("{cname} {f} %zu\\n", offsetof({cname}, {f}));')
+    lines.append('return 0; }')
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", "-std=c99", f"-I{ROOT}/include", str(src), "-o", str(exe)], check=True)
+    got = {}
+    for line in subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.splitlines():
+        cname, f, v = line.split()
+        got[(cname, f)] = int(v)
+    for cname, py in structs.items():
+        assert got[(cname, "size")] == ctypes.sizeof(py), cname
+        for f, _ in py._fields_:
+            assert got[(cname, f)] == getattr(py, f).offset, (cname, f)
+
+
+def test_server_calls_without_device(fb):
+    import torch
+    assert fb.lib.fb_fft_server_destroy(None) == 0
+    assert fb.lib.fb_fft_server_drain(None) == -6
+    assert fb.lib.fb_fft_server_cancel(None, 0) == -6
+    assert fb.lib.fb_fft_server_clock(None) == -1.0
+    assert fb.lib.fb_fft_server_stats_get(None, None) == -6
+    h = ctypes.c_void_p()
+    assert fb.lib.fb_fft_server_create(None, 1, 0, 1) == -1
+    assert fb.lib.fb_fft_server_create(ctypes.byref(h), 0, 0, 1) == -1
+    assert fb.lib.fb_fft_server_create(ctypes.byref(h), 1, 0, 0) == -1
+    if not torch.cuda.is_available():
+        assert fb.lib.fb_fft_server_create(ctypes.byref(h), 1, 0, 1) == -7
+        assert not h.value
 
 
 def test_launch_counter_starts_at_zero_without_gpu(fb):

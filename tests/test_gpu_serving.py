@@ -1,0 +1,196 @@
+"""Request server (fb_fft_server_*): every result is the same alone and in the
+mix, matches the FP64 oracle, admission respects the device-memory budget,
+cancellation and rejection behave as documented."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2004_09883_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+FWD, INV = -1, 1
+
+
+def tol(n: int) -> float:
+    return 2e-6 * math.log2(n) if n > 1 else 1e-7
+
+
+MIX = [(4096,), (256,), (1 << 20,), (1 << 22,), (6000,), (3 * 5 ** 6,), (60, 45), (512, 512), (16, 250),
+       (128, 128, 128), (8, 100, 27), (1,), (2,), (1000, 1), (80000,), (96, 96), (8, 8, 8), (45, 64, 125)]
+
+
+def _mix(seed, copies=3):
+    shapes = [s for _ in range(copies) for s in MIX]
+    rng = np.random.default_rng(seed)
+    rng.shuffle(shapes)
+    dirs = [FWD if rng.random() < 0.6 else INV for _ in shapes]
+    return shapes, dirs
+
+
+def _alone(fb, torch, shape, direction, x):
+    """The request on its own through the per-call API."""
+    with fb.Plan(list(shape), 1) as p:
+        y = p.exec(x, None, direction)
+        torch.cuda.synchronize()
+        p.check()
+    return y
+
+
+@pytest.mark.parametrize("slots", [1, 8])
+def test_mix_equals_alone_and_oracle(fb, slots):
+    import torch
+    from paper_2004_09883_gb300 import serving
+    shapes, dirs = _mix(1200 + slots)
+    w = serving.Workload(shapes, 7000, dirs)
+    arrivals = serving.poisson_arrivals(len(shapes), 20000.0, 5)
+    with fb.Server(slots=slots, hbm_cap_bytes=1 << 30) as srv:
+        serving.run_served(srv, w, arrivals)
+        st = srv.stats()
+    assert st["completed"] == len(shapes) and st["rejected"] == 0
+    assert st["max_in_flight"] <= slots
+    assert st["arena_peak"] <= st["arena_bytes"]
+    checked = set()
+    for i, (s, d) in enumerate(zip(shapes, dirs)):
+        y_alone = _alone(fb, torch, s, d, w.x[i])
+        assert torch.equal(w.y[i], y_alone), f"request {i} {s}: mix result differs from alone"
+        if (s, d) not in checked:  # each distinct request kind once against the oracle
+            checked.add((s, d))
+            ref = oracle.fft(w.x[i].cpu().numpy().astype(np.complex128).reshape(s), list(s), d)
+            err = oracle.rel_l2(w.y[i].cpu().numpy().reshape(1, -1), ref.reshape(1, -1))[0]
+            assert err <= tol(int(np.prod(s))), f"{s} dir {d}: rel L2 {err:.3e}"
+
+
+def test_host_arrays_through_staging(fb):
+    import torch
+    from paper_2004_09883_gb300 import serving
+    shapes, dirs = _mix(1300, copies=1)
+    w = serving.Workload(shapes, 7100, dirs, host=True)
+    with fb.Server(slots=4, hbm_cap_bytes=256 << 20) as srv:
+        serving.run_served(srv, w, np.zeros(len(shapes)), host_io=True)
+        st = srv.stats()
+    assert st["arena_in_use"] == 0 and 0 < st["arena_peak"] <= 256 << 20
+    for i, (s, d) in enumerate(zip(shapes, dirs)):
+        y_alone = _alone(fb, torch, s, d, w.x[i]).cpu()
+        assert torch.equal(w.hy[i], y_alone), f"request {i} {s}"
+
+
+def test_in_place_host_request(fb):
+    x = inputs.uniform_c64((3, 4096), 77)
+    import torch
+    h = torch.from_numpy(x.copy()).pin_memory()
+    with fb.Server(slots=2, hbm_cap_bytes=64 << 20) as srv:
+        srv.submit_ptr([4096], h.data_ptr(), h.data_ptr(), 1, FWD, batch=3, host_io=True)
+        srv.drain()
+        (tag, st, *_), = srv.poll()
+    assert (tag, st) == (1, 0)
+    ref = oracle.fft(x.astype(np.complex128), [4096], FWD)
+    err = oracle.rel_l2(h.numpy().reshape(3, -1), ref.reshape(3, -1))
+    assert err.max() <= tol(4096)
+
+
+def test_budget_holds_requests_back(fb):
+    """Arena for one host request at a time: the others wait in FIFO order."""
+    import torch
+    n = 1 << 20
+    need = n * 8 + n * 8  # staging + four-step scratch
+    xs = [torch.from_numpy(inputs.uniform_c64((n,), 80 + i)).pin_memory() for i in range(4)]
+    ys = [torch.empty_like(v).pin_memory() for v in xs]
+    with fb.Server(slots=4, hbm_cap_bytes=need + need // 2) as srv:
+        for i in range(4):
+            srv.submit_ptr([n], xs[i].data_ptr(), ys[i].data_ptr(), i, FWD, host_io=True)
+        srv.drain()
+        done = srv.poll()
+        st = srv.stats()
+    assert [d[0] for d in sorted(done, key=lambda d: d[4])] == [0, 1, 2, 3]  # admitted in FIFO order
+    assert st["max_in_flight"] == 1 and st["arena_peak"] <= need + need // 2
+    for i in range(4):
+        ref = oracle.fft(xs[i].numpy().astype(np.complex128), [n], FWD)
+        assert oracle.rel_l2(ys[i].numpy().reshape(1, -1), ref.reshape(1, -1))[0] <= tol(n)
+
+
+def test_over_budget_and_bad_requests_rejected(fb):
+    import torch
+    x = torch.zeros(1 << 16, dtype=torch.complex64, device="cuda")
+    h = torch.zeros(1 << 18, dtype=torch.complex64).pin_memory()
+    with fb.Server(slots=2, hbm_cap_bytes=1 << 20) as srv:
+        with pytest.raises(fb.FFTError) as e:  # 2 MiB staging + 2 MiB four-step scratch > 1 MiB
+            srv.submit_ptr([1 << 18], h.data_ptr(), h.data_ptr(), 0, FWD, host_io=True)
+        assert e.value.status == -9
+        with pytest.raises(fb.FFTError) as e:
+            srv.submit_ptr([7], x.data_ptr(), x.data_ptr(), 1, FWD)
+        assert e.value.status == -2
+        with pytest.raises(fb.FFTError) as e:
+            srv.submit_ptr([64], x.data_ptr(), x.data_ptr(), 2, 0)
+        assert e.value.status == -1
+        with pytest.raises(fb.FFTError) as e:  # partial overlap of device in/out
+            srv.submit_ptr([64], x.data_ptr(), x.data_ptr() + 8, 3, FWD)
+        assert e.value.status == -1
+        srv.submit_ptr([64], x.data_ptr(), x.data_ptr(), 4, FWD)  # in place is fine
+        srv.drain()
+        assert [d[:2] for d in srv.poll()] == [(4, 0)]
+        st = srv.stats()
+    assert st["rejected"] == 4 and st["completed"] == 1
+
+
+def test_cancel_pending_request(fb):
+    """Two host requests that each need most of the arena: the second waits
+    while the first (a 128 MiB copy each way) runs, and can be cancelled."""
+    import torch
+    n = 1 << 24
+    a = torch.zeros(n, dtype=torch.complex64).pin_memory()
+    b = torch.from_numpy(inputs.uniform_c64((4096,), 3)).pin_memory()
+    bo = torch.empty_like(b).pin_memory()
+    with fb.Server(slots=2, hbm_cap_bytes=n * 8 * 2 + (1 << 20)) as srv:
+        srv.submit_ptr([n], a.data_ptr(), a.data_ptr(), 0, FWD, host_io=True)
+        srv.submit_ptr([n], a.data_ptr(), a.data_ptr(), 1, FWD, host_io=True)  # waits for the arena
+        srv.cancel(1)
+        with pytest.raises(fb.FFTError):
+            srv.cancel(1)  # no longer queued
+        srv.submit_ptr([4096], b.data_ptr(), bo.data_ptr(), 2, FWD, host_io=True)
+        srv.drain()
+        done = {d[0]: d for d in srv.poll()}
+        st = srv.stats()
+    assert done[1][1] == -8 and done[1][2] == -1
+    assert done[0][1] == 0 and done[2][1] == 0
+    assert st["cancelled"] == 1 and st["completed"] == 2
+    ref = oracle.fft(b.numpy().astype(np.complex128), [4096], FWD)
+    assert oracle.rel_l2(bo.numpy().reshape(1, -1), ref.reshape(1, -1))[0] <= tol(4096)
+
+
+def test_plan_cache_eviction_keeps_results(fb):
+    """At most max_plans idle plans stay resident; evicted shapes are rebuilt."""
+    import torch
+    from paper_2004_09883_gb300 import serving
+    shapes = [(64,), (128,), (3000,), (64,), (27, 27), (128,), (5 ** 5,), (64,)] * 3
+    w = serving.Workload(shapes, 7300)
+    with fb.Server(slots=3, hbm_cap_bytes=16 << 20, max_plans=2) as srv:
+        for i, s in enumerate(shapes):  # one at a time, so earlier plans are idle
+            srv.submit_ptr(s, w.x[i].data_ptr(), w.y[i].data_ptr(), i, FWD)
+            srv.drain()
+            assert [d[:2] for d in srv.poll()] == [(i, 0)]
+            assert srv.stats()["plans"] <= 2
+        st = srv.stats()
+    assert st["plan_builds"] > 5
+    for i, s in enumerate(shapes):
+        assert torch.equal(w.y[i], _alone(fb, torch, s, FWD, w.x[i]))
+
+
+def test_server_handle_errors(fb):
+    import ctypes
+    assert fb.lib.fb_fft_server_destroy(None) == 0
+    assert fb.lib.fb_fft_server_drain(None) == -6
+    assert fb.lib.fb_fft_server_clock(None) == -1.0
+    h = ctypes.c_void_p()
+    assert fb.lib.fb_fft_server_create(ctypes.byref(h), 0, 0, 1) == -1
+    assert fb.lib.fb_fft_server_create(ctypes.byref(h), 65, 0, 1) == -1
+    assert fb.lib.fb_fft_server_create(ctypes.byref(h), 1, -1, 1) == -1
+    with fb.Server(slots=1, hbm_cap_bytes=0) as srv:
+        assert srv.poll(wait=True) == []  # nothing queued: returns at once
+        with pytest.raises(fb.FFTError) as e:  # four-step scratch cannot fit a zero budget
+            import torch
+            x = torch.zeros(1 << 16, dtype=torch.complex64, device="cuda")
+            srv.submit_ptr([1 << 16], x.data_ptr(), x.data_ptr(), 0, FWD)
+        assert e.value.status == -9
