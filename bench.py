@@ -9,7 +9,7 @@ beside it.  Four input/output buffer pairs (512 MiB) rotate between steps so
 the working set exceeds the 126 MB L2.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
-                  [--workload 3d|1d4096|1d4096L|1d2p20|uneven|serving]
+                  [--workload 3d|1d4096|1d4096L|1d2p20|1d2p20tc|uneven|serving]
 
 Under torchrun each rank runs its own replica (independent transforms, no
 collective on the data path); rank 0 prints one JSON line.  --impl reference
@@ -47,6 +47,8 @@ WORKLOADS = {
                    lengths=(4096, 64, 65536)),
     "1d2p20": dict(name="1d_c2c_2p20_batch32_fwd", dims=[1 << 20], batch=32,
                    seed=inputs.seed_for(inputs.WORKLOAD_1D_2P20x32), dist="normal", inverse=False),
+    "1d2p20tc": dict(name="1d_c2c_2p20_batch32_fwd_tensor_core_radix16", dims=[1 << 20], batch=32,
+                     seed=inputs.seed_for(inputs.WORKLOAD_1D_2P20x32), dist="normal", inverse=False, tc=True),
     "serving": dict(name="serving_mix_2000_requests_1d_2d_3d_poisson", dims=None, batch=1,
                     seed=inputs.seed_for(inputs.WORKLOAD_SERVING), dist="uniform", inverse=False,
                     serving=dict(requests=2000, host_requests=600, slots=8, hbm_cap=40 * 10 ** 9,
@@ -351,13 +353,15 @@ def run_gpu(args, wl: dict) -> None:
     host_inputs = [make_input(wl, replica_rep(rank, r)) for r in range(nbuf)]
     xin = [torch.from_numpy(h.reshape(-1)).to(dev) for h in host_inputs]
     xout = [torch.empty_like(xin[0]) for _ in range(nbuf)]
-    plan = fbfft.Plan(dims, batch, scale_inv_n=wl["inverse"], stream=stream)
+    tc = bool(wl.get("tc"))
+    plan = fbfft.Plan(dims, batch, scale_inv_n=wl["inverse"], stream=stream, tensor_cores=tc)
 
-    def step(i):
+    def step(i, p=None):
+        p = p or plan
         a, b = xin[i % nbuf], xout[i % nbuf]
-        plan.exec_ptr(a.data_ptr(), b.data_ptr(), fbfft.FORWARD)
+        p.exec_ptr(a.data_ptr(), b.data_ptr(), fbfft.FORWARD)
         if wl["inverse"]:
-            plan.exec_ptr(b.data_ptr(), b.data_ptr(), fbfft.INVERSE)
+            p.exec_ptr(b.data_ptr(), b.data_ptr(), fbfft.INVERSE)
 
     def barrier():
         torch.cuda.synchronize(dev)
@@ -396,6 +400,36 @@ def run_gpu(args, wl: dict) -> None:
     clk = clocks.summary(wall0, wall1) if clocks else None
     if clocks:
         clocks.stop()
+
+    # tensor-core workload: the plain FP32 plan on the same buffers, and both
+    # paths' error against the oracle on a sample of the batch
+    precision = None
+    if tc:
+        p32 = fbfft.Plan(dims, batch, scale_inv_n=wl["inverse"], stream=stream)
+        for i in range(args.warmup):
+            step(i, p32)
+        barrier()
+        ev0.record(stream)
+        for i in range(args.steps):
+            step(i, p32)
+        ev1.record(stream)
+        barrier()
+        ms32 = max_over_ranks(ev0.elapsed_time(ev1) / args.steps, dist, dev)
+        precision = {"fp32_path": {"value": round(whole_job_rate(world, bytes_step, ms32) / 1e9, 3), "unit": "GB/s",
+                                   "ms_per_step": round(ms32, 5)},
+                     "speedup_vs_fp32_path": round(ms32 / ms, 3), "tolerance_rel_l2": 5e-5}
+        if rank == 0 and not args.quick:
+            import oracle
+            k = 2
+            x = host_inputs[0].reshape(batch, n)[:k]
+            ref = oracle.fft(x.astype(np.complex128), dims, fbfft.FORWARD, False, len(os.sched_getaffinity(0)))
+            for name, p in (("tensor_cores", plan), ("fp32", p32)):
+                y = p.exec(xin[0], None, fbfft.FORWARD)
+                torch.cuda.synchronize(dev)
+                got = y.cpu().numpy().reshape(batch, n)[:k]
+                precision[f"{name}_max_rel_l2"] = float(oracle.rel_l2(got, ref.reshape(k, n)).max())
+            precision["error_sample"] = f"batch items 0..{k - 1} of input buffer 0 against the FP64 oracle"
+        p32.close()
 
     # end to end through the drop-in host-array call: every step copies the
     # input host->device and the result device->host inside the call
@@ -456,7 +490,7 @@ def run_gpu(args, wl: dict) -> None:
         line = {
             "metric": METRIC, "value": round(value, 3), "unit": "GB/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": round(ms, 5), "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "vs_baseline": None, "dtype": "f16 hi/lo products, f32 accumulate" if tc else "f32", "data": "synthetic",
             "config": {"workload": wl["name"], "dims": dims, "batch": batch, "dtype_storage": "complex64",
                        "l2": f"{nbuf} rotating input/output buffer pairs "
                              f"({nbuf * 2 * 8 * n * batch / 2 ** 20:.0f} MiB) > 126 MB L2",
@@ -472,6 +506,8 @@ def run_gpu(args, wl: dict) -> None:
                        for p in passes],
             "kernel_hash": kernel_hash(),
         }
+        if precision:
+            line["precision"] = precision
         print(json.dumps(line), flush=True)
     plan.close()
     if dist is not None:

@@ -51,6 +51,13 @@ typedef enum fb_fft_status {
 
 /* Plan flags. */
 #define FB_FFT_SCALE_INV_N 0x1u /* multiply the result of every INVERSE exec by 1/prod(dims) */
+/* Run the radix-16 stages of power-of-two lines of length >= 256 on the
+ * tensor cores: each stage's 16-point DFT as one FP16 matrix product per 128
+ * butterflies, inputs and DFT matrix split into hi + lo halves (three
+ * products, FP32 accumulation, per-butterfly power-of-two scaling).  Relative
+ * L2 error per result <= 5e-5 (the FP32 path: <= 2e-6 log2 N).  Other stages
+ * and other lengths run the FP32 butterflies.  Not for fb_fft_plan_many. */
+#define FB_FFT_TENSOR_CORES 0x2u
 
 /* Largest supported length along one axis of a rank-2/3 plan, and of a
  * rank-1 plan (a rank-1 length above FB_FFT_MAX_SMEM_LEN runs as a two-pass
@@ -67,7 +74,7 @@ typedef enum fb_fft_status {
  *          and 5-smooth (2^a 3^b 5^c); <= FB_FFT_MAX_SMEM_LEN for rank >= 2,
  *          <= FB_FFT_MAX_1D_LEN for rank 1.
  *   batch  number of transforms (>= 0) laid out back to back.
- *   flags  FB_FFT_SCALE_INV_N or 0.
+ *   flags  0 or FB_FFT_SCALE_INV_N and/or FB_FFT_TENSOR_CORES.
  *   stream cudaStream_t the plan launches on (NULL = legacy default stream).
  * Builds the twiddle tables on the GPU (FP64 evaluation, rounded to FP32) and
  * allocates the plan's scratch; both are owned by the plan.  Uses the current
@@ -213,6 +220,7 @@ const char* fb_fft_last_error(void);
 /*
  * Plan description (host-side facts of the schedule).
  *   passes         kernel launches per exec
+ *   tc_passes      of which with radix-16 stages on the tensor cores
  *   smem_len_max   longest line held in one CTA's shared memory
  *   scratch_bytes  plan-owned device scratch (four-step intermediate)
  *   twiddle_bytes  plan-owned device twiddle tables
@@ -220,7 +228,7 @@ const char* fb_fft_last_error(void);
  */
 typedef struct fb_fft_info {
     int passes;
-    int reserved;
+    int tc_passes;
     long long smem_len_max;
     long long scratch_bytes;
     long long twiddle_bytes;

@@ -94,6 +94,7 @@ struct PassPlan {
     int slot = 0;                // batched-uneven plans: side stream the pass runs on
     long long off_in_idx = -1;   // batched-uneven plans: index of the pass's offset
     long long off_out_idx = -1;  // tables in the plan's device offset buffer
+    bool tc = false;             // radix-16 stages on the tensor cores
 };
 
 bool is_smooth(long long n)
@@ -204,6 +205,7 @@ struct TwiddleBuilder {
 // The compiled kernel a pass runs in one direction.
 LineKernel pass_kernel(const PassPlan& q, bool fwd)
 {
+    if (q.tc) return line_kernel_p2tc(q.threads, fwd, q.lg, q.io);
     if (q.kind == 2) return line_kernel_mixed(fwd, q.lg);
     if (q.kind == 1) return line_kernel_generic(fwd);
     return line_kernel_p2(q.threads, fwd, q.lg, q.io);
@@ -213,7 +215,7 @@ LineKernel pass_kernel(const PassPlan& q, bool fwd)
 int make_line_pass(PassPlan& p, TwiddleBuilder& twb, long long L, long long O, long long C,
                    long long in_sn, long long in_sc, long long in_so, long long out_sk, long long out_sc,
                    long long out_so, bool in_tfast, bool out_tfast, bool ptw, bool odd_first = false,
-                   int max_lines = 0)
+                   int max_lines = 0, bool tc = false)
 {
     p = PassPlan{};  // zero descriptor, default member values (no offset tables)
     PassDesc& d = p.d;
@@ -242,6 +244,8 @@ int make_line_pass(PassPlan& p, TwiddleBuilder& twb, long long L, long long O, l
         p.io = ptw ? kIoCCP : (in_tfast ? kIoCC : (out_tfast ? kIoNC : kIoNN));
         p.threads = (cfast && L >= 512) ? 512 : 256;
         if (!line_kernel_p2(p.threads, true, p.lg, p.io).fn) return FB_FFT_ERR_UNSUPPORTED_SIZE;
+        // radix-16 stages on the tensor cores where the line has at least two of them' worth (L >= 256)
+        p.tc = tc && line_kernel_p2tc(p.threads, true, p.lg, p.io).fn != nullptr;
         T = p2_tile_lines(p.threads, p.lg, p.io);
         land = p2_land_elems(p.threads, p.lg, p.io);
         d.tws = p2_smem_twiddles(p.lg);
@@ -293,10 +297,11 @@ int make_line_pass(PassPlan& p, TwiddleBuilder& twb, long long L, long long O, l
     d.box_rows = br > 0 ? br : 1;
     d.land_stride = (int)land;
     d.ptw = ptw ? 1 : 0;
-    p.smem = line_smem_bytes(d.land_stride, (int)L, (int)T, nst, p.async_ok, d.tws);
+    const size_t tc_extra = p.tc ? kTcExtraSmem : 0;
+    p.smem = line_smem_bytes(d.land_stride, (int)L, (int)T, nst, p.async_ok, d.tws) + tc_extra;
     if (p.smem > kMaxSmemBytes) {
         p.async_ok = false;
-        p.smem = line_smem_bytes(d.land_stride, (int)L, (int)T, nst, false, d.tws);
+        p.smem = line_smem_bytes(d.land_stride, (int)L, (int)T, nst, false, d.tws) + tc_extra;
     }
     if (p.smem > kMaxSmemBytes) return FB_FFT_ERR_UNSUPPORTED_SIZE;
     p.grid = d.ntiles;  // capped to the resident CTA count when the plan is built
@@ -528,6 +533,7 @@ int schedule_plan(fb_fft_plan_s* p, TwiddleBuilder& twb)
         return rc != FB_FFT_OK ? rc : check_schedule(p);
     }
     const long long B = p->batch;
+    const bool tc = (p->flags & FB_FFT_TENSOR_CORES) != 0;
     if (p->rank == 1 && p->N > FB_FFT_MAX_SMEM_LEN) {
         long long N1, N2;
         int rc = split_fourstep(p->N, &N1, &N2);
@@ -544,7 +550,7 @@ int schedule_plan(fb_fft_plan_s* p, TwiddleBuilder& twb)
         for (long long b0 = 0; b0 < B; b0 += chunk) {
             const long long nb = std::min(chunk, B - b0);
             PassPlan a, r;
-            rc = make_line_pass(a, twb, N1, nb, N2, N2, 1, N, N2, 1, N, true, true, true);
+            rc = make_line_pass(a, twb, N1, nb, N2, N2, 1, N, N2, 1, N, true, true, true, false, 0, tc);
             if (rc != FB_FFT_OK) return rc;
             a.d.ptw_log = plog;
             a.src = kBufIn, a.src_off = b0 * N;
@@ -553,7 +559,7 @@ int schedule_plan(fb_fft_plan_s* p, TwiddleBuilder& twb)
             // stash table offsets in the pointer fields until exec binds them
             a.d.ptw_lo = reinterpret_cast<const float2*>(lo_off);
             a.d.ptw_hi = reinterpret_cast<const float2*>(hi_off);
-            rc = make_line_pass(r, twb, N2, nb, N1, 1, N2, N, N1, 1, N, false, true, false);
+            rc = make_line_pass(r, twb, N2, nb, N1, 1, N2, N, N1, 1, N, false, true, false, false, 0, tc);
             if (rc != FB_FFT_OK) return rc;
             r.src = kBufScratch, r.src_off = 0;
             r.dst = kBufOut, r.dst_off = b0 * N;
@@ -577,9 +583,10 @@ int schedule_plan(fb_fft_plan_s* p, TwiddleBuilder& twb)
             PassPlan q;
             int rc;
             if (S == 1)
-                rc = make_line_pass(q, twb, L, 1, B * Opre, 1, L, 0, 1, L, 0, false, false, false);
+                rc = make_line_pass(q, twb, L, 1, B * Opre, 1, L, 0, 1, L, 0, false, false, false, false, 0, tc);
             else
-                rc = make_line_pass(q, twb, L, B * Opre, S, S, 1, L * S, S, 1, L * S, true, true, false);
+                rc = make_line_pass(q, twb, L, B * Opre, S, S, 1, L * S, S, 1, L * S, true, true, false, false, 0,
+                                    tc);
             if (rc != FB_FFT_OK) return rc;
             q.src = first ? kBufIn : kBufOut;
             q.dst = kBufOut;
@@ -726,7 +733,8 @@ int launch_pass(fb_fft_plan_s* p, const PassPlan& q, const float2* in, float2* o
             d.async_io = 0;
     }
     if (p->debug_timeout && d.async_io) d.debug_extra_tx = 16;
-    const size_t smem = line_smem_bytes(d.land_stride, d.L, 1 << d.logT, d.nst, d.async_io != 0, d.tws);
+    const size_t smem = line_smem_bytes(d.land_stride, d.L, 1 << d.logT, d.nst, d.async_io != 0, d.tws) +
+                        (q.tc ? kTcExtraSmem : 0);
     if (q.last && !fwd && (p->flags & FB_FFT_SCALE_INV_N)) {
         d.apply_scale = 1;
         d.scale = (float)(1.0 / (double)(q.scale_n ? q.scale_n : p->N));
@@ -813,11 +821,17 @@ int exec_many(fb_fft_plan_s* p, const float2* in, float2* out, int direction)
     return FB_FFT_OK;
 }
 
+int tc_pass_count(const std::vector<PassPlan>& passes)
+{
+    return (int)std::count_if(passes.begin(), passes.end(), [](const PassPlan& q) { return q.tc; });
+}
+
 long long plan_elems(const fb_fft_plan_s* p) { return p->many ? p->total : p->N * p->batch; }
 
 int validate(int rank, const long long* dims, long long batch, unsigned flags, long long* N_out)
 {
-    if (rank < 1 || rank > 3 || !dims || batch < 0 || (flags & ~FB_FFT_SCALE_INV_N)) return FB_FFT_ERR_INVALID_ARG;
+    if (rank < 1 || rank > 3 || !dims || batch < 0 || (flags & ~(FB_FFT_SCALE_INV_N | FB_FFT_TENSOR_CORES)))
+        return FB_FFT_ERR_INVALID_ARG;
     long long N = 1;
     for (int d = 0; d < rank; ++d) {
         if (dims[d] < 1) return FB_FFT_ERR_INVALID_ARG;
@@ -979,6 +993,7 @@ int fb_fft_plan_query(int rank, const long long* dims, long long batch, unsigned
     if (rc != FB_FFT_OK) return rc;
     std::memset(info, 0, sizeof(*info));
     info->passes = (int)p.passes.size();
+    info->tc_passes = tc_pass_count(p.passes);
     info->smem_len_max = p.smem_len_max;
     info->scratch_bytes = (long long)p.scratch_bytes;
     info->twiddle_bytes = p.tw_elems * (long long)sizeof(float2);
@@ -1151,6 +1166,7 @@ int fb_fft_plan_many_query(int count, const long long* lengths, unsigned flags, 
     if (rc != FB_FFT_OK) return rc;
     std::memset(info, 0, sizeof(*info));
     info->passes = (int)p.passes.size();
+    info->tc_passes = tc_pass_count(p.passes);
     info->smem_len_max = p.smem_len_max;
     info->scratch_bytes = (long long)p.scratch_bytes;
     info->twiddle_bytes = p.tw_elems * (long long)sizeof(float2);
@@ -1268,6 +1284,7 @@ int fb_fft_plan_info(fb_fft_plan_t plan, fb_fft_info* info)
     if (!info) return FB_FFT_ERR_INVALID_ARG;
     std::memset(info, 0, sizeof(*info));
     info->passes = (int)plan->passes.size();
+    info->tc_passes = tc_pass_count(plan->passes);
     info->smem_len_max = plan->smem_len_max;
     info->scratch_bytes = (long long)plan->scratch_bytes;
     info->twiddle_bytes = plan->tw_elems * (long long)sizeof(float2);

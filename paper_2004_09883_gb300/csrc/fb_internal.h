@@ -99,9 +99,15 @@ struct LineKernel {
     int lg;
     int io;
     int kind = 0;
+    bool tc = false;  // radix-16 stages on the tensor cores
 };
+// Extra shared memory of a tensor-core line pass: B^T (4 KB) + alignment.
+constexpr size_t kTcExtraSmem = 4096 + 128;
 // The kernel for a pass; fn == nullptr when that combination is not compiled.
 LineKernel line_kernel_p2(int threads, bool forward, int lg, int io);
+// Tensor-core variant (power-of-two L >= 256, the thread count the planner
+// picks for that length and layout).
+LineKernel line_kernel_p2tc(int threads, bool forward, int lg, int io);
 LineKernel line_kernel_generic(bool forward);
 LineKernel line_kernel_mixed(bool forward, int lg2);
 // Launch / occupancy / name of a table entry (shared-memory opt-in handled inside).

@@ -15,6 +15,8 @@ LineKernel line_kernel_p2_512_fwd_a(int lg, int io);
 LineKernel line_kernel_p2_512_fwd_b(int lg, int io);
 LineKernel line_kernel_p2_512_inv_a(int lg, int io);
 LineKernel line_kernel_p2_512_inv_b(int lg, int io);
+LineKernel line_kernel_p2tc_fwd(int threads, int lg, int io);
+LineKernel line_kernel_p2tc_inv(int threads, int lg, int io);
 
 LineKernel line_kernel_generic(bool forward)
 {
@@ -33,6 +35,13 @@ LineKernel line_kernel_p2(int threads, bool forward, int lg, int io)
         return forward ? (a ? line_kernel_p2_512_fwd_a(lg, io) : line_kernel_p2_512_fwd_b(lg, io))
                        : (a ? line_kernel_p2_512_inv_a(lg, io) : line_kernel_p2_512_inv_b(lg, io));
     return none;
+}
+
+LineKernel line_kernel_p2tc(int threads, bool forward, int lg, int io)
+{
+    const LineKernel none{nullptr, 0, false, 0, 0};
+    if (lg < 8 || lg > kMaxLineLog2 || io < kIoNN || io > kIoCCP) return none;
+    return forward ? line_kernel_p2tc_fwd(threads, lg, io) : line_kernel_p2tc_inv(threads, lg, io);
 }
 
 namespace {
@@ -86,7 +95,7 @@ void line_kernel_name(const LineKernel& k, char* buf, size_t n)
     if (k.kind == 2)
         snprintf(buf, n, "k_fft_mixed<%d,%s,2^%d>", k.threads, k.fwd ? "fwd" : "inv", k.lg);
     else if (k.kind == 0)
-        snprintf(buf, n, "k_fft_p2<%d,%s,L=%d,%s>", k.threads - 32, k.fwd ? "fwd" : "inv", 1 << k.lg,
+        snprintf(buf, n, "k_fft_p2%s<%d,%s,L=%d,%s>", k.tc ? "tc" : "", k.threads - 32, k.fwd ? "fwd" : "inv", 1 << k.lg,
                  (k.io >= 0 && k.io < 4) ? io_names[k.io] : "?");
     else
         snprintf(buf, n, "k_fft_generic<%d,%s>", k.threads, k.fwd ? "fwd" : "inv");

@@ -9,6 +9,7 @@
 #pragma once
 
 #include "fft_device.cuh"
+#include "fft_tc.cuh"
 
 namespace fbfft {
 
@@ -201,17 +202,114 @@ __device__ __forceinline__ void p2_stage(const PassDesc& d, float2* land, float2
     }
 }
 
+// A radix-16 stage on the tensor cores (fft_tc.cuh): same gather, twiddles
+// and scatter as p2_stage, the 16-point DFT as one FP16 hi/lo matrix product
+// per 128 butterflies.  Needs exactly one butterfly per compute thread and at
+// least two stages (the A tiles live in the work buffer).
 template <int THREADS, bool FWD, int LG, int IO, int S>
+__device__ __forceinline__ void p2_stage_tc(const PassDesc& d, float2* land, float2* work, int Tv, int c0,
+                                            const float2* tws, TcState& tc)
+{
+    using C = P2<THREADS, LG, IO>;
+    constexpr int L = C::L, T = C::T, G = C::G;
+    constexpr int R = 16;
+    constexpr int NS = pow2_ns(LG, S);
+    constexpr int LR = L / R;
+    constexpr bool first = S == 0;
+    constexpr bool last = S == C::NST - 1;
+    constexpr bool tfast = (first && C::IN_T) || (last && C::OUT_T);
+    static_assert(pow2_radix(LG, S) == 16 && C::NST >= 2, "tensor-core stage: radix 16, not the only stage");
+    static_assert(T * LR == THREADS && THREADS % 128 == 0, "tensor-core stage: one butterfly per thread");
+    static_assert(T * L * 8 <= T * C::LS * 8, "A tiles fit the work buffer");
+    const int tid = threadIdx.x;
+    const int t = tfast ? (tid & (T - 1)) : (tid / G);
+    const int j = tfast ? (tid >> C::LOGT) : (tid & (G - 1));
+    const bool tok = t < Tv;
+    float2 v[R];
+    if (tok) {
+        if constexpr (first) {
+#pragma unroll
+            for (int r = 0; r < R; ++r) v[r] = C::IN_T ? land[(j + r * LR) * T + t] : land[t * C::LLS + j + r * LR];
+        } else {
+            const float2* p = work + t * C::LS;
+#pragma unroll
+            for (int r = 0; r < R; ++r) v[r] = p[spad(j + r * LR)];
+        }
+    } else {
+#pragma unroll
+        for (int r = 0; r < R; ++r) v[r] = make_float2(0.f, 0.f);
+    }
+    if constexpr (!first) compute_sync<THREADS>();  // A rows overwrite the work buffer just read
+    const int k = j & (NS - 1);
+    if constexpr (NS > 1) {
+        if constexpr (C::TWS > 0) {
+            const float2* tw = tws + p2_tws_off(LG, S) + k;
+#pragma unroll
+            for (int r = 1; r < R; ++r) v[r] = twmul<FWD>(v[r], tw[(r - 1) * NS]);
+        } else {
+            const float2* tw = d.tw + d.twoff[S] + k;
+#pragma unroll
+            for (int r = 1; r < R; ++r) v[r] = twmul<FWD>(v[r], __ldg(tw + (r - 1) * NS));
+        }
+    }
+    const unsigned abase = smem_u32(work);
+    const int e = tc_put_row(v, abase, tid >> 7, tid & 127);
+    fence_proxy_async();  // the A rows -> visible to the tensor cores
+    compute_sync<THREADS>();
+    if (tid == 0) tc_issue<THREADS / 128>(tc, abase);
+    const bool ok = mbar_wait_bounded(tc.bar, tc.uses & 1u);
+    tc.uses++;
+    if (!ok && (tid & 31) == 0) atomicExch(d.err, 1);
+    tc_fence_after();
+    tc_get_row(tc, e, v);  // every product has landed: the A tiles are dead, the work buffer is free
+    if (!tok) return;
+    if constexpr (!last) {
+        float2* p = work + t * C::LS;
+        const int base = (j - k) * R + k;
+#pragma unroll
+        for (int r = 0; r < R; ++r) p[spad(base + r * NS)] = v[r];
+    } else {
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            const int kk = j + r * LR;
+            float2 y = v[r];
+            if constexpr (C::PTW) {
+                const unsigned m = (unsigned)(c0 + t) * (unsigned)kk;  // < N < 2^31
+                const float2 w = cmul(__ldg(d.ptw_hi + (m >> d.ptw_log)),
+                                      __ldg(d.ptw_lo + (m & ((1u << d.ptw_log) - 1))));
+                y = twmul<FWD>(y, w);
+            }
+            if (d.apply_scale) y = d.scale * y;
+            if constexpr (C::OUT_T)
+                land[kk * T + t] = y;
+            else
+                land[t * C::OLS + kk] = y;
+        }
+    }
+}
+
+// Stage S, on the tensor cores when TC and the stage is radix 16.
+template <int THREADS, bool FWD, int LG, int IO, int S, bool TC>
+__device__ __forceinline__ void p2_run_stage(const PassDesc& d, float2* land, float2* work, int Tv, int c0,
+                                             const float2* tws, TcState& tc)
+{
+    if constexpr (TC && pow2_radix(LG, S) == 16)
+        p2_stage_tc<THREADS, FWD, LG, IO, S>(d, land, work, Tv, c0, tws, tc);
+    else
+        p2_stage<THREADS, FWD, LG, IO, S>(d, land, work, Tv, c0, tws);
+}
+
+template <int THREADS, bool FWD, int LG, int IO, int S, bool TC>
 __device__ __forceinline__ void p2_stages_from(const PassDesc& d, float2* land, float2* work, int Tv, int c0,
-                                               bool async, const float2* tws)
+                                               bool async, const float2* tws, TcState& tc)
 {
     using C = P2<THREADS, LG, IO>;
     if constexpr (S < C::NST) {
-        p2_stage<THREADS, FWD, LG, IO, S>(d, land, work, Tv, c0, tws);
+        p2_run_stage<THREADS, FWD, LG, IO, S, TC>(d, land, work, Tv, c0, tws, tc);
         if constexpr (S == C::NST - 1)
             if (async) fence_proxy_async();  // output tile -> visible to the TMA store
         compute_sync<THREADS>();              // (last stage: the work buffer is free again)
-        p2_stages_from<THREADS, FWD, LG, IO, S + 1>(d, land, work, Tv, c0, async, tws);
+        p2_stages_from<THREADS, FWD, LG, IO, S + 1, TC>(d, land, work, Tv, c0, async, tws, tc);
     }
 }
 
@@ -332,14 +430,16 @@ __device__ __forceinline__ void p2_plain_store(const PassDesc& d, const TileIdx&
 }
 
 // The power-of-two line pass.  THREADS compute threads plus one producer
-// warp.  Persistent CTAs walk tiles blockIdx.x, +gridDim.x, ...  With TMA on
+// warp.  TC: radix-16 stages on the tensor cores (fft_tc.cuh); the CTA then
+// also holds B^T (4 KB after the stage twiddles) and tc_tmem_cols(THREADS)
+// TMEM columns, allocated by compute warp 0 and freed before it exits.  Persistent CTAs walk tiles blockIdx.x, +gridDim.x, ...  With TMA on
 // (d.async_io) the producer warp owns every copy: it loads tile i into landing
 // buffer i%2 (mbarrier full[i%2], counted in bytes), and once the compute
 // warps release a buffer (mbarrier empty[i%2]) it stores the finished tile and
 // reloads the buffer with tile i+2.  Compute warps only wait for `full` and
 // synchronise among themselves on a named barrier, so copy bookkeeping never
 // stalls them.  Every wait is bounded.
-template <int THREADS, bool FWD, int LG, int IO>
+template <int THREADS, bool FWD, int LG, int IO, bool TC = false>
 __global__ void __maxnreg__(96) k_fft_p2(const __grid_constant__ LineArgs a)
 {
     using C = P2<THREADS, LG, IO>;
@@ -348,6 +448,8 @@ __global__ void __maxnreg__(96) k_fft_p2(const __grid_constant__ LineArgs a)
     unsigned char* smem_raw = smem_dyn + ((128u - (smem_u32(smem_dyn) & 127u)) & 127u);
     unsigned long long* full = reinterpret_cast<unsigned long long*>(smem_raw);        // [2]
     unsigned long long* empty = reinterpret_cast<unsigned long long*>(smem_raw) + 2;   // [2]
+    unsigned long long* mma_bar = reinterpret_cast<unsigned long long*>(smem_raw) + 4;
+    unsigned* tmem_slot = reinterpret_cast<unsigned*>(smem_raw + 40);
     float2* land0 = reinterpret_cast<float2*>(smem_raw + 128);
     const bool async = d.async_io != 0;
     float2* work = land0 + (async ? 2 : 1) * C::LAND;
@@ -361,8 +463,9 @@ __global__ void __maxnreg__(96) k_fft_p2(const __grid_constant__ LineArgs a)
         mbar_init(&full[1], 1);
         mbar_init(&empty[0], THREADS);
         mbar_init(&empty[1], THREADS);
-        fence_mbar_init();
     }
+    if (TC && threadIdx.x == 0) mbar_init(mma_bar, 1);
+    if ((async || TC) && threadIdx.x == 0) fence_mbar_init();
     __syncthreads();
 
     if (warp == kProducer) {
@@ -395,6 +498,19 @@ __global__ void __maxnreg__(96) k_fft_p2(const __grid_constant__ LineArgs a)
     }
 
     // ---- compute warps ----
+    TcState tc{0u, mma_bar, 0u, 0u};
+    if constexpr (TC) {
+        unsigned char* bmat = reinterpret_cast<unsigned char*>(
+            (reinterpret_cast<uintptr_t>(tws + C::TWS) + 127) & ~static_cast<uintptr_t>(127));
+        if (warp == 0) tc_alloc(tmem_slot, tc_tmem_cols(THREADS));
+        tc_build_b<THREADS, FWD>(bmat);
+        fence_proxy_async();  // B^T -> visible to the tensor cores
+        tc_fence_before();
+        compute_sync<THREADS>();
+        tc_fence_after();
+        tc.tmem = *tmem_slot;
+        tc.bsm = smem_u32(bmat);
+    }
     if constexpr (C::TWS > 0) {
         p2_copy_twiddles<THREADS, LG, 1>(d, tws);
         compute_sync<THREADS>();
@@ -409,19 +525,19 @@ __global__ void __maxnreg__(96) k_fft_p2(const __grid_constant__ LineArgs a)
             const bool bad = !mbar_wait_bounded(&full[buf], (unsigned)(i >> 1) & 1u);
             if (compute_sync_or<THREADS>(bad)) {
                 if (threadIdx.x == 0) atomicExch(d.err, 1);
-                return;  // the producer's own bounded waits end it
+                break;  // the producer's own bounded waits end it
             }
         } else {
             p2_plain_load<THREADS, LG, IO>(d, ti, land);
             compute_sync<THREADS>();
         }
-        p2_stage<THREADS, FWD, LG, IO, 0>(d, land, work, ti.Tv, c0, tws);
+        p2_run_stage<THREADS, FWD, LG, IO, 0, TC>(d, land, work, ti.Tv, c0, tws, tc);
         if constexpr (C::NST == 1) {
             if (async) fence_proxy_async();
         } else {
             compute_sync<THREADS>();
         }
-        p2_stages_from<THREADS, FWD, LG, IO, 1>(d, land, work, ti.Tv, c0, async, tws);
+        p2_stages_from<THREADS, FWD, LG, IO, 1, TC>(d, land, work, ti.Tv, c0, async, tws, tc);
         if (async) {
             mbar_arrive(&empty[buf]);  // after this thread's proxy fence
         } else {
@@ -430,13 +546,22 @@ __global__ void __maxnreg__(96) k_fft_p2(const __grid_constant__ LineArgs a)
             compute_sync<THREADS>();
         }
     }
+    if constexpr (TC) {
+        tc_fence_before();
+        compute_sync<THREADS>();
+        if (warp == 0) {
+            tc_fence_after();
+            tc_dealloc(tc.tmem, tc_tmem_cols(THREADS));
+        }
+    }
 }
 
-template <int THREADS, bool FWD, int LG, int IO>
+template <int THREADS, bool FWD, int LG, int IO, bool TC = false>
 LineKernel p2_entry()
 {
-    LineKernel k = make_entry<THREADS>(k_fft_p2<THREADS, FWD, LG, IO>, FWD, LG, IO);
+    LineKernel k = make_entry<THREADS>(k_fft_p2<THREADS, FWD, LG, IO, TC>, FWD, LG, IO);
     k.threads = THREADS + 32;  // compute warps + the producer warp
+    k.tc = TC;
     return k;
 }
 

@@ -18,6 +18,7 @@ LIB_PATH = os.path.join(_HERE, "libfbfft.so")
 FORWARD = -1
 INVERSE = 1
 SCALE_INV_N = 0x1
+TENSOR_CORES = 0x2
 MAX_SMEM_LEN = 4096
 MAX_1D_LEN = 4096 * 4096
 
@@ -38,7 +39,7 @@ class FFTError(RuntimeError):
 
 
 class Info(ctypes.Structure):
-    _fields_ = [("passes", ctypes.c_int), ("reserved", ctypes.c_int),
+    _fields_ = [("passes", ctypes.c_int), ("tc_passes", ctypes.c_int),
                 ("smem_len_max", ctypes.c_longlong), ("scratch_bytes", ctypes.c_longlong),
                 ("twiddle_bytes", ctypes.c_longlong), ("elements", ctypes.c_longlong),
                 ("batch", ctypes.c_longlong)]
@@ -148,12 +149,16 @@ def split(n: int) -> tuple[int, int]:
     return n1.value, n2.value
 
 
-def plan_query(dims, batch: int = 1, scale_inv_n: bool = False) -> dict:
+def _flags(scale_inv_n: bool, tensor_cores: bool) -> int:
+    return (SCALE_INV_N if scale_inv_n else 0) | (TENSOR_CORES if tensor_cores else 0)
+
+
+def plan_query(dims, batch: int = 1, scale_inv_n: bool = False, tensor_cores: bool = False) -> dict:
     """Host-only planner run: what fb_fft_plan would build (no GPU needed)."""
     dims = [int(d) for d in dims]
     cd = (_ll * len(dims))(*dims)
     inf = Info()
-    _check(lib.fb_fft_plan_query(len(dims), cd, int(batch), SCALE_INV_N if scale_inv_n else 0,
+    _check(lib.fb_fft_plan_query(len(dims), cd, int(batch), _flags(scale_inv_n, tensor_cores),
                                  ctypes.byref(inf)), "fb_fft_plan_query")
     return {f: getattr(inf, f) for f, _ in Info._fields_ if f != "reserved"}
 
@@ -204,11 +209,11 @@ def _stream_handle(stream) -> int:
 class Plan:
     """A planned complex64 C2C transform: ``dims`` (row-major) x ``batch``."""
 
-    def __init__(self, dims, batch: int = 1, scale_inv_n: bool = False, stream=None):
+    def __init__(self, dims, batch: int = 1, scale_inv_n: bool = False, stream=None, tensor_cores: bool = False):
         dims = [int(d) for d in (dims if hasattr(dims, "__len__") else [dims])]
         self.dims = dims
         self.batch = int(batch)
-        self.flags = SCALE_INV_N if scale_inv_n else 0
+        self.flags = _flags(scale_inv_n, tensor_cores)
         self.n = int(np.prod(dims))
         self._h = _vp()
         cd = (_ll * len(dims))(*dims)
@@ -461,16 +466,16 @@ class Server:
         dims = [int(d) for d in (dims if hasattr(dims, "__len__") else [dims])]
         return len(dims), (_ll * len(dims))(*dims)
 
-    def prepare(self, dims, batch: int = 1, scale_inv_n: bool = False) -> None:
+    def prepare(self, dims, batch: int = 1, scale_inv_n: bool = False, tensor_cores: bool = False) -> None:
         r, cd = self._dims(dims)
-        _check(lib.fb_fft_server_prepare(self._h, r, cd, int(batch), SCALE_INV_N if scale_inv_n else 0),
+        _check(lib.fb_fft_server_prepare(self._h, r, cd, int(batch), _flags(scale_inv_n, tensor_cores)),
                "fb_fft_server_prepare")
 
     def submit_ptr(self, dims, in_ptr: int, out_ptr: int, tag: int, direction: int = FORWARD, batch: int = 1,
-                   scale_inv_n: bool = False, host_io: bool = False) -> None:
+                   scale_inv_n: bool = False, host_io: bool = False, tensor_cores: bool = False) -> None:
         """Queue one transform on raw pointers (device, or host when host_io)."""
         r, cd = self._dims(dims)
-        _check(lib.fb_fft_server_submit(self._h, r, cd, int(batch), SCALE_INV_N if scale_inv_n else 0,
+        _check(lib.fb_fft_server_submit(self._h, r, cd, int(batch), _flags(scale_inv_n, tensor_cores),
                                         int(direction), _vp(in_ptr), _vp(out_ptr), 1 if host_io else 0, int(tag)),
                "fb_fft_server_submit")
 

@@ -254,3 +254,23 @@ def test_many_planner_schedules_pass_host_checks(fb, seed):
     distinct_small = len({n for n in lens if n <= fb.MAX_SMEM_LEN})
     assert info["passes"] >= distinct_small + 2 * len({n for n in lens if n > fb.MAX_SMEM_LEN})
     assert info["scratch_bytes"] >= 8 * max(lens)
+
+
+@pytest.mark.parametrize("dims,tc", [([128], 0), ([256], 1), ([1024], 1), ([4096], 1), ([1 << 20], 2), ([1 << 13], 0), ([1 << 16], 2),
+                                     ([256, 256], 2), ([16, 2048, 8], 1), ([300, 256], 1), ([60, 45], 0),
+                                     ([3 * 1024], 0)])
+def test_tensor_core_flag_planning(fb, dims, tc):
+    """Passes over power-of-two lines of length >= 256 take the tensor-core
+    kernels; the pass list is otherwise the FP32 plan's."""
+    q = fb.plan_query(dims, 2, tensor_cores=True)
+    q32 = fb.plan_query(dims, 2)
+    assert q["tc_passes"] == tc and q32["tc_passes"] == 0
+    assert q["passes"] == q32["passes"] and q["scratch_bytes"] == q32["scratch_bytes"]
+
+
+def test_tensor_core_flag_rejected_where_unsupported(fb):
+    lens = (ctypes.c_longlong * 2)(256, 512)
+    inf = fb.Info()
+    assert fb.lib.fb_fft_plan_many_query(2, lens, fb.TENSOR_CORES, ctypes.byref(inf)) == -1
+    assert fb.lib.fb_fft_exec_1d_noalloc(None, None, 256, 0, -1, fb.TENSOR_CORES, None) == -1
+    assert fb.lib.fb_fft_plan_query(1, (ctypes.c_longlong * 1)(256), 1, 0x4, ctypes.byref(inf)) == -1
