@@ -117,7 +117,7 @@ int fb_fft_set_graph(fb_fft_plan_t plan, int enable);
  *   streams            side streams the length groups spread over (1..32; default 4)
  *   use_graph          1/0: replay one CUDA graph per exec (default) / launch directly;
  *                      any other value = default
- *   chunk_bytes        four-step intermediate per chunk of a length group (default 32 MiB)
+ *   chunk_bytes        four-step intermediate per chunk of a length group (default 512 MiB)
  *   odd_radices_first  lengths with factors 3/5 (generic kernel): 1 runs the 5s and 3s
  *                      before the power-of-two radices
  *   max_lines          generic kernel: at most this many lines per tile (0 = no extra cap)

@@ -8,8 +8,10 @@
 //                                multiplied by exp(s*2*pi*i*n2*k1/N)  (-> scratch)
 //                        pass B: length-N2 DFTs along the N1 rows, written
 //                                transposed to X[k1 + N1*k2]          (-> out)
-//                        The batch runs in chunks whose intermediate is small
-//                        enough to stay in the 126 MB L2 between A and B.
+//                        The batch runs in chunks of at most 512 MiB of
+//                        intermediate: few, long launches keep every CTA's
+//                        TMA pipeline full (measured faster than chunks small
+//                        enough to keep the intermediate in the 126 MB L2).
 //   rank 2/3             one pass per axis (last axis first), in place on out.
 #include <cuda_runtime.h>
 
@@ -52,13 +54,13 @@ int cuda_fail(cudaError_t e, const char* what)
 constexpr uint32_t kMagic = 0xFBFF7A11u;
 constexpr uint32_t kDead = 0xDEADFBFFu;
 
-// Four-step batch chunk: intermediate bytes kept L2-resident between passes.
+// Four-step batch chunk: bytes of intermediate (scratch) per column/row pass pair.
 long long fourstep_chunk_bytes()
 {
     static long long v = [] {
         const char* s = std::getenv("FB_FFT_FOURSTEP_CHUNK_BYTES");
         long long b = s ? std::atoll(s) : 0;
-        return b > 0 ? b : (32LL << 20);
+        return b > 0 ? b : (512LL << 20);
     }();
     return v;
 }
@@ -242,10 +244,11 @@ int make_line_pass(PassPlan& p, TwiddleBuilder& twb, long long L, long long O, l
         // so long lines on a strided side take the 512-thread kernel.
         if (in_tfast && !out_tfast) return FB_FFT_ERR_UNSUPPORTED_SIZE;  // never planned
         p.io = ptw ? kIoCCP : (in_tfast ? kIoCC : (out_tfast ? kIoNC : kIoNN));
-        p.threads = (cfast && L >= 512) ? 512 : 256;
+        // radix-16 stages on the tensor cores for L >= 256: 256-thread CTAs, two per
+        // SM, so one CTA's butterflies overlap the other's matrix products
+        p.tc = tc && line_kernel_p2tc(256, true, p.lg, p.io).fn != nullptr;
+        p.threads = (!p.tc && cfast && L >= 512) ? 512 : 256;
         if (!line_kernel_p2(p.threads, true, p.lg, p.io).fn) return FB_FFT_ERR_UNSUPPORTED_SIZE;
-        // radix-16 stages on the tensor cores where the line has at least two of them' worth (L >= 256)
-        p.tc = tc && line_kernel_p2tc(p.threads, true, p.lg, p.io).fn != nullptr;
         T = p2_tile_lines(p.threads, p.lg, p.io);
         land = p2_land_elems(p.threads, p.lg, p.io);
         d.tws = p2_smem_twiddles(p.lg);

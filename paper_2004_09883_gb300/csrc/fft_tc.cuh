@@ -103,10 +103,6 @@ __device__ __forceinline__ void st_shared_v4(unsigned addr, unsigned a, unsigned
 {
     asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(addr), "r"(a), "r"(b), "r"(c), "r"(d) : "memory");
 }
-__device__ __forceinline__ unsigned pack_half2(__half lo_k, __half hi_k)
-{
-    return (unsigned)__half_as_ushort(lo_k) | ((unsigned)__half_as_ushort(hi_k) << 16);
-}
 
 // B^T = [M_hi | M_lo] for direction FWD, in the K-major layout (all compute threads).
 template <int THREADS, bool FWD>
@@ -116,12 +112,13 @@ __device__ __forceinline__ void tc_build_b(unsigned char* b)
         const int n = e >> 6, k = e & 63;
         const int kk = k & 31;
         const int r = kk & 15, jj = n & 15;
-        double s, c;
-        sincospi((double)((jj * r) & 15) / 8.0, &s, &c);  // exp(s 2 pi i j r / 16) = c + i (sign) s
-        const double wr = c, wi = FWD ? -s : s;
-        const double val = kk < 16 ? (n < 16 ? wr : wi) : (n < 16 ? -wi : wr);
-        const __half hi = __float2half_rn((float)val);
-        const __half out = k < 32 ? hi : __float2half_rn((float)(val - (double)__half2float(hi)));
+        float s, c;
+        // FP32 is enough: the FP16 pair keeps ~22 bits; FP64 is a slow unit on this part
+        sincospif((float)((jj * r) & 15) * 0.125f, &s, &c);  // exp(s 2 pi i j r / 16) = c + i (sign) s
+        const float wr = c, wi = FWD ? -s : s;
+        const float val = kk < 16 ? (n < 16 ? wr : wi) : (n < 16 ? -wi : wr);
+        const __half hi = __float2half_rn(val);
+        const __half out = k < 32 ? hi : __float2half_rn(val - __half2float(hi));
         const int off = (n >> 3) * kTcSbo + (k >> 3) * kTcLbo + (n & 7) * 16 + (k & 7) * 2;
         *reinterpret_cast<__half*>(b + off) = out;
     }
@@ -155,10 +152,11 @@ __device__ __forceinline__ int tc_put_row(const float2 (&v)[16], unsigned abase,
             const int k0 = c * 8 + 2 * p;
             const float a = (k0 < 16 ? v[k0].x : v[k0 - 16].y) * down;
             const float b = (k0 + 1 < 16 ? v[k0 + 1].x : v[k0 + 1 - 16].y) * down;
-            const __half ha = __float2half_rn(a), hb = __float2half_rn(b);
-            const __half la = __float2half_rn(a - __half2float(ha)), lb = __float2half_rn(b - __half2float(hb));
-            hw[p] = pack_half2(ha, hb);
-            lw[p] = pack_half2(la, lb);
+            const __half2 h = __floats2half2_rn(a, b);  // (a, b) -> low, high half
+            const float2 hf = __half22float2(h);
+            const __half2 l = __floats2half2_rn(a - hf.x, b - hf.y);
+            hw[p] = *reinterpret_cast<const unsigned*>(&h);
+            lw[p] = *reinterpret_cast<const unsigned*>(&l);
         }
         st_shared_v4(rowaddr + c * kTcLbo, hw[0], hw[1], hw[2], hw[3]);
         st_shared_v4(rowaddr + (4 + c) * kTcLbo, lw[0], lw[1], lw[2], lw[3]);

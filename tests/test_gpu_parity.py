@@ -112,11 +112,27 @@ def test_1d_fourstep(fb, n, batch, direction):
     assert_close(y, ref_fft(x, [n], direction), [n])
 
 
-def test_fourstep_in_place_chunked(fb):
-    n, batch = 1 << 16, 70  # 70 x 512 KiB spans several L2-sized chunks, ragged last chunk
+def test_fourstep_in_place_one_chunk(fb):
+    n, batch = 1 << 16, 70
     x = inputs.uniform_c64((batch, n), 5)
     y = gpu_fft(fb, x, [n], -1, inplace=True)
     assert_close(y, ref_fft(x, [n], -1), [n])
+
+
+def test_fourstep_batch_in_several_chunks(fb):
+    """1100 x 2^16 values = 550 MiB of intermediate: a 512 MiB chunk of 1024
+    transforms, then a ragged chunk of 76; items at both chunk edges are checked."""
+    import torch
+    n, batch = 1 << 16, 1100
+    x = torch.from_numpy(inputs.uniform_c64((batch, n), 6)).cuda()
+    with fb.Plan([n], batch) as p:
+        assert p.info()["scratch_bytes"] == 1024 * n * 8
+        y = p.exec(x, x, -1)  # in place
+        torch.cuda.synchronize()
+        p.check()
+    x0 = inputs.uniform_c64((batch, n), 6)
+    for i in (0, 1023, 1024, 1099):
+        assert_close(y[i].cpu().numpy(), ref_fft(x0[i], [n], -1), [n], f"item {i}")
 
 
 # --------------------------------------------------------------------------
