@@ -213,6 +213,38 @@ LineKernel pass_kernel(const PassPlan& q, bool fwd)
     return line_kernel_p2(q.threads, fwd, q.lg, q.io);
 }
 
+// Dynamic shared memory of a pass's kernel (exact for the compile-time
+// power-of-two kernels, a bound for the others).
+size_t pass_smem(const PassPlan& q, bool async)
+{
+    const size_t ptw = q.d.ptw_smem ? (size_t)((1LL << q.d.ptw_log) + q.d.ptw_hi_cnt) * sizeof(float2) : 0;
+    if (q.kind == 0) return (size_t)p2_smem_bytes(q.threads, q.lg, q.io, async, q.tc) + ptw;
+    return line_smem_bytes(q.d.land_stride, q.d.L, 1 << q.d.logT, q.d.nst, async, q.d.tws);
+}
+
+// Resident CTAs per SM of a pass (shared memory and the 96-register cap).
+int pass_ctas_per_sm(const PassPlan& q, size_t smem)
+{
+    const int by_smem = (int)(233472 / (smem + 1024));  // 228 KB per SM, 1 KB reserved per CTA
+    const int by_regs = 65536 / ((q.threads + 32) * 96);
+    return std::min(by_smem, by_regs);
+}
+
+// Four-step column pass (ptw_log set): keep the post-twiddle tables in shared
+// memory when that costs the compile-time kernel no resident CTA.
+void ptw_to_smem(PassPlan& a, long long hi_cnt)
+{
+    if (a.kind != 0 || a.tc || !a.d.ptw) return;
+    const int before = pass_ctas_per_sm(a, a.smem);
+    PassPlan b = a;
+    b.d.ptw_smem = 1;
+    b.d.ptw_hi_cnt = (int)hi_cnt;
+    const size_t smem = pass_smem(b, b.async_ok);
+    if (smem > kMaxSmemBytes || pass_ctas_per_sm(b, smem) < before) return;
+    a = b;
+    a.smem = smem;
+}
+
 // Fill a line pass: L-point DFTs over lines (o, c); strides in elements.
 int make_line_pass(PassPlan& p, TwiddleBuilder& twb, long long L, long long O, long long C,
                    long long in_sn, long long in_sc, long long in_so, long long out_sk, long long out_sc,
@@ -300,11 +332,10 @@ int make_line_pass(PassPlan& p, TwiddleBuilder& twb, long long L, long long O, l
     d.box_rows = br > 0 ? br : 1;
     d.land_stride = (int)land;
     d.ptw = ptw ? 1 : 0;
-    const size_t tc_extra = p.tc ? kTcExtraSmem : 0;
-    p.smem = line_smem_bytes(d.land_stride, (int)L, (int)T, nst, p.async_ok, d.tws) + tc_extra;
+    p.smem = pass_smem(p, p.async_ok);
     if (p.smem > kMaxSmemBytes) {
         p.async_ok = false;
-        p.smem = line_smem_bytes(d.land_stride, (int)L, (int)T, nst, false, d.tws) + tc_extra;
+        p.smem = pass_smem(p, false);
     }
     if (p.smem > kMaxSmemBytes) return FB_FFT_ERR_UNSUPPORTED_SIZE;
     p.grid = d.ntiles;  // capped to the resident CTA count when the plan is built
@@ -465,6 +496,7 @@ int schedule_many(fb_fft_plan_s* p, TwiddleBuilder& twb)
             a.d.ptw_log = plog;
             a.d.ptw_lo = reinterpret_cast<const float2*>(lo_off);
             a.d.ptw_hi = reinterpret_cast<const float2*>(hi_off);
+            ptw_to_smem(a, hi_cnt);
             a.off_in_idx = at;
             if ((N1 & (N1 - 1)) != 0) a.async_ok = false;
             a.src = kBufIn, a.dst = kBufScratch;
@@ -556,6 +588,7 @@ int schedule_plan(fb_fft_plan_s* p, TwiddleBuilder& twb)
             rc = make_line_pass(a, twb, N1, nb, N2, N2, 1, N, N2, 1, N, true, true, true, false, 0, tc);
             if (rc != FB_FFT_OK) return rc;
             a.d.ptw_log = plog;
+            ptw_to_smem(a, hi_cnt);
             a.src = kBufIn, a.src_off = b0 * N;
             a.dst = kBufScratch, a.dst_off = 0;
             a.group = 0;
@@ -736,8 +769,7 @@ int launch_pass(fb_fft_plan_s* p, const PassPlan& q, const float2* in, float2* o
             d.async_io = 0;
     }
     if (p->debug_timeout && d.async_io) d.debug_extra_tx = 16;
-    const size_t smem = line_smem_bytes(d.land_stride, d.L, 1 << d.logT, d.nst, d.async_io != 0, d.tws) +
-                        (q.tc ? kTcExtraSmem : 0);
+    const size_t smem = pass_smem(q, d.async_io != 0);
     if (q.last && !fwd && (p->flags & FB_FFT_SCALE_INV_N)) {
         d.apply_scale = 1;
         d.scale = (float)(1.0 / (double)(q.scale_n ? q.scale_n : p->N));

@@ -62,6 +62,8 @@ struct PassDesc {
     int* err;              // device error word: 1 = a bounded wait gave up
     unsigned debug_extra_tx;  // test hook: bytes announced per tile that never arrive
     int tws;               // stage-twiddle entries the kernel copies to shared memory
+    int ptw_smem;          // 1: the kernel copies the four-step tables (ptw_lo, ptw_hi) to shared memory
+    int ptw_hi_cnt;        // entries of ptw_hi (ptw_lo has 2^ptw_log)
     // Batched uneven lengths: element offset of each transform's start in
     // in / out (device arrays, or null for the regular strides above).
     // Contiguous layouts index them by line, strided ones by outer index.

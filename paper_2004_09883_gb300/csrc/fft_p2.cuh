@@ -62,6 +62,28 @@ __host__ __device__ constexpr int p2_land_elems(int threads, int lg, int io)
     return (p2_max(in_e, out_e) + 15) & ~15;
 }
 
+// Padded work-buffer line stride.  Strided modes read/write it across lines
+// (consecutive threads on consecutive lines): an odd stride.  The contiguous
+// mode with G < 16 threads per line puts 16/G lines in one half-warp: a stride
+// of G (mod 16) values puts them on disjoint banks.
+__host__ __device__ constexpr int p2_work_stride(int threads, int lg, int io)
+{
+    const int L = 1 << lg;
+    const int LS0 = L + L / 16;
+    const int G = threads / p2_tile_lines(threads, lg, io);
+    return (io == kIoNN && G < 16) ? LS0 + ((G - LS0 % 16) % 16 + 16) % 16 : LS0 + 1;
+}
+// Dynamic shared memory of a power-of-two line pass: alignment slack and
+// mbarriers (256 B), landing buffer(s), the work buffer (when there is more
+// than one stage), stage twiddles, and for tensor-core kernels B^T + alignment.
+__host__ __device__ constexpr long long p2_smem_bytes(int threads, int lg, int io, bool async, bool tc)
+{
+    return 256 + 8LL * (p2_land_elems(threads, lg, io) * (async ? 2 : 1) +
+                        (pow2_nst(lg) > 1 ? (long long)p2_work_stride(threads, lg, io) * p2_tile_lines(threads, lg, io) : 0) +
+                        p2_smem_twiddles(lg)) +
+           (tc ? (long long)kTcExtraSmem : 0);
+}
+
 template <int THREADS, int LG, int IO>
 struct P2 {
     static constexpr int L = 1 << LG;
@@ -72,12 +94,7 @@ struct P2 {
     static constexpr int LOGT = ilog2(T);
     static constexpr int G = THREADS / T;
     static constexpr int NST = pow2_nst(LG);
-    // Padded work-buffer line stride.  Strided modes read/write it across
-    // lines (consecutive threads on consecutive lines): an odd stride.  The
-    // contiguous mode with G < 16 threads per line puts 16/G lines in one
-    // half-warp: a stride of G (mod 16) values puts them on disjoint banks.
-    static constexpr int LS0 = L + L / 16;
-    static constexpr int LS = (IO == kIoNN && G < 16) ? LS0 + ((G - LS0 % 16) % 16 + 16) % 16 : LS0 + 1;
+    static constexpr int LS = p2_work_stride(THREADS, LG, IO);  // padded work-buffer line stride
     static constexpr int LLS = L + p2_row_pad(THREADS, LG, IO, false);  // landing line stride (contiguous in)
     static constexpr int OLS = L + p2_row_pad(THREADS, LG, IO, true);   // landing line stride (contiguous out)
     static constexpr int LAND = p2_land_elems(THREADS, LG, IO);
@@ -187,8 +204,14 @@ __device__ __forceinline__ void p2_stage(const PassDesc& d, float2* land, float2
                     float2 y = v[q][r];
                     if constexpr (C::PTW) {
                         const unsigned m = (unsigned)(c0 + t) * (unsigned)kk;  // < N < 2^31
-                        const float2 w = cmul(__ldg(d.ptw_hi + (m >> d.ptw_log)),
-                                              __ldg(d.ptw_lo + (m & ((1u << d.ptw_log) - 1))));
+                        const unsigned mlo = m & ((1u << d.ptw_log) - 1), mhi = m >> d.ptw_log;
+                        float2 w;
+                        if (d.ptw_smem) {  // tables copied behind the stage twiddles
+                            const float2* pt = tws + C::TWS;
+                            w = cmul(pt[(1u << d.ptw_log) + mhi], pt[mlo]);
+                        } else {
+                            w = cmul(__ldg(d.ptw_hi + mhi), __ldg(d.ptw_lo + mlo));
+                        }
                         y = twmul<FWD>(y, w);
                     }
                     if (d.apply_scale) y = d.scale * y;
@@ -514,6 +537,15 @@ __global__ void __maxnreg__(96) k_fft_p2(const __grid_constant__ LineArgs a)
     if constexpr (C::TWS > 0) {
         p2_copy_twiddles<THREADS, LG, 1>(d, tws);
         compute_sync<THREADS>();
+    }
+    if constexpr (C::PTW && !TC) {
+        if (d.ptw_smem) {  // four-step tables: lo then hi, behind the stage twiddles
+            float2* pt = tws + C::TWS;
+            const int lo = 1 << d.ptw_log;
+            for (int e = threadIdx.x; e < lo; e += THREADS) pt[e] = __ldg(d.ptw_lo + e);
+            for (int e = threadIdx.x; e < d.ptw_hi_cnt; e += THREADS) pt[lo + e] = __ldg(d.ptw_hi + e);
+            compute_sync<THREADS>();
+        }
     }
     int i = 0;
     for (long long tile = blockIdx.x; tile < d.ntiles; tile += step, ++i) {
