@@ -226,7 +226,8 @@ size_t pass_smem(const PassPlan& q, bool async)
 int pass_ctas_per_sm(const PassPlan& q, size_t smem)
 {
     const int by_smem = (int)(233472 / (smem + 1024));  // 228 KB per SM, 1 KB reserved per CTA
-    const int by_regs = 65536 / ((q.threads + 32) * 96);
+    const int by_regs = q.kind == 0 ? 65536 / ((q.threads + p2_producer_threads(q.lg)) * p2_launch_regs(q.threads, q.lg))
+                                    : 65536 / ((q.threads + 32) * 96);
     return std::min(by_smem, by_regs);
 }
 

@@ -101,7 +101,10 @@ struct LineKernel {
     int lg;
     int io;
     int kind = 0;
-    bool tc = false;  // radix-16 stages on the tensor cores
+    bool tc = false;     // radix-16 stages on the tensor cores
+    int producers = 0;   // threads beside the compute threads (power-of-two kernels: producer warp(s))
+    int split_regs = 0;  // > 0: registers per thread the kernel must be launched with (it
+                         // rebalances them with setmaxnreg, which needs exactly that pool)
 };
 // Extra shared memory of a tensor-core line pass: B^T (4 KB) + alignment.
 constexpr size_t kTcExtraSmem = 4096 + 128;

@@ -64,6 +64,9 @@ cudaError_t ensure_smem_attr(const LineKernel& k)
     cudaFuncAttributes fa;
     e = cudaFuncGetAttributes(&fa, (const void*)k.fn);
     if (e != cudaSuccess) return e;
+    // a kernel that rebalances registers with setmaxnreg must get exactly the
+    // pool its split was sized for; with fewer, setmaxnreg.inc would never return
+    if (k.split_regs > 0 && fa.numRegs != k.split_regs) return cudaErrorInvalidKernelImage;
     e = cudaFuncSetAttribute((const void*)k.fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              optin - (int)fa.sharedSizeBytes);
     if (e != cudaSuccess) return e;
@@ -95,7 +98,7 @@ void line_kernel_name(const LineKernel& k, char* buf, size_t n)
     if (k.kind == 2)
         snprintf(buf, n, "k_fft_mixed<%d,%s,2^%d>", k.threads, k.fwd ? "fwd" : "inv", k.lg);
     else if (k.kind == 0)
-        snprintf(buf, n, "k_fft_p2%s<%d,%s,L=%d,%s>", k.tc ? "tc" : "", k.threads - 32, k.fwd ? "fwd" : "inv", 1 << k.lg,
+        snprintf(buf, n, "k_fft_p2%s<%d,%s,L=%d,%s>", k.tc ? "tc" : "", k.threads - k.producers, k.fwd ? "fwd" : "inv", 1 << k.lg,
                  (k.io >= 0 && k.io < 4) ? io_names[k.io] : "?");
     else
         snprintf(buf, n, "k_fft_generic<%d,%s>", k.threads, k.fwd ? "fwd" : "inv");

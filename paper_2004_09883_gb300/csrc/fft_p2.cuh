@@ -462,8 +462,35 @@ __device__ __forceinline__ void p2_plain_store(const PassDesc& d, const TileIdx&
 // reloads the buffer with tile i+2.  Compute warps only wait for `full` and
 // synchronise among themselves on a named barrier, so copy bookkeeping never
 // stalls them.  Every wait is bounded.
+// Register split.  Three-stage schedules (L >= 512) need ~124 registers per
+// compute thread, but with one producer warp beside 8 or 16 compute warps one
+// SM sub-partition holds 5 warps and the cap is 96 (16384 registers each).
+// Those kernels get a whole producer warpgroup instead: it lowers its
+// registers to 24 (setmaxnreg.dec) and the compute warps raise theirs from
+// the launch count to what the released registers allow (setmaxnreg.inc),
+// per sub-partition: 4 x 112 + 24 <= 5 x 96 (512 threads, 1 CTA per SM),
+// 2 x (2 x 104 + 24) <= 2 x 3 x 80 (256 threads, 2 CTAs per SM).
+__host__ __device__ constexpr bool p2_split(int lg) { return pow2_nst(lg) >= 3; }
+__host__ __device__ constexpr int p2_producer_threads(int lg) { return p2_split(lg) ? 128 : 32; }
+__host__ __device__ constexpr int p2_launch_regs(int threads, int lg)
+{
+    return p2_split(lg) ? (threads == 512 ? 96 : 80) : 96;
+}
+template <int THREADS, int LG>
+struct P2Regs {
+    static constexpr bool SPLIT = p2_split(LG);
+    static constexpr int PRODUCER_THREADS = p2_producer_threads(LG);
+    static constexpr int LAUNCH = p2_launch_regs(THREADS, LG);
+    static constexpr int PRODUCER = 24;
+    static constexpr int COMPUTE =
+        SPLIT ? ((THREADS + PRODUCER_THREADS) * LAUNCH - PRODUCER_THREADS * PRODUCER) / THREADS / 8 * 8 : LAUNCH;
+    static_assert(THREADS * COMPUTE + PRODUCER_THREADS * PRODUCER <= (THREADS + PRODUCER_THREADS) * LAUNCH,
+                  "register split exceeds the CTA's launch allocation");
+    static_assert(!SPLIT || (THREADS == 256 || THREADS == 512), "register split sized for 256 or 512 threads");
+};
+
 template <int THREADS, bool FWD, int LG, int IO, bool TC = false>
-__global__ void __maxnreg__(96) k_fft_p2(const __grid_constant__ LineArgs a)
+__global__ void __maxnreg__((P2Regs<THREADS, LG>::LAUNCH)) k_fft_p2(const __grid_constant__ LineArgs a)
 {
     using C = P2<THREADS, LG, IO>;
     const PassDesc& d = a.d;
@@ -491,8 +518,10 @@ __global__ void __maxnreg__(96) k_fft_p2(const __grid_constant__ LineArgs a)
     if ((async || TC) && threadIdx.x == 0) fence_mbar_init();
     __syncthreads();
 
-    if (warp == kProducer) {
-        if (!async) return;
+    using RG = P2Regs<THREADS, LG>;
+    if (warp >= kProducer) {
+        if constexpr (RG::SPLIT) asm volatile("setmaxnreg.dec.sync.aligned.u32 %0;" ::"n"(RG::PRODUCER));
+        if (warp != kProducer || !async) return;  // the rest of a producer warpgroup has nothing to do
         // ---- producer warp ----
         bool ok = true;
         int i = 0;
@@ -521,6 +550,7 @@ __global__ void __maxnreg__(96) k_fft_p2(const __grid_constant__ LineArgs a)
     }
 
     // ---- compute warps ----
+    if constexpr (RG::SPLIT) asm volatile("setmaxnreg.inc.sync.aligned.u32 %0;" ::"n"(RG::COMPUTE));
     TcState tc{0u, mma_bar, 0u, 0u};
     if constexpr (TC) {
         unsigned char* bmat = reinterpret_cast<unsigned char*>(
@@ -592,7 +622,9 @@ template <int THREADS, bool FWD, int LG, int IO, bool TC = false>
 LineKernel p2_entry()
 {
     LineKernel k = make_entry<THREADS>(k_fft_p2<THREADS, FWD, LG, IO, TC>, FWD, LG, IO);
-    k.threads = THREADS + 32;  // compute warps + the producer warp
+    k.threads = THREADS + P2Regs<THREADS, LG>::PRODUCER_THREADS;  // compute warps + producer warp(s)
+    k.producers = P2Regs<THREADS, LG>::PRODUCER_THREADS;
+    k.split_regs = P2Regs<THREADS, LG>::SPLIT ? P2Regs<THREADS, LG>::LAUNCH : 0;
     k.tc = TC;
     return k;
 }
