@@ -76,6 +76,17 @@ int many_streams()
     return v;
 }
 
+// CTA size of passes over short contiguous lines (128 or 256 compute threads).
+int nn_small_threads()
+{
+    static int v = [] {
+        const char* s = std::getenv("FB_FFT_NN_SMALL_THREADS");
+        const int n = s ? std::atoi(s) : 0;
+        return n == 256 ? 256 : 128;
+    }();
+    return v;
+}
+
 enum BufKind { kBufIn = 0, kBufOut = 1, kBufScratch = 2 };
 constexpr size_t kMaxSmemBytes = 227 * 1024;
 
@@ -281,6 +292,8 @@ int make_line_pass(PassPlan& p, TwiddleBuilder& twb, long long L, long long O, l
         // SM, so one CTA's butterflies overlap the other's matrix products
         p.tc = tc && line_kernel_p2tc(256, true, p.lg, p.io).fn != nullptr;
         p.threads = (!p.tc && cfast && L >= 512) ? 512 : 256;
+        // short contiguous lines: 128-thread CTAs, three per SM, three tiles in flight each
+        if (!p.tc && !cfast && L >= 32 && L <= 256 && nn_small_threads() == 128) p.threads = 128;
         if (!line_kernel_p2(p.threads, true, p.lg, p.io).fn) return FB_FFT_ERR_UNSUPPORTED_SIZE;
         T = p2_tile_lines(p.threads, p.lg, p.io);
         land = p2_land_elems(p.threads, p.lg, p.io);

@@ -76,9 +76,13 @@ __host__ __device__ constexpr int p2_work_stride(int threads, int lg, int io)
 // Dynamic shared memory of a power-of-two line pass: alignment slack and
 // mbarriers (256 B), landing buffer(s), the work buffer (when there is more
 // than one stage), stage twiddles, and for tensor-core kernels B^T + alignment.
+// Landing buffers in flight per CTA: 128-thread CTAs (short contiguous lines,
+// three CTAs per SM) keep three, so two tile loads stay in flight while one
+// tile is transformed.
+__host__ __device__ constexpr int p2_nbuf(int threads) { return threads == 128 ? 3 : 2; }
 __host__ __device__ constexpr long long p2_smem_bytes(int threads, int lg, int io, bool async, bool tc)
 {
-    return 256 + 8LL * (p2_land_elems(threads, lg, io) * (async ? 2 : 1) +
+    return 256 + 8LL * (p2_land_elems(threads, lg, io) * (async ? p2_nbuf(threads) : 1) +
                         (pow2_nst(lg) > 1 ? (long long)p2_work_stride(threads, lg, io) * p2_tile_lines(threads, lg, io) : 0) +
                         p2_smem_twiddles(lg)) +
            (tc ? (long long)kTcExtraSmem : 0);
@@ -98,6 +102,7 @@ struct P2 {
     static constexpr int LLS = L + p2_row_pad(THREADS, LG, IO, false);  // landing line stride (contiguous in)
     static constexpr int OLS = L + p2_row_pad(THREADS, LG, IO, true);   // landing line stride (contiguous out)
     static constexpr int LAND = p2_land_elems(THREADS, LG, IO);
+    static constexpr int NBUF = p2_nbuf(THREADS);  // landing buffers
     static constexpr int BR = L < 256 ? L : 256;  // rows per 3-D TMA box
     static constexpr int TWS = p2_smem_twiddles(LG);  // twiddle entries kept in shared memory (0: global)
     static_assert(T * L <= THREADS * kElemsPerThread, "tile exceeds the CTA's registers");
@@ -452,16 +457,6 @@ __device__ __forceinline__ void p2_plain_store(const PassDesc& d, const TileIdx&
     }
 }
 
-// The power-of-two line pass.  THREADS compute threads plus one producer
-// warp.  TC: radix-16 stages on the tensor cores (fft_tc.cuh); the CTA then
-// also holds B^T (4 KB after the stage twiddles) and tc_tmem_cols(THREADS)
-// TMEM columns, allocated by compute warp 0 and freed before it exits.  Persistent CTAs walk tiles blockIdx.x, +gridDim.x, ...  With TMA on
-// (d.async_io) the producer warp owns every copy: it loads tile i into landing
-// buffer i%2 (mbarrier full[i%2], counted in bytes), and once the compute
-// warps release a buffer (mbarrier empty[i%2]) it stores the finished tile and
-// reloads the buffer with tile i+2.  Compute warps only wait for `full` and
-// synchronise among themselves on a named barrier, so copy bookkeeping never
-// stalls them.  Every wait is bounded.
 // Register split.  Three-stage schedules (L >= 512) need ~124 registers per
 // compute thread, but with one producer warp beside 8 or 16 compute warps one
 // SM sub-partition holds 5 warps and the cap is 96 (16384 registers each).
@@ -489,6 +484,18 @@ struct P2Regs {
     static_assert(!SPLIT || (THREADS == 256 || THREADS == 512), "register split sized for 256 or 512 threads");
 };
 
+// The power-of-two line pass.  THREADS compute threads plus one producer warp
+// (or warpgroup, see the register split).  Persistent CTAs walk tiles
+// blockIdx.x, +gridDim.x, ...  With TMA on (d.async_io) the producer warp owns
+// every copy: it loads tile i into landing buffer i % NBUF (mbarrier full[b],
+// counted in bytes), and once the compute warps release a buffer (mbarrier
+// empty[b]) it stores the finished tile and reloads the buffer with tile
+// i + NBUF.  Compute warps only wait for `full` and synchronise among
+// themselves on a named barrier, so copy bookkeeping never stalls them.
+// Every wait is bounded.  TC: radix-16 stages on the tensor cores
+// (fft_tc.cuh); the CTA then also holds B^T (4 KB after the stage twiddles)
+// and tc_tmem_cols(THREADS) TMEM columns, allocated by compute warp 0 and
+// freed before it exits.
 template <int THREADS, bool FWD, int LG, int IO, bool TC = false>
 __global__ void __maxnreg__((P2Regs<THREADS, LG>::LAUNCH)) k_fft_p2(const __grid_constant__ LineArgs a)
 {
@@ -496,23 +503,25 @@ __global__ void __maxnreg__((P2Regs<THREADS, LG>::LAUNCH)) k_fft_p2(const __grid
     const PassDesc& d = a.d;
     extern __shared__ __align__(128) unsigned char smem_dyn[];
     unsigned char* smem_raw = smem_dyn + ((128u - (smem_u32(smem_dyn) & 127u)) & 127u);
-    unsigned long long* full = reinterpret_cast<unsigned long long*>(smem_raw);        // [2]
-    unsigned long long* empty = reinterpret_cast<unsigned long long*>(smem_raw) + 2;   // [2]
-    unsigned long long* mma_bar = reinterpret_cast<unsigned long long*>(smem_raw) + 4;
-    unsigned* tmem_slot = reinterpret_cast<unsigned*>(smem_raw + 40);
+    constexpr int NBUF = C::NBUF;
+    unsigned long long* full = reinterpret_cast<unsigned long long*>(smem_raw);            // [NBUF]
+    unsigned long long* empty = reinterpret_cast<unsigned long long*>(smem_raw) + NBUF;    // [NBUF]
+    unsigned long long* mma_bar = reinterpret_cast<unsigned long long*>(smem_raw) + 2 * NBUF;
+    unsigned* tmem_slot = reinterpret_cast<unsigned*>(mma_bar + 1);
+    static_assert(8 * (2 * NBUF + 1) + 4 <= 128, "barriers fit the 128-byte header");
     float2* land0 = reinterpret_cast<float2*>(smem_raw + 128);
     const bool async = d.async_io != 0;
-    float2* work = land0 + (async ? 2 : 1) * C::LAND;
+    float2* work = land0 + (async ? NBUF : 1) * C::LAND;
     // stage twiddles (when small) follow the work buffer
     float2* tws = work + (C::NST > 1 ? C::T * C::LS : 0);
     const long long step = gridDim.x;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     constexpr int kProducer = THREADS / 32;
     if (async && threadIdx.x == 0) {
-        mbar_init(&full[0], 1);
-        mbar_init(&full[1], 1);
-        mbar_init(&empty[0], THREADS);
-        mbar_init(&empty[1], THREADS);
+        for (int b = 0; b < NBUF; ++b) {
+            mbar_init(&full[b], 1);
+            mbar_init(&empty[b], THREADS);
+        }
     }
     if (TC && threadIdx.x == 0) mbar_init(mma_bar, 1);
     if ((async || TC) && threadIdx.x == 0) fence_mbar_init();
@@ -527,20 +536,20 @@ __global__ void __maxnreg__((P2Regs<THREADS, LG>::LAUNCH)) k_fft_p2(const __grid
         int i = 0;
         long long tile = blockIdx.x;
         for (; tile < d.ntiles; tile += step, ++i) {
-            const int b = i & 1;
-            if (i >= 2) {  // buffer b still holds tile i-2: wait until it is computed, store it
-                ok = mbar_wait_bounded(&empty[b], (unsigned)((i - 2) >> 1) & 1u);
+            const int b = i % NBUF;
+            if (i >= NBUF) {  // buffer b still holds tile i-NBUF: wait until it is computed, store it
+                ok = mbar_wait_bounded(&empty[b], (unsigned)((i - NBUF) / NBUF) & 1u);
                 if (!ok) break;
-                p2_issue_store<THREADS, LG, IO>(d, &a.tm_out, tile - 2 * step, land0 + b * C::LAND, lane);
+                p2_issue_store<THREADS, LG, IO>(d, &a.tm_out, tile - NBUF * step, land0 + b * C::LAND, lane);
                 bulk_wait_read_all();  // the store has read the buffer
                 __syncwarp();
             }
             p2_issue_load<THREADS, LG, IO>(d, &a.tm_in, tile, land0 + b * C::LAND, &full[b], lane);
         }
-        // drain: store the last (up to two) tiles once computed
-        for (int k = (i >= 2 ? i - 2 : 0); ok && k < i; ++k) {
-            const int b = k & 1;
-            ok = mbar_wait_bounded(&empty[b], (unsigned)(k >> 1) & 1u);
+        // drain: store the last (up to NBUF) tiles once computed
+        for (int k = (i >= NBUF ? i - NBUF : 0); ok && k < i; ++k) {
+            const int b = k % NBUF;
+            ok = mbar_wait_bounded(&empty[b], (unsigned)(k / NBUF) & 1u);
             if (ok) p2_issue_store<THREADS, LG, IO>(d, &a.tm_out, blockIdx.x + (long long)k * step,
                                                     land0 + b * C::LAND, lane);
         }
@@ -580,11 +589,11 @@ __global__ void __maxnreg__((P2Regs<THREADS, LG>::LAUNCH)) k_fft_p2(const __grid
     int i = 0;
     for (long long tile = blockIdx.x; tile < d.ntiles; tile += step, ++i) {
         const TileIdx ti = p2_tile_index(d, tile, C::LOGT, C::T);
-        const int buf = async ? (i & 1) : 0;
+        const int buf = async ? (i % NBUF) : 0;
         float2* land = land0 + buf * C::LAND;
         const int c0 = (int)ti.c0;
         if (async) {
-            const bool bad = !mbar_wait_bounded(&full[buf], (unsigned)(i >> 1) & 1u);
+            const bool bad = !mbar_wait_bounded(&full[buf], (unsigned)(i / NBUF) & 1u);
             if (compute_sync_or<THREADS>(bad)) {
                 if (threadIdx.x == 0) atomicExch(d.err, 1);
                 break;  // the producer's own bounded waits end it
