@@ -209,6 +209,17 @@ __device__ __forceinline__ void fence_mbar_init()
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
 }
+// Programmatic dependent launch.  Every line-pass kernel lets the next pass
+// on its stream start its CTAs (prologue: barriers, shared-memory set-up) as
+// soon as SMs free up, and itself waits, before its first global access, until
+// the previous pass has completed and its writes are visible.  Launched
+// without the attribute, both are no-ops.
+__device__ __forceinline__ void pdl_start()
+{
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+}
+
 // Make this thread's generic-proxy shared-memory writes visible to the TMA engine.
 __device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
 
@@ -543,6 +554,7 @@ __global__ void __launch_bounds__(THREADS, 1) k_fft_generic(const __grid_constan
         for (int w = threadIdx.x; w < (int)(sizeof(PassDesc) / 4); w += THREADS) dst[w] = src[w];
     }
     __syncthreads();
+    pdl_start();
     const PassDesc& d = sd;
     if (async && threadIdx.x == 0) {
         mbar_init(&bar[0], 1);
@@ -650,6 +662,7 @@ __global__ void __launch_bounds__(THREADS, 1) k_fft_mixed(const __grid_constant_
         for (int w = threadIdx.x; w < (int)(sizeof(PassDesc) / 4); w += THREADS) dst[w] = src[w];
     }
     __syncthreads();
+    pdl_start();
     const PassDesc& d = sd;
     constexpr int E = kMixedElems;
     constexpr int NP2 = pow2_nst(LG2);

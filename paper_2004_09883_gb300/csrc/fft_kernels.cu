@@ -1,5 +1,6 @@
 // fft_kernels.cu -- the generic line-pass kernel, the kernel table and the
 // launch path shared by all line-pass kernels.
+#include <cstdlib>
 #include <mutex>
 #include <unordered_map>
 
@@ -48,6 +49,15 @@ LineKernel line_kernel_p2tc(int threads, bool forward, int lg, int io)
 }
 
 namespace {
+bool pdl_enabled()
+{
+    static const bool v = [] {
+        const char* s = std::getenv("FB_FFT_PDL");
+        return !(s && s[0] == '0');
+    }();
+    return v;
+}
+
 // The opt-in dynamic shared-memory limit is a per-device function attribute:
 // set it once per (kernel, device).
 cudaError_t ensure_smem_attr(const LineKernel& k)
@@ -84,8 +94,20 @@ cudaError_t line_launch(const LineKernel& k, const LineArgs& a, long long grid, 
     cudaError_t e = ensure_smem_attr(k);
     if (e != cudaSuccess) return e;
     const unsigned g = (unsigned)(grid > 0x7fffffffLL ? 0x7fffffffLL : grid);
-    k.fn<<<g, k.threads, smem, stream>>>(a);
-    return cudaGetLastError();
+    // programmatic dependent launch: the kernel may start while the previous
+    // pass on the stream drains (every line kernel waits for it before its
+    // first global access, see pdl_start)
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(g);
+    cfg.blockDim = dim3(k.threads);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = stream;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = pdl_enabled() ? 1 : 0;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, k.fn, a);
 }
 
 cudaError_t line_occupancy(const LineKernel& k, size_t smem, int* blocks_per_sm)

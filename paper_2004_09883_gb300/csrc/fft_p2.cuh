@@ -526,6 +526,7 @@ __global__ void __maxnreg__((P2Regs<THREADS, LG>::LAUNCH)) k_fft_p2(const __grid
     if (TC && threadIdx.x == 0) mbar_init(mma_bar, 1);
     if ((async || TC) && threadIdx.x == 0) fence_mbar_init();
     __syncthreads();
+    pdl_start();
 
     using RG = P2Regs<THREADS, LG>;
     if (warp >= kProducer) {
