@@ -297,7 +297,7 @@ int make_line_pass(PassPlan& p, TwiddleBuilder& twb, long long L, long long O, l
         if (!line_kernel_p2(p.threads, true, p.lg, p.io).fn) return FB_FFT_ERR_UNSUPPORTED_SIZE;
         T = p2_tile_lines(p.threads, p.lg, p.io);
         land = p2_land_elems(p.threads, p.lg, p.io);
-        d.tws = p2_smem_twiddles(p.lg);
+        d.tws = p.tc ? 0 : p2_smem_twiddles(p.lg);
     } else {
         p.io = -1;
         int a2 = 0;

@@ -84,7 +84,7 @@ __host__ __device__ constexpr long long p2_smem_bytes(int threads, int lg, int i
 {
     return 256 + 8LL * (p2_land_elems(threads, lg, io) * (async ? p2_nbuf(threads) : 1) +
                         (pow2_nst(lg) > 1 ? (long long)p2_work_stride(threads, lg, io) * p2_tile_lines(threads, lg, io) : 0) +
-                        p2_smem_twiddles(lg)) +
+                        (tc ? 0 : p2_smem_twiddles(lg))) +
            (tc ? (long long)kTcExtraSmem : 0);
 }
 
@@ -269,16 +269,10 @@ __device__ __forceinline__ void p2_stage_tc(const PassDesc& d, float2* land, flo
     }
     if constexpr (!first) compute_sync<THREADS>();  // A rows overwrite the work buffer just read
     const int k = j & (NS - 1);
-    if constexpr (NS > 1) {
-        if constexpr (C::TWS > 0) {
-            const float2* tw = tws + p2_tws_off(LG, S) + k;
+    if constexpr (NS > 1) {  // tensor-core kernels keep the stage twiddles in global memory (L1-cached)
+        const float2* tw = d.tw + d.twoff[S] + k;
 #pragma unroll
-            for (int r = 1; r < R; ++r) v[r] = twmul<FWD>(v[r], tw[(r - 1) * NS]);
-        } else {
-            const float2* tw = d.tw + d.twoff[S] + k;
-#pragma unroll
-            for (int r = 1; r < R; ++r) v[r] = twmul<FWD>(v[r], __ldg(tw + (r - 1) * NS));
-        }
+        for (int r = 1; r < R; ++r) v[r] = twmul<FWD>(v[r], __ldg(tw + (r - 1) * NS));
     }
     const unsigned abase = smem_u32(work);
     const int e = tc_put_row(v, abase, tid >> 7, tid & 127);
@@ -321,10 +315,13 @@ template <int THREADS, bool FWD, int LG, int IO, int S, bool TC>
 __device__ __forceinline__ void p2_run_stage(const PassDesc& d, float2* land, float2* work, int Tv, int c0,
                                              const float2* tws, TcState& tc)
 {
-    if constexpr (TC && pow2_radix(LG, S) == 16)
+    if constexpr (TC && pow2_radix(LG, S) == 16) {
         p2_stage_tc<THREADS, FWD, LG, IO, S>(d, land, work, Tv, c0, tws, tc);
-    else
+    } else {
+        // tensor-core kernels copy no stage twiddles: their FP32 stage is the first (no twiddles)
+        static_assert(!TC || pow2_ns(LG, S) == 1, "FP32 stage with twiddles in a tensor-core kernel");
         p2_stage<THREADS, FWD, LG, IO, S>(d, land, work, Tv, c0, tws);
+    }
 }
 
 template <int THREADS, bool FWD, int LG, int IO, int S, bool TC>
@@ -493,7 +490,8 @@ struct P2Regs {
 // i + NBUF.  Compute warps only wait for `full` and synchronise among
 // themselves on a named barrier, so copy bookkeeping never stalls them.
 // Every wait is bounded.  TC: radix-16 stages on the tensor cores
-// (fft_tc.cuh); the CTA then also holds B^T (4 KB after the stage twiddles)
+// (fft_tc.cuh); the CTA then also holds B^T (4 KB after the work buffer;
+// its stage twiddles stay in global memory)
 // and tc_tmem_cols(THREADS) TMEM columns, allocated by compute warp 0 and
 // freed before it exits.
 template <int THREADS, bool FWD, int LG, int IO, bool TC = false>
@@ -564,7 +562,7 @@ __global__ void __maxnreg__((P2Regs<THREADS, LG>::LAUNCH)) k_fft_p2(const __grid
     TcState tc{0u, mma_bar, 0u, 0u};
     if constexpr (TC) {
         unsigned char* bmat = reinterpret_cast<unsigned char*>(
-            (reinterpret_cast<uintptr_t>(tws + C::TWS) + 127) & ~static_cast<uintptr_t>(127));
+            (reinterpret_cast<uintptr_t>(tws) + 127) & ~static_cast<uintptr_t>(127));
         if (warp == 0) tc_alloc(tmem_slot, tc_tmem_cols(THREADS));
         tc_build_b<THREADS, FWD>(bmat);
         fence_proxy_async();  // B^T -> visible to the tensor cores
@@ -574,7 +572,7 @@ __global__ void __maxnreg__((P2Regs<THREADS, LG>::LAUNCH)) k_fft_p2(const __grid
         tc.tmem = *tmem_slot;
         tc.bsm = smem_u32(bmat);
     }
-    if constexpr (C::TWS > 0) {
+    if constexpr (C::TWS > 0 && !TC) {
         p2_copy_twiddles<THREADS, LG, 1>(d, tws);
         compute_sync<THREADS>();
     }
