@@ -273,6 +273,11 @@ int fb_fft_profile(fb_fft_plan_t plan, int enable);
 int fb_fft_profile_read(fb_fft_plan_t plan, double* ms_total, long long* launches,
                         int capacity, int* npasses);
 
+/* fb_fft_pass_launch -- launch configuration of the plan's pass p (0 <= p <
+ * fb_fft_info.passes, in launch order): CTAs, threads per CTA, dynamic
+ * shared memory in bytes (with TMA on).  Errors: BAD_PLAN, INVALID_ARG. */
+int fb_fft_pass_launch(fb_fft_plan_t plan, int pass, long long* grid, int* block, long long* smem_bytes);
+
 /* Name of the kernel pass p launches (static string), or NULL. */
 const char* fb_fft_pass_name(fb_fft_plan_t plan, int pass);
 

@@ -563,7 +563,7 @@ __global__ void __maxnreg__((P2Regs<THREADS, LG>::LAUNCH)) k_fft_p2(const __grid
     if constexpr (TC) {
         unsigned char* bmat = reinterpret_cast<unsigned char*>(
             (reinterpret_cast<uintptr_t>(tws) + 127) & ~static_cast<uintptr_t>(127));
-        if (warp == 0) tc_alloc(tmem_slot, tc_tmem_cols(THREADS));
+        if (warp == 0) tc_alloc<tc_tmem_cols(THREADS)>(tmem_slot);
         tc_build_b<THREADS, FWD>(bmat);
         fence_proxy_async();  // B^T -> visible to the tensor cores
         tc_fence_before();
@@ -621,7 +621,7 @@ __global__ void __maxnreg__((P2Regs<THREADS, LG>::LAUNCH)) k_fft_p2(const __grid
         compute_sync<THREADS>();
         if (warp == 0) {
             tc_fence_after();
-            tc_dealloc(tc.tmem, tc_tmem_cols(THREADS));
+            tc_dealloc<tc_tmem_cols(THREADS)>(tc.tmem);
         }
     }
 }

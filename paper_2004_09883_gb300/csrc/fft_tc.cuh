@@ -56,16 +56,19 @@ __host__ __device__ constexpr unsigned tc_idesc(int M, int N)
     return (1u << 4) | ((unsigned)(N >> 3) << 17) | ((unsigned)(M >> 4) << 24);
 }
 
-__device__ __forceinline__ void tc_alloc(unsigned* slot, unsigned ncols)
+// The column count is an immediate, so the toolchain sees how much TMEM a CTA takes.
+template <int NCOLS>
+__device__ __forceinline__ void tc_alloc(unsigned* slot)
 {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(slot)),
-                 "r"(ncols)
+                 "n"(NCOLS)
                  : "memory");
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
 }
-__device__ __forceinline__ void tc_dealloc(unsigned taddr, unsigned ncols)
+template <int NCOLS>
+__device__ __forceinline__ void tc_dealloc(unsigned taddr)
 {
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "n"(NCOLS) : "memory");
 }
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }

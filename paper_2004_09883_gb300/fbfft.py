@@ -95,6 +95,7 @@ _sig = {
     "fb_fft_profile_read": (_int, [_vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(_ll), _int,
                                    ctypes.POINTER(_int)]),
     "fb_fft_pass_name": (ctypes.c_char_p, [_vp, _int]),
+    "fb_fft_pass_launch": (_int, [_vp, _int, ctypes.POINTER(_ll), ctypes.POINTER(_int), ctypes.POINTER(_ll)]),
     "fb_fft_launch_count": (_ll, []),
     "fb_fft_twiddles": (_int, [_ll, _ll, ctypes.POINTER(ctypes.c_float)]),
     "fb_fft_debug_inject_timeout": (_int, [_vp, _int]),
@@ -317,6 +318,16 @@ class Plan:
         inf = Info()
         _check(lib.fb_fft_plan_info(self._h, ctypes.byref(inf)), "fb_fft_plan_info")
         return {f: getattr(inf, f) for f, _ in Info._fields_ if f != "reserved"}
+
+    def launch_config(self) -> list[tuple[int, int, int]]:
+        """(grid, threads per CTA, dynamic shared bytes) of every pass, in launch order."""
+        out = []
+        for i in range(self.info()["passes"]):
+            g, b, m = _ll(), _int(), _ll()
+            _check(lib.fb_fft_pass_launch(self._h, i, ctypes.byref(g), ctypes.byref(b), ctypes.byref(m)),
+                   "fb_fft_pass_launch")
+            out.append((g.value, b.value, m.value))
+        return out
 
     def pass_names(self) -> list[str]:
         names = []
