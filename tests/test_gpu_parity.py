@@ -299,3 +299,22 @@ def test_gpu_linearity_and_parseval_large(fb):
         e_out = float(np.sum(np.abs(to_host(fx).astype(np.complex128)) ** 2))
     assert rel < 4 * tol(n)
     assert abs(e_out - e_in) / e_in < 4 * tol(n)
+
+
+@pytest.mark.parametrize("dims,batch,tc", [([256, 256, 128], 1, False), ([1 << 20], 8, False), ([1 << 20], 8, True),
+                                           ([4096], 8192, False), ([128], 32768, False), ([1024], 8192, True)])
+def test_launch_configuration_fits_the_gpu(fb, dims, batch, tc):
+    """Every pass's grid is a whole number of CTAs per SM (persistent CTAs),
+    its CTA a whole number of warps, its shared memory within the opt-in limit;
+    tensor-core passes run two CTAs per SM once there are enough tiles."""
+    import torch
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    with fb.Plan(dims, batch, tensor_cores=tc) as p:
+        cfg = p.launch_config()
+        info = p.info()
+    assert len(cfg) == info["passes"]
+    for grid, block, smem in cfg:
+        assert grid >= 1 and block % 32 == 0 and 0 < smem <= 227 * 1024
+        assert grid % sms == 0 or grid < sms, (grid, sms)
+    if tc and batch * int(np.prod(dims)) >= 1 << 23:
+        assert all(g == 2 * sms for g, _, _ in cfg), cfg
