@@ -225,6 +225,28 @@ def workload_shapes(wl: dict) -> list[tuple]:
     return [(int(n),) for n in uneven_lengths(wl)]
 
 
+def oracle_single_thread(wl: dict, budget_s: float) -> dict:
+    """The oracle on one host thread, one batch item at a time (forward, plus
+    inverse when the workload has one) until `budget_s` is spent (at least
+    one item); GB/s in the workload's byte accounting."""
+    import oracle
+
+    bytes_step, _, _ = algorithmic(wl)
+    per_item = bytes_step / wl["batch"]
+    x = make_input(wl, 0)
+    done, t_total, k = 0.0, 0.0, 0
+    while k == 0 or (t_total < budget_s and k < wl["batch"]):
+        item = x[k % wl["batch"]].astype(np.complex128)
+        t = time.perf_counter()
+        y = oracle.fft(item, wl["dims"], -1, False, 1)
+        if wl["inverse"]:
+            oracle.fft(y, wl["dims"], 1, True, 1)
+        t_total += time.perf_counter() - t
+        done += per_item
+        k += 1
+    return {"value": done / t_total / 1e9, "seconds": t_total, "items": k}
+
+
 def oracle_uneven_sample(wl: dict, budget_s: float, threads: int) -> dict:
     """Time the oracle on a many-transform workload's transforms, in order,
     until the budget is spent (at least one); GB/s over the transforms done."""
@@ -465,6 +487,52 @@ def run_gpu(args, wl: dict) -> None:
                "h2d_bytes_per_step": io, "d2h_bytes_per_step": io, "ms_per_step": e2e_ms,
                "path": "fb_fft_exec_host (pinned host arrays)" + (", forward then inverse" if wl["inverse"] else ", forward")}
 
+    # error against the oracle on the first batch items of input buffer 0
+    errors = None
+    if rank == 0 and not args.quick and not tc:
+        import oracle
+        k = min(batch, 4)
+        thr = len(os.sched_getaffinity(0))
+        x0 = host_inputs[0].reshape(batch, n)[:k]
+        y = plan.exec(xin[0], None, fbfft.FORWARD)
+        torch.cuda.synchronize(dev)
+        yk = y.cpu().numpy().reshape(batch, n)[:k]
+        ref = oracle.fft(x0.astype(np.complex128).reshape([k] + dims), dims, fbfft.FORWARD, False, thr)
+        e = oracle.rel_l2(yk, ref.reshape(k, n))
+        errors = {"forward_max_rel_l2": float(e.max()), "forward_median_rel_l2": float(np.median(e)),
+                  "tolerance_rel_l2": 2e-6 * math.log2(n), "items": k}
+        if wl["inverse"]:
+            z = plan.exec(y, None, fbfft.INVERSE)
+            torch.cuda.synchronize(dev)
+            zk = z.cpu().numpy().reshape(batch, n)[:k]
+            refi = oracle.fft(yk.astype(np.complex128).reshape([k] + dims), dims, fbfft.INVERSE, True, thr)
+            ei = oracle.rel_l2(zk, refi.reshape(k, n))
+            rt = oracle.rel_l2(zk, x0.astype(np.complex128))
+            errors.update({"inverse_max_rel_l2": float(ei.max()), "round_trip_max_rel_l2": float(rt.max())})
+
+    # library context: cuFFT through torch.fft on the same buffers (not part of the product)
+    context = None
+    if not args.quick:
+        axes = tuple(range(1, len(dims) + 1))
+
+        def lib_step(i):
+            yy = torch.fft.fftn(xin[i % nbuf].view([batch] + dims), dim=axes)
+            if wl["inverse"]:
+                torch.fft.ifftn(yy, dim=axes)
+
+        for i in range(args.warmup):
+            lib_step(i)
+        barrier()
+        ev0.record(stream)
+        for i in range(args.steps):
+            lib_step(i)
+        ev1.record(stream)
+        barrier()
+        lib_ms = ev0.elapsed_time(ev1) / args.steps
+        context = {"library": "cuFFT via torch.fft on the same GPU and buffers (a reference point, not part of "
+                              "this product)", "value": round(bytes_step / (lib_ms / 1e3) / 1e9, 3), "unit": "GB/s",
+                   "ms_per_step": round(lib_ms, 5)}
+
     if rank == 0:
         peaks = load_peaks()
         value = whole_job_rate(world, bytes_step, ms) / 1e9
@@ -490,9 +558,13 @@ def run_gpu(args, wl: dict) -> None:
         cpu_baseline = None
         if not args.quick:
             cb = oracle_sample(wl, budget_s=float(args.cpu_budget), threads=threads)
+            st1 = oracle_single_thread(wl, budget_s=3.0)
             cpu_baseline = {"value": round(cb["value"], 4), "unit": "GB/s", "cores": threads, "kind": "oracle",
                             "sample": f"{cb['steps']} full step(s) of {wl['name']} by the FP64 oracle in "
-                                      f"{cb['seconds']:.1f} s on {cpu_model()}"}
+                                      f"{cb['seconds']:.1f} s on {cpu_model()}",
+                            "single_thread": {"value": round(st1["value"], 5), "unit": "GB/s",
+                                              "sample": f"{st1['items']} batch item(s), one thread, "
+                                                        f"{st1['seconds']:.1f} s"}}
         line = {
             "metric": METRIC, "value": round(value, 3), "unit": "GB/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": round(ms, 5), "higher_is_better": True, "scaling": "weak",
@@ -514,6 +586,10 @@ def run_gpu(args, wl: dict) -> None:
         }
         if precision:
             line["precision"] = precision
+        if errors:
+            line["errors_vs_oracle"] = errors
+        if context:
+            line["context"] = context
         print(json.dumps(line), flush=True)
     plan.close()
     if dist is not None:
