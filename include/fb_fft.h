@@ -121,6 +121,11 @@ int fb_fft_set_graph(fb_fft_plan_t plan, int enable);
  *   odd_radices_first  lengths with factors 3/5 (generic kernel): 1 runs the 5s and 3s
  *                      before the power-of-two radices
  *   max_lines          generic kernel: at most this many lines per tile (0 = no extra cap)
+ *   per_length         1: one launch per length group for every kernel; 0 (default):
+ *                      passes of lengths with a factor 3 or 5 that share a
+ *                      power-of-two factor run as one launch (up to 64 lengths
+ *                      each), four-step groups with disjoint scratch, in two phases
+ *                      (single passes and four-step columns, then four-step rows)
  */
 typedef struct fb_fft_many_opts {
     int streams;
@@ -128,6 +133,7 @@ typedef struct fb_fft_many_opts {
     long long chunk_bytes;
     int odd_radices_first;
     int max_lines;
+    int per_length;
 } fb_fft_many_opts;
 int fb_fft_plan_many_ex(fb_fft_plan_t* plan, int count, const long long* lengths, unsigned flags, void* stream,
                         const fb_fft_many_opts* opts);
@@ -273,9 +279,11 @@ int fb_fft_profile(fb_fft_plan_t plan, int enable);
 int fb_fft_profile_read(fb_fft_plan_t plan, double* ms_total, long long* launches,
                         int capacity, int* npasses);
 
-/* fb_fft_pass_launch -- launch configuration of the plan's pass p (0 <= p <
- * fb_fft_info.passes, in launch order): CTAs, threads per CTA, dynamic
- * shared memory in bytes (with TMA on).  Errors: BAD_PLAN, INVALID_ARG. */
+/* fb_fft_pass_launch -- launch configuration of the plan's pass p, in plan
+ * order (fb_fft_info.passes of them for regular plans): CTAs, threads per
+ * CTA, dynamic shared memory in bytes (with TMA on).  A batched-uneven pass
+ * that runs inside a merged launch reports grid 0.  Errors: BAD_PLAN,
+ * INVALID_ARG. */
 int fb_fft_pass_launch(fb_fft_plan_t plan, int pass, long long* grid, int* block, long long* smem_bytes);
 
 /* Name of the kernel pass p launches (static string), or NULL. */

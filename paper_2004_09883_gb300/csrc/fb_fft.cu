@@ -22,6 +22,8 @@
 #include <cstdlib>
 #include <cstdio>
 #include <cstring>
+#include <map>
+#include <memory>
 #include <new>
 #include <vector>
 
@@ -108,6 +110,20 @@ struct PassPlan {
     long long off_in_idx = -1;   // batched-uneven plans: index of the pass's offset
     long long off_out_idx = -1;  // tables in the plan's device offset buffer
     bool tc = false;             // radix-16 stages on the tensor cores
+    int multi = -1;              // batched-uneven plans: the merged launch this pass belongs to
+};
+
+// Batched-uneven plans: mixed-kernel passes of one phase and power-of-two
+// factor, run as one k_fft_mixed_multi launch.
+struct MultiLaunch {
+    std::vector<int> members;  // pass indices
+    int lg2 = 0;
+    int phase = 0;             // 0: single passes and four-step columns, 1: four-step rows
+    int slot = 0;
+    long long tiles = 0;
+    long long grid = 0;
+    int land_max = 0;
+    size_t smem = 0;
 };
 
 bool is_smooth(long long n)
@@ -394,6 +410,9 @@ struct fb_fft_plan_s {
     long long chunk_bytes = 0;   // 0: fourstep_chunk_bytes()
     bool odd_first = false;
     int max_lines = 0;
+    bool merge_mixed = true;               // batched uneven: merged mixed-kernel launches
+    std::vector<MultiLaunch> multis;
+    std::unique_ptr<MultiArgs> margs;      // launch-argument staging (copied at every launch)
     struct GraphEntry {
         const void* in;
         void* out;
@@ -460,7 +479,7 @@ int schedule_many(fb_fft_plan_s* p, TwiddleBuilder& twb)
             groups.back().second.push_back(i);
         }
     }
-    p->group_names = {"many.single_pass", "many.fourstep.columns", "many.fourstep.rows"};
+    p->group_names = {"many.single_pass", "many.fourstep.columns", "many.fourstep.rows", "many.merged_mixed"};
     // every slot owns a scratch region, so four-step groups on different
     // slots overlap; groups on one slot reuse its region in turn
     std::vector<long long> slot_need(p->nslots, 0);
@@ -532,20 +551,72 @@ int schedule_many(fb_fft_plan_s* p, TwiddleBuilder& twb)
         }
         p->smem_len_max = std::max(p->smem_len_max, std::max(N1, N2));
     }
-    // scratch regions: slot s starts after the regions of slots < s
-    std::vector<long long> region(p->nslots, 0);
     long long scratch_need = 0;
-    for (int sl = 0; sl < p->nslots; ++sl) {
-        region[sl] = scratch_need;
-        scratch_need += (slot_need[sl] + 31) & ~31LL;  // keep regions 256-byte aligned
-    }
-    for (PassPlan& q : p->passes) {
-        if (q.dst == kBufScratch) q.dst_off = region[q.slot];
-        if (q.src == kBufScratch) q.src_off = region[q.slot];
+    if (!p->merge_mixed) {
+        // scratch regions: slot s starts after the regions of slots < s
+        std::vector<long long> region(p->nslots, 0);
+        for (int sl = 0; sl < p->nslots; ++sl) {
+            region[sl] = scratch_need;
+            scratch_need += (slot_need[sl] + 31) & ~31LL;  // keep regions 256-byte aligned
+        }
+        for (PassPlan& q : p->passes) {
+            if (q.dst == kBufScratch) q.dst_off = region[q.slot];
+            if (q.src == kBufScratch) q.src_off = region[q.slot];
+        }
+    } else {
+        // every four-step chunk its own region: a merged launch runs many
+        // chunks' column (or row) passes at once.  Passes were pushed as
+        // (columns, rows) pairs, so a row pass takes its column pass's region.
+        long long last = 0;
+        for (PassPlan& q : p->passes) {
+            if (q.dst == kBufScratch) {
+                const long long O = q.d.ntiles / q.d.tiles_per_o;
+                last = scratch_need;
+                q.dst_off = last;
+                scratch_need += (O * (long long)q.d.L * q.d.C + 31) & ~31LL;
+            }
+            if (q.src == kBufScratch) q.src_off = last;
+        }
+        // merged launches: mixed-kernel passes grouped by phase and power-of-two factor
+        std::map<std::pair<int, int>, std::vector<int>> buckets;
+        for (int i = 0; i < (int)p->passes.size(); ++i) {
+            const PassPlan& q = p->passes[i];
+            if (q.kind == 2) buckets[{q.group == 2 ? 1 : 0, q.lg}].push_back(i);
+        }
+        int rrm = 0;
+        for (auto& kv : buckets) {
+            const std::vector<int>& v = kv.second;
+            if (v.size() < 2) continue;
+            for (size_t b0 = 0; b0 < v.size(); b0 += kMultiMax) {
+                MultiLaunch m;
+                m.phase = kv.first.first;
+                m.lg2 = kv.first.second;
+                m.slot = rrm++ % p->nslots;
+                long long work_max = 0;
+                for (size_t k = b0; k < std::min(v.size(), b0 + (size_t)kMultiMax); ++k) {
+                    PassPlan& q = p->passes[v[k]];
+                    q.multi = (int)p->multis.size();
+                    m.members.push_back(v[k]);
+                    m.tiles += q.d.ntiles;
+                    m.land_max = std::max(m.land_max, q.d.land_stride);
+                    work_max = std::max(work_max, ((long long)q.d.L + (q.d.L >> 4) + 16) << q.d.logT);
+                }
+                m.smem = 256 + (size_t)(2LL * m.land_max + work_max) * sizeof(float2);
+                p->multis.push_back(m);
+            }
+        }
     }
     p->scratch_bytes = (size_t)scratch_need * sizeof(float2);
     p->tw_elems = std::max(2LL, twb.total);
     return FB_FFT_OK;
+}
+
+// Kernel launches one exec of a plan makes.
+long long launches_per_exec(const fb_fft_plan_s* p)
+{
+    long long n = (long long)p->multis.size();
+    for (const PassPlan& q : p->passes) n += q.multi < 0 ? 1 : 0;
+    return n;
 }
 
 // Invariants of a schedule, checked on the host before anything launches:
@@ -571,6 +642,19 @@ int check_schedule(const fb_fft_plan_s* p)
         if (q.dst == kBufScratch && q.dst_off + window > scratch_elems) return FB_FFT_ERR_INVALID_ARG;
         if (q.src == kBufScratch && q.src_off + window > scratch_elems) return FB_FFT_ERR_INVALID_ARG;
         if (q.slot < 0 || q.slot >= p->nslots) return FB_FFT_ERR_INVALID_ARG;
+        if (q.multi >= (int)p->multis.size()) return FB_FFT_ERR_INVALID_ARG;
+    }
+    // merged launches: members are mixed-kernel passes of the launch's phase
+    // and factor, at most kMultiMax of them, with landing tiles that fit
+    for (const MultiLaunch& m : p->multis) {
+        if (m.members.empty() || m.members.size() > (size_t)kMultiMax) return FB_FFT_ERR_INVALID_ARG;
+        if (m.slot < 0 || m.slot >= p->nslots || m.smem > kMaxSmemBytes) return FB_FFT_ERR_INVALID_ARG;
+        for (int i : m.members) {
+            const PassPlan& q = p->passes[i];
+            if (q.kind != 2 || q.lg != m.lg2 || (q.group == 2 ? 1 : 0) != m.phase) return FB_FFT_ERR_INVALID_ARG;
+            if (q.d.land_stride > m.land_max || ((long long)q.d.L << q.d.logT) > m.land_max)
+                return FB_FFT_ERR_INVALID_ARG;
+        }
     }
     return FB_FFT_OK;
 }
@@ -712,13 +796,25 @@ int build_plan(fb_fft_plan_s* p)
             if (q.off_in_idx >= 0) q.d.off_in = p->d_off + q.off_in_idx;
             if (q.off_out_idx >= 0) q.d.off_out = p->d_off + q.off_out_idx;
         }
+        for (MultiLaunch& m : p->multis) {
+            int occ = 0;
+            FB_CK(mixed_multi_occupancy(true, m.lg2, m.smem, &occ));
+            if (occ < 1) return cuda_fail(cudaErrorInvalidConfiguration, "merged pass occupancy");
+            m.grid = std::min(m.tiles, (long long)sms * occ);
+            for (int i : m.members) p->passes[i].grid = 0;  // launched through the merged launch only
+        }
+        if (!p->multis.empty()) {
+            p->margs.reset(new (std::nothrow) MultiArgs());
+            if (!p->margs) return FB_FFT_ERR_ALLOC;
+        }
         for (int sl = 0; sl < p->nslots; ++sl) {
             cudaStream_t st;
             FB_CK(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
             p->side.push_back(st);
         }
         FB_CK(cudaStreamCreateWithFlags(&p->capture, cudaStreamNonBlocking));
-        for (int e = 0; e <= p->nslots; ++e) {
+        // [0] fork, [1 + s] join of slot s, [1 + nslots + s] end of phase 0 on slot s
+        for (int e = 0; e <= 2 * p->nslots; ++e) {
             cudaEvent_t ev;
             FB_CK(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
             p->fork_join.push_back(ev);
@@ -822,15 +918,85 @@ int launch_pass(fb_fft_plan_s* p, const PassPlan& q, const float2* in, float2* o
     return FB_FFT_OK;
 }
 
+// One merged launch of mixed-kernel passes (MultiArgs by value).
+int launch_multi(fb_fft_plan_s* p, const MultiLaunch& m, const float2* in, float2* out, bool fwd,
+                 cudaStream_t stream, bool count)
+{
+    MultiArgs& a = *p->margs;
+    a.njobs = (int)m.members.size();
+    a.land_max = m.land_max;
+    a.tile_start[0] = 0;
+    for (int k = 0; k < a.njobs; ++k) {
+        const PassPlan& q = p->passes[m.members[k]];
+        PassDesc d = q.d;
+        const float2* src = q.src == kBufIn ? in : (q.src == kBufOut ? out : p->scratch);
+        float2* dst = q.dst == kBufOut ? out : p->scratch;
+        d.in = src + q.src_off;
+        d.out = dst + q.dst_off;
+        d.async_io = 0;
+        if (q.last && !fwd && (p->flags & FB_FFT_SCALE_INV_N)) {
+            d.apply_scale = 1;
+            d.scale = (float)(1.0 / (double)(q.scale_n ? q.scale_n : p->N));
+        }
+        a.d[k] = d;
+        a.tile_start[k + 1] = a.tile_start[k] + d.ntiles;
+    }
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (p->profiling) {
+        if (p->ev_used + 2 > p->ev.size()) {
+            for (int i = 0; i < 64; ++i) {
+                cudaEvent_t e;
+                FB_CK(cudaEventCreate(&e));
+                p->ev.push_back(e);
+            }
+            p->ev_group.resize(p->ev.size() / 2, 0);
+        }
+        e0 = p->ev[p->ev_used];
+        e1 = p->ev[p->ev_used + 1];
+        p->ev_group[p->ev_used / 2] = 3;
+        p->ev_used += 2;
+        cudaEventRecord(e0, stream);
+    }
+    const cudaError_t le = mixed_multi_launch(fwd, m.lg2, a, m.grid, m.smem, stream);
+    if (le != cudaSuccess) return cuda_fail(le, "k_fft_mixed_multi");
+    if (count) g_launches.fetch_add(1, std::memory_order_relaxed);
+    if (p->profiling) cudaEventRecord(e1, stream);
+    return FB_FFT_OK;
+}
+
 // Batched uneven plan: fork the side streams off `origin`, run each pass on
-// its slot, join back into `origin`.
+// its slot, join back into `origin`.  With merged launches: phase 0 (single
+// passes, four-step columns), every slot waits for every slot, phase 1
+// (four-step rows).
 int launch_many(fb_fft_plan_s* p, cudaStream_t origin, const float2* in, float2* out, bool fwd, bool count)
 {
     FB_CK(cudaEventRecord(p->fork_join[0], origin));
     for (int sl = 0; sl < p->nslots; ++sl) FB_CK(cudaStreamWaitEvent(p->side[sl], p->fork_join[0], 0));
-    for (const PassPlan& q : p->passes) {
-        const int rc = launch_pass(p, q, in, out, fwd, p->side[q.slot], count, p->scratch, nullptr);
-        if (rc != FB_FFT_OK) return rc;
+    if (!p->merge_mixed) {
+        for (const PassPlan& q : p->passes) {
+            const int rc = launch_pass(p, q, in, out, fwd, p->side[q.slot], count, p->scratch, nullptr);
+            if (rc != FB_FFT_OK) return rc;
+        }
+    } else {
+        for (int phase = 0; phase < 2; ++phase) {
+            if (phase == 1) {
+                for (int sl = 0; sl < p->nslots; ++sl)
+                    FB_CK(cudaEventRecord(p->fork_join[1 + p->nslots + sl], p->side[sl]));
+                for (int sl = 0; sl < p->nslots; ++sl)
+                    for (int s2 = 0; s2 < p->nslots; ++s2)
+                        if (s2 != sl) FB_CK(cudaStreamWaitEvent(p->side[sl], p->fork_join[1 + p->nslots + s2], 0));
+            }
+            for (const MultiLaunch& m : p->multis) {
+                if (m.phase != phase) continue;
+                const int rc = launch_multi(p, m, in, out, fwd, p->side[m.slot], count);
+                if (rc != FB_FFT_OK) return rc;
+            }
+            for (const PassPlan& q : p->passes) {
+                if (q.multi >= 0 || (q.group == 2 ? 1 : 0) != phase) continue;
+                const int rc = launch_pass(p, q, in, out, fwd, p->side[q.slot], count, p->scratch, nullptr);
+                if (rc != FB_FFT_OK) return rc;
+            }
+        }
     }
     for (int sl = 0; sl < p->nslots; ++sl) {
         FB_CK(cudaEventRecord(p->fork_join[1 + sl], p->side[sl]));
@@ -848,7 +1014,7 @@ int exec_many(fb_fft_plan_s* p, const float2* in, float2* out, int direction)
     for (auto& g : p->graphs)
         if (g.in == in && g.out == out && g.dir == direction) {
             FB_CK(cudaGraphLaunch(g.exec, p->stream));
-            g_launches.fetch_add((long long)p->passes.size(), std::memory_order_relaxed);
+            g_launches.fetch_add(launches_per_exec(p), std::memory_order_relaxed);
             return FB_FFT_OK;
         }
     // capture on the plan's own stream (the caller's may be the legacy
@@ -872,7 +1038,7 @@ int exec_many(fb_fft_plan_s* p, const float2* in, float2* out, int direction)
     }
     p->graphs.push_back({in, out, direction, exec});
     FB_CK(cudaGraphLaunch(exec, p->stream));
-    g_launches.fetch_add((long long)p->passes.size(), std::memory_order_relaxed);
+    g_launches.fetch_add(launches_per_exec(p), std::memory_order_relaxed);
     return FB_FFT_OK;
 }
 
@@ -1109,6 +1275,7 @@ int fb_fft_plan_many_ex(fb_fft_plan_t* plan, int count, const long long* lengths
         p->chunk_bytes = opts->chunk_bytes;
         p->odd_first = opts->odd_radices_first != 0;
         p->max_lines = opts->max_lines;
+        p->merge_mixed = opts->per_length == 0;
     }
     int rc = build_plan(p);
     if (rc != FB_FFT_OK) {
@@ -1156,7 +1323,7 @@ int fb_fft_autotune_many(int count, const long long* lengths, unsigned flags, co
     int rc = measure(cur, &cur_ms);
     // coordinate descent, one knob at a time
     const int streams[] = {1, 2, 8, 16, 32};
-    const long long chunks[] = {8LL << 20, 16LL << 20, 64LL << 20, 128LL << 20};
+    const long long chunks[] = {8LL << 20, 16LL << 20, 64LL << 20, 128LL << 20, 512LL << 20};
     const int lines[] = {4, 16, 64};
     for (int v : streams) {
         if (rc != FB_FFT_OK) break;
@@ -1185,6 +1352,13 @@ int fb_fft_autotune_many(int count, const long long* lengths, unsigned flags, co
         if (rc != FB_FFT_OK) break;
         fb_fft_many_opts o = cur;
         o.max_lines = v;
+        float ms;
+        rc = measure(o, &ms);
+        if (rc == FB_FFT_OK && ms < cur_ms) cur = o, cur_ms = ms;
+    }
+    if (rc == FB_FFT_OK) {
+        fb_fft_many_opts o = cur;
+        o.per_length = 1;
         float ms;
         rc = measure(o, &ms);
         if (rc == FB_FFT_OK && ms < cur_ms) cur = o, cur_ms = ms;
@@ -1220,7 +1394,7 @@ int fb_fft_plan_many_query(int count, const long long* lengths, unsigned flags, 
     p.magic = kDead;
     if (rc != FB_FFT_OK) return rc;
     std::memset(info, 0, sizeof(*info));
-    info->passes = (int)p.passes.size();
+    info->passes = (int)launches_per_exec(&p);
     info->tc_passes = tc_pass_count(p.passes);
     info->smem_len_max = p.smem_len_max;
     info->scratch_bytes = (long long)p.scratch_bytes;
@@ -1338,7 +1512,7 @@ int fb_fft_plan_info(fb_fft_plan_t plan, fb_fft_info* info)
     if (!plan_ok(plan)) return FB_FFT_ERR_BAD_PLAN;
     if (!info) return FB_FFT_ERR_INVALID_ARG;
     std::memset(info, 0, sizeof(*info));
-    info->passes = (int)plan->passes.size();
+    info->passes = (int)launches_per_exec(plan);
     info->tc_passes = tc_pass_count(plan->passes);
     info->smem_len_max = plan->smem_len_max;
     info->scratch_bytes = (long long)plan->scratch_bytes;

@@ -71,6 +71,23 @@ struct PassDesc {
     const long long* off_out;
 };
 
+// Several passes of one mixed kernel in one launch (batched uneven lengths:
+// every length with the same power-of-two factor).  Job j owns global tiles
+// [tile_start[j], tile_start[j+1]); its descriptor is d[j] (plain copies, no
+// TMA: the jobs' tiles go through offset tables).  The whole struct is the
+// kernel parameter (about 20 KB, under the 32 KB parameter limit), so a
+// captured graph holds it by value.
+constexpr int kMultiMax = 64;
+struct MultiArgs {
+    long long tile_start[kMultiMax + 1];
+    int njobs;
+    int land_max;  // elements of the landing buffer; the work buffer follows it
+    PassDesc d[kMultiMax];
+};
+cudaError_t mixed_multi_launch(bool forward, int lg2, const MultiArgs& a, long long grid, size_t smem,
+                               cudaStream_t stream);
+cudaError_t mixed_multi_occupancy(bool forward, int lg2, size_t smem, int* blocks_per_sm);
+
 // Kernel argument: the descriptor plus the TMA tensor maps of the c-fast
 // input/output views {C, L, O} (encoded per launch, they hold addresses).
 struct LineArgs {

@@ -369,6 +369,19 @@ __device__ __forceinline__ void issue_tile_store(const PassDesc& d, const CUtens
     bulk_commit();
 }
 
+// Per-thread asynchronous copies (cp.async, 8 bytes each): any gather
+// pattern, completion tracked per thread by commit groups.
+__device__ __forceinline__ void cp_async8(void* smem_dst, const void* gsrc)
+{
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(smem_u32(smem_dst)), "l"(gsrc) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait()
+{
+    asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+
 // Plain-copy fallback (misaligned bases, odd strides): the whole CTA copies.
 template <int THREADS>
 __device__ __forceinline__ void plain_tile_load(const PassDesc& d, const TileIdx& ti, float2* land)
@@ -384,6 +397,25 @@ __device__ __forceinline__ void plain_tile_load(const PassDesc& d, const TileIdx
         for (int e = threadIdx.x; e < T * L; e += THREADS) {
             const int n = e >> d.logT, t = e & (T - 1);
             if (t < ti.Tv) land[e] = gin[(long long)n * d.in_sn + t];
+        }
+    }
+}
+// The same gather as plain_tile_load, issued as cp.async copies (the caller
+// commits and waits).
+template <int THREADS>
+__device__ __forceinline__ void async_tile_load(const PassDesc& d, const TileIdx& ti, float2* land)
+{
+    const int L = d.L, T = 1 << d.logT;
+    const float2* gin = tile_in_base(d, ti, d.in_tfast != 0);
+    if (!d.in_tfast) {
+        for (int e = threadIdx.x; e < ti.Tv * L; e += THREADS) {
+            const int t = e / L, n = e - t * L;
+            cp_async8(&land[e], line_in(d, ti, gin, t) + (long long)n * d.in_sn);
+        }
+    } else {
+        for (int e = threadIdx.x; e < T * L; e += THREADS) {
+            const int n = e >> d.logT, t = e & (T - 1);
+            if (t < ti.Tv) cp_async8(&land[e], gin + (long long)n * d.in_sn + t);
         }
     }
 }
@@ -727,6 +759,82 @@ __global__ void __launch_bounds__(THREADS, 1) k_fft_mixed(const __grid_constant_
         }
     }
     if (async && threadIdx.x == 0) bulk_wait_all();
+}
+
+// The mixed line pass over several jobs (MultiArgs): persistent CTAs walk the
+// global tiles blockIdx.x, +gridDim.x, ...; a tile's job is found by advancing
+// through the prefix table (tiles only grow).  Two landing buffers, each with
+// its tile's descriptor in shared memory: while tile i is transformed, every
+// thread's cp.async copies bring tile i+1 through its job's offset table.
+template <int THREADS, bool FWD, int LG2>
+__global__ void __launch_bounds__(THREADS, 1) k_fft_mixed_multi(const __grid_constant__ MultiArgs a)
+{
+    extern __shared__ __align__(128) unsigned char smem_dyn[];
+    unsigned char* smem_raw = smem_dyn + ((128u - (smem_u32(smem_dyn) & 127u)) & 127u);
+    float2* land0 = reinterpret_cast<float2*>(smem_raw + 128);
+    float2* work = land0 + 2 * a.land_max;
+    __shared__ PassDesc sd[2];  // sd[b]: descriptor of the tile in landing buffer b
+    constexpr int E = kMixedElems;
+    constexpr int NP2 = pow2_nst(LG2);
+    const long long total = a.tile_start[a.njobs];
+    const long long step = gridDim.x;
+    auto copy_desc = [&](int job, int b) {
+        const int* src = reinterpret_cast<const int*>(&a.d[job]);
+        int* dst = reinterpret_cast<int*>(&sd[b]);
+        for (int w = threadIdx.x; w < (int)(sizeof(PassDesc) / 4); w += THREADS) dst[w] = src[w];
+    };
+    pdl_start();
+    int j = 0;
+    long long g = blockIdx.x;
+    if (g < total) {
+        while (j + 1 < a.njobs && g >= a.tile_start[j + 1]) ++j;
+        copy_desc(j, 0);
+        __syncthreads();
+        async_tile_load<THREADS>(sd[0], tile_index(sd[0], g - a.tile_start[j]), land0);
+        cp_async_commit();
+    }
+    long long jstart = a.tile_start[j];
+    for (int i = 0; g < total; g += step, ++i) {
+        const int b = i & 1;
+        const long long gl = g - jstart;  // this tile within its job
+        const long long gn = g + step;
+        if (gn < total) {  // the next tile's job and descriptor, then its copies
+            while (j + 1 < a.njobs && gn >= a.tile_start[j + 1]) ++j;
+            jstart = a.tile_start[j];
+            copy_desc(j, b ^ 1);
+            __syncthreads();
+            async_tile_load<THREADS>(sd[b ^ 1], tile_index(sd[b ^ 1], gn - jstart), land0 + (b ^ 1) * a.land_max);
+            cp_async_commit();
+            cp_async_wait<1>();  // this tile's copies have landed (the next tile's may still fly)
+        } else {
+            cp_async_wait<0>();
+        }
+        __syncthreads();
+        const PassDesc& d = sd[b];
+        float2* land = land0 + b * a.land_max;
+        const TileIdx ti = tile_index(d, gl);
+        const int c0 = (int)ti.c0;
+        int s0 = NP2;
+        if constexpr (NP2 > 0) {
+            mixed_p2_stages<THREADS, FWD, LG2, 0, E>(d, land, work, ti.Tv, c0);
+        } else {
+            if (d.nst == 1)
+                run_odd_stage<THREADS, FWD, kPosOnly, E>(d.radix[0], d, 1, 0, land, work, ti.Tv, c0);
+            else
+                run_odd_stage<THREADS, FWD, kPosFirst, E>(d.radix[0], d, 1, 0, land, work, ti.Tv, c0);
+            __syncthreads();
+            s0 = 1;
+        }
+        for (int s = s0; s < d.nst; ++s) {
+            if (s == d.nst - 1)
+                run_odd_stage<THREADS, FWD, kPosLast, E>(d.radix[s], d, d.ns[s], d.twoff[s], land, work, ti.Tv, c0);
+            else
+                run_odd_stage<THREADS, FWD, kPosMid, E>(d.radix[s], d, d.ns[s], d.twoff[s], land, work, ti.Tv, c0);
+            __syncthreads();
+        }
+        plain_tile_store<THREADS>(d, ti, land);
+        __syncthreads();  // buffer b and sd[b] are free for the tile after next
+    }
 }
 
 // A kernel's table entry: its pointer, CTA size and a printable name.

@@ -87,7 +87,8 @@ def test_many_single_transform_and_empty(fb):
         _check(p, [x], p.unpack(y.cpu().numpy()), -1)
 
 
-@pytest.mark.parametrize("opts", [dict(streams=1, use_graph=0, chunk_bytes=8 << 20, odd_radices_first=1, max_lines=4),
+@pytest.mark.parametrize("opts", [dict(streams=1, use_graph=0, chunk_bytes=8 << 20, odd_radices_first=1, max_lines=4,
+                                       per_length=1),
                                   dict(streams=16, use_graph=1, chunk_bytes=1 << 20, odd_radices_first=0, max_lines=16)])
 def test_many_knobs_keep_results(fb, opts):
     import torch
@@ -115,3 +116,29 @@ def test_autotuner_returns_a_working_setting(fb):
         y = p.exec(d, None, -1)
         p.check()
         _check(p, xs, p.unpack(y.cpu().numpy()), -1)
+
+
+@pytest.mark.parametrize("direction,scale", [(-1, False), (1, True)])
+def test_merged_launches_equal_per_length_launches(fb, direction, scale):
+    """Merged mixed-kernel launches (default) and one launch per length give
+    the same bits, with far fewer launches."""
+    import torch
+    lens = list(inputs.uneven_lengths(300, 64, 65536, inputs.seed_for(inputs.WORKLOAD_UNEVEN_4096, 7)))
+    lens += [75, 6000, 45000, 3 * 5 ** 6, 2, 3]
+    xs = _batch(lens, 950)
+    with fb.PlanMany(lens, scale_inv_n=scale) as pm, \
+            fb.PlanMany(lens, scale_inv_n=scale, opts={"per_length": 1}) as pl:
+        d = torch.from_numpy(pm.pack(xs)).cuda()
+        l0 = fb.launch_count()
+        ym = pm.exec(d, None, direction)
+        torch.cuda.synchronize()
+        l1 = fb.launch_count()
+        yl = pl.exec(d, None, direction)
+        torch.cuda.synchronize()
+        l2 = fb.launch_count()
+        pm.check()
+        pl.check()
+        assert torch.equal(ym, yl)
+        assert (l1 - l0) < (l2 - l1)
+        ys = pm.unpack(ym.cpu().numpy())
+    _check(pm, xs, ys, direction, scale)
