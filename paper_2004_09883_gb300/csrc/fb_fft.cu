@@ -179,6 +179,18 @@ int factorize(long long n, int* r, int cap, bool odd_first = false)
     return c;
 }
 
+// n = n1 * n2 with n1 the divisor of n closest to sqrt(n) from below and
+// both factors fitting one line pass.
+int split_square(long long n, long long* n1, long long* n2)
+{
+    long long best = 0;
+    for (long long d = 1; d * d <= n; ++d)
+        if (n % d == 0 && n / d <= FB_FFT_MAX_SMEM_LEN) best = d;
+    if (best == 0) return FB_FFT_ERR_UNSUPPORTED_SIZE;
+    *n1 = best, *n2 = n / best;
+    return FB_FFT_OK;
+}
+
 int split_fourstep(long long n, long long* n1, long long* n2)
 {
     if (n < 1) return FB_FFT_ERR_INVALID_ARG;
@@ -493,7 +505,11 @@ int schedule_many(fb_fft_plan_s* p, TwiddleBuilder& twb)
             for (size_t k = b0; k < b0 + nb; ++k) p->h_off.push_back(p->offsets[idx[k]]);
             return at;
         };
-        if (L <= FB_FFT_MAX_SMEM_LEN) {
+        // with merged launches, lengths that only the generic (run-time
+        // schedule) kernel would take run as two mixed passes (four-step) in
+        // the merged launches instead
+        const bool via_fourstep = p->merge_mixed && !pow2 && L > kMixedMaxLen;
+        if (L <= FB_FFT_MAX_SMEM_LEN && !via_fourstep) {
             PassPlan q;
             int rc = make_line_pass(q, twb, L, 1, (long long)idx.size(), 1, L, 0, 1, L, 0, false, false, false,
                                     p->odd_first, p->max_lines);
@@ -510,7 +526,7 @@ int schedule_many(fb_fft_plan_s* p, TwiddleBuilder& twb)
             continue;
         }
         long long N1, N2;
-        int rc = split_fourstep(L, &N1, &N2);
+        int rc = L <= FB_FFT_MAX_SMEM_LEN ? split_square(L, &N1, &N2) : split_fourstep(L, &N1, &N2);
         if (rc != FB_FFT_OK) return rc;
         const int plog = (ilog2ll(L) + 1) / 2;
         const long long lo_cnt = 1LL << plog, hi_cnt = (L + lo_cnt - 1) >> plog;
