@@ -120,11 +120,11 @@ def test_autotuner_returns_a_working_setting(fb):
 
 @pytest.mark.parametrize("direction,scale", [(-1, False), (1, True)])
 def test_merged_launches_equal_per_length_launches(fb, direction, scale):
-    """Merged mixed-kernel launches (default) and one launch per length give
-    the same bits, with far fewer launches."""
+    """Merged mixed-kernel launches (default) and one launch per length agree,
+    with far fewer launches."""
     import torch
     lens = list(inputs.uneven_lengths(300, 64, 65536, inputs.seed_for(inputs.WORKLOAD_UNEVEN_4096, 7)))
-    lens += [75, 6000, 45000, 3 * 5 ** 6, 2, 3]
+    lens += [75, 6000, 45000, 3 * 5 ** 6, 2, 3, 3000, 2187, 3125, 4050]
     xs = _batch(lens, 950)
     with fb.PlanMany(lens, scale_inv_n=scale) as pm, \
             fb.PlanMany(lens, scale_inv_n=scale, opts={"per_length": 1}) as pl:
@@ -138,7 +138,13 @@ def test_merged_launches_equal_per_length_launches(fb, direction, scale):
         l2 = fb.launch_count()
         pm.check()
         pl.check()
-        assert torch.equal(ym, yl)
         assert (l1 - l0) < (l2 - l1)
         ys = pm.unpack(ym.cpu().numpy())
+        yls = pl.unpack(yl.cpu().numpy())
+    # same kernels, same bits -- except lengths 2049..4096 with a factor 3 or 5,
+    # which the merged plan runs as two mixed passes (four-step)
+    for n, a, b in zip(lens, ys, yls):
+        if not (2048 < n <= 4096 and n & (n - 1)):
+            assert np.array_equal(a, b), n
     _check(pm, xs, ys, direction, scale)
+    _check(pl, xs, yls, direction, scale)
