@@ -761,15 +761,17 @@ __global__ void __launch_bounds__(THREADS, 1) k_fft_mixed(const __grid_constant_
     if (async && threadIdx.x == 0) bulk_wait_all();
 }
 
-// (Power-of-two factors 2..16 fit 128 registers: two CTAs per SM overlap one
-// another's barriers; the others need more and run one CTA per SM.)
+// (Power-of-two factors up to 16 run two CTAs per SM, which overlap one
+// another's barriers: 2..16 fit 128 registers; odd lengths spill about 0.5 KB
+// there and still measured 1.2x faster than at one CTA per SM.  Larger
+// factors need more registers and run one CTA per SM.)
 // The mixed line pass over several jobs (MultiArgs): persistent CTAs walk the
 // global tiles blockIdx.x, +gridDim.x, ...; a tile's job is found by advancing
 // through the prefix table (tiles only grow).  Two landing buffers, each with
 // its tile's descriptor in shared memory: while tile i is transformed, every
 // thread's cp.async copies bring tile i+1 through its job's offset table.
 template <int THREADS, bool FWD, int LG2>
-__global__ void __launch_bounds__(THREADS, (LG2 >= 1 && LG2 <= 4 ? 2 : 1)) k_fft_mixed_multi(const __grid_constant__ MultiArgs a)
+__global__ void __launch_bounds__(THREADS, (LG2 <= 4 ? 2 : 1)) k_fft_mixed_multi(const __grid_constant__ MultiArgs a)
 {
     extern __shared__ __align__(128) unsigned char smem_dyn[];
     unsigned char* smem_raw = smem_dyn + ((128u - (smem_u32(smem_dyn) & 127u)) & 127u);
