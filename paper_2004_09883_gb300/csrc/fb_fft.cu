@@ -78,15 +78,19 @@ int many_streams()
     return v;
 }
 
-// CTA size of passes over short contiguous lines (128 or 256 compute threads).
-int nn_small_threads()
+// CTA size of passes over short contiguous lines of length L: 64 compute
+// threads up to 128 points, 128 for 256 points (small CTAs, several per SM,
+// three tiles in flight each; on the 3-D bench's L = 128 pass 64 measured 4 %
+// faster than 128 and 12 % faster than 256).  FB_FFT_NN_SMALL_THREADS = 64,
+// 128 or 256 forces one size.
+int nn_small_threads(long long L)
 {
     static int v = [] {
         const char* s = std::getenv("FB_FFT_NN_SMALL_THREADS");
         const int n = s ? std::atoi(s) : 0;
-        return n == 256 ? 256 : 128;
+        return (n == 64 || n == 128 || n == 256) ? n : 0;
     }();
-    return v;
+    return v ? v : (L <= 128 ? 64 : 128);
 }
 
 enum BufKind { kBufIn = 0, kBufOut = 1, kBufScratch = 2 };
@@ -322,7 +326,7 @@ int make_line_pass(PassPlan& p, TwiddleBuilder& twb, long long L, long long O, l
         p.tc = tc && line_kernel_p2tc(256, true, p.lg, p.io).fn != nullptr;
         p.threads = (!p.tc && cfast && L >= 512) ? 512 : 256;
         // short contiguous lines: 128-thread CTAs, three per SM, three tiles in flight each
-        if (!p.tc && !cfast && L >= 32 && L <= 256 && nn_small_threads() == 128) p.threads = 128;
+        if (!p.tc && !cfast && L >= 32 && L <= 256) p.threads = nn_small_threads(L);
         if (!line_kernel_p2(p.threads, true, p.lg, p.io).fn) return FB_FFT_ERR_UNSUPPORTED_SIZE;
         T = p2_tile_lines(p.threads, p.lg, p.io);
         land = p2_land_elems(p.threads, p.lg, p.io);

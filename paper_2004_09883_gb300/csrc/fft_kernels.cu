@@ -18,6 +18,8 @@ LineKernel line_kernel_p2_512_inv_a(int lg, int io);
 LineKernel line_kernel_p2_512_inv_b(int lg, int io);
 LineKernel line_kernel_p2_128_fwd(int lg, int io);
 LineKernel line_kernel_p2_128_inv(int lg, int io);
+LineKernel line_kernel_p2_64_fwd(int lg, int io);
+LineKernel line_kernel_p2_64_inv(int lg, int io);
 LineKernel line_kernel_p2tc_fwd(int threads, int lg, int io);
 LineKernel line_kernel_p2tc_inv(int threads, int lg, int io);
 
@@ -32,6 +34,7 @@ LineKernel line_kernel_p2(int threads, bool forward, int lg, int io)
     if (lg < 1 || lg > kMaxLineLog2 || io < kIoNN || io > kIoCCP) return none;
     const bool a = io == kIoNN || io == kIoCC;
     if (threads == 128) return forward ? line_kernel_p2_128_fwd(lg, io) : line_kernel_p2_128_inv(lg, io);
+    if (threads == 64) return forward ? line_kernel_p2_64_fwd(lg, io) : line_kernel_p2_64_inv(lg, io);
     if (threads == 256)
         return forward ? (a ? line_kernel_p2_256_fwd_a(lg, io) : line_kernel_p2_256_fwd_b(lg, io))
                        : (a ? line_kernel_p2_256_inv_a(lg, io) : line_kernel_p2_256_inv_b(lg, io));

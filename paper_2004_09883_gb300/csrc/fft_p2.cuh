@@ -79,7 +79,7 @@ __host__ __device__ constexpr int p2_work_stride(int threads, int lg, int io)
 // Landing buffers in flight per CTA: 128-thread CTAs (short contiguous lines,
 // three CTAs per SM) keep three, so two tile loads stay in flight while one
 // tile is transformed.
-__host__ __device__ constexpr int p2_nbuf(int threads) { return threads == 128 ? 3 : 2; }
+__host__ __device__ constexpr int p2_nbuf(int threads) { return threads <= 128 ? 3 : 2; }
 __host__ __device__ constexpr long long p2_smem_bytes(int threads, int lg, int io, bool async, bool tc)
 {
     return 256 + 8LL * (p2_land_elems(threads, lg, io) * (async ? p2_nbuf(threads) : 1) +

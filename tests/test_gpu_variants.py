@@ -1,6 +1,6 @@
 """Launch variants that change scheduling, not arithmetic, give the same bits:
 programmatic dependent launch off (FB_FFT_PDL=0) and 256-thread CTAs for short
-contiguous lines (FB_FFT_NN_SMALL_THREADS=256).  Each runs in a subprocess
+contiguous lines (FB_FFT_NN_SMALL_THREADS=64/128/256).  Each runs in a subprocess
 (the library reads the variables once)."""
 import os
 import subprocess
@@ -18,7 +18,8 @@ import sys, numpy as np, torch
 sys.path.insert(0, sys.argv[1])
 from paper_2004_09883_gb300 import fbfft, inputs
 out = []
-for dims, b in [([256, 256, 128], 1), ([128], 512), ([64, 100], 3), ([1 << 20], 2), ([4096], 16)]:
+for dims, b in [([256, 256, 128], 1), ([128], 512), ([64, 100], 3), ([1 << 20], 2), ([4096], 16), ([256], 300),
+                ([32], 999)]:
     x = torch.from_numpy(inputs.uniform_c64([b] + dims, 4242)).cuda()
     with fbfft.Plan(dims, b, scale_inv_n=True) as p:
         y = p.exec(x, None, -1)
@@ -40,6 +41,7 @@ def _run(tmp_path, name, env_extra):
 
 def test_launch_variants_give_identical_bits(fb, tmp_path):
     base = _run(tmp_path, "base", {})
-    for name, env in [("no_pdl", {"FB_FFT_PDL": "0"}), ("nn256", {"FB_FFT_NN_SMALL_THREADS": "256"})]:
+    for name, env in [("no_pdl", {"FB_FFT_PDL": "0"}), ("nn256", {"FB_FFT_NN_SMALL_THREADS": "256"}),
+                      ("nn128", {"FB_FFT_NN_SMALL_THREADS": "128"}), ("nn64", {"FB_FFT_NN_SMALL_THREADS": "64"})]:
         got = _run(tmp_path, name, env)
         assert np.array_equal(base, got), name
