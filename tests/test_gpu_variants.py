@@ -1,6 +1,6 @@
 """Launch variants that change scheduling, not arithmetic, give the same bits:
-programmatic dependent launch off (FB_FFT_PDL=0) and 256-thread CTAs for short
-contiguous lines (FB_FFT_NN_SMALL_THREADS=64/128/256).  Each runs in a subprocess
+programmatic dependent launch off (FB_FFT_PDL=0) and the CTA size of passes
+over short contiguous lines (FB_FFT_NN_SMALL_THREADS=64/128/256).  Each runs in a subprocess
 (the library reads the variables once)."""
 import os
 import subprocess
