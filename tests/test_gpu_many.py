@@ -124,7 +124,7 @@ def test_merged_launches_equal_per_length_launches(fb, direction, scale):
     with far fewer launches."""
     import torch
     lens = list(inputs.uneven_lengths(300, 64, 65536, inputs.seed_for(inputs.WORKLOAD_UNEVEN_4096, 7)))
-    lens += [75, 6000, 45000, 3 * 5 ** 6, 2, 3, 3000, 2187, 3125, 4050]
+    lens += [75, 6000, 45000, 3 * 5 ** 6, 2, 3, 3000, 2187, 3125, 4050, 64, 128, 512, 2048, 4096, 8192, 65536]
     xs = _batch(lens, 950)
     with fb.PlanMany(lens, scale_inv_n=scale) as pm, \
             fb.PlanMany(lens, scale_inv_n=scale, opts={"per_length": 1}) as pl:
@@ -141,10 +141,11 @@ def test_merged_launches_equal_per_length_launches(fb, direction, scale):
         assert (l1 - l0) < (l2 - l1)
         ys = pm.unpack(ym.cpu().numpy())
         yls = pl.unpack(yl.cpu().numpy())
-    # same kernels, same bits -- except lengths 2049..4096 with a factor 3 or 5,
-    # which the merged plan runs as two mixed passes (four-step)
+    # same kernels, same bits for the lengths with a factor 3 or 5 that both
+    # plans give to the mixed kernel; the merged plan also runs power-of-two
+    # lines of 64..2048 points and lengths 2049..4096 (as two passes) there
     for n, a, b in zip(lens, ys, yls):
-        if not (2048 < n <= 4096 and n & (n - 1)):
+        if n & (n - 1) and not 2048 < n <= 4096:
             assert np.array_equal(a, b), n
     _check(pm, xs, ys, direction, scale)
     _check(pl, xs, yls, direction, scale)
