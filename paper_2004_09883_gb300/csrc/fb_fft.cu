@@ -294,13 +294,12 @@ void ptw_to_smem(PassPlan& a, long long hi_cnt)
 int make_line_pass(PassPlan& p, TwiddleBuilder& twb, long long L, long long O, long long C,
                    long long in_sn, long long in_sc, long long in_so, long long out_sk, long long out_sc,
                    long long out_so, bool in_tfast, bool out_tfast, bool ptw, bool odd_first = false,
-                   int max_lines = 0, bool tc = false, bool force_mixed = false)
+                   int max_lines = 0, bool tc = false)
 {
     p = PassPlan{};  // zero descriptor, default member values (no offset tables)
     PassDesc& d = p.d;
     const bool pow2_len = (L & (L - 1)) == 0;
-    // mixed kernels fix the radix order; force_mixed: a power-of-two line for the merged mixed kernel
-    const bool mixed_len = (!pow2_len && L <= kMixedMaxLen) || force_mixed;
+    const bool mixed_len = !pow2_len && L <= kMixedMaxLen;  // mixed kernels fix the radix order
     int nst = factorize(L, d.radix, kMaxStages, odd_first && !pow2_len && !mixed_len);
     if (nst < 0) return nst;
     if (nst > kMaxStages) return FB_FFT_ERR_UNSUPPORTED_SIZE;
@@ -314,7 +313,7 @@ int make_line_pass(PassPlan& p, TwiddleBuilder& twb, long long L, long long O, l
     for (int s = 0; s < nst; ++s) d.twoff[s] = off[s];
 
     const bool cfast = in_tfast || out_tfast;
-    const bool pow2 = (L & (L - 1)) == 0 && !force_mixed;
+    const bool pow2 = (L & (L - 1)) == 0;
     p.lg = pow2 ? ilog2ll(L) : 0;
     long long T = 1, land = 0;
     if (pow2) {
@@ -346,7 +345,7 @@ int make_line_pass(PassPlan& p, TwiddleBuilder& twb, long long L, long long O, l
         if (max_lines > 0) T = std::min<long long>(T, pow2floor(max_lines));
         T = std::max<long long>(1, std::min(T, pow2ceil(C)));
         land = land_stride_elems((int)L, (int)T);
-        if (force_mixed ? !mixed_multi_available(p.lg) : !pass_kernel(p, true).fn) return FB_FFT_ERR_UNSUPPORTED_SIZE;
+        if (!pass_kernel(p, true).fn) return FB_FFT_ERR_UNSUPPORTED_SIZE;
     }
 
     d.L = (int)L;
@@ -501,10 +500,6 @@ int schedule_many(fb_fft_plan_s* p, TwiddleBuilder& twb)
     // slots overlap; groups on one slot reuse its region in turn
     std::vector<long long> slot_need(p->nslots, 0);
     int rr = 0, rr4 = 0;
-    // with merged launches, power-of-two lines of 64..2048 points join them too
-    auto merged_pow2 = [&](long long n) {
-        return p->merge_mixed && (n & (n - 1)) == 0 && n >= (1LL << kMergedPow2MinLog2) && n <= kMixedMaxLen;
-    };
     for (auto& g : groups) {
         const long long L = g.first;
         const std::vector<long long>& idx = g.second;
@@ -521,7 +516,7 @@ int schedule_many(fb_fft_plan_s* p, TwiddleBuilder& twb)
         if (L <= FB_FFT_MAX_SMEM_LEN && !via_fourstep) {
             PassPlan q;
             int rc = make_line_pass(q, twb, L, 1, (long long)idx.size(), 1, L, 0, 1, L, 0, false, false, false,
-                                    p->odd_first, p->max_lines, false, merged_pow2(L));
+                                    p->odd_first, p->max_lines);
             if (rc != FB_FFT_OK) return rc;
             q.off_in_idx = q.off_out_idx = push_offsets(0, idx.size());
             if (!pow2) q.async_ok = false;  // the generic kernel copies offset-table tiles itself
@@ -550,8 +545,7 @@ int schedule_many(fb_fft_plan_s* p, TwiddleBuilder& twb)
             const long long nb = std::min(chunk, cnt - b0);
             const long long at = push_offsets((size_t)b0, (size_t)nb);
             PassPlan a, r;
-            rc = make_line_pass(a, twb, N1, nb, N2, N2, 1, L, N2, 1, L, true, true, true, p->odd_first, p->max_lines,
-                                false, merged_pow2(N1));
+            rc = make_line_pass(a, twb, N1, nb, N2, N2, 1, L, N2, 1, L, true, true, true, p->odd_first, p->max_lines);
             if (rc != FB_FFT_OK) return rc;
             a.d.ptw_log = plog;
             a.d.ptw_lo = reinterpret_cast<const float2*>(lo_off);
@@ -563,7 +557,7 @@ int schedule_many(fb_fft_plan_s* p, TwiddleBuilder& twb)
             a.group = 1;
             a.slot = slot;
             rc = make_line_pass(r, twb, N2, nb, N1, 1, N2, L, N1, 1, L, false, true, false, p->odd_first,
-                                p->max_lines, false, merged_pow2(N2));
+                                p->max_lines);
             if (rc != FB_FFT_OK) return rc;
             r.off_out_idx = at;
             if ((N2 & (N2 - 1)) != 0) r.async_ok = false;
@@ -612,6 +606,7 @@ int schedule_many(fb_fft_plan_s* p, TwiddleBuilder& twb)
         int rrm = 0;
         for (auto& kv : buckets) {
             const std::vector<int>& v = kv.second;
+            if (v.size() < 2) continue;
             for (size_t b0 = 0; b0 < v.size(); b0 += kMultiMax) {
                 MultiLaunch m;
                 m.phase = kv.first.first;
@@ -783,13 +778,6 @@ int build_plan(fb_fft_plan_s* p)
     int sms = 0;
     FB_CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, p->device));
     for (PassPlan& q : p->passes) {
-        q.d.err = p->err;
-        q.d.tw = p->tw;
-        if (q.d.ptw) {
-            q.d.ptw_lo = p->tw + reinterpret_cast<long long>(q.d.ptw_lo);
-            q.d.ptw_hi = p->tw + reinterpret_cast<long long>(q.d.ptw_hi);
-        }
-        if (q.multi >= 0) continue;  // launched by its merged launch (grid set below)
         int occ = 0;
         const LineKernel k = pass_kernel(q, true);
         FB_CK(line_occupancy(k, q.smem, &occ));
@@ -800,6 +788,12 @@ int build_plan(fb_fft_plan_s* p)
         // the resources.  (A grid above what fits would only run in waves.)
         if (q.tc) occ = std::max(occ, pass_ctas_per_sm(q, q.smem));
         q.grid = std::min(q.grid, (long long)sms * occ);
+        q.d.err = p->err;
+        q.d.tw = p->tw;
+        if (q.d.ptw) {
+            q.d.ptw_lo = p->tw + reinterpret_cast<long long>(q.d.ptw_lo);
+            q.d.ptw_hi = p->tw + reinterpret_cast<long long>(q.d.ptw_hi);
+        }
     }
     if (p->scratch_bytes && !p->ext_scratch) {
         if (cudaMalloc(&p->scratch, p->scratch_bytes) != cudaSuccess) {

@@ -78,7 +78,6 @@ struct PassDesc {
 // kernel parameter (about 20 KB, under the 32 KB parameter limit), so a
 // captured graph holds it by value.
 constexpr int kMultiMax = 64;
-constexpr int kMergedPow2MinLog2 = 6;  // power-of-two lines >= 64 points may run merged
 struct MultiArgs {
     long long tile_start[kMultiMax + 1];
     int njobs;
@@ -88,7 +87,6 @@ struct MultiArgs {
 cudaError_t mixed_multi_launch(bool forward, int lg2, const MultiArgs& a, long long grid, size_t smem,
                                cudaStream_t stream);
 cudaError_t mixed_multi_occupancy(bool forward, int lg2, size_t smem, int* blocks_per_sm);
-bool mixed_multi_available(int lg2);  // a merged kernel exists for this power-of-two factor
 
 // Kernel argument: the descriptor plus the TMA tensor maps of the c-fast
 // input/output views {C, L, O} (encoded per launch, they hold addresses).

@@ -660,26 +660,15 @@ __device__ __forceinline__ void run_odd_stage(int R, const PassDesc& d, int Ns, 
         stage<3, THREADS, FWD, POS, E>(d, Ns, twoff, land, work, Tv, c0);
 }
 // Compile-time power-of-two prefix of a mixed schedule (stage S < pow2_nst(LG2)).
-// When the prefix is the whole schedule (a power-of-two line of >= 64 points
-// run by the merged kernel, d.nst == pow2_nst(LG2)), its last stage writes the
-// output.  (Only compiled for LG2 >= 6: the planner never sends shorter
-// power-of-two lines here, and the extra stage variants cost registers.)
 template <int THREADS, bool FWD, int LG2, int S, int E>
 __device__ __forceinline__ void mixed_p2_stages(const PassDesc& d, float2* land, float2* work, int Tv, int c0)
 {
     if constexpr (S < pow2_nst(LG2)) {
         constexpr int R = pow2_radix(LG2, S);
-        constexpr bool last_p2 = S == pow2_nst(LG2) - 1 && LG2 >= kMergedPow2MinLog2;
-        if (last_p2 && d.nst == pow2_nst(LG2)) {
-            if constexpr (S == 0)
-                stage<R, THREADS, FWD, kPosOnly, E>(d, 1, 0, land, work, Tv, c0);
-            else
-                stage<R, THREADS, FWD, kPosLast, E>(d, d.ns[S], d.twoff[S], land, work, Tv, c0);
-        } else if constexpr (S == 0) {
+        if constexpr (S == 0)
             stage<R, THREADS, FWD, kPosFirst, E>(d, 1, 0, land, work, Tv, c0);
-        } else {
+        else
             stage<R, THREADS, FWD, kPosMid, E>(d, d.ns[S], d.twoff[S], land, work, Tv, c0);
-        }
         __syncthreads();
         mixed_p2_stages<THREADS, FWD, LG2, S + 1, E>(d, land, work, Tv, c0);
     }

@@ -27,8 +27,6 @@ MultiFn multi_fn(int lg2)
     case 7: return k_fft_mixed_multi<kMixedThreads, FWD, 7>;
     case 8: return k_fft_mixed_multi<kMixedThreads, FWD, 8>;
     case 9: return k_fft_mixed_multi<kMixedThreads, FWD, 9>;
-    case 10: return k_fft_mixed_multi<kMixedThreads, FWD, 10>;  // power-of-two lines 1024 and 2048
-    case 11: return k_fft_mixed_multi<kMixedThreads, FWD, 11>;
     default: return nullptr;
     }
 }
@@ -68,8 +66,6 @@ bool pdl_on()
 }
 
 }  // namespace
-
-bool mixed_multi_available(int lg2) { return multi_fn<true>(lg2) != nullptr; }
 
 cudaError_t mixed_multi_occupancy(bool forward, int lg2, size_t smem, int* blocks_per_sm)
 {
