@@ -62,10 +62,17 @@ KERNEL_SOURCES = sorted(
 
 
 def kernel_hash() -> str:
+    """Hash of the kernel sources' code: comments and blank lines are left
+    out, so documentation edits keep a committed capture valid."""
+    import re
     h = hashlib.sha256()
     for f in KERNEL_SOURCES:
-        with open(os.path.join(ROOT, f), "rb") as fh:
-            h.update(fh.read())
+        with open(os.path.join(ROOT, f), encoding="utf-8") as fh:
+            text = re.sub(r"/\*.*?\*/", "", fh.read(), flags=re.S)
+        for line in text.splitlines():
+            code = line.split("//", 1)[0].rstrip()
+            if code:
+                h.update(code.encode() + b"\n")
     return h.hexdigest()[:16]
 
 

@@ -477,11 +477,12 @@ long long many_layout(int count, const long long* lengths, long long* offsets)
     return off;
 }
 
-// Batched uneven lengths: one pass (or one four-step pair per L2-sized
-// chunk) per distinct length, each covering all transforms of that length
-// through an offset table.  Single-pass groups are spread over side streams
-// 1..nslots-1, four-step groups over all slots, each slot with its own
-// scratch region.
+// Batched uneven lengths: one pass (or one four-step pair per chunk) per
+// distinct length, each covering all transforms of that length through an
+// offset table.  Without merging, single-pass groups are spread over side
+// streams 1..nslots-1 and four-step groups over all slots, each slot with its
+// own scratch region; with merging (the default), mixed-kernel passes become
+// merged launches and every four-step chunk has its own scratch region.
 int schedule_many(fb_fft_plan_s* p, TwiddleBuilder& twb)
 {
     std::vector<std::pair<long long, std::vector<long long>>> groups;  // (L, transform indices)

@@ -13,13 +13,11 @@ constexpr int kMaxStages = 8;
 constexpr int kElemsPerThread = 16;  // E: complex values one thread holds per stage
 constexpr int kGenericElems = 8;     // E of the generic (run-time schedule) kernel
 
-// Thread-block shapes of the line-pass kernel: tile capacity = threads * E.
-// Power-of-two lines get kernels with compile-time radix schedules (256
-// threads for L <= 4096, 512 threads for 512 <= L <= 4096); other 5-smooth
-// lines use the generic 256-thread kernel that reads its schedule at run time.
-enum LineCfg { kCfg256 = 0, kCfg512 = 1, kNumCfg = 2 };
-constexpr int cfg_threads(int cfg) { return cfg == kCfg256 ? 256 : 512; }
-constexpr long long cfg_capacity(int cfg) { return (long long)cfg_threads(cfg) * kElemsPerThread; }
+// Thread-block shapes of the line-pass kernels (tile capacity = compute
+// threads x values per thread): power-of-two lines take compile-time kernels
+// of 64, 128, 256 or 512 compute threads (fft_p2.cuh); lines with a factor 3
+// or 5 take the mixed kernels (up to 2048 points) or the generic kernel, which
+// reads its whole schedule at run time.
 constexpr int kGenericThreads = 512;  // generic kernel: 512 x 8 = 4096 values per tile
 // Mixed kernels (power-of-two radices at compile time, then 5s and 3s):
 // 256 threads x 8 values, lines up to 2048 with a factor 3 or 5.
