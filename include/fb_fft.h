@@ -51,7 +51,8 @@ typedef enum fb_fft_status {
 
 /* Plan flags. */
 #define FB_FFT_SCALE_INV_N 0x1u /* multiply the result of every INVERSE exec by 1/prod(dims) */
-/* Run the radix-16 stages of power-of-two lines of length >= 256 on the
+/* The same transform (Sec. 5.1(a); the paper fixes no arithmetic precision)
+ * with the radix-16 stages of power-of-two lines of length >= 256 on the
  * tensor cores: each stage's 16-point DFT as one FP16 matrix product per 128
  * butterflies, inputs and DFT matrix split into hi + lo halves (three
  * products, FP32 accumulation, per-butterfly power-of-two scaling).  Relative
@@ -279,7 +280,8 @@ int fb_fft_profile(fb_fft_plan_t plan, int enable);
 int fb_fft_profile_read(fb_fft_plan_t plan, double* ms_total, long long* launches,
                         int capacity, int* npasses);
 
-/* fb_fft_pass_launch -- launch configuration of the plan's pass p, in plan
+/* fb_fft_pass_launch -- (introspection, no paper counterpart) launch
+ * configuration of the plan's pass p, in plan
  * order (fb_fft_info.passes of them for regular plans): CTAs, threads per
  * CTA, dynamic shared memory in bytes (with TMA on).  A batched-uneven pass
  * that runs inside a merged launch reports grid 0.  Errors: BAD_PLAN,
