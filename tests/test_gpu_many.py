@@ -42,7 +42,9 @@ def test_many_matches_oracle(fb, graph):
         out2 = p.exec(d, None, -1)  # second exec replays the cached graph
         p.check()
         ys = p.unpack(out.cpu().numpy())
-        assert torch.equal(out, out2)
+        # the packed layout pads odd lengths to even: compare the transforms, not the padding
+        for a, b in zip(p.unpack(out.cpu().numpy()), p.unpack(out2.cpu().numpy())):
+            assert np.array_equal(a, b)
     _check(p, xs, ys, -1)
 
 
@@ -56,7 +58,8 @@ def test_many_graph_equals_direct_and_inverse_scaled(fb):
         p.set_graph(False)
         direct = p.exec(d, None, 1)
         p.check()
-        assert torch.equal(g, direct)
+        for a, b in zip(p.unpack(g.cpu().numpy()), p.unpack(direct.cpu().numpy())):
+            assert np.array_equal(a, b)
         ys = p.unpack(g.cpu().numpy())
     _check(p, xs, ys, 1, scale=True)
 
@@ -142,9 +145,8 @@ def test_merged_launches_equal_per_length_launches(fb, direction, scale):
         ys = pm.unpack(ym.cpu().numpy())
         yls = pl.unpack(yl.cpu().numpy())
     # same kernel, same bits for single-pass lengths with a factor 3 or 5 (both
-    # plans run them in the mixed kernel); the merged plan also moves power-of-two
-    # lines of 64..2048 points (single passes and four-step parts) and lengths
-    # 2049..4096 (as two passes) there, which the oracle check below covers
+    # plans run them in the mixed kernel); the merged plan runs lengths
+    # 2049..4096 with such a factor as two passes, which the oracle check covers
     for n, a, b in zip(lens, ys, yls):
         if n & (n - 1) and n <= 2048:
             assert np.array_equal(a, b), n
