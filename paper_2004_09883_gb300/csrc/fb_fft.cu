@@ -78,17 +78,6 @@ int many_streams()
     return v;
 }
 
-// Radix-9 stages (two radix-3 stages fused) in the mixed kernels
-// (FB_FFT_RADIX9 = 0 keeps the 3s apart).
-bool radix9_enabled()
-{
-    static const bool v = [] {
-        const char* s = std::getenv("FB_FFT_RADIX9");
-        return !(s && s[0] == '0');
-    }();
-    return v;
-}
-
 // CTA size of passes over short contiguous lines of length L: 64 compute
 // threads up to 128 points, 128 for 256 points (small CTAs, several per SM,
 // three tiles in flight each; on the 3-D bench's L = 128 pass 64 measured 4 %
@@ -313,17 +302,6 @@ int make_line_pass(PassPlan& p, TwiddleBuilder& twb, long long L, long long O, l
     const bool mixed_len = !pow2_len && L <= kMixedMaxLen;  // mixed kernels fix the radix order
     int nst = factorize(L, d.radix, kMaxStages, odd_first && !pow2_len && !mixed_len);
     if (nst < 0) return nst;
-    if (mixed_len && radix9_enabled() && nst <= kMaxStages) {
-        // the mixed kernels' run-time stages: fuse pairs of 3s into 9s (the
-        // odd stages follow the power-of-two ones: ..., 5, ..., 3, 3, ... -> 9)
-        int out = 0, threes = 0;
-        for (int s2 = 0; s2 < nst; ++s2)
-            if (d.radix[s2] == 3) ++threes;
-            else d.radix[out++] = d.radix[s2];
-        for (; threes >= 2; threes -= 2) d.radix[out++] = 9;
-        if (threes) d.radix[out++] = 3;
-        nst = out;
-    }
     if (nst > kMaxStages) return FB_FFT_ERR_UNSUPPORTED_SIZE;
     d.nst = nst;
     long long Ns = 1;

@@ -59,12 +59,6 @@ __host__ __device__ __forceinline__ float2 rot(float2 z, float C, float S)
 #define FB_C5_2 -0.80901699437494742410f  // cos(4pi/5)
 #define FB_S5_1  0.95105651629515357212f  // sin(2pi/5)
 #define FB_S5_2  0.58778525229247312917f  // sin(4pi/5)
-#define FB_C9_1  0.76604444311897803520f  // cos(2pi/9)
-#define FB_S9_1  0.64278760968653932632f  // sin(2pi/9)
-#define FB_C9_2  0.17364817766693034885f  // cos(4pi/9)
-#define FB_S9_2  0.98480775301220805937f  // sin(4pi/9)
-#define FB_C9_4 -0.93969262078590838405f  // cos(8pi/9)
-#define FB_S9_4  0.34202014332566873304f  // sin(8pi/9)
 
 template <bool FWD>
 __host__ __device__ __forceinline__ void dft2(float2& a, float2& b)
@@ -160,30 +154,6 @@ __host__ __device__ __forceinline__ void dft16(float2* v)
     for (int i = 0; i < 16; ++i) v[i] = y[i];
 }
 
-// 9 = 3 x 3: with r = 3*r1 + r2 and k = k1 + 3*k2,
-// w9^{rk} = w3^{r1 k1} w9^{r2 k1} w3^{r2 k2}.
-template <bool FWD>
-__host__ __device__ __forceinline__ void dft9(float2* v)
-{
-#pragma unroll
-    for (int r2 = 0; r2 < 3; ++r2) dft3<FWD>(v[r2], v[3 + r2], v[6 + r2]);
-    // v[3*k1 + r2] now holds A[r2][k1]; multiply by w9^{r2*k1}
-    v[4] = rot<FWD>(v[4], FB_C9_1, FB_S9_1);  // k1=1, r2=1: m=1
-    v[5] = rot<FWD>(v[5], FB_C9_2, FB_S9_2);  // k1=1, r2=2: m=2
-    v[7] = rot<FWD>(v[7], FB_C9_2, FB_S9_2);  // k1=2, r2=1: m=2
-    v[8] = rot<FWD>(v[8], FB_C9_4, FB_S9_4);  // k1=2, r2=2: m=4
-#pragma unroll
-    for (int k1 = 0; k1 < 3; ++k1) dft3<FWD>(v[3 * k1], v[3 * k1 + 1], v[3 * k1 + 2]);
-    // v[3*k1 + k2] holds Y[k1 + 3*k2]: transpose the 3x3 index
-    float2 y[9];
-#pragma unroll
-    for (int k1 = 0; k1 < 3; ++k1)
-#pragma unroll
-        for (int k2 = 0; k2 < 3; ++k2) y[k1 + 3 * k2] = v[3 * k1 + k2];
-#pragma unroll
-    for (int i = 0; i < 9; ++i) v[i] = y[i];
-}
-
 template <int R, bool FWD>
 __host__ __device__ __forceinline__ void dft(float2* v)
 {
@@ -192,7 +162,6 @@ __host__ __device__ __forceinline__ void dft(float2* v)
     else if constexpr (R == 4) dft4<FWD>(v[0], v[1], v[2], v[3]);
     else if constexpr (R == 5) dft5<FWD>(v);
     else if constexpr (R == 8) dft8<FWD>(v);
-    else if constexpr (R == 9) dft9<FWD>(v);
     else if constexpr (R == 16) dft16<FWD>(v);
 }
 
@@ -680,15 +649,13 @@ __global__ void __launch_bounds__(THREADS, 1) k_fft_generic(const __grid_constan
     if (async && threadIdx.x == 0) bulk_wait_all();
 }
 
-// Run-time dispatch over the odd radices only (5, 9 = two 3s fused, 3).
+// Run-time dispatch over the odd radices only (5, 3).
 template <int THREADS, bool FWD, int POS, int E>
 __device__ __forceinline__ void run_odd_stage(int R, const PassDesc& d, int Ns, int twoff, float2* land, float2* work,
                                               int Tv, int c0)
 {
     if (R == 5)
         stage<5, THREADS, FWD, POS, E>(d, Ns, twoff, land, work, Tv, c0);
-    else if (R == 9)
-        stage<9, THREADS, FWD, POS, E>(d, Ns, twoff, land, work, Tv, c0);
     else
         stage<3, THREADS, FWD, POS, E>(d, Ns, twoff, land, work, Tv, c0);
 }

@@ -53,7 +53,6 @@ int main()
     both<4>(g);
     both<5>(g);
     both<8>(g);
-    both<9>(g);
     both<16>(g);
     return 0;
 }
