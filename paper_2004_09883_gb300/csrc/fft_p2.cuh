@@ -267,7 +267,7 @@ __device__ __forceinline__ void p2_stage_tc(const PassDesc& d, float2* land, flo
 #pragma unroll
         for (int r = 0; r < R; ++r) v[r] = make_float2(0.f, 0.f);
     }
-    if constexpr (!first) compute_sync<THREADS>();  // A rows overwrite the work buffer just read
+    if constexpr (!first && !kTcATmem) compute_sync<THREADS>();  // A rows overwrite the work buffer just read
     const int k = j & (NS - 1);
     if constexpr (NS > 1) {  // tensor-core kernels keep the stage twiddles in global memory (L1-cached)
         const float2* tw = d.tw + d.twoff[S] + k;
@@ -275,10 +275,22 @@ __device__ __forceinline__ void p2_stage_tc(const PassDesc& d, float2* land, flo
         for (int r = 1; r < R; ++r) v[r] = twmul<FWD>(v[r], __ldg(tw + (r - 1) * NS));
     }
     const unsigned abase = smem_u32(work);
-    const int e = tc_put_row(v, abase, tid >> 7, tid & 127);
-    fence_proxy_async();  // the A rows -> visible to the tensor cores
+    int e;
+    if constexpr (kTcATmem) {
+        e = tc_put_row_tmem(v, tc);
+        tc_fence_before();  // the TMEM stores, before the barrier the issuing thread waits at
+    } else {
+        e = tc_put_row(v, abase, tid >> 7, tid & 127);
+        fence_proxy_async();  // the A rows -> visible to the tensor cores
+    }
+    // (also: every thread's gather is done before any thread scatters below)
     compute_sync<THREADS>();
-    if (tid == 0) tc_issue<THREADS / 128>(tc, abase);
+    if (tid == 0) {
+        if constexpr (kTcATmem)
+            tc_issue_tmem<THREADS / 128>(tc);
+        else
+            tc_issue<THREADS / 128>(tc, abase);
+    }
     const bool ok = mbar_wait_bounded(tc.bar, tc.uses & 1u);
     tc.uses++;
     if (!ok && (tid & 31) == 0) atomicExch(d.err, 1);
@@ -559,7 +571,7 @@ __global__ void __maxnreg__((P2Regs<THREADS, LG>::LAUNCH)) k_fft_p2(const __grid
 
     // ---- compute warps ----
     if constexpr (RG::SPLIT) asm volatile("setmaxnreg.inc.sync.aligned.u32 %0;" ::"n"(RG::COMPUTE));
-    TcState tc{0u, mma_bar, 0u, 0u};
+    TcState tc{0u, mma_bar, 0u, 0u, 0u};
     if constexpr (TC) {
         unsigned char* bmat = reinterpret_cast<unsigned char*>(
             (reinterpret_cast<uintptr_t>(tws) + 127) & ~static_cast<uintptr_t>(127));
@@ -571,6 +583,7 @@ __global__ void __maxnreg__((P2Regs<THREADS, LG>::LAUNCH)) k_fft_p2(const __grid
         tc_fence_after();
         tc.tmem = *tmem_slot;
         tc.bsm = smem_u32(bmat);
+        tc.a = tc.tmem + 32u * (THREADS / 128);  // A rows after the accumulators
     }
     if constexpr (C::TWS > 0 && !TC) {
         p2_copy_twiddles<THREADS, LG, 1>(d, tws);

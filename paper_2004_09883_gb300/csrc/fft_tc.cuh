@@ -36,8 +36,22 @@ constexpr int kTcBBytes = 32 * 128;              // B^T: 32 rows x 64 halves
 constexpr int kTcLbo = 128;                      // bytes between K-adjacent core matrices
 constexpr int kTcSbo = 1024;                     // bytes between 8-row groups (8 core matrices per row group)
 
-// TMEM columns a CTA of `threads` compute threads allocates (32 per group, power of two >= 32).
-__host__ __device__ constexpr int tc_tmem_cols(int threads) { return threads / 128 * 32 < 32 ? 32 : threads / 128 * 32; }
+// Where the A rows live: TMEM (default; written with tcgen05.st, read by the
+// MMA as its A operand) or shared memory (FB_FFT_TC_A_SMEM; the work buffer,
+// through a K-major descriptor).
+#ifdef FB_FFT_TC_A_SMEM
+constexpr bool kTcATmem = false;
+#else
+constexpr bool kTcATmem = true;
+#endif
+
+// TMEM columns a CTA of `threads` compute threads allocates: 32 accumulator
+// columns per 128-row group, and as many again for the A rows when they live
+// in TMEM (power of two >= 32).
+__host__ __device__ constexpr int tc_tmem_cols(int threads)
+{
+    return (threads / 128) * 32 * (kTcATmem ? 2 : 1) < 32 ? 32 : (threads / 128) * 32 * (kTcATmem ? 2 : 1);
+}
 
 // Shared-memory matrix descriptor (tcgen05): start address, leading- and
 // stride-dimension byte offsets, descriptor version 1, no swizzle.
@@ -88,6 +102,29 @@ __device__ __forceinline__ void tc_commit(unsigned long long* bar)
     asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
                  : "memory");
 }
+// A operand from TMEM: [a-tmem] instead of a shared-memory descriptor.
+__device__ __forceinline__ void tc_mma_ta(unsigned dt, unsigned at, unsigned long long bd, unsigned idesc,
+                                          unsigned accumulate)
+{
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %3, p;\n\t}" ::"r"(dt),
+        "r"(at), "l"(bd), "r"(idesc), "r"(accumulate)
+        : "memory");
+}
+// 16 consecutive 32-bit columns of this thread's TMEM lane, then wait for them.
+__device__ __forceinline__ void tc_st16(unsigned taddr, const unsigned (&r)[16])
+{
+    asm volatile(
+        "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+        "%15, %16};" ::"r"(taddr),
+        "r"(r[0]), "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]), "r"(r[7]), "r"(r[8]),
+        "r"(r[9]), "r"(r[10]), "r"(r[11]), "r"(r[12]), "r"(r[13]), "r"(r[14]), "r"(r[15])
+        : "memory");
+}
+__device__ __forceinline__ void tc_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
+
 // 32 consecutive FP32 columns of this thread's TMEM lane.
 __device__ __forceinline__ void tc_ld32(unsigned taddr, unsigned (&r)[32])
 {
@@ -128,39 +165,87 @@ __device__ __forceinline__ void tc_build_b(unsigned char* b)
 }
 
 struct TcState {
-    unsigned tmem;             // TMEM base address (lane 0, first column)
+    unsigned tmem;             // TMEM base address (lane 0, first column): accumulators
     unsigned long long* bar;   // MMA completion mbarrier
     unsigned bsm;              // shared address of B^T
     unsigned uses;             // completed MMA rounds (mbarrier phase)
+    unsigned a;                // TMEM address of the A rows (when kTcATmem)
 };
+
+// The scale exponent of a butterfly: 2^-e brings its largest component into [0.5, 1).
+__device__ __forceinline__ int tc_scale_exp(const float2 (&v)[16])
+{
+    float m = 0.f;
+#pragma unroll
+    for (int r = 0; r < 16; ++r) m = fmaxf(m, fmaxf(fabsf(v[r].x), fabsf(v[r].y)));
+    const int e = ((__float_as_int(m) >> 23) & 0xff) - 126;  // m in [2^(e-1), 2^e)
+    return e < -126 ? -126 : (e > 126 ? 126 : e);
+}
+// K pair p (K = 2p, 2p+1; 0..15 real parts, 16..31 imaginary parts) of the
+// scaled butterfly as packed halves: hi and lo words.
+__device__ __forceinline__ void tc_split_pair(const float2 (&v)[16], float down, int p, unsigned& hw, unsigned& lw)
+{
+    const int k0 = 2 * p;
+    const float a = (k0 < 16 ? v[k0].x : v[k0 - 16].y) * down;
+    const float b = (k0 + 1 < 16 ? v[k0 + 1].x : v[k0 + 1 - 16].y) * down;
+    const __half2 h = __floats2half2_rn(a, b);  // (a, b) -> low, high half
+    const float2 hf = __half22float2(h);
+    const __half2 l = __floats2half2_rn(a - hf.x, b - hf.y);
+    hw = *reinterpret_cast<const unsigned*>(&h);
+    lw = *reinterpret_cast<const unsigned*>(&l);
+}
+
+// TMEM variant: scale, split and write this thread's row of A (hi: 16
+// columns, lo: the next 16) into its lane; waits for the stores.  Returns e.
+__device__ __forceinline__ int tc_put_row_tmem(const float2 (&v)[16], const TcState& tc)
+{
+    const int e = tc_scale_exp(v);
+    const float down = __int_as_float((127 - e) << 23);
+    unsigned hw[16], lw[16];
+#pragma unroll
+    for (int p = 0; p < 16; ++p) tc_split_pair(v, down, p, hw[p], lw[p]);
+    const int warp = threadIdx.x >> 5;
+    const unsigned row = tc.a + ((unsigned)(32 * (warp & 3)) << 16) + 32u * (unsigned)(warp >> 2);
+    tc_st16(row, hw);
+    tc_st16(row + 16, lw);
+    tc_wait_st();
+    return e;
+}
+
+// TMEM variant of the issue: A operands [a_g + 0 / 8] (hi, K 0-15 / 16-31) and
+// [a_g + 16 / 24] (lo), 8 columns = 16 halves per K step.
+template <int GROUPS>
+__device__ __forceinline__ void tc_issue_tmem(const TcState& tc)
+{
+    constexpr unsigned idesc = tc_idesc(128, 32);
+    tc_fence_after();
+#pragma unroll
+    for (int g = 0; g < GROUPS; ++g) {
+        const unsigned a = tc.a + 32 * g, d = tc.tmem + 32 * g;
+        tc_mma_ta(d, a, tc_desc(tc.bsm), idesc, 0);                                  // hi * M_hi
+        tc_mma_ta(d, a + 8, tc_desc(tc.bsm + 2 * kTcLbo), idesc, 1);
+        tc_mma_ta(d, a + 16, tc_desc(tc.bsm), idesc, 1);                             // lo * M_hi
+        tc_mma_ta(d, a + 24, tc_desc(tc.bsm + 2 * kTcLbo), idesc, 1);
+        tc_mma_ta(d, a, tc_desc(tc.bsm + 4 * kTcLbo), idesc, 1);                     // hi * M_lo
+        tc_mma_ta(d, a + 8, tc_desc(tc.bsm + 6 * kTcLbo), idesc, 1);
+    }
+    tc_commit(tc.bar);
+}
 
 // Scale, split and store this thread's butterfly as A row `row` of group `grp`
 // (A tiles start at shared address `abase`).  Returns the exponent e of the
 // scale 2^-e applied.
 __device__ __forceinline__ int tc_put_row(const float2 (&v)[16], unsigned abase, int grp, int row)
 {
-    float m = 0.f;
-#pragma unroll
-    for (int r = 0; r < 16; ++r) m = fmaxf(m, fmaxf(fabsf(v[r].x), fabsf(v[r].y)));
-    int e = ((__float_as_int(m) >> 23) & 0xff) - 126;  // m in [2^(e-1), 2^e)
-    e = e < -126 ? -126 : (e > 126 ? 126 : e);
+    const int e = tc_scale_exp(v);
     const float down = __int_as_float((127 - e) << 23);
     const unsigned rowaddr = abase + grp * kTcGroupBytes + (row >> 3) * kTcSbo + (row & 7) * 16;
-    // K order: 0..15 real parts, 16..31 imaginary parts; chunks 0..3 hi, 4..7 lo
+    // chunks 0..3 hi, 4..7 lo (8 halves each)
 #pragma unroll
     for (int c = 0; c < 4; ++c) {
         unsigned hw[4], lw[4];
 #pragma unroll
-        for (int p = 0; p < 4; ++p) {
-            const int k0 = c * 8 + 2 * p;
-            const float a = (k0 < 16 ? v[k0].x : v[k0 - 16].y) * down;
-            const float b = (k0 + 1 < 16 ? v[k0 + 1].x : v[k0 + 1 - 16].y) * down;
-            const __half2 h = __floats2half2_rn(a, b);  // (a, b) -> low, high half
-            const float2 hf = __half22float2(h);
-            const __half2 l = __floats2half2_rn(a - hf.x, b - hf.y);
-            hw[p] = *reinterpret_cast<const unsigned*>(&h);
-            lw[p] = *reinterpret_cast<const unsigned*>(&l);
-        }
+        for (int p = 0; p < 4; ++p) tc_split_pair(v, down, 4 * c + p, hw[p], lw[p]);
         st_shared_v4(rowaddr + c * kTcLbo, hw[0], hw[1], hw[2], hw[3]);
         st_shared_v4(rowaddr + (4 + c) * kTcLbo, lw[0], lw[1], lw[2], lw[3]);
     }
