@@ -304,11 +304,7 @@ int make_line_pass(PassPlan& p, TwiddleBuilder& twb, long long L, long long O, l
     if (nst < 0) return nst;
     if (nst > kMaxStages) return FB_FFT_ERR_UNSUPPORTED_SIZE;
     d.nst = nst;
-    long long Ns = 1;
-    for (int s = 0; s < nst; ++s) {
-        d.ns[s] = (int)Ns;
-        Ns *= d.radix[s];
-    }
+    set_stage_products(d);
     const std::vector<int> off = twb.add_stages(L, d.radix, nst);
     for (int s = 0; s < nst; ++s) d.twoff[s] = off[s];
 

@@ -115,6 +115,7 @@ int fill_pass(Pass& p, StackTwiddles& tw, long long L, long long O, long long C,
         }
         Ns *= d.radix[s];
     }
+    set_stage_products(d);
     const bool pow2 = (L & (L - 1)) == 0;
     const bool cfast = in_t || out_t;
     long long T, land;

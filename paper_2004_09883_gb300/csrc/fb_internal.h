@@ -48,6 +48,7 @@ struct PassDesc {
     int radix[kMaxStages];
     int ns[kMaxStages];    // product of the radices before stage s
     int twoff[kMaxStages]; // element offset of stage s's twiddle table
+    unsigned ns_mag[kMaxStages];  // ceil(2^32 / ns[s]) for ns[s] > 1: j mod ns[s] by one multiply-high
     int in_tfast;          // 1: first stage maps threads across lines (input contiguous across c)
     int out_tfast;         // 1: last stage maps threads across lines (output contiguous across c)
     int ptw;               // 1: multiply output (c, k) by exp(s 2 pi i c k / ptw_n)
@@ -68,6 +69,19 @@ struct PassDesc {
     const long long* off_in;
     const long long* off_out;
 };
+
+// Fill ns[] (product of the earlier radices) and its multiply-high
+// reciprocals from radix[0..nst).  floor(j * ceil(2^32/x) / 2^32) == j / x
+// while j * x < 2^32, which holds for every j < L / radix the kernels use.
+inline void set_stage_products(PassDesc& d)
+{
+    long long Ns = 1;
+    for (int s = 0; s < d.nst; ++s) {
+        d.ns[s] = (int)Ns;
+        d.ns_mag[s] = Ns > 1 ? (unsigned)(((1ULL << 32) + (unsigned long long)Ns - 1) / (unsigned long long)Ns) : 0u;
+        Ns *= d.radix[s];
+    }
+}
 
 // Several passes of one mixed kernel in one launch (batched uneven lengths:
 // every length with the same power-of-two factor).  Job j owns global tiles

@@ -382,59 +382,88 @@ __device__ __forceinline__ void cp_async_wait()
     asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
 }
 
-// Plain-copy fallback (misaligned bases, odd strides): the whole CTA copies.
+// Tile copies by the whole CTA.  Contiguous tiles ([t][n]): THREADS >> logT
+// threads per line (T <= THREADS, both powers of two), consecutive threads on
+// consecutive elements of one line, so a thread finds its line once per tile
+// (one offset-table read) and needs no division.  Strided tiles ([n][t]):
+// consecutive threads on consecutive lines.
+template <int THREADS, bool ASYNC>
+__device__ __forceinline__ void tile_copy_in(const PassDesc& d, const TileIdx& ti, float2* land)
+{
+    const int L = d.L, logT = d.logT, T = 1 << logT;
+    const float2* gin = tile_in_base(d, ti, d.in_tfast != 0);
+    const long long sn = d.in_sn;
+    int t, n, step;
+    float2* dst;
+    const float2* src;
+    int dstep;
+    if (!d.in_tfast) {
+        const int lgt = ilog2(THREADS) - logT;  // log2 threads per line
+        t = threadIdx.x >> lgt;
+        n = threadIdx.x & ((1 << lgt) - 1);
+        step = 1 << lgt;
+        if (t >= ti.Tv) return;
+        src = line_in(d, ti, gin, t) + n * sn;
+        dst = land + t * L + n;
+        dstep = step;
+    } else {
+        t = threadIdx.x & (T - 1);
+        n = threadIdx.x >> logT;
+        step = THREADS >> logT;
+        if (t >= ti.Tv) return;
+        src = gin + n * sn + t;
+        dst = land + (n << logT) + t;
+        dstep = step << logT;
+    }
+    const long long sstep = step * sn;
+    for (; n < L; n += step, src += sstep, dst += dstep) {
+        if constexpr (ASYNC)
+            cp_async8(dst, src);
+        else
+            *dst = *src;
+    }
+}
+// Plain-copy fallback (misaligned bases, odd strides).
 template <int THREADS>
 __device__ __forceinline__ void plain_tile_load(const PassDesc& d, const TileIdx& ti, float2* land)
 {
-    const int L = d.L, T = 1 << d.logT;
-    const float2* gin = tile_in_base(d, ti, d.in_tfast != 0);
-    if (!d.in_tfast) {
-        for (int e = threadIdx.x; e < ti.Tv * L; e += THREADS) {
-            const int t = e / L, n = e - t * L;
-            land[e] = line_in(d, ti, gin, t)[(long long)n * d.in_sn];
-        }
-    } else {
-        for (int e = threadIdx.x; e < T * L; e += THREADS) {
-            const int n = e >> d.logT, t = e & (T - 1);
-            if (t < ti.Tv) land[e] = gin[(long long)n * d.in_sn + t];
-        }
-    }
+    tile_copy_in<THREADS, false>(d, ti, land);
 }
-// The same gather as plain_tile_load, issued as cp.async copies (the caller
-// commits and waits).
+// The same copies issued as cp.async (the caller commits and waits).
 template <int THREADS>
 __device__ __forceinline__ void async_tile_load(const PassDesc& d, const TileIdx& ti, float2* land)
 {
-    const int L = d.L, T = 1 << d.logT;
-    const float2* gin = tile_in_base(d, ti, d.in_tfast != 0);
-    if (!d.in_tfast) {
-        for (int e = threadIdx.x; e < ti.Tv * L; e += THREADS) {
-            const int t = e / L, n = e - t * L;
-            cp_async8(&land[e], line_in(d, ti, gin, t) + (long long)n * d.in_sn);
-        }
-    } else {
-        for (int e = threadIdx.x; e < T * L; e += THREADS) {
-            const int n = e >> d.logT, t = e & (T - 1);
-            if (t < ti.Tv) cp_async8(&land[e], gin + (long long)n * d.in_sn + t);
-        }
-    }
+    tile_copy_in<THREADS, true>(d, ti, land);
 }
 template <int THREADS>
 __device__ __forceinline__ void plain_tile_store(const PassDesc& d, const TileIdx& ti, const float2* land)
 {
-    const int L = d.L, T = 1 << d.logT;
+    const int L = d.L, logT = d.logT, T = 1 << logT;
     float2* gout = tile_out_base(d, ti, d.out_tfast != 0);
+    const long long sk = d.out_sk;
+    int t, k, step, sstep_l;
+    const float2* src;
+    float2* dst;
     if (!d.out_tfast) {
-        for (int e = threadIdx.x; e < ti.Tv * L; e += THREADS) {
-            const int t = e / L, k = e - t * L;
-            line_out(d, ti, gout, t)[(long long)k * d.out_sk] = land[e];
-        }
+        const int lgt = ilog2(THREADS) - logT;
+        t = threadIdx.x >> lgt;
+        k = threadIdx.x & ((1 << lgt) - 1);
+        step = 1 << lgt;
+        if (t >= ti.Tv) return;
+        dst = line_out(d, ti, gout, t) + k * sk;
+        src = land + t * L + k;
+        sstep_l = step;
     } else {
-        for (int e = threadIdx.x; e < T * L; e += THREADS) {
-            const int k = e >> d.logT, t = e & (T - 1);
-            if (t < ti.Tv) gout[(long long)k * d.out_sk + t] = land[e];
-        }
+        t = threadIdx.x & (T - 1);
+        k = threadIdx.x >> logT;
+        step = THREADS >> logT;
+        if (t >= ti.Tv) return;
+        dst = gout + k * sk + t;
+        src = land + (k << logT) + t;
+        sstep_l = step << logT;
     }
+    const long long dstep = step * sk;
+    for (; k < L; k += step, src += sstep_l, dst += dstep) *dst = *src;
 }
 
 // One Stockham stage for the whole tile.  Threads cover butterflies (t, j):
@@ -446,9 +475,10 @@ __device__ __forceinline__ void plain_tile_store(const PassDesc& d, const TileId
 enum StagePos { kPosOnly = 0, kPosFirst = 1, kPosMid = 2, kPosLast = 3 };
 
 template <int R, int THREADS, bool FWD, int POS, int E = kElemsPerThread>
-__device__ __forceinline__ void stage(const PassDesc& d, int Ns, int twoff, float2* land, float2* work, int Tv,
-                                      int c0)
+__device__ __forceinline__ void stage(const PassDesc& d, int st, float2* land, float2* work, int Tv, int c0)
 {
+    const int Ns = d.ns[st], twoff = d.twoff[st];
+    const unsigned nsm = d.ns_mag[st];  // ceil(2^32 / Ns): j mod Ns without a division (Ns > 1)
     constexpr int Q = (E + R - 1) / R;
     constexpr bool first = POS == kPosOnly || POS == kPosFirst;
     constexpr bool last = POS == kPosOnly || POS == kPosLast;
@@ -493,8 +523,8 @@ __device__ __forceinline__ void stage(const PassDesc& d, int Ns, int twoff, floa
     for (int q = 0; q < Q; ++q) {
         const int j = jb + q * G;
         if (tok && j < LR) {
-            const int k = j % Ns;
-            if (!first && Ns > 1) {
+            const int k = first ? 0 : j - (int)__umulhi((unsigned)j, nsm) * Ns;
+            if (!first) {
                 const float2* tw = d.tw + twoff + k;
 #pragma unroll
                 for (int r = 1; r < R; ++r) v[q][r] = twmul<FWD>(v[q][r], __ldg(tw + (r - 1) * Ns));
@@ -529,16 +559,15 @@ __device__ __forceinline__ void stage(const PassDesc& d, int Ns, int twoff, floa
 }
 
 template <int THREADS, bool FWD, int POS, int E>
-__device__ __forceinline__ void run_stage(int R, const PassDesc& d, int Ns, int twoff, float2* land, float2* work,
-                                          int Tv, int c0)
+__device__ __forceinline__ void run_stage(const PassDesc& d, int st, float2* land, float2* work, int Tv, int c0)
 {
-    switch (R) {
-    case 16: stage<16, THREADS, FWD, POS, E>(d, Ns, twoff, land, work, Tv, c0); break;
-    case 8: stage<8, THREADS, FWD, POS, E>(d, Ns, twoff, land, work, Tv, c0); break;
-    case 5: stage<5, THREADS, FWD, POS, E>(d, Ns, twoff, land, work, Tv, c0); break;
-    case 4: stage<4, THREADS, FWD, POS, E>(d, Ns, twoff, land, work, Tv, c0); break;
-    case 3: stage<3, THREADS, FWD, POS, E>(d, Ns, twoff, land, work, Tv, c0); break;
-    default: stage<2, THREADS, FWD, POS, E>(d, Ns, twoff, land, work, Tv, c0); break;
+    switch (d.radix[st]) {
+    case 16: stage<16, THREADS, FWD, POS, E>(d, st, land, work, Tv, c0); break;
+    case 8: stage<8, THREADS, FWD, POS, E>(d, st, land, work, Tv, c0); break;
+    case 5: stage<5, THREADS, FWD, POS, E>(d, st, land, work, Tv, c0); break;
+    case 4: stage<4, THREADS, FWD, POS, E>(d, st, land, work, Tv, c0); break;
+    case 3: stage<3, THREADS, FWD, POS, E>(d, st, land, work, Tv, c0); break;
+    default: stage<2, THREADS, FWD, POS, E>(d, st, land, work, Tv, c0); break;
     }
 }
 
@@ -618,9 +647,9 @@ __global__ void __launch_bounds__(THREADS, 1) k_fft_generic(const __grid_constan
             __syncthreads();
         }
         if (d.nst == 1)
-            run_stage<THREADS, FWD, kPosOnly, kGenericElems>(d.radix[0], d, 1, 0, land, work, ti.Tv, c0);
+            run_stage<THREADS, FWD, kPosOnly, kGenericElems>(d, 0, land, work, ti.Tv, c0);
         else
-            run_stage<THREADS, FWD, kPosFirst, kGenericElems>(d.radix[0], d, 1, 0, land, work, ti.Tv, c0);
+            run_stage<THREADS, FWD, kPosFirst, kGenericElems>(d, 0, land, work, ti.Tv, c0);
         if (async && d.nst == 1) fence_proxy_async();
         __syncthreads();
         // The previous tile's store has had a stage to drain: recycle its
@@ -631,11 +660,9 @@ __global__ void __launch_bounds__(THREADS, 1) k_fft_generic(const __grid_constan
         }
         for (int s = 1; s < d.nst; ++s) {
             if (s == d.nst - 1)
-                run_stage<THREADS, FWD, kPosLast, kGenericElems>(d.radix[s], d, d.ns[s], d.twoff[s], land, work,
-                                                                 ti.Tv, c0);
+                run_stage<THREADS, FWD, kPosLast, kGenericElems>(d, s, land, work, ti.Tv, c0);
             else
-                run_stage<THREADS, FWD, kPosMid, kGenericElems>(d.radix[s], d, d.ns[s], d.twoff[s], land, work,
-                                                                ti.Tv, c0);
+                run_stage<THREADS, FWD, kPosMid, kGenericElems>(d, s, land, work, ti.Tv, c0);
             if (async && s == d.nst - 1) fence_proxy_async();
             __syncthreads();
         }
@@ -651,13 +678,12 @@ __global__ void __launch_bounds__(THREADS, 1) k_fft_generic(const __grid_constan
 
 // Run-time dispatch over the odd radices only (5, 3).
 template <int THREADS, bool FWD, int POS, int E>
-__device__ __forceinline__ void run_odd_stage(int R, const PassDesc& d, int Ns, int twoff, float2* land, float2* work,
-                                              int Tv, int c0)
+__device__ __forceinline__ void run_odd_stage(const PassDesc& d, int st, float2* land, float2* work, int Tv, int c0)
 {
-    if (R == 5)
-        stage<5, THREADS, FWD, POS, E>(d, Ns, twoff, land, work, Tv, c0);
+    if (d.radix[st] == 5)
+        stage<5, THREADS, FWD, POS, E>(d, st, land, work, Tv, c0);
     else
-        stage<3, THREADS, FWD, POS, E>(d, Ns, twoff, land, work, Tv, c0);
+        stage<3, THREADS, FWD, POS, E>(d, st, land, work, Tv, c0);
 }
 // Compile-time power-of-two prefix of a mixed schedule (stage S < pow2_nst(LG2)).
 template <int THREADS, bool FWD, int LG2, int S, int E>
@@ -665,10 +691,7 @@ __device__ __forceinline__ void mixed_p2_stages(const PassDesc& d, float2* land,
 {
     if constexpr (S < pow2_nst(LG2)) {
         constexpr int R = pow2_radix(LG2, S);
-        if constexpr (S == 0)
-            stage<R, THREADS, FWD, kPosFirst, E>(d, 1, 0, land, work, Tv, c0);
-        else
-            stage<R, THREADS, FWD, kPosMid, E>(d, d.ns[S], d.twoff[S], land, work, Tv, c0);
+        stage<R, THREADS, FWD, S == 0 ? kPosFirst : kPosMid, E>(d, S, land, work, Tv, c0);
         __syncthreads();
         mixed_p2_stages<THREADS, FWD, LG2, S + 1, E>(d, land, work, Tv, c0);
     }
@@ -732,9 +755,9 @@ __global__ void __launch_bounds__(THREADS, 1) k_fft_mixed(const __grid_constant_
             mixed_p2_stages<THREADS, FWD, LG2, 0, E>(d, land, work, ti.Tv, c0);
         } else {
             if (d.nst == 1)
-                run_odd_stage<THREADS, FWD, kPosOnly, E>(d.radix[0], d, 1, 0, land, work, ti.Tv, c0);
+                run_odd_stage<THREADS, FWD, kPosOnly, E>(d, 0, land, work, ti.Tv, c0);
             else
-                run_odd_stage<THREADS, FWD, kPosFirst, E>(d.radix[0], d, 1, 0, land, work, ti.Tv, c0);
+                run_odd_stage<THREADS, FWD, kPosFirst, E>(d, 0, land, work, ti.Tv, c0);
             if (async && d.nst == 1) fence_proxy_async();
             __syncthreads();
             s0 = 1;
@@ -745,9 +768,9 @@ __global__ void __launch_bounds__(THREADS, 1) k_fft_mixed(const __grid_constant_
         }
         for (int s = s0; s < d.nst; ++s) {
             if (s == d.nst - 1)
-                run_odd_stage<THREADS, FWD, kPosLast, E>(d.radix[s], d, d.ns[s], d.twoff[s], land, work, ti.Tv, c0);
+                run_odd_stage<THREADS, FWD, kPosLast, E>(d, s, land, work, ti.Tv, c0);
             else
-                run_odd_stage<THREADS, FWD, kPosMid, E>(d.radix[s], d, d.ns[s], d.twoff[s], land, work, ti.Tv, c0);
+                run_odd_stage<THREADS, FWD, kPosMid, E>(d, s, land, work, ti.Tv, c0);
             if (async && s == d.nst - 1) fence_proxy_async();
             __syncthreads();
         }
@@ -823,17 +846,17 @@ __global__ void __launch_bounds__(THREADS, (LG2 <= 4 ? 2 : 1)) k_fft_mixed_multi
             mixed_p2_stages<THREADS, FWD, LG2, 0, E>(d, land, work, ti.Tv, c0);
         } else {
             if (d.nst == 1)
-                run_odd_stage<THREADS, FWD, kPosOnly, E>(d.radix[0], d, 1, 0, land, work, ti.Tv, c0);
+                run_odd_stage<THREADS, FWD, kPosOnly, E>(d, 0, land, work, ti.Tv, c0);
             else
-                run_odd_stage<THREADS, FWD, kPosFirst, E>(d.radix[0], d, 1, 0, land, work, ti.Tv, c0);
+                run_odd_stage<THREADS, FWD, kPosFirst, E>(d, 0, land, work, ti.Tv, c0);
             __syncthreads();
             s0 = 1;
         }
         for (int s = s0; s < d.nst; ++s) {
             if (s == d.nst - 1)
-                run_odd_stage<THREADS, FWD, kPosLast, E>(d.radix[s], d, d.ns[s], d.twoff[s], land, work, ti.Tv, c0);
+                run_odd_stage<THREADS, FWD, kPosLast, E>(d, s, land, work, ti.Tv, c0);
             else
-                run_odd_stage<THREADS, FWD, kPosMid, E>(d.radix[s], d, d.ns[s], d.twoff[s], land, work, ti.Tv, c0);
+                run_odd_stage<THREADS, FWD, kPosMid, E>(d, s, land, work, ti.Tv, c0);
             __syncthreads();
         }
         plain_tile_store<THREADS>(d, ti, land);
