@@ -225,12 +225,13 @@ struct TwiddleBuilder {
         total += (count + 1) & ~1LL;  // keep every table 16-byte aligned
         return off;
     }
-    // Stage tables of length L; returns offsets per stage.
+    // Stage tables of length L; returns offsets per stage, then (entry nst)
+    // the 16 x 15 factor table of a split last stage (p2_tw_split), else 0.
     std::vector<int> add_stages(long long L, const int* radix, int nst)
     {
         for (auto& e : stage_cache)
             if (e.first == L) return e.second;
-        std::vector<int> off(nst, 0);
+        std::vector<int> off(nst + 1, 0);
         long long Ns = 1;
         for (int s = 0; s < nst; ++s) {
             const long long cnt = Ns * (radix[s] - 1);
@@ -241,6 +242,11 @@ struct TwiddleBuilder {
                 total += (cnt + 1) & ~1LL;
             }
             Ns *= radix[s];
+        }
+        if ((L & (L - 1)) == 0 && p2_tw_split(ilog2ll(L))) {
+            jobs.push_back(TwiddleJob{total, 16 * 15, L, 0, 1, 16, 16});  // w_L^{r k}, k < 16, r = 1..15
+            off[nst] = (int)total;
+            total += 16 * 15;
         }
         stage_cache.emplace_back(L, off);
         return off;
@@ -306,7 +312,7 @@ int make_line_pass(PassPlan& p, TwiddleBuilder& twb, long long L, long long O, l
     d.nst = nst;
     set_stage_products(d);
     const std::vector<int> off = twb.add_stages(L, d.radix, nst);
-    for (int s = 0; s < nst; ++s) d.twoff[s] = off[s];
+    for (int s = 0; s <= nst && s < kMaxStages; ++s) d.twoff[s] = off[s];
 
     const bool cfast = in_tfast || out_tfast;
     const bool pow2 = (L & (L - 1)) == 0;

@@ -115,6 +115,14 @@ int fill_pass(Pass& p, StackTwiddles& tw, long long L, long long O, long long C,
         }
         Ns *= d.radix[s];
     }
+    if ((L & (L - 1)) == 0) {
+        int lg = 0;
+        while ((1LL << lg) < L) ++lg;
+        if (p2_tw_split(lg)) {  // the 16 x 15 factor table of the split last stage
+            d.twoff[nst] = (int)tw.total;
+            if (!tw.add(TwiddleJob{tw.total, 16 * 15, L, 0, 1, 16, 16})) return FB_FFT_ERR_UNSUPPORTED_SIZE;
+        }
+    }
     set_stage_products(d);
     const bool pow2 = (L & (L - 1)) == 0;
     const bool cfast = in_t || out_t;

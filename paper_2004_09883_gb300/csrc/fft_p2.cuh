@@ -44,10 +44,22 @@ __host__ __device__ constexpr int p2_row_pad(int threads, int lg, int io, bool o
     const bool strided = out_side ? io_out_strided(io) : io_in_strided(io);
     return (!strided && G < 16) ? (G >= 2 ? G : 2) : 0;
 }
+// Three-stage schedules whose last two radices are 16 (L = 2048, 4096) have
+// a last-stage table of L - L/16 entries, too many for shared memory.  With
+// k = 16 kh + kl (kh < Ns of the middle stage), that stage's twiddle factors:
+//   w_L^{k r} = w_{L/16}^{kh r} * w_L^{kl r},
+// the first factor an entry of the middle stage's table, the second of a
+// 16 x 15 table of its own (offset twoff[NST]).
+__host__ __device__ constexpr bool p2_tw_split(int lg)
+{
+    return pow2_nst(lg) == 3 && pow2_radix(lg, 1) == 16 && pow2_radix(lg, 2) == 16 &&
+           pow2_ns(lg, 1) * 15 + pow2_ns(lg, 2) * 15 > 1024;
+}
 // Stage twiddle tables (stages 1..NST-1) small enough to copy into shared
 // memory once per CTA: their total entry count, or 0 when they stay in global.
 __host__ __device__ constexpr int p2_smem_twiddles(int lg)
 {
+    if (p2_tw_split(lg)) return pow2_ns(lg, 1) * 15 + 16 * 15;
     int total = 0;
     for (int s = 1; s < pow2_nst(lg); ++s) total += pow2_ns(lg, s) * (pow2_radix(lg, s) - 1);
     return total <= 1024 ? total : 0;
@@ -185,7 +197,14 @@ __device__ __forceinline__ void p2_stage(const PassDesc& d, float2* land, float2
         if (tok && ((q + 1) * G <= LR || j < LR)) {
             const int k = j & (NS - 1);
             if constexpr (NS > 1) {
-                if constexpr (C::TWS > 0) {
+                if constexpr (p2_tw_split(LG) && S == 2) {
+                    constexpr int NS1 = pow2_ns(LG, 1);
+                    const float2* th = tws + p2_tws_off(LG, 1) + (k >> 4);  // w_{L/16}^{kh r}
+                    const float2* tl = tws + p2_tws_off(LG, 2) + (k & 15);  // w_L^{kl r}
+#pragma unroll
+                    for (int r = 1; r < R; ++r)
+                        v[q][r] = twmul<FWD>(v[q][r], cmul(th[(r - 1) * NS1], tl[(r - 1) * 16]));
+                } else if constexpr (C::TWS > 0) {
                     const float2* tw = tws + p2_tws_off(LG, S) + k;
 #pragma unroll
                     for (int r = 1; r < R; ++r) v[q][r] = twmul<FWD>(v[q][r], tw[(r - 1) * NS]);
@@ -355,8 +374,9 @@ template <int THREADS, int LG, int S>
 __device__ __forceinline__ void p2_copy_twiddles(const PassDesc& d, float2* tws)
 {
     if constexpr (S < pow2_nst(LG)) {
-        constexpr int n = pow2_ns(LG, S) * (pow2_radix(LG, S) - 1);
-        const float2* src = d.tw + d.twoff[S];
+        constexpr bool lo = p2_tw_split(LG) && S == 2;  // the 16 x 15 factor table instead
+        constexpr int n = lo ? 16 * 15 : pow2_ns(LG, S) * (pow2_radix(LG, S) - 1);
+        const float2* src = d.tw + d.twoff[lo ? 3 : S];
         for (int e = threadIdx.x; e < n; e += THREADS) tws[p2_tws_off(LG, S) + e] = __ldg(src + e);
         p2_copy_twiddles<THREADS, LG, S + 1>(d, tws);
     }

@@ -17,7 +17,7 @@ __global__ void k_twiddles(float2* __restrict__ tw, TwiddleJob job)
     } else {
         const long long r = i / job.Ns + 1;
         const long long k = i % job.Ns;
-        D = (long long)job.Ns * job.R;
+        D = job.D > 0 ? job.D : (long long)job.Ns * job.R;  // D set: w_D^{r k} (a split factor table)
         m = (r * k) % D;
     }
     double s, c;
