@@ -127,6 +127,7 @@ struct MultiLaunch {
     long long tiles = 0;
     long long grid = 0;
     int land_max = 0;
+    int work_max = 0;
     size_t smem = 0;
 };
 
@@ -624,7 +625,8 @@ int schedule_many(fb_fft_plan_s* p, TwiddleBuilder& twb)
                     m.land_max = std::max(m.land_max, q.d.land_stride);
                     work_max = std::max(work_max, ((long long)q.d.L + (q.d.L >> 4) + 16) << q.d.logT);
                 }
-                m.smem = 256 + (size_t)(2LL * m.land_max + work_max) * sizeof(float2);
+                m.work_max = (int)((work_max + 15) & ~15LL);
+                m.smem = 256 + (size_t)(2LL * m.land_max + 2LL * m.work_max) * sizeof(float2);
                 p->multis.push_back(m);
             }
         }
@@ -948,6 +950,7 @@ int launch_multi(fb_fft_plan_s* p, const MultiLaunch& m, const float2* in, float
     MultiArgs& a = *p->margs;
     a.njobs = (int)m.members.size();
     a.land_max = m.land_max;
+    a.work_max = m.work_max;
     a.tile_start[0] = 0;
     for (int k = 0; k < a.njobs; ++k) {
         const PassPlan& q = p->passes[m.members[k]];

@@ -93,7 +93,8 @@ constexpr int kMultiMax = 64;
 struct MultiArgs {
     long long tile_start[kMultiMax + 1];
     int njobs;
-    int land_max;  // elements of the landing buffer; the work buffer follows it
+    int land_max;  // elements of a landing buffer; two of them, then two work buffers
+    int work_max;  // elements of a work buffer
     PassDesc d[kMultiMax];
 };
 cudaError_t mixed_multi_launch(bool forward, int lg2, const MultiArgs& a, long long grid, size_t smem,

@@ -473,21 +473,40 @@ __device__ __forceinline__ void plain_tile_store(const PassDesc& d, const TileId
 // (with the four-step twiddle and the 1/N scale applied), the stages between
 // work in place on the padded work buffer.
 enum StagePos { kPosOnly = 0, kPosFirst = 1, kPosMid = 2, kPosLast = 3 };
+__host__ __device__ constexpr bool last_pos(int pos) { return pos == kPosOnly || pos == kPosLast; }
 
-template <int R, int THREADS, bool FWD, int POS, int E = kElemsPerThread>
-__device__ __forceinline__ void stage(const PassDesc& d, int st, float2* land, float2* work, int Tv, int c0)
+template <int R, int THREADS, bool FWD, int POS, int E = kElemsPerThread, bool PP = false>
+__device__ __forceinline__ void stage(const PassDesc& d, int st, float2* land, float2* work, int Tv, int c0,
+                                      float2* work2 = nullptr)
 {
-    const int Ns = d.ns[st], twoff = d.twoff[st];
+    // PP: two work buffers; stage st writes buffer st & 1 and reads the other,
+    // so a middle stage needs no barrier between its reads and its writes.
+    float2* wr = work;
+    const float2* rd = work;
+    if constexpr (PP) {
+        wr = (st & 1) ? work2 : work;
+        rd = (st & 1) ? work : work2;
+    }
+    // Every descriptor field is read here, before the stage stores anything:
+    // the descriptor may sit in shared memory, and a later read would have to
+    // be repeated after each store to the tile buffers.
+    const int Ns = d.ns[st];
     const unsigned nsm = d.ns_mag[st];  // ceil(2^32 / Ns): j mod Ns without a division (Ns > 1)
+    const float2* twb = d.tw + d.twoff[st];
+    const int logT = d.logT, L = d.L, LS = d.LS;
+    const bool in_tf = d.in_tfast != 0, out_tf = d.out_tfast != 0;
+    const bool ptw = last_pos(POS) && d.ptw != 0;
+    const int ptw_log = d.ptw_log;
+    const float2* ptw_hi = d.ptw_hi;
+    const float2* ptw_lo = d.ptw_lo;
+    const float scale = (last_pos(POS) && d.apply_scale) ? d.scale : 1.0f;
     constexpr int Q = (E + R - 1) / R;
     constexpr bool first = POS == kPosOnly || POS == kPosFirst;
     constexpr bool last = POS == kPosOnly || POS == kPosLast;
-    const bool tfast = (first && d.in_tfast) || (last && d.out_tfast);
+    const bool tfast = (first && in_tf) || (last && out_tf);
     const int tid = threadIdx.x;
-    const int logT = d.logT;
     const int T = 1 << logT;
     const int G = THREADS >> logT;  // threads per line
-    const int L = d.L;
     const int LR = L / R;
     int t, jb;
     if (tfast) {
@@ -504,7 +523,7 @@ __device__ __forceinline__ void stage(const PassDesc& d, int st, float2* land, f
         const int j = jb + q * G;
         if (tok && j < LR) {
             if constexpr (first) {
-                if (d.in_tfast) {
+                if (in_tf) {
 #pragma unroll
                     for (int r = 0; r < R; ++r) v[q][r] = land[((j + r * LR) << logT) + t];
                 } else {
@@ -512,27 +531,27 @@ __device__ __forceinline__ void stage(const PassDesc& d, int st, float2* land, f
                     for (int r = 0; r < R; ++r) v[q][r] = land[t * L + j + r * LR];
                 }
             } else {
-                const float2* p = work + t * d.LS;
+                const float2* p = rd + t * LS;
 #pragma unroll
                 for (int r = 0; r < R; ++r) v[q][r] = p[spad(j + r * LR)];
             }
         }
     }
-    if constexpr (first == last) __syncthreads();  // reads and writes share one buffer
+    if constexpr (first == last && (!PP || first)) __syncthreads();  // reads and writes share one buffer
 #pragma unroll
     for (int q = 0; q < Q; ++q) {
         const int j = jb + q * G;
         if (tok && j < LR) {
             const int k = first ? 0 : j - (int)__umulhi((unsigned)j, nsm) * Ns;
             if (!first) {
-                const float2* tw = d.tw + twoff + k;
+                const float2* tw = twb + k;
 #pragma unroll
                 for (int r = 1; r < R; ++r) v[q][r] = twmul<FWD>(v[q][r], __ldg(tw + (r - 1) * Ns));
             }
             dft<R, FWD>(v[q]);
             const int base = (j - k) * R + k;
             if constexpr (!last) {
-                float2* p = work + t * d.LS;
+                float2* p = wr + t * LS;
 #pragma unroll
                 for (int r = 0; r < R; ++r) p[spad(base + r * Ns)] = v[q][r];
             } else {
@@ -541,14 +560,13 @@ __device__ __forceinline__ void stage(const PassDesc& d, int st, float2* land, f
                 for (int r = 0; r < R; ++r) {
                     const int kk = base + r * Ns;
                     float2 y = v[q][r];
-                    if (d.ptw) {
+                    if (ptw) {
                         const unsigned m = c * (unsigned)kk;  // < N < 2^31
-                        const float2 w = cmul(__ldg(d.ptw_hi + (m >> d.ptw_log)),
-                                              __ldg(d.ptw_lo + (m & ((1u << d.ptw_log) - 1))));
+                        const float2 w = cmul(__ldg(ptw_hi + (m >> ptw_log)), __ldg(ptw_lo + (m & ((1u << ptw_log) - 1))));
                         y = twmul<FWD>(y, w);
                     }
-                    if (d.apply_scale) y = d.scale * y;
-                    if (d.out_tfast)
+                    y = scale * y;
+                    if (out_tf)
                         land[(kk << logT) + t] = y;
                     else
                         land[t * L + kk] = y;
@@ -677,23 +695,25 @@ __global__ void __launch_bounds__(THREADS, 1) k_fft_generic(const __grid_constan
 }
 
 // Run-time dispatch over the odd radices only (5, 3).
-template <int THREADS, bool FWD, int POS, int E>
-__device__ __forceinline__ void run_odd_stage(const PassDesc& d, int st, float2* land, float2* work, int Tv, int c0)
+template <int THREADS, bool FWD, int POS, int E, bool PP = false>
+__device__ __forceinline__ void run_odd_stage(const PassDesc& d, int st, float2* land, float2* work, int Tv, int c0,
+                                              float2* work2 = nullptr)
 {
     if (d.radix[st] == 5)
-        stage<5, THREADS, FWD, POS, E>(d, st, land, work, Tv, c0);
+        stage<5, THREADS, FWD, POS, E, PP>(d, st, land, work, Tv, c0, work2);
     else
-        stage<3, THREADS, FWD, POS, E>(d, st, land, work, Tv, c0);
+        stage<3, THREADS, FWD, POS, E, PP>(d, st, land, work, Tv, c0, work2);
 }
 // Compile-time power-of-two prefix of a mixed schedule (stage S < pow2_nst(LG2)).
-template <int THREADS, bool FWD, int LG2, int S, int E>
-__device__ __forceinline__ void mixed_p2_stages(const PassDesc& d, float2* land, float2* work, int Tv, int c0)
+template <int THREADS, bool FWD, int LG2, int S, int E, bool PP = false>
+__device__ __forceinline__ void mixed_p2_stages(const PassDesc& d, float2* land, float2* work, int Tv, int c0,
+                                                float2* work2 = nullptr)
 {
     if constexpr (S < pow2_nst(LG2)) {
         constexpr int R = pow2_radix(LG2, S);
-        stage<R, THREADS, FWD, S == 0 ? kPosFirst : kPosMid, E>(d, S, land, work, Tv, c0);
+        stage<R, THREADS, FWD, S == 0 ? kPosFirst : kPosMid, E, PP>(d, S, land, work, Tv, c0, work2);
         __syncthreads();
-        mixed_p2_stages<THREADS, FWD, LG2, S + 1, E>(d, land, work, Tv, c0);
+        mixed_p2_stages<THREADS, FWD, LG2, S + 1, E, PP>(d, land, work, Tv, c0, work2);
     }
 }
 
@@ -793,6 +813,7 @@ __global__ void __launch_bounds__(THREADS, 1) k_fft_mixed(const __grid_constant_
 // through the prefix table (tiles only grow).  Two landing buffers, each with
 // its tile's descriptor in shared memory: while tile i is transformed, every
 // thread's cp.async copies bring tile i+1 through its job's offset table.
+// Two work buffers: the stages alternate between them (one barrier per stage).
 template <int THREADS, bool FWD, int LG2>
 __global__ void __launch_bounds__(THREADS, (LG2 <= 4 ? 2 : 1)) k_fft_mixed_multi(const __grid_constant__ MultiArgs a)
 {
@@ -800,6 +821,7 @@ __global__ void __launch_bounds__(THREADS, (LG2 <= 4 ? 2 : 1)) k_fft_mixed_multi
     unsigned char* smem_raw = smem_dyn + ((128u - (smem_u32(smem_dyn) & 127u)) & 127u);
     float2* land0 = reinterpret_cast<float2*>(smem_raw + 128);
     float2* work = land0 + 2 * a.land_max;
+    float2* work2 = work + a.work_max;  // second work buffer: middle stages alternate
     __shared__ PassDesc sd[2];  // sd[b]: descriptor of the tile in landing buffer b
     constexpr int E = kMixedElems;
     constexpr int NP2 = pow2_nst(LG2);
@@ -843,20 +865,20 @@ __global__ void __launch_bounds__(THREADS, (LG2 <= 4 ? 2 : 1)) k_fft_mixed_multi
         const int c0 = (int)ti.c0;
         int s0 = NP2;
         if constexpr (NP2 > 0) {
-            mixed_p2_stages<THREADS, FWD, LG2, 0, E>(d, land, work, ti.Tv, c0);
+            mixed_p2_stages<THREADS, FWD, LG2, 0, E, true>(d, land, work, ti.Tv, c0, work2);
         } else {
             if (d.nst == 1)
-                run_odd_stage<THREADS, FWD, kPosOnly, E>(d, 0, land, work, ti.Tv, c0);
+                run_odd_stage<THREADS, FWD, kPosOnly, E, true>(d, 0, land, work, ti.Tv, c0, work2);
             else
-                run_odd_stage<THREADS, FWD, kPosFirst, E>(d, 0, land, work, ti.Tv, c0);
+                run_odd_stage<THREADS, FWD, kPosFirst, E, true>(d, 0, land, work, ti.Tv, c0, work2);
             __syncthreads();
             s0 = 1;
         }
         for (int s = s0; s < d.nst; ++s) {
             if (s == d.nst - 1)
-                run_odd_stage<THREADS, FWD, kPosLast, E>(d, s, land, work, ti.Tv, c0);
+                run_odd_stage<THREADS, FWD, kPosLast, E, true>(d, s, land, work, ti.Tv, c0, work2);
             else
-                run_odd_stage<THREADS, FWD, kPosMid, E>(d, s, land, work, ti.Tv, c0);
+                run_odd_stage<THREADS, FWD, kPosMid, E, true>(d, s, land, work, ti.Tv, c0, work2);
             __syncthreads();
         }
         plain_tile_store<THREADS>(d, ti, land);
