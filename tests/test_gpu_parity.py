@@ -104,12 +104,21 @@ def test_1d_in_place_and_scaled_inverse(fb, n):
 # 1-D four-step (two passes through the plan's scratch)
 # --------------------------------------------------------------------------
 @pytest.mark.parametrize("n,batch", [(8192, 3), (65536, 2), (3 * 5 ** 7, 1), (1 << 20, 2),
-                                     (6000, 5), (2 * 3 ** 9, 1), (1 << 22, 1)])
+                                     (6000, 5), (2 * 3 ** 9, 1), (1 << 22, 1), (1 << 23, 1)])
 @pytest.mark.parametrize("direction", [-1, 1])
 def test_1d_fourstep(fb, n, batch, direction):
     x = inputs.normal_c64((batch, n), 3 + n)
     y = gpu_fft(fb, x, [n], direction)
     assert_close(y, ref_fft(x, [n], direction), [n])
+
+
+def test_fourstep_largest_length(fb):
+    """FB_FFT_MAX_1D_LEN = 4096 x 4096: both passes take 4096-point lines
+    (columns strided with the post-twiddle fused, rows transposed out)."""
+    n = 1 << 24
+    x = inputs.normal_c64((1, n), 24)
+    y = gpu_fft(fb, x, [n], -1)
+    assert_close(y, ref_fft(x, [n], -1), [n])
 
 
 def test_fourstep_in_place_one_chunk(fb):
@@ -140,7 +149,8 @@ def test_fourstep_batch_in_several_chunks(fb):
 # --------------------------------------------------------------------------
 @pytest.mark.parametrize("dims,batch", [([16, 12], 3), ([256, 256], 2), ([512, 512], 1), ([100, 30], 4),
                                         ([8, 8, 8], 5), ([30, 20, 12], 2), ([128, 128, 128], 1),
-                                        ([6, 250, 18], 1), ([3, 5, 4096], 1), ([4096, 2, 3], 1)])
+                                        ([6, 250, 18], 1), ([3, 5, 4096], 1), ([4096, 2, 3], 1),
+                                        ([2048, 3, 5], 1), ([5, 2048], 2)])
 @pytest.mark.parametrize("direction", [-1, 1])
 def test_multi_d(fb, dims, batch, direction):
     x = inputs.uniform_c64([batch] + dims, 21)
