@@ -1,0 +1,30 @@
+"""Index arithmetic of the line-pass kernels, compiled for the host from the
+kernels' own headers: j mod Ns by multiply-high reciprocals (exact for every
+case the kernels meet), and the split last-stage twiddle tables of the 2048-
+and 4096-point schedules (their products equal exp(-2 pi i k r / L))."""
+import os
+import shutil
+import subprocess
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def test_index_arithmetic(tmp_path):
+    nvcc = shutil.which("nvcc") or "/usr/local/cuda/bin/nvcc"
+    if not os.path.exists(nvcc):
+        pytest.skip("nvcc not available")
+    exe = tmp_path / "idx"
+    subprocess.run([nvcc, "-std=c++17", "-O2", "-gencode", "arch=compute_103a,code=sm_103a",
+                    f"-I{ROOT}/include", f"-I{ROOT}/paper_2004_09883_gb300/csrc",
+                    os.path.join(ROOT, "tests", "index_host.cu"), "-o", str(exe)], check=True)
+    lines = subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split("\n")
+    rows = {ln.split()[0]: ln.split()[1:] for ln in lines if ln}
+    cases, bad = map(int, rows["mod_by_reciprocal"])
+    assert cases > 100_000 and bad == 0
+    # 2048 and 4096 points split their last stage; 512 and 1024 keep one table
+    assert rows["split_lg9"][0] == "none" and rows["split_lg10"][0] == "none"
+    for lg in (11, 12):
+        n, worst, sizes_ok = rows[f"split_lg{lg}"]
+        assert int(n) == (1 << lg) // 16 * 15 and float(worst) < 1e-13 and sizes_ok == "1"
