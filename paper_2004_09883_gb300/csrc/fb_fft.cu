@@ -101,7 +101,9 @@ struct PassPlan {
     int threads;  // CTA size of the chosen kernel
     int lg;       // log2(L) for a compile-time power-of-two kernel, 0 = generic kernel
     int io;       // IoMode of the power-of-two kernel
-    int kind;     // 0 power-of-two kernel, 1 generic kernel, 2 mixed kernel (lg = log2 of the 2-factor)
+    int kind;     // 0 power-of-two kernel, 1 generic kernel, 2 mixed kernel (lg = log2 of the 2-factor),
+                  // 3 plane pass (two trailing axes, lg1 = log2 rows, lg = log2 row length)
+    int lg1 = 0;
     long long grid;
     size_t smem;
     bool async_ok;  // tiles can move by TMA (given 16-byte aligned buffer bases)
@@ -258,6 +260,7 @@ struct TwiddleBuilder {
 LineKernel pass_kernel(const PassPlan& q, bool fwd)
 {
     if (q.tc) return line_kernel_p2tc(q.threads, fwd, q.lg, q.io);
+    if (q.kind == 3) return line_kernel_plane(fwd, q.lg1, q.lg, q.threads);
     if (q.kind == 2) return line_kernel_mixed(fwd, q.lg);
     if (q.kind == 1) return line_kernel_generic(fwd);
     return line_kernel_p2(q.threads, fwd, q.lg, q.io);
@@ -269,12 +272,14 @@ size_t pass_smem(const PassPlan& q, bool async)
 {
     const size_t ptw = q.d.ptw_smem ? (size_t)((1LL << q.d.ptw_log) + q.d.ptw_hi_cnt) * sizeof(float2) : 0;
     if (q.kind == 0) return (size_t)p2_smem_bytes(q.threads, q.lg, q.io, async, q.tc) + ptw;
+    if (q.kind == 3) return (size_t)plane_smem_bytes(q.lg1, q.lg, q.threads);
     return line_smem_bytes(q.d.land_stride, q.d.L, 1 << q.d.logT, q.d.nst, async, q.d.tws);
 }
 
 // Resident CTAs per SM of a pass (shared memory and the 96-register cap).
 int pass_ctas_per_sm(const PassPlan& q, size_t smem)
 {
+    if (q.kind == 3) return 1;  // plane pass: one CTA per SM
     const int by_smem = (int)(233472 / (smem + 1024));  // 228 KB per SM, 1 KB reserved per CTA
     const int by_regs = q.kind == 0 ? 65536 / ((q.threads + p2_producer_threads(q.lg)) * p2_launch_regs(q.threads, q.lg))
                                     : 65536 / ((q.threads + 32) * 96);
@@ -392,6 +397,45 @@ int make_line_pass(PassPlan& p, TwiddleBuilder& twb, long long L, long long O, l
     return FB_FFT_OK;
 }
 
+// Plane pass: the 2-D DFT over `planes` contiguous planes of L1 rows x L2
+// values (the two trailing axes of a multi-D transform, one cluster per plane).
+int make_plane_pass(PassPlan& p, TwiddleBuilder& twb, long long L1, long long L2, long long planes)
+{
+    p = PassPlan{};
+    PassDesc& d = p.d;
+    p.kind = 3;
+    p.io = -1;
+    p.lg = ilog2ll(L2);
+    p.lg1 = ilog2ll(L1);
+    // compute threads per CTA: FB_FFT_PLANE_THREADS = 256 or 512 picks one
+    // where both are compiled
+    p.threads = 512;
+    if (const char* s = std::getenv("FB_FFT_PLANE_THREADS"))
+        if (std::atoi(s) == 256 && line_kernel_plane(true, p.lg1, p.lg, 256).fn) p.threads = 256;
+    const LineKernel k = line_kernel_plane(true, p.lg1, p.lg, p.threads);
+    if (!k.fn || (L1 & (L1 - 1)) || (L2 & (L2 - 1))) return FB_FFT_ERR_UNSUPPORTED_SIZE;
+    // second-stage tables of the two-stage schedules (radix 16, then L / 16),
+    // the same the line passes of these lengths use: [0] rows, [1] columns
+    for (int side = 0; side < 2; ++side) {
+        const long long L = side == 0 ? L2 : L1;
+        int radix[kMaxStages];
+        const int nst = factorize(L, radix, kMaxStages);
+        if (nst != 2 || radix[0] != 16 || radix[1] != L / 16) return FB_FFT_ERR_UNSUPPORTED_SIZE;
+        d.twoff[side] = twb.add_stages(L, radix, nst)[1];
+    }
+    d.L = (int)L2;
+    d.in_sn = L2, d.in_so = L1 * L2;
+    d.out_sk = L2, d.out_so = L1 * L2;
+    d.C = L2;
+    d.tiles_per_o = 1;
+    d.ntiles = planes;
+    d.scale = 1.0f;
+    p.async_ok = planes < (1LL << 31);
+    p.smem = (size_t)plane_smem_bytes(p.lg1, p.lg, p.threads);
+    p.grid = planes * k.cluster;  // capped to the clusters that fit when the plan is built
+    return FB_FFT_OK;
+}
+
 }  // namespace
 
 struct fb_fft_plan_s {
@@ -415,6 +459,7 @@ struct fb_fft_plan_s {
     int* err = nullptr;  // device error word written by bounded waits
     long long smem_len_max = 0;
     bool debug_timeout = false;  // test hook: make every TMA wait run out
+    bool no_plane = false;       // plane passes disabled (their cluster does not fit this GPU)
     // batched uneven lengths (fb_fft_plan_many)
     bool many = false;
     long long total = 0;                 // elements of the packed layout
@@ -684,6 +729,23 @@ int check_schedule(const fb_fft_plan_s* p)
     return FB_FFT_OK;
 }
 
+// Rank-2/3 plans: run the two trailing axes as one plane pass when
+// FB_FFT_PLANE=1 and the plane shape is compiled (128 or 256 by 128 or 256).
+// Off by default: on the 256 x 256 x 128 volume the plane pass takes 68 us
+// where the two line passes it replaces take 47 us (its cluster-wide phases
+// leave one CTA per SM waiting at every barrier).
+bool use_plane_pass(const fb_fft_plan_s* p)
+{
+    if (p->rank < 2 || p->no_plane || (p->flags & FB_FFT_TENSOR_CORES)) return false;
+    const long long L1 = p->dims[p->rank - 2], L2 = p->dims[p->rank - 1];
+    if (!line_kernel_plane(true, ilog2ll(L1), ilog2ll(L2), 512).fn) return false;
+    long long planes = p->batch;
+    for (int e = 0; e < p->rank - 2; ++e) planes *= p->dims[e];
+    if (planes < 1 || planes >= (1LL << 31)) return false;
+    const char* s = std::getenv("FB_FFT_PLANE");
+    return s && s[0] == '1';
+}
+
 // Host part of planning: the pass list and the twiddle jobs (no device work).
 int schedule_plan(fb_fft_plan_s* p, TwiddleBuilder& twb)
 {
@@ -734,7 +796,24 @@ int schedule_plan(fb_fft_plan_s* p, TwiddleBuilder& twb)
         static const char* one_name[1] = {"lines"};
         bool first = true;
         int ngroups = 0;
-        for (int ax = p->rank - 1; ax >= 0; --ax) {
+        int ax_top = p->rank - 1;
+        if (use_plane_pass(p)) {  // the two trailing axes in one pass
+            const long long L1 = p->dims[p->rank - 2], L2 = p->dims[p->rank - 1];
+            long long planes = B;
+            for (int e = 0; e < p->rank - 2; ++e) planes *= p->dims[e];
+            PassPlan q;
+            const int rc = make_plane_pass(q, twb, L1, L2, planes);
+            if (rc != FB_FFT_OK) return rc;
+            q.src = kBufIn;
+            q.dst = kBufOut;
+            q.group = ngroups++;
+            first = false;
+            p->passes.push_back(q);
+            p->group_names.push_back("plane");
+            p->smem_len_max = std::max(L1, L2);
+            ax_top = p->rank - 3;
+        }
+        for (int ax = ax_top; ax >= 0; --ax) {
             const long long L = p->dims[ax];
             if (L == 1) continue;
             long long S = 1, Opre = 1;
@@ -767,6 +846,24 @@ int build_plan(fb_fft_plan_s* p)
     TwiddleBuilder twb;
     int rc = schedule_plan(p, twb);
     if (rc != FB_FFT_OK) return rc;
+    // a plane pass needs one whole cluster resident; where none fits, plan
+    // the axis passes instead
+    for (const PassPlan& q : p->passes) {
+        if (q.kind != 3) continue;
+        int ncl = 0;
+        if (line_cluster_occupancy(pass_kernel(q, true), q.smem, &ncl) != cudaSuccess || ncl < 1) {
+            cudaGetLastError();
+            p->no_plane = true;
+        }
+    }
+    if (p->no_plane) {
+        p->passes.clear();
+        p->group_names.clear();
+        p->smem_len_max = 0;
+        twb = TwiddleBuilder();
+        rc = schedule_plan(p, twb);
+        if (rc != FB_FFT_OK) return rc;
+    }
     // Twiddle tables: one device buffer, built by the FP64 kernel.
     if (cudaMalloc(&p->tw, (size_t)p->tw_elems * sizeof(float2)) != cudaSuccess) {
         cudaGetLastError();
@@ -785,6 +882,14 @@ int build_plan(fb_fft_plan_s* p)
     for (PassPlan& q : p->passes) {
         int occ = 0;
         const LineKernel k = pass_kernel(q, true);
+        if (q.kind == 3) {  // persistent clusters: as many as fit at once
+            int ncl = 0;
+            FB_CK(line_cluster_occupancy(k, q.smem, &ncl));
+            q.grid = std::min(q.grid, (long long)ncl * k.cluster);
+            q.d.err = p->err;
+            q.d.tw = p->tw;
+            continue;
+        }
         FB_CK(line_occupancy(k, q.smem, &occ));
         if (occ < 1) return cuda_fail(cudaErrorInvalidConfiguration, "line pass occupancy");
         // The occupancy query answers one CTA per SM for every kernel that
@@ -899,7 +1004,16 @@ int launch_pass(fb_fft_plan_s* p, const PassPlan& q, const float2* in, float2* o
     d.in = src + q.src_off;
     d.out = dst + q.dst_off;
     d.async_io = 0;
-    if (q.async_ok && (((uintptr_t)d.in | (uintptr_t)d.out) & 15) == 0) {
+    if (q.kind == 3) {
+        // plane pass: bulk row loads, one tensor store of each CTA's column block
+        // (view {L2, L1, planes}, box {L2 / cluster, L1, 1})
+        const LineKernel pk = pass_kernel(q, true);
+        const int L1 = 1 << q.lg1;
+        if (q.async_ok && (((uintptr_t)d.in | (uintptr_t)d.out) & 15) == 0 &&
+            encode_view(&args.tm_out, d.out, d.C, L1, d.ntiles, d.out_sk, d.out_so, d.L / std::max(1, pk.cluster),
+                        L1) == 0)
+            d.async_io = 1;
+    } else if (q.async_ok && (((uintptr_t)d.in | (uintptr_t)d.out) & 15) == 0) {
         d.async_io = 1;
         const long long O = d.ntiles / d.tiles_per_o;
         if (d.in_tfast && !d.off_in &&

@@ -135,6 +135,8 @@ struct LineKernel {
     int producers = 0;   // threads beside the compute threads (power-of-two kernels: producer warp(s))
     int split_regs = 0;  // > 0: registers per thread the kernel must be launched with (it
                          // rebalances them with setmaxnreg, which needs exactly that pool)
+    int lg1 = 0;         // plane pass (kind 3): log2 of the rows per plane (lg: of the row length)
+    int cluster = 0;     // > 1: CTAs per thread-block cluster
 };
 // Extra shared memory of a tensor-core line pass: B^T (4 KB) + alignment.
 constexpr size_t kTcExtraSmem = 4096 + 128;
@@ -144,6 +146,13 @@ LineKernel line_kernel_p2(int threads, bool forward, int lg, int io);
 // picks for that length and layout).
 LineKernel line_kernel_p2tc(int threads, bool forward, int lg, int io);
 LineKernel line_kernel_generic(bool forward);
+// Plane pass (fft_plane.cuh): 2-D DFT over L1 = 2^lg1 rows of L2 = 2^lg2
+// contiguous values, one cluster of CTAs per plane; lg1, lg2 in {7, 8};
+// threads = compute threads per CTA, 512 or 256 (not for 256 x 256).
+LineKernel line_kernel_plane(bool forward, int lg1, int lg2, int threads);
+long long plane_smem_bytes(int lg1, int lg2, int threads);
+// Clusters of a cluster kernel that fit the GPU at once.
+cudaError_t line_cluster_occupancy(const LineKernel& k, size_t smem, int* clusters);
 LineKernel line_kernel_mixed(bool forward, int lg2);
 // Launch / occupancy / name of a table entry (shared-memory opt-in handled inside).
 cudaError_t line_launch(const LineKernel& k, const LineArgs& a, long long grid, size_t smem, cudaStream_t stream);

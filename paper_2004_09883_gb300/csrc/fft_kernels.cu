@@ -105,12 +105,40 @@ cudaError_t line_launch(const LineKernel& k, const LineArgs& a, long long grid, 
     cfg.blockDim = dim3(k.threads);
     cfg.dynamicSmemBytes = smem;
     cfg.stream = stream;
-    cudaLaunchAttribute attr[1];
+    cudaLaunchAttribute attr[2];
     attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
     attr[0].val.programmaticStreamSerializationAllowed = pdl_enabled() ? 1 : 0;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
+    if (k.cluster > 1) {  // the grid is a whole number of clusters (the planner sizes it so)
+        if (g % (unsigned)k.cluster != 0) return cudaErrorInvalidConfiguration;
+        attr[1].id = cudaLaunchAttributeClusterDimension;
+        attr[1].val.clusterDim.x = (unsigned)k.cluster;
+        attr[1].val.clusterDim.y = 1;
+        attr[1].val.clusterDim.z = 1;
+        cfg.numAttrs = 2;
+    }
     return cudaLaunchKernelEx(&cfg, k.fn, a);
+}
+
+cudaError_t line_cluster_occupancy(const LineKernel& k, size_t smem, int* clusters)
+{
+    *clusters = 0;
+    cudaError_t e = ensure_smem_attr(k);
+    if (e != cudaSuccess) return e;
+    const int cs = k.cluster > 1 ? k.cluster : 1;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)cs);
+    cfg.blockDim = dim3(k.threads);
+    cfg.dynamicSmemBytes = smem;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = (unsigned)cs;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaOccupancyMaxActiveClusters(clusters, (const void*)k.fn, &cfg);
 }
 
 cudaError_t line_occupancy(const LineKernel& k, size_t smem, int* blocks_per_sm)
@@ -123,7 +151,9 @@ cudaError_t line_occupancy(const LineKernel& k, size_t smem, int* blocks_per_sm)
 void line_kernel_name(const LineKernel& k, char* buf, size_t n)
 {
     static const char* io_names[4] = {"NN", "CC", "NC", "CCP"};
-    if (k.kind == 2)
+    if (k.kind == 3)
+        snprintf(buf, n, "k_fft_plane<%dx%d,%s>", 1 << k.lg1, 1 << k.lg, k.fwd ? "fwd" : "inv");
+    else if (k.kind == 2)
         snprintf(buf, n, "k_fft_mixed<%d,%s,2^%d>", k.threads, k.fwd ? "fwd" : "inv", k.lg);
     else if (k.kind == 0)
         snprintf(buf, n, "k_fft_p2%s<%d,%s,L=%d,%s>", k.tc ? "tc" : "", k.threads - k.producers, k.fwd ? "fwd" : "inv", 1 << k.lg,

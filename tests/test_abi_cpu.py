@@ -215,8 +215,28 @@ def test_planner_accepts_every_tested_shape(fb, dims, batch):
     if len(dims) == 1 and n > fb.MAX_SMEM_LEN:
         assert info["passes"] % 2 == 0 and info["scratch_bytes"] > 0
     else:
-        assert info["passes"] == len(nontrivial)
+        assert info["passes"] == len(nontrivial)  # one per axis (the plane pass is opt-in)
         assert info["scratch_bytes"] == 0
+
+
+@pytest.mark.parametrize("dims,batch", [([256, 256, 128], 1), ([4, 256, 128], 2), ([256, 128], 3),
+                                        ([128, 128], 1), ([2, 256, 256], 1), ([128, 256], 5)])
+def test_plane_pass_switch(fb, dims, batch, monkeypatch):
+    """FB_FFT_PLANE=1 fuses the two trailing axes into one plane pass;
+    unset or 0, one pass per axis."""
+    axes = len([d for d in dims if d > 1])
+    monkeypatch.setenv("FB_FFT_PLANE", "0")
+    assert fb.plan_query(dims, batch)["passes"] == axes
+    monkeypatch.setenv("FB_FFT_PLANE", "1")
+    assert fb.plan_query(dims, batch)["passes"] == axes - 1
+    monkeypatch.setenv("FB_FFT_PLANE", "1")
+    assert fb.plan_query(dims, batch, tensor_cores=True)["passes"] == axes  # FP32 butterflies only
+    monkeypatch.delenv("FB_FFT_PLANE")
+    assert fb.plan_query(dims, batch)["passes"] == axes
+    # planes of other shapes always run per axis
+    monkeypatch.setenv("FB_FFT_PLANE", "1")
+    assert fb.plan_query([64, 128], 4)["passes"] == 2
+    assert fb.plan_query([512, 128], 4)["passes"] == 2
 
 
 @pytest.mark.parametrize("n", inputs.smooth_lengths(4097, 1 << 24)[::7])
