@@ -453,6 +453,28 @@ def run_gpu(args, wl: dict) -> None:
         precision = {"fp32_path": {"value": round(whole_job_rate(world, bytes_step, ms32) / 1e9, 3), "unit": "GB/s",
                                    "ms_per_step": round(ms32, 5)},
                      "speedup_vs_fp32_path": round(ms32 / ms, 3), "tolerance_rel_l2": 5e-5}
+        # the plain per-call FP32 path: one exec per transform (a resident
+        # batch-1 plan), as the replaced CPU routine is called per transform
+        p1 = fbfft.Plan(dims, 1, stream=stream)
+
+        def step_per_call(i):
+            a, b = xin[i % nbuf], xout[i % nbuf]
+            for k in range(batch):
+                p1.exec_ptr(a.data_ptr() + k * n * 8, b.data_ptr() + k * n * 8, fbfft.FORWARD)
+        for i in range(args.warmup):
+            step_per_call(i)
+        barrier()
+        ev0.record(stream)
+        for i in range(args.steps):
+            step_per_call(i)
+        ev1.record(stream)
+        barrier()
+        ms1 = max_over_ranks(ev0.elapsed_time(ev1) / args.steps, dist, dev)
+        p1.check()
+        p1.close()
+        precision["per_call_fp32_path"] = {"value": round(whole_job_rate(world, bytes_step, ms1) / 1e9, 3),
+                                           "unit": "GB/s", "ms_per_step": round(ms1, 5), "calls_per_step": batch}
+        precision["speedup_vs_per_call_fp32_path"] = round(ms1 / ms, 3)
         if rank == 0 and not args.quick:
             import oracle
             # every result of input buffer 0 against the FP64 oracle
