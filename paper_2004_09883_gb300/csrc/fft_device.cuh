@@ -21,8 +21,16 @@
 
 namespace fbfft {
 
+// Complex add and subtract.  On sm_100 and later the device path issues one
+// paired FP32 instruction (add.rn.f32x2) per complex value, the same two
+// round-to-nearest results as two scalar adds with half the issue slots.
+#if defined(__CUDA_ARCH__) && __CUDA_ARCH__ >= 1000
+__device__ __forceinline__ float2 operator+(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 operator-(float2 a, float2 b) { return __fadd2_rn(a, make_float2(-b.x, -b.y)); }
+#else
 __host__ __device__ __forceinline__ float2 operator+(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
 __host__ __device__ __forceinline__ float2 operator-(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+#endif
 __host__ __device__ __forceinline__ float2 operator*(float s, float2 a) { return make_float2(s * a.x, s * a.y); }
 
 __host__ __device__ __forceinline__ float2 cmul(float2 a, float2 b)
@@ -68,14 +76,38 @@ __host__ __device__ __forceinline__ void dft2(float2& a, float2& b)
     b = t - b;
 }
 
+// t +- (s i) d, written per component: the (s i) product swaps d's halves,
+// which a paired add could only take after two moves.
+template <bool FWD>
+__host__ __device__ __forceinline__ void add_sub_si(float2 t, float2 d, float2& plus, float2& minus)
+{
+    if (FWD) {
+        plus = make_float2(t.x + d.y, t.y - d.x);
+        minus = make_float2(t.x - d.y, t.y + d.x);
+    } else {
+        plus = make_float2(t.x - d.y, t.y + d.x);
+        minus = make_float2(t.x + d.y, t.y - d.x);
+    }
+}
+
 template <bool FWD>
 __host__ __device__ __forceinline__ void dft4(float2& v0, float2& v1, float2& v2, float2& v3)
 {
-    const float2 t0 = v0 + v2, t1 = v0 - v2, t2 = v1 + v3, t3 = mul_si<FWD>(v1 - v3);
+    const float2 t0 = v0 + v2, t1 = v0 - v2, t2 = v1 + v3, d = v1 - v3;
     v0 = t0 + t2;
     v2 = t0 - t2;
-    v1 = t1 + t3;
-    v3 = t1 - t3;
+    add_sub_si<FWD>(t1, d, v1, v3);  // t1 +- (s i) (v1 - v3)
+}
+// dft4 of (v0, v1, (s i) v2, v3): the third input's factor folded into its adds.
+template <bool FWD>
+__host__ __device__ __forceinline__ void dft4_si2(float2& v0, float2& v1, float2& v2, float2& v3)
+{
+    float2 t0, t1;
+    add_sub_si<FWD>(v0, v2, t0, t1);
+    const float2 t2 = v1 + v3, d = v1 - v3;
+    v0 = t0 + t2;
+    v2 = t0 - t2;
+    add_sub_si<FWD>(t1, d, v1, v3);
 }
 
 template <bool FWD>
@@ -113,14 +145,12 @@ __host__ __device__ __forceinline__ void dft8(float2* v)
     dft4<FWD>(e0, e1, e2, e3);
     dft4<FWD>(o0, o1, o2, o3);
     o1 = rot<FWD>(o1, FB_R2, FB_R2);
-    o2 = mul_si<FWD>(o2);
     o3 = rot<FWD>(o3, -FB_R2, FB_R2);
     v[0] = e0 + o0;
     v[4] = e0 - o0;
     v[1] = e1 + o1;
     v[5] = e1 - o1;
-    v[2] = e2 + o2;
-    v[6] = e2 - o2;
+    add_sub_si<FWD>(e2, o2, v[2], v[6]);  // e2 +- w8^2 o2, w8^2 = s i
     v[3] = e3 + o3;
     v[7] = e3 - o3;
 }
@@ -137,13 +167,15 @@ __host__ __device__ __forceinline__ void dft16(float2* v)
     v[6] = rot<FWD>(v[6], FB_R2, FB_R2);          // k1=1, r2=2: m=2
     v[7] = rot<FWD>(v[7], FB_S16_1, FB_C16_1);    // k1=1, r2=3: m=3
     v[9] = rot<FWD>(v[9], FB_R2, FB_R2);          // k1=2, r2=1: m=2
-    v[10] = mul_si<FWD>(v[10]);                   // k1=2, r2=2: m=4
+    // k1=2, r2=2: m=4, w16^4 = s i, folded into the row's dft4 below
     v[11] = rot<FWD>(v[11], -FB_R2, FB_R2);       // k1=2, r2=3: m=6
     v[13] = rot<FWD>(v[13], FB_S16_1, FB_C16_1);  // k1=3, r2=1: m=3
     v[14] = rot<FWD>(v[14], -FB_R2, FB_R2);       // k1=3, r2=2: m=6
     v[15] = rot<FWD>(v[15], -FB_C16_1, -FB_S16_1);// k1=3, r2=3: m=9
-#pragma unroll
-    for (int k1 = 0; k1 < 4; ++k1) dft4<FWD>(v[4 * k1], v[4 * k1 + 1], v[4 * k1 + 2], v[4 * k1 + 3]);
+    dft4<FWD>(v[0], v[1], v[2], v[3]);
+    dft4<FWD>(v[4], v[5], v[6], v[7]);
+    dft4_si2<FWD>(v[8], v[9], v[10], v[11]);
+    dft4<FWD>(v[12], v[13], v[14], v[15]);
     // v[4*k1 + k2] holds Y[k1 + 4*k2]: transpose the 4x4 index
     float2 y[16];
 #pragma unroll
