@@ -172,7 +172,11 @@ int fb_fft_exec(fb_fft_plan_t plan, const void* in, void* out, int direction);
  * plan-owned device buffer, transforms, copies the result to host_out and
  * waits for it.  host_in/host_out may be the same array (in place) and may be
  * pageable or pinned host memory.  The first call allocates the device
- * staging buffer (owned by the plan).  Errors: BAD_PLAN, INVALID_ARG, ALLOC, CUDA.
+ * staging buffer (owned by the plan).  With pinned arrays and a batch of at
+ * least two 32 MiB chunks, the batch moves in chunks whose copy in,
+ * transform and copy out overlap (plan-owned copy streams and chunk plans,
+ * created on first use; same results); FB_FFT_HOST_PIPELINE=0 turns this off.
+ * Errors: BAD_PLAN, INVALID_ARG, ALLOC, CUDA, TIMEOUT.
  */
 int fb_fft_exec_host(fb_fft_plan_t plan, const void* host_in, void* host_out, int direction);
 

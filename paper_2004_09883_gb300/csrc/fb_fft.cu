@@ -456,6 +456,13 @@ struct fb_fft_plan_s {
     bool ext_scratch = false;  // scratch supplied per exec (server plans)
     float2* staging = nullptr;
     size_t staging_bytes = 0;
+    // fb_fft_exec_host on pinned arrays: the batch in chunks, each chunk's
+    // copy in, transform and copy out on three streams so they overlap
+    fb_fft_plan_s* host_chunk = nullptr;  // plan of host_chunk_batch transforms
+    fb_fft_plan_s* host_tail = nullptr;   // plan of the last, shorter chunk
+    long long host_chunk_batch = 0;
+    cudaStream_t h2d = nullptr, d2h = nullptr;
+    std::vector<cudaEvent_t> host_ev;
     int* err = nullptr;  // device error word written by bounded waits
     long long smem_len_max = 0;
     bool debug_timeout = false;  // test hook: make every TMA wait run out
@@ -498,6 +505,11 @@ bool plan_ok(fb_fft_plan_t p) { return p && p->magic == kMagic; }
 void free_plan(fb_fft_plan_s* p)
 {
     if (!p) return;
+    free_plan(p->host_chunk);
+    free_plan(p->host_tail);
+    if (p->h2d) cudaStreamDestroy(p->h2d);
+    if (p->d2h) cudaStreamDestroy(p->d2h);
+    for (cudaEvent_t e : p->host_ev) cudaEventDestroy(e);
     if (p->tw) cudaFree(p->tw);
     if (p->scratch) cudaFree(p->scratch);
     if (p->staging) cudaFree(p->staging);
@@ -1263,6 +1275,100 @@ int plan_new(fb_fft_plan_s** out, int rank, const long long* dims, long long bat
     return FB_FFT_OK;
 }
 
+// fb_fft_exec_host pipelining: chunks of about this many bytes.
+constexpr long long kHostChunkBytes = 32LL << 20;
+
+bool host_pinned(const void* ptr)
+{
+    cudaPointerAttributes at;
+    if (cudaPointerGetAttributes(&at, ptr) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return at.type == cudaMemoryTypeHost;
+}
+
+// Transforms per chunk for a pipelined host-array exec, or 0 when the call
+// should run whole: batched regular plans of at least two chunks, pinned
+// arrays (copies from pageable memory do not overlap), FB_FFT_HOST_PIPELINE
+// not 0.  Chunks start 16-byte aligned (even count when N is odd), so they
+// keep the TMA paths.
+long long host_chunk_batch(const fb_fft_plan_s* p, const void* in, const void* out)
+{
+    if (p->many || p->batch < 2) return 0;
+    const char* s = std::getenv("FB_FFT_HOST_PIPELINE");
+    if (s && s[0] == '0') return 0;
+    const long long item = p->N * (long long)sizeof(float2);
+    long long cb = std::max(1LL, kHostChunkBytes / item);
+    if (p->N % 2) cb = std::max(2LL, cb & ~1LL);
+    cb = std::max(cb, (p->batch + 63) / 64);  // at most 64 chunks
+    if (p->N % 2) cb = (cb + 1) & ~1LL;
+    if (cb * 2 > p->batch) return 0;
+    if (!host_pinned(in) || !host_pinned(out)) return 0;
+    return cb;
+}
+
+// Copy in, transform and copy out chunk by chunk on the h2d stream, the
+// plan's stream and the d2h stream: chunk k+1 arrives while chunk k is
+// transformed and chunk k-1 leaves.  Each chunk runs a plan of its batch
+// size (the same kernels and per-transform arithmetic as the whole plan).
+int exec_host_pipelined(fb_fft_plan_s* p, const float2* hin, float2* hout, int direction, long long cb)
+{
+    const long long B = p->batch, N = p->N;
+    const long long K = (B + cb - 1) / cb, tail = B - (K - 1) * cb;
+    if (p->host_chunk_batch != cb) {
+        free_plan(p->host_chunk);
+        free_plan(p->host_tail);
+        p->host_chunk = p->host_tail = nullptr;
+        p->host_chunk_batch = 0;
+        int rc = plan_new(&p->host_chunk, p->rank, p->dims, cb, p->flags, p->stream, false);
+        if (rc != FB_FFT_OK) return rc;
+        if (tail != cb) {
+            rc = plan_new(&p->host_tail, p->rank, p->dims, tail, p->flags, p->stream, false);
+            if (rc != FB_FFT_OK) return rc;
+        }
+        p->host_chunk_batch = cb;
+    }
+    if (!p->h2d) FB_CK(cudaStreamCreateWithFlags(&p->h2d, cudaStreamNonBlocking));
+    if (!p->d2h) FB_CK(cudaStreamCreateWithFlags(&p->d2h, cudaStreamNonBlocking));
+    while ((long long)p->host_ev.size() < 2 * K + 1) {
+        cudaEvent_t e;
+        FB_CK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+        p->host_ev.push_back(e);
+    }
+    auto enqueue = [&]() -> int {
+        // the staging buffer is reused: start after the plan's earlier work
+        FB_CK(cudaEventRecord(p->host_ev[2 * K], p->stream));
+        FB_CK(cudaStreamWaitEvent(p->h2d, p->host_ev[2 * K], 0));
+        for (long long k = 0; k < K; ++k) {
+            const long long nb = k + 1 < K ? cb : tail;
+            const long long off = k * cb * N;
+            const size_t bytes = (size_t)(nb * N) * sizeof(float2);
+            fb_fft_plan_s* c = nb == cb ? p->host_chunk : p->host_tail;
+            FB_CK(cudaMemcpyAsync(p->staging + off, hin + off, bytes, cudaMemcpyHostToDevice, p->h2d));
+            FB_CK(cudaEventRecord(p->host_ev[2 * k], p->h2d));
+            FB_CK(cudaStreamWaitEvent(p->stream, p->host_ev[2 * k], 0));
+            const int rc = exec_device(c, p->staging + off, p->staging + off, direction);
+            if (rc != FB_FFT_OK) return rc;
+            FB_CK(cudaEventRecord(p->host_ev[2 * k + 1], p->stream));
+            FB_CK(cudaStreamWaitEvent(p->d2h, p->host_ev[2 * k + 1], 0));
+            FB_CK(cudaMemcpyAsync(hout + off, p->staging + off, bytes, cudaMemcpyDeviceToHost, p->d2h));
+        }
+        return FB_FFT_OK;
+    };
+    int rc = enqueue();
+    // wait for every copy, also after an error: the caller's arrays stay in use until then
+    const cudaError_t e1 = cudaStreamSynchronize(p->h2d), e2 = cudaStreamSynchronize(p->stream),
+                      e3 = cudaStreamSynchronize(p->d2h);
+    if (rc != FB_FFT_OK) return rc;
+    if (e1 != cudaSuccess) return cuda_fail(e1, "exec_host copy in");
+    if (e2 != cudaSuccess) return cuda_fail(e2, "exec_host transform");
+    if (e3 != cudaSuccess) return cuda_fail(e3, "exec_host copy out");
+    rc = fb_fft_check(p->host_chunk);
+    if (rc == FB_FFT_OK && p->host_tail) rc = fb_fft_check(p->host_tail);
+    return rc;
+}
+
 }  // namespace
 
 namespace fbfft {
@@ -1579,6 +1685,8 @@ int fb_fft_exec_host(fb_fft_plan_t plan, const void* host_in, void* host_out, in
         }
         plan->staging_bytes = bytes;
     }
+    const long long cb = host_chunk_batch(plan, host_in, host_out);
+    if (cb > 0) return exec_host_pipelined(plan, (const float2*)host_in, (float2*)host_out, direction, cb);
     FB_CK(cudaMemcpyAsync(plan->staging, host_in, bytes, cudaMemcpyHostToDevice, plan->stream));
     int rc = exec_device(plan, plan->staging, plan->staging, direction);
     if (rc != FB_FFT_OK) return rc;
