@@ -467,6 +467,7 @@ struct fb_fft_plan_s {
     long long smem_len_max = 0;
     bool debug_timeout = false;  // test hook: make every TMA wait run out
     bool no_plane = false;       // plane passes disabled (their cluster does not fit this GPU)
+    bool no_evict_first = false; // FB_FFT_EVICT_FIRST=0: first-pass loads without the L2 evict-first policy
     // batched uneven lengths (fb_fft_plan_many)
     bool many = false;
     long long total = 0;                 // elements of the packed layout
@@ -1015,6 +1016,7 @@ int launch_pass(fb_fft_plan_s* p, const PassPlan& q, const float2* in, float2* o
     if (err) d.err = err;
     d.in = src + q.src_off;
     d.out = dst + q.dst_off;
+    d.evict_first = (q.src == kBufIn && in != out && !p->many && !p->no_evict_first) ? 1 : 0;
     d.async_io = 0;
     if (q.kind == 3) {
         // plane pass: bulk row loads, one tensor store of each CTA's column block
@@ -1266,6 +1268,7 @@ int plan_new(fb_fft_plan_s** out, int rank, const long long* dims, long long bat
     p->stream = stream;
     p->N = N;
     p->ext_scratch = ext_scratch;
+    if (const char* s = std::getenv("FB_FFT_EVICT_FIRST")) p->no_evict_first = s[0] == '0';
     int rc = build_plan(p);
     if (rc != FB_FFT_OK) {
         free_plan(p);

@@ -288,15 +288,30 @@ __device__ __forceinline__ bool mbar_wait_bounded(unsigned long long* bar, unsig
         if (global_ns() - t0 > kWaitLimitNs) return false;
     return true;
 }
-// global -> shared, contiguous bytes; completion counted on `bar`.
+// L2 policy for data read once: its lines go first when L2 needs room.
+__device__ __forceinline__ unsigned long long l2_evict_first_policy()
+{
+    unsigned long long pol;
+    asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(pol));
+    return pol;
+}
+// global -> shared, contiguous bytes; completion counted on `bar`; with
+// `hint`, the source lines take the L2 policy `pol`.
 __device__ __forceinline__ void bulk_load_1d(void* dst, const void* src, unsigned bytes, unsigned long long* bar,
-                                             int* err = nullptr)
+                                             int* err = nullptr, bool hint = false, unsigned long long pol = 0)
 {
     if (err) FB_SELFCHECK(err, 11, src, dst, bytes, 16, 16);
-    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-                     smem_u32(dst)),
-                 "l"(src), "r"(bytes), "r"(smem_u32(bar))
-                 : "memory");
+    if (hint)
+        asm volatile(
+            "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint [%0], [%1], %2, [%3], "
+            "%4;" ::"r"(smem_u32(dst)),
+            "l"(src), "r"(bytes), "r"(smem_u32(bar)), "l"(pol)
+            : "memory");
+    else
+        asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                         smem_u32(dst)),
+                     "l"(src), "r"(bytes), "r"(smem_u32(bar))
+                     : "memory");
 }
 // shared -> global, contiguous bytes; tracked by the issuing thread's bulk group.
 __device__ __forceinline__ void bulk_store_1d(void* dst, const void* src, unsigned bytes, int* err = nullptr)
@@ -308,14 +323,21 @@ __device__ __forceinline__ void bulk_store_1d(void* dst, const void* src, unsign
 }
 // 3-D tiled tensor copies (coordinates innermost first).
 __device__ __forceinline__ void tma_load_3d(void* dst, const void* tmap, int x, int y, int z, unsigned long long* bar,
-                                            int* err = nullptr)
+                                            int* err = nullptr, bool hint = false, unsigned long long pol = 0)
 {
     if (err) FB_SELFCHECK(err, 13, tmap, dst, 16u, 64, 128);
-    asm volatile(
-        "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], "
-        "[%5];" ::"r"(smem_u32(dst)),
-        "l"(tmap), "r"(x), "r"(y), "r"(z), "r"(smem_u32(bar))
-        : "memory");
+    if (hint)
+        asm volatile(
+            "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes.L2::cache_hint [%0], [%1, "
+            "{%2, %3, %4}], [%5], %6;" ::"r"(smem_u32(dst)),
+            "l"(tmap), "r"(x), "r"(y), "r"(z), "r"(smem_u32(bar)), "l"(pol)
+            : "memory");
+    else
+        asm volatile(
+            "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, "
+            "%4}], [%5];" ::"r"(smem_u32(dst)),
+            "l"(tmap), "r"(x), "r"(y), "r"(z), "r"(smem_u32(bar))
+            : "memory");
 }
 __device__ __forceinline__ void tma_store_3d(const void* tmap, int x, int y, int z, const void* src,
                                              int* err = nullptr)

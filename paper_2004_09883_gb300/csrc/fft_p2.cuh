@@ -400,28 +400,32 @@ __device__ __forceinline__ void p2_issue_load(const PassDesc& d, const CUtensorM
     using C = P2<THREADS, LG, IO>;
     const TileIdx ti = p2_tile_index(d, tile, C::LOGT, C::T);
     const float2* src = tile_in_base(d, ti, C::IN_T);
+    // the caller's input is read once per exec: let its lines leave L2 first,
+    // so the pass's output stays there for the next pass
+    const bool ef = d.evict_first != 0;
+    const unsigned long long pol = ef ? l2_evict_first_policy() : 0ull;
     if constexpr (!C::IN_T) {
         const unsigned bytes = (unsigned)(ti.Tv * C::L) * 8u;
         if (lane == 0) mbar_arrive_expect_tx(bar, bytes + d.debug_extra_tx);
         __syncwarp();
         if (C::LLS == C::L && !d.off_in) {
-            if (lane == 0) bulk_load_1d(land, src, bytes, bar, d.err);
+            if (lane == 0) bulk_load_1d(land, src, bytes, bar, d.err, ef, pol);
         } else {
             for (int t = lane; t < ti.Tv; t += 32)
-                bulk_load_1d(land + t * C::LLS, line_in(d, ti, src, t), C::L * 8u, bar, d.err);
+                bulk_load_1d(land + t * C::LLS, line_in(d, ti, src, t), C::L * 8u, bar, d.err, ef, pol);
         }
     } else if (!d.off_in) {
         if (lane == 0) {
             mbar_arrive_expect_tx(bar, (unsigned)(C::T * C::L) * 8u + d.debug_extra_tx);
             for (int n0 = 0; n0 < C::L; n0 += C::BR)
-                tma_load_3d(land + n0 * C::T, tm, (int)ti.c0, n0, (int)ti.o, bar, d.err);
+                tma_load_3d(land + n0 * C::T, tm, (int)ti.c0, n0, (int)ti.o, bar, d.err, ef, pol);
         }
     } else {
         // irregular transform bases: one bulk copy per row of Tv columns
         if (lane == 0) mbar_arrive_expect_tx(bar, (unsigned)(ti.Tv * C::L) * 8u + d.debug_extra_tx);
         __syncwarp();
         for (int n = lane; n < C::L; n += 32)
-            bulk_load_1d(land + n * C::T, src + (long long)n * d.in_sn, (unsigned)ti.Tv * 8u, bar, d.err);
+            bulk_load_1d(land + n * C::T, src + (long long)n * d.in_sn, (unsigned)ti.Tv * 8u, bar, d.err, ef, pol);
     }
 }
 // Producer warp (all lanes): start the TMA stores of one finished tile.
