@@ -124,7 +124,8 @@ inline size_t line_smem_bytes(long long land_elems, int L, int T, int nst, bool 
 
 // One compiled line-pass kernel.  kind 0: compile-time power-of-two kernel
 // (lg = log2 L, io = its IoMode); 1: generic kernel; 2: mixed kernel
-// (lg = log2 of L's power-of-two factor).
+// (lg = log2 of L's power-of-two factor); 3: plane pass (lg1 = log2 rows,
+// lg = log2 row length, launched in clusters of `cluster` CTAs).
 struct LineKernel {
     void (*fn)(LineArgs);
     int threads;
