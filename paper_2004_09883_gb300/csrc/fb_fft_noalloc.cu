@@ -99,7 +99,7 @@ struct Pass {
 int fill_pass(Pass& p, StackTwiddles& tw, long long L, long long O, long long C, long long in_sn, long long in_sc,
               long long in_so, long long out_sk, long long out_sc, long long out_so, bool in_t, bool out_t, bool ptw)
 {
-    std::memset(&p, 0, sizeof(p));
+    p = Pass{};  // every field zero (no offset tables, no post-twiddle, no scale)
     PassDesc& d = p.d;
     int nst = 0;
     int rc = fb_fft_factorize(L, d.radix, kMaxStages, &nst);
