@@ -5,10 +5,12 @@
 // in range, that no two threads write one slot in a phase, and that the
 // result equals the 2-D DFT (row then column sums of exp(s 2 pi i n k / L),
 // in double).  Prints "plane L1 L2 threads dir worst_rel_l2 violations" per
-// case.
+// case, and per shape "banks L1 L2 threads" followed by the worst bank
+// conflict degree of each phase's shared-memory accesses (1 = none).
 #include <cmath>
 #include <complex>
 #include <cstdio>
+#include <algorithm>
 #include <cstring>
 #include <random>
 #include <vector>
@@ -170,9 +172,56 @@ static void run_case(unsigned seed, int* violations, double* rel)
     *violations = bad;
 }
 
+// Shared-memory bank conflicts of the kernel's accesses: for every phase and
+// every value r a thread moves, each half-warp's 16 eight-byte slots (the
+// unit one conflict-free wavefront serves) must fall in 16 different slot
+// positions mod 16; identical slots are one broadcast.  Returns the worst
+// number of distinct slots sharing a position, per phase.
+template <int LG1, int LG2, int TH>
+static void bank_check()
+{
+    using P = PlaneCfg<LG1, LG2, TH>;
+    auto worst = [](auto slot_of) {
+        int w = 1;
+        for (int t0 = 0; t0 < P::THREADS; t0 += 16)
+            for (int r = 0; r < 16; ++r) {
+                int cnt[16] = {0};
+                int seen[16];
+                int ns = 0;
+                for (int l = 0; l < 16; ++l) {
+                    const int s = slot_of(t0 + l, r);
+                    if (s < 0) continue;
+                    bool dup = false;
+                    for (int k = 0; k < ns; ++k) dup = dup || seen[k] == s;
+                    if (dup) continue;
+                    seen[ns++] = s;
+                    w = std::max(w, ++cnt[s & 15]);
+                }
+            }
+        return w;
+    };
+    const int row_in = worst([](int t, int r) { return P::row_of(t) * P::RS + P::row_s0_in(P::rj_of(t), r); });
+    const int row_out = worst([](int t, int r) { return P::row_of(t) * P::RS + P::row_s0_out(P::rj_of(t), r); });
+    const int row_s1 = worst([](int t, int r) {
+        const int u = r / P::G2, rr = r % P::G2;  // the thread's 16 values: butterfly u, input rr
+        return P::row_of(t) * P::RS + P::row_s1(P::rj_of(t) + P::G2 * u, rr);
+    });
+    const int gather = worst([](int t, int r) {
+        return P::lrow(P::cj_of(t), r) * P::RS + P::col_slot(P::cl_of(t));  // CTA 0's columns
+    });
+    const int col_out = worst([](int t, int r) { return P::blk(16 * P::cj_of(t) + r, P::cl_of(t)); });
+    const int col_s1 = worst([](int t, int r) {
+        const int u = r / P::G1, rr = r % P::G1;
+        return P::blk(P::cj_of(t) + P::G1 * u + 16 * rr, P::cl_of(t));
+    });
+    std::printf("banks %d %d %d %d %d %d %d %d %d\n", 1 << LG1, 1 << LG2, TH, row_in, row_out, row_s1, gather, col_out,
+                col_s1);
+}
+
 template <int LG1, int LG2, int TH>
 static void both(unsigned seed)
 {
+    bank_check<LG1, LG2, TH>();
     int v;
     double e;
     run_case<LG1, LG2, TH, true>(seed, &v, &e);

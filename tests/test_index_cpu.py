@@ -36,7 +36,9 @@ def test_plane_pass_emulation(tmp_path):
     on the host thread by thread and phase by phase with the kernel's own
     index functions and butterflies: every shared-memory slot, owner CTA and
     row in range, no slot written twice in a phase, and the result equal to
-    the 2-D DFT summed in double for every compiled plane shape."""
+    the 2-D DFT summed in double for every compiled plane shape; and every
+    shared-memory access pattern of every phase free of bank conflicts (each
+    half-warp's 16 eight-byte slots in 16 different bank pairs)."""
     nvcc = shutil.which("nvcc") or "/usr/local/cuda/bin/nvcc"
     if not os.path.exists(nvcc):
         pytest.skip("nvcc not available")
@@ -45,6 +47,10 @@ def test_plane_pass_emulation(tmp_path):
                     f"-I{ROOT}/include", f"-I{ROOT}/paper_2004_09883_gb300/csrc",
                     os.path.join(ROOT, "tests", "plane_host.cu"), "-o", str(exe)], check=True)
     lines = subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split("\n")
+    banks = [ln.split() for ln in lines if ln.startswith("banks")]
+    assert len(banks) == 7
+    for row in banks:  # every shared-memory access of every phase: one wavefront per half-warp
+        assert all(int(v) == 1 for v in row[4:]), row
     rows = [ln.split() for ln in lines if ln.startswith("plane")]
     shapes = {(int(r[1]), int(r[2]), int(r[3])) for r in rows}
     assert shapes == {(256, 128, 512), (128, 128, 512), (256, 256, 512), (128, 256, 512),
