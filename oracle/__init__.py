@@ -121,13 +121,25 @@ def twiddle(m: int, d: int, sign: int = -1) -> complex:
 
 
 def rel_l2(y, ref) -> np.ndarray:
-    """Per-transform relative L2 error ||y - ref|| / ||ref|| over the last axis
-    after flattening each batch item (FP64)."""
+    """Per-transform relative L2 error ||y - ref||_2 / ||ref||_2 in FP64, the
+    error measure of every parity check.
+
+    ``y`` and ``ref`` have the same shape: 1-D (one transform) or 2-D with one
+    transform per row (``(batch, n)``; reshape multi-dimensional transforms to
+    that first).  Other shapes raise ValueError, so a volume passed unreshaped
+    cannot be split into per-row errors by accident.  A row whose reference
+    is all zero reports the absolute norm ||y||_2.  Returns a float64 array
+    of one error per transform.
+    """
     y = np.asarray(y, dtype=np.complex128)
     ref = np.asarray(ref, dtype=np.complex128)
-    y2 = y.reshape(y.shape[0], -1) if y.ndim > 1 else y.reshape(1, -1)
+    if y.shape != ref.shape:
+        raise ValueError(f"rel_l2: shapes differ {y.shape} vs {ref.shape}")
+    if y.ndim not in (1, 2):
+        raise ValueError(f"rel_l2: want 1-D or (batch, n) arrays, got shape {y.shape}")
+    y2 = y.reshape(1, -1) if y.ndim == 1 else y
     r2 = ref.reshape(y2.shape)
-    num = np.linalg.norm(y2 - r2, axis=1)
-    den = np.linalg.norm(r2, axis=1)
+    num = np.sqrt(np.sum(np.abs(y2 - r2) ** 2, axis=1))
+    den = np.sqrt(np.sum(np.abs(r2) ** 2, axis=1))
     den = np.where(den == 0, 1.0, den)
     return num / den
