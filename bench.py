@@ -1,6 +1,6 @@
 """Benchmark of the FFT function block on GB300.
 
-Workload (default): 3-D complex64 C2C 256x256x128, re/im iid standard normal
+Headline workload: 3-D complex64 C2C 256x256x128, re/im iid standard normal
 from a fixed seed, forward then inverse with 1/N scale; one step = one forward
 and one inverse exec of that volume (the whole hot path).  Metric: effective
 HBM bandwidth, algorithmic bytes (one read + one write of the volume per exec,
@@ -8,12 +8,25 @@ HBM bandwidth, algorithmic bytes (one read + one write of the volume per exec,
 beside it.  Four input/output buffer pairs (512 MiB) rotate between steps so
 the working set exceeds the 126 MB L2.
 
+The default run (no --workload) prints ONE JSON line: the headline workload's
+line, with every other workload's own line under the key ``workloads`` (each
+with its time, GB/s, the dominant kernel's event-timed roofline, its error
+against the FP64 oracle and its clocks):
+
+  1d4096     1-D N=4096 x 64, uniform
+  1d4096L    1-D N=4096 x 16384, uniform (the large batched transform)
+  1d2p20     1-D N=2^20 x 32, normal, FP32 path
+  1d2p20tc   the same with the radix-16 stages on the tensor cores
+  uneven     4096 1-D transforms, lengths 5-smooth log-uniform in [64, 65536]
+  serving    2000 requests of mixed 1-D/2-D/3-D shapes, Poisson arrivals
+  grid2048   2-D 2048x2048 (the paper's FFT grid), forward then inverse 1/N
+
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
-                  [--workload 3d|1d4096|1d4096L|1d2p20|1d2p20tc|uneven|serving]
+                  [--workload 3d|1d4096|...]   (one workload alone)
 
 Under torchrun each rank runs its own replica (independent transforms, no
-collective on the data path); rank 0 prints one JSON line.  --impl reference
-times the CPU oracle (FP64) on this machine's cores on the same workload.
+collective on the data path); rank 0 prints the line.  --impl reference times
+the CPU oracle (FP64) on this machine's cores on the headline workload.
 """
 from __future__ import annotations
 
@@ -26,6 +39,7 @@ import subprocess
 import sys
 import threading
 import time
+from concurrent.futures import ThreadPoolExecutor
 
 import numpy as np
 
@@ -52,8 +66,15 @@ WORKLOADS = {
     "serving": dict(name="serving_mix_2000_requests_1d_2d_3d_poisson", dims=None, batch=1,
                     seed=inputs.seed_for(inputs.WORKLOAD_SERVING), dist="uniform", inverse=False,
                     serving=dict(requests=2000, host_requests=600, slots=8, hbm_cap=40 * 10 ** 9,
-                                 fractions=[0.1, 0.25, 0.5, 0.75, 0.9, 1.1])),
+                                 fractions=[0.1, 0.25, 0.5, 0.75, 0.9, 1.1], checked=100)),
+    "grid2048": dict(name="2d_c2c_2048x2048_fwd_then_inv_scaled", dims=[2048, 2048], batch=1,
+                     seed=inputs.seed_for(inputs.WORKLOAD_GRID_2048x2048), dist="normal", inverse=True),
 }
+HEADLINE = "3d"
+SUITE = ["1d4096", "1d4096L", "1d2p20", "1d2p20tc", "uneven", "serving", "grid2048"]
+# error check: every batch item up to this many elements, else the first ERR_ITEMS items
+ERR_ALL_ELEMS = 1 << 25
+ERR_ITEMS = 64
 # sources that decide what the timed kernels do (device code and the planner's launch choices)
 KERNEL_SOURCES = sorted(
     os.path.join("paper_2004_09883_gb300", "csrc", f)
@@ -201,6 +222,21 @@ def algorithmic(wl: dict) -> tuple[float, float, int]:
     return execs * 2 * 8.0 * n * wl["batch"], execs * 5.0 * n * math.log2(n) * wl["batch"], execs
 
 
+def config_of(wl: dict, world: int) -> dict:
+    """The workload's `config` object, the same on the GPU arm and the reference arm."""
+    n = int(np.prod(wl["dims"]))
+    nbuf = buffers_for(wl)
+    return {"workload": wl["name"], "dims": wl["dims"], "batch": wl["batch"], "dtype_storage": "complex64",
+            "l2": f"{nbuf} rotating input/output buffer pairs ({nbuf * 2 * 8 * n * wl['batch'] / 2 ** 20:.0f} MiB)"
+                  f" > 126 MB L2",
+            "parallelism": "replicas" if world > 1 else "single GPU"}
+
+
+def buffers_for(wl: dict) -> int:
+    n = int(np.prod(wl["dims"]))
+    return min(8, max(2, int(math.ceil(512 * 2 ** 20 / (2 * 8 * n * wl["batch"])))))
+
+
 # ---------------------------------------------------------------------------
 # CPU oracle timing (reference arm and the cpu_baseline object)
 # ---------------------------------------------------------------------------
@@ -273,6 +309,18 @@ def oracle_uneven_sample(wl: dict, budget_s: float, threads: int) -> dict:
     return {"value": done_bytes / t_total / 1e9, "seconds": t_total, "transforms": k}
 
 
+def oracle_each(items, threads: int, sign: int = -1, scale: bool = False) -> list:
+    """The oracle on a list of (array, dims): one transform per worker thread
+    (its C routine runs without the interpreter lock)."""
+    import oracle
+
+    def one(it):
+        x, dims = it
+        return oracle.fft(np.asarray(x).astype(np.complex128), list(dims), sign, scale)
+    with ThreadPoolExecutor(max(1, threads)) as ex:
+        return list(ex.map(one, items))
+
+
 def cpu_model() -> str:
     try:
         with open("/proc/cpuinfo") as f:
@@ -284,11 +332,15 @@ def cpu_model() -> str:
     return "unknown"
 
 
+def host_threads() -> int:
+    return len(os.sched_getaffinity(0))
+
+
 def run_reference(args, wl: dict) -> None:
     world, rank, _ = dist_setup()
     if rank != 0:
         return
-    threads = len(os.sched_getaffinity(0))
+    threads = host_threads()
     if wl.get("lengths") or wl.get("serving"):  # many transforms: each step a bounded sample of them
         per_step = max(0.5, 150.0 / max(1, args.steps + args.warmup))
         for _ in range(args.warmup):
@@ -317,7 +369,6 @@ def run_reference(args, wl: dict) -> None:
 
     x = make_input(wl, 0).astype(np.complex128)
     dims = wl["dims"]
-    n = int(np.prod(dims))
     # size the per-step sample (batch items) to the budget
     t = time.perf_counter()
     oracle.fft(x[:1], dims, -1, False, threads)
@@ -344,8 +395,8 @@ def run_reference(args, wl: dict) -> None:
         "impl": "reference", "metric": METRIC, "value": round(value, 4), "unit": "GB/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": wl["name"], "dims": dims, "batch": wl["batch"], "l2": "n/a (CPU)",
-                   "parallelism": "host threads"},
+        # the same workload description as the GPU arm's line (the oracle runs on its host cores)
+        "config": config_of(wl, world),
         "gflops": flops_step * frac / dt / 1e9,
         "cpu_baseline": {"value": round(value, 4), "unit": "GB/s", "cores": threads, "kind": "oracle",
                          "sample": desc},
@@ -357,33 +408,109 @@ def run_reference(args, wl: dict) -> None:
 # ---------------------------------------------------------------------------
 # GPU arm
 # ---------------------------------------------------------------------------
-def run_gpu(args, wl: dict) -> None:
+class Ctx:
+    """Device, process group and library of one rank (set up once per run)."""
+
+    def __init__(self):
+        import torch
+
+        self.world, self.rank, self.local = dist_setup()
+        torch.cuda.set_device(self.local)
+        self.dev = torch.device("cuda", self.local)
+        self.dist = None
+        if self.world > 1:
+            import torch.distributed as dist
+            dist.init_process_group("nccl", device_id=self.dev)
+            self.dist = dist
+        from paper_2004_09883_gb300 import build as fbbuild
+        fbbuild.build()
+        from paper_2004_09883_gb300 import fbfft
+        self.fb = fbfft
+        self.stream = torch.cuda.current_stream(self.dev)
+
+    def barrier(self):
+        import torch
+        torch.cuda.synchronize(self.dev)
+        if self.dist is not None:
+            self.dist.barrier()
+        torch.cuda.synchronize(self.dev)
+
+    def max(self, x: float) -> float:
+        return max_over_ranks(x, self.dist, self.dev)
+
+    def close(self):
+        if self.dist is not None:
+            self.dist.barrier()
+            self.dist.destroy_process_group()
+
+
+def event_timed(ctx: Ctx, step, steps: int, warmup: int):
+    """(ms per step, max over ranks; library launches) of `steps` calls of
+    step(i) between two CUDA events on the launching stream, after `warmup`
+    untimed calls."""
     import torch
+    for i in range(warmup):
+        step(i)
+    ctx.barrier()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    l0 = ctx.fb.launch_count()
+    e0.record(ctx.stream)
+    for i in range(steps):
+        step(i)
+    e1.record(ctx.stream)
+    ctx.barrier()
+    return ctx.max(e0.elapsed_time(e1) / steps), ctx.fb.launch_count() - l0
 
-    world, rank, local = dist_setup()
-    torch.cuda.set_device(local)
-    dev = torch.device("cuda", local)
-    if world > 1:
-        import torch.distributed as dist
-        dist.init_process_group("nccl", device_id=dev)
-    else:
-        dist = None
 
-    from paper_2004_09883_gb300 import build as fbbuild
-    fbbuild.build()
-    from paper_2004_09883_gb300 import fbfft
+def roofline_of(passes, prof_steps: int, execs: int, bytes_per_exec: float, wl_name: str, peaks: dict,
+                basis: str | None = None):
+    """Roofline of the dominant kernel: the pass role with the largest measured
+    time.  One launch covers the exec's data divided by the role's launches per
+    exec (four-step roles run once per batch chunk); algorithmic bytes = one
+    read + one write of that data."""
+    dom = max(passes, key=lambda r: r[1]) if passes else None
+    if not dom or dom[2] <= 0:
+        return None
+    per_launch_ms = dom[1] / dom[2]
+    launches_per_exec = dom[2] / (prof_steps * execs)
+    launch_bytes = bytes_per_exec / launches_per_exec
+    achieved = launch_bytes / (per_launch_ms / 1e3) / 1e9
+    tr = load_traffic(wl_name)
+    traffic = tr["dram_bytes_per_launch"] if tr and tr.get("pass") == dom[0] else None
+    r = {"bound": "hbm", "achieved": round(achieved, 2), "peak": peaks["hbm_gbs"], "unit": "GB/s",
+         "frac": round(achieved / peaks["hbm_gbs"], 4), "traffic": traffic,
+         "kernel_pass": dom[0], "launch_ms": round(per_launch_ms, 5), "algorithmic_bytes_per_launch": launch_bytes,
+         "peak_source": f"{peaks['source']} (MEASURED_PEAKS.json hbm_gbs, burst copy)"
+         if peaks["source"] == "measured" else "fallback 6.8 TB/s"}
+    if traffic is not None:
+        r["traffic_note"] = ("dram__bytes_read.sum + dram__bytes_write.sum of this kernel's launch in one ncu "
+                             "capture: reads plus the write-back that happens during the launch (the rest of "
+                             "the output is written back to HBM during later launches)")
+    if basis:
+        r["basis"] = basis
+    return r
 
+
+def error_items(batch: int, n: int) -> int:
+    return batch if batch * n <= ERR_ALL_ELEMS else min(batch, ERR_ITEMS)
+
+
+def gpu_regular(args, ctx: Ctx, wl: dict, headline: bool) -> dict:
+    """A regular plan (rank 1-3, batch): timed steps, per-pass roofline,
+    e2e through fb_fft_exec_host, errors against the oracle, CPU baseline."""
+    import torch
+    fbfft = ctx.fb
+    dev, stream, world, rank = ctx.dev, ctx.stream, ctx.world, ctx.rank
     dims, batch = wl["dims"], wl["batch"]
     n = int(np.prod(dims))
     bytes_step, flops_step, execs = algorithmic(wl)
-    nbuf = max(2, int(math.ceil(512 * 2 ** 20 / (2 * 8 * n * batch))))
-    nbuf = min(nbuf, 8)
-    stream = torch.cuda.current_stream(dev)
+    nbuf = buffers_for(wl)
     host_inputs = [make_input(wl, replica_rep(rank, r)) for r in range(nbuf)]
     xin = [torch.from_numpy(h.reshape(-1)).to(dev) for h in host_inputs]
     xout = [torch.empty_like(xin[0]) for _ in range(nbuf)]
     tc = bool(wl.get("tc"))
     plan = fbfft.Plan(dims, batch, scale_inv_n=wl["inverse"], stream=stream, tensor_cores=tc)
+    threads = host_threads()
 
     def step(i, p=None):
         p = p or plan
@@ -392,13 +519,7 @@ def run_gpu(args, wl: dict) -> None:
         if wl["inverse"]:
             p.exec_ptr(b.data_ptr(), b.data_ptr(), fbfft.INVERSE)
 
-    def barrier():
-        torch.cuda.synchronize(dev)
-        if dist is not None:
-            dist.barrier()
-        torch.cuda.synchronize(dev)
-
-    clocks = ClockSampler(local) if rank == 0 and not args.quick else None
+    clocks = ClockSampler(ctx.local) if rank == 0 and not args.quick else None
     for i in range(args.warmup):
         step(i)
     # pre-roll: untimed extra warm-up so the clock samples see a loaded GPU
@@ -409,47 +530,30 @@ def run_gpu(args, wl: dict) -> None:
         i += 1
         if i % 64 == 0:
             torch.cuda.synchronize(dev)
-    barrier()
-    launches0 = fbfft.launch_count()
-    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     wall0 = time.time()
-    ev0.record(stream)
-    for i in range(args.steps):
-        step(i)
-    ev1.record(stream)
-    barrier()
+    ms, launches = event_timed(ctx, step, args.steps, 0)
     wall1 = time.time()
-    launches = fbfft.launch_count() - launches0
-    ms = ev0.elapsed_time(ev1) / args.steps
     # per-pass launch times, in a separate run: the event pair around every
     # launch serialises the passes, which the timed loop above lets overlap
     prof_steps = max(3, min(args.steps, 50))
     plan.profile(True)
     for i in range(prof_steps):
         step(i)
-    barrier()
+    ctx.barrier()
     passes = plan.profile_read()
     plan.profile(False)
     plan.check()
-    ms = max_over_ranks(ms, dist, dev)
     clk = clocks.summary(wall0, wall1) if clocks else None
     if clocks:
         clocks.stop()
 
-    # tensor-core workload: the plain FP32 plan on the same buffers, and both
-    # paths' error against the oracle on a sample of the batch
+    # tensor-core workload: the plain FP32 plan on the same buffers, the plain
+    # per-call FP32 path, and every result of both plans against the oracle
     precision = None
+    errors = None
     if tc:
         p32 = fbfft.Plan(dims, batch, scale_inv_n=wl["inverse"], stream=stream)
-        for i in range(args.warmup):
-            step(i, p32)
-        barrier()
-        ev0.record(stream)
-        for i in range(args.steps):
-            step(i, p32)
-        ev1.record(stream)
-        barrier()
-        ms32 = max_over_ranks(ev0.elapsed_time(ev1) / args.steps, dist, dev)
+        ms32, _ = event_timed(ctx, lambda i: step(i, p32), args.steps, args.warmup)
         precision = {"fp32_path": {"value": round(whole_job_rate(world, bytes_step, ms32) / 1e9, 3), "unit": "GB/s",
                                    "ms_per_step": round(ms32, 5)},
                      "speedup_vs_fp32_path": round(ms32 / ms, 3), "tolerance_rel_l2": 5e-5}
@@ -461,15 +565,7 @@ def run_gpu(args, wl: dict) -> None:
             a, b = xin[i % nbuf], xout[i % nbuf]
             for k in range(batch):
                 p1.exec_ptr(a.data_ptr() + k * n * 8, b.data_ptr() + k * n * 8, fbfft.FORWARD)
-        for i in range(args.warmup):
-            step_per_call(i)
-        barrier()
-        ev0.record(stream)
-        for i in range(args.steps):
-            step_per_call(i)
-        ev1.record(stream)
-        barrier()
-        ms1 = max_over_ranks(ev0.elapsed_time(ev1) / args.steps, dist, dev)
+        ms1, _ = event_timed(ctx, step_per_call, args.steps, args.warmup)
         p1.check()
         p1.close()
         precision["per_call_fp32_path"] = {"value": round(whole_job_rate(world, bytes_step, ms1) / 1e9, 3),
@@ -477,16 +573,18 @@ def run_gpu(args, wl: dict) -> None:
         precision["speedup_vs_per_call_fp32_path"] = round(ms1 / ms, 3)
         if rank == 0 and not args.quick:
             import oracle
-            # every result of input buffer 0 against the FP64 oracle
             x = host_inputs[0].reshape(batch, n)
-            ref = oracle.fft(x.astype(np.complex128), dims, fbfft.FORWARD, False, len(os.sched_getaffinity(0)))
+            ref = oracle.fft(x.astype(np.complex128), dims, fbfft.FORWARD, False, threads).reshape(batch, n)
             for name, p in (("tensor_cores", plan), ("fp32", p32)):
                 y = p.exec(xin[0], None, fbfft.FORWARD)
                 torch.cuda.synchronize(dev)
-                e = oracle.rel_l2(y.cpu().numpy().reshape(batch, n), ref.reshape(batch, n))
+                e = oracle.rel_l2(y.cpu().numpy().reshape(batch, n), ref)
                 precision[f"{name}_max_rel_l2"] = float(e.max())
                 precision[f"{name}_median_rel_l2"] = float(np.median(e))
                 precision[f"{name}_rel_l2_per_result"] = [float(f"{v:.3e}") for v in e]
+                if name == "tensor_cores":
+                    errors = {"forward_max_rel_l2": float(e.max()), "forward_median_rel_l2": float(np.median(e)),
+                              "tolerance_rel_l2": 5e-5, "items": batch, "pass": bool(e.max() <= 5e-5)}
             precision["errors"] = f"all {batch} results of input buffer 0 against the FP64 oracle"
         p32.close()
 
@@ -496,7 +594,7 @@ def run_gpu(args, wl: dict) -> None:
     if not args.quick:
         hbuf = [torch.from_numpy(h.reshape(-1)).pin_memory() for h in host_inputs[:2]]
         hres = [torch.empty_like(hbuf[0]).pin_memory() for _ in range(2)]
-        e2e_steps = max(3, min(args.steps, 20))
+        e2e_steps = max(3, min(args.steps, 20 if headline else 5))
 
         def e2e_step(i):
             src, dst = hbuf[i % 2], hres[i % 2]
@@ -506,40 +604,42 @@ def run_gpu(args, wl: dict) -> None:
 
         for i in range(2):
             e2e_step(i)
-        barrier()
+        ctx.barrier()
         t0 = time.perf_counter()
         for i in range(e2e_steps):
             e2e_step(i)
-        barrier()
-        e2e_ms = (time.perf_counter() - t0) / e2e_steps * 1e3
-        e2e_ms = max_over_ranks(e2e_ms, dist, dev)
+        ctx.barrier()
+        e2e_ms = ctx.max((time.perf_counter() - t0) / e2e_steps * 1e3)
         io = 8 * n * batch * execs
         e2e = {"value": round(whole_job_rate(world, bytes_step, e2e_ms) / 1e9, 3), "unit": "GB/s",
                "h2d_bytes_per_step": io, "d2h_bytes_per_step": io, "ms_per_step": e2e_ms,
                "path": "fb_fft_exec_host (pinned host arrays)" + (", forward then inverse" if wl["inverse"] else ", forward")}
 
-    # error against the oracle on the first batch items of input buffer 0
-    errors = None
+    # error against the oracle: every batch item of input buffer 0 (the first
+    # ERR_ITEMS items of very large batches)
     if rank == 0 and not args.quick and not tc:
         import oracle
-        k = min(batch, 4)
-        thr = len(os.sched_getaffinity(0))
+        k = error_items(batch, n)
         x0 = host_inputs[0].reshape(batch, n)[:k]
         y = plan.exec(xin[0], None, fbfft.FORWARD)
         torch.cuda.synchronize(dev)
         yk = y.cpu().numpy().reshape(batch, n)[:k]
-        ref = oracle.fft(x0.astype(np.complex128).reshape([k] + dims), dims, fbfft.FORWARD, False, thr)
+        ref = oracle.fft(x0.astype(np.complex128).reshape([k] + dims), dims, fbfft.FORWARD, False, threads)
         e = oracle.rel_l2(yk, ref.reshape(k, n))
+        tol = 2e-6 * math.log2(n)
         errors = {"forward_max_rel_l2": float(e.max()), "forward_median_rel_l2": float(np.median(e)),
-                  "tolerance_rel_l2": 2e-6 * math.log2(n), "items": k}
+                  "tolerance_rel_l2": tol, "items": k, "of_items": batch}
+        ok = e.max() <= tol
         if wl["inverse"]:
             z = plan.exec(y, None, fbfft.INVERSE)
             torch.cuda.synchronize(dev)
             zk = z.cpu().numpy().reshape(batch, n)[:k]
-            refi = oracle.fft(yk.astype(np.complex128).reshape([k] + dims), dims, fbfft.INVERSE, True, thr)
+            refi = oracle.fft(yk.astype(np.complex128).reshape([k] + dims), dims, fbfft.INVERSE, True, threads)
             ei = oracle.rel_l2(zk, refi.reshape(k, n))
             rt = oracle.rel_l2(zk, x0.astype(np.complex128))
             errors.update({"inverse_max_rel_l2": float(ei.max()), "round_trip_max_rel_l2": float(rt.max())})
+            ok = ok and ei.max() <= tol and rt.max() <= tol
+        errors["pass"] = bool(ok)
 
     # library context: cuFFT through torch.fft on the same buffers (not part of the product)
     context = None
@@ -551,45 +651,20 @@ def run_gpu(args, wl: dict) -> None:
             if wl["inverse"]:
                 torch.fft.ifftn(yy, dim=axes)
 
-        for i in range(args.warmup):
-            lib_step(i)
-        barrier()
-        ev0.record(stream)
-        for i in range(args.steps):
-            lib_step(i)
-        ev1.record(stream)
-        barrier()
-        lib_ms = ev0.elapsed_time(ev1) / args.steps
+        lib_ms, _ = event_timed(ctx, lib_step, args.steps, args.warmup)
         context = {"library": "cuFFT via torch.fft on the same GPU and buffers (a reference point, not part of "
                               "this product)", "value": round(bytes_step / (lib_ms / 1e3) / 1e9, 3), "unit": "GB/s",
                    "ms_per_step": round(lib_ms, 5)}
 
+    line = None
     if rank == 0:
         peaks = load_peaks()
         value = whole_job_rate(world, bytes_step, ms) / 1e9
-        # dominant kernel: the pass role with the largest measured time
-        dom = max(passes, key=lambda r: r[1]) if passes else None
-        roofline = None
-        if dom and dom[2] > 0:
-            per_launch_ms = dom[1] / dom[2]
-            # one read + one write of what one launch covers (four-step passes
-            # run once per batch chunk, so a launch covers batch / chunks items)
-            launches_per_exec = dom[2] / (prof_steps * execs)
-            launch_bytes = 2 * 8.0 * n * batch / launches_per_exec
-            achieved = launch_bytes / (per_launch_ms / 1e3) / 1e9
-            tr = load_traffic(wl["name"])
-            roofline = {"bound": "hbm", "achieved": round(achieved, 2), "peak": peaks["hbm_gbs"],
-                        "unit": "GB/s", "frac": round(achieved / peaks["hbm_gbs"], 4),
-                        "traffic": tr["dram_bytes_per_launch"] if tr and tr.get("pass") == dom[0] else None,
-                        "kernel_pass": dom[0], "launch_ms": round(per_launch_ms, 5),
-                        "algorithmic_bytes_per_launch": launch_bytes,
-                        "peak_source": f"{peaks['source']} (MEASURED_PEAKS.json hbm_gbs, burst copy)"
-                        if peaks["source"] == "measured" else "fallback 6.8 TB/s"}
-        threads = len(os.sched_getaffinity(0))
+        roofline = roofline_of(passes, prof_steps, execs, 2 * 8.0 * n * batch, wl["name"], peaks)
         cpu_baseline = None
         if not args.quick:
-            cb = oracle_sample(wl, budget_s=float(args.cpu_budget), threads=threads)
-            st1 = oracle_single_thread(wl, budget_s=3.0)
+            cb = oracle_sample(wl, budget_s=float(args.cpu_budget if headline else args.cpu_budget_sub), threads=threads)
+            st1 = oracle_single_thread(wl, budget_s=3.0 if headline else 1.0)
             cpu_baseline = {"value": round(cb["value"], 4), "unit": "GB/s", "cores": threads, "kind": "oracle",
                             "sample": f"{cb['steps']} full step(s) of {wl['name']} by the FP64 oracle in "
                                       f"{cb['seconds']:.1f} s on {cpu_model()}",
@@ -600,10 +675,7 @@ def run_gpu(args, wl: dict) -> None:
             "metric": METRIC, "value": round(value, 3), "unit": "GB/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": round(ms, 5), "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f16 hi/lo products, f32 accumulate" if tc else "f32", "data": "synthetic",
-            "config": {"workload": wl["name"], "dims": dims, "batch": batch, "dtype_storage": "complex64",
-                       "l2": f"{nbuf} rotating input/output buffer pairs "
-                             f"({nbuf * 2 * 8 * n * batch / 2 ** 20:.0f} MiB) > 126 MB L2",
-                       "parallelism": "replicas" if world > 1 else "single GPU"},
+            "config": config_of(wl, world),
             "gflops": round(whole_job_rate(world, flops_step, ms) / 1e9, 2),
             "hbm_frac_effective": round(value / world / peaks["hbm_gbs"], 4),
             "roofline": roofline,
@@ -621,11 +693,8 @@ def run_gpu(args, wl: dict) -> None:
             line["errors_vs_oracle"] = errors
         if context:
             line["context"] = context
-        print(json.dumps(line), flush=True)
     plan.close()
-    if dist is not None:
-        dist.barrier()
-        dist.destroy_process_group()
+    return line
 
 
 def uneven_lengths(wl: dict) -> np.ndarray:
@@ -633,29 +702,19 @@ def uneven_lengths(wl: dict) -> np.ndarray:
     return inputs.uneven_lengths(count, lo, hi, wl["seed"])
 
 
-def run_gpu_many(args, wl: dict) -> None:
-    """Batched uneven 1-D lengths: one graph launch per step (fb_fft_plan_many)
-    against the plain per-call path (one fb_fft_exec per transform, plans
-    cached per length) on the same buffers."""
+def gpu_many(args, ctx: Ctx, wl: dict, headline: bool) -> dict:
+    """Batched uneven 1-D lengths: one exec of the autotuned batched plan
+    (fb_fft_plan_many) per step against the plain per-call path (one
+    fb_fft_exec per transform, plans cached per length) on the same buffers;
+    every transform checked against the oracle."""
     import torch
-
-    world, rank, local = dist_setup()
-    torch.cuda.set_device(local)
-    dev = torch.device("cuda", local)
-    dist = None
-    if world > 1:
-        import torch.distributed as dist
-        dist.init_process_group("nccl", device_id=dev)
-    from paper_2004_09883_gb300 import build as fbbuild
-    fbbuild.build()
-    from paper_2004_09883_gb300 import fbfft
-
+    fbfft = ctx.fb
+    dev, stream, world, rank = ctx.dev, ctx.stream, ctx.world, ctx.rank
     lens = uneven_lengths(wl)
-    stream = torch.cuda.current_stream(dev)
     _, total = fbfft.many_layout(lens)
     nbuf = 2
-    xin = [torch.from_numpy(inputs.uniform_c64((total,), wl["seed"] + 1000 * replica_rep(rank, r))).to(dev)
-           for r in range(nbuf)]
+    host_in = [inputs.uniform_c64((total,), wl["seed"] + 1000 * replica_rep(rank, r)) for r in range(nbuf)]
+    xin = [torch.from_numpy(h).to(dev) for h in host_in]
     xout = [torch.empty_like(xin[0]) for _ in range(nbuf)]
     # the library's autotuner picks the plan knobs on this workload (untimed;
     # --quick keeps the defaults so profiler runs stay short)
@@ -668,38 +727,16 @@ def run_gpu_many(args, wl: dict) -> None:
     bytes_step = float(sum(2 * 8 * int(n) for n in lens))
     flops_step = float(sum(5 * int(n) * math.log2(int(n)) for n in lens))
 
-    def barrier():
-        torch.cuda.synchronize(dev)
-        if dist is not None:
-            dist.barrier()
-        torch.cuda.synchronize(dev)
-
-    def timed(step, steps):
-        for i in range(args.warmup):
-            step(i)
-        barrier()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        l0 = fbfft.launch_count()
-        e0.record(stream)
-        for i in range(steps):
-            step(i)
-        e1.record(stream)
-        barrier()
-        return max_over_ranks(e0.elapsed_time(e1) / steps, dist, dev), fbfft.launch_count() - l0
-
     def batched(i):
         plan.exec_ptr(xin[i % nbuf].data_ptr(), xout[i % nbuf].data_ptr(), fbfft.FORWARD)
 
-    clocks = ClockSampler(local) if rank == 0 and not args.quick else None
+    clocks = ClockSampler(ctx.local) if rank == 0 and not args.quick else None
     wall0 = time.time()
-    ms, launches = timed(batched, args.steps)
+    ms, launches = event_timed(ctx, batched, args.steps, args.warmup)
     wall1 = time.time()
     plan.check()
-
-    def batched_default(i):
-        default_plan.exec_ptr(xin[i % nbuf].data_ptr(), xout[i % nbuf].data_ptr(), fbfft.FORWARD)
-
-    ms_default, _ = timed(batched_default, max(3, min(args.steps, 20)))
+    ms_default, _ = event_timed(ctx, lambda i: default_plan.exec_ptr(
+        xin[i % nbuf].data_ptr(), xout[i % nbuf].data_ptr(), fbfft.FORWARD), max(3, min(args.steps, 20)), 3)
     # the plain per-call path: one exec per transform on the same data
     plans = {}
     for n in sorted(set(int(x) for x in lens)):
@@ -711,11 +748,24 @@ def run_gpu_many(args, wl: dict) -> None:
         for n, o in zip(lens, offs):
             plans[int(n)].exec_ptr(a + 8 * int(o), b + 8 * int(o), fbfft.FORWARD)
 
-    plain_steps = max(3, min(args.steps, 20))
-    ms_plain, _ = timed(per_call, plain_steps)
+    ms_plain, _ = event_timed(ctx, per_call, max(3, min(args.steps, 20)), 3)
     clk = clocks.summary(wall0, wall1) if clocks else None
     if clocks:
         clocks.stop()
+    errors = None
+    if rank == 0 and not args.quick:
+        y = plan.exec(xin[0], None, fbfft.FORWARD)
+        torch.cuda.synchronize(dev)
+        yh = y.cpu().numpy()
+        import oracle
+        refs = oracle_each([(host_in[0][o:o + n], [int(n)]) for o, n in zip(offs, lens)], host_threads())
+        e = np.array([oracle.rel_l2(yh[o:o + n], r)[0] for o, n, r in zip(offs, lens, refs)])
+        tols = np.array([2e-6 * math.log2(int(n)) for n in lens])
+        errors = {"forward_max_rel_l2": float(e.max()), "forward_median_rel_l2": float(np.median(e)),
+                  "max_error_over_tolerance": float((e / tols).max()),
+                  "tolerance_rel_l2": "2e-6 log2 N per transform", "items": len(lens), "of_items": len(lens),
+                  "pass": bool((e <= tols).all())}
+    line = None
     if rank == 0:
         peaks = load_peaks()
         value = whole_job_rate(world, bytes_step, ms) / 1e9
@@ -726,31 +776,37 @@ def run_gpu_many(args, wl: dict) -> None:
             "config": {"workload": wl["name"], "transforms": len(lens), "distinct_lengths": len(plans),
                        "elements": int(sum(int(n) for n in lens)), "l2": "2 rotating buffer pairs of "
                        f"{total * 8 / 2 ** 20:.0f} MiB each > 126 MB L2", "parallelism": "replicas" if world > 1
-                       else "single GPU", "path": "fb_fft_plan_many, one CUDA graph launch per step"},
+                       else "single GPU", "path": "fb_fft_plan_many, autotuned, one exec per step"},
             "gflops": round(whole_job_rate(world, flops_step, ms) / 1e9, 2),
             "hbm_frac_effective": round(value / world / peaks["hbm_gbs"], 4),
+            "roofline": {"bound": "hbm", "achieved": round(bytes_step / (ms / 1e3) / 1e9, 2),
+                         "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                         "frac": round(bytes_step / (ms / 1e3) / 1e9 / peaks["hbm_gbs"], 4), "traffic": None,
+                         "kernel_pass": "whole exec", "launches_per_exec": round(launches / max(1, args.steps), 2),
+                         "algorithmic_bytes_per_launch": bytes_step,
+                         "basis": "one read + one write of every transform / exec time (all launches of one exec)"},
             "plain_per_call": {"value": round(whole_job_rate(world, bytes_step, ms_plain) / 1e9, 3), "unit": "GB/s",
                                "ms_per_step": round(ms_plain, 4), "execs_per_step": len(lens)},
             "speedup_vs_plain_per_call": round(ms_plain / ms, 3),
             "autotuned": tuned.as_dict(), "untuned_plan_ms_per_step": round(ms_default, 4),
             "cpu_baseline": None if args.quick else (lambda cb: {
-                "value": round(cb["value"], 4), "unit": "GB/s", "cores": len(os.sched_getaffinity(0)),
+                "value": round(cb["value"], 4), "unit": "GB/s", "cores": host_threads(),
                 "kind": "oracle", "sample": f"first {cb['transforms']} transforms of the workload by the FP64 "
                                             f"oracle in {cb['seconds']:.1f} s on {cpu_model()}"})(
-                oracle_uneven_sample(wl, float(args.cpu_budget), len(os.sched_getaffinity(0)))),
+                oracle_uneven_sample(wl, float(args.cpu_budget if headline else args.cpu_budget_sub),
+                                     host_threads())),
             "gpu_launches": int(launches), "clocks": clk, "kernel_hash": kernel_hash(),
         }
-        print(json.dumps(line), flush=True)
+        if errors:
+            line["errors_vs_oracle"] = errors
     for p in plans.values():
         p.close()
     plan.close()
     default_plan.close()
-    if dist is not None:
-        dist.barrier()
-        dist.destroy_process_group()
+    return line
 
 
-def run_gpu_serving(args, wl: dict) -> None:
+def gpu_serving(args, ctx: Ctx, wl: dict, headline: bool) -> dict:
     """Request server against the plain per-call path on one arrival trace:
     saturation throughput (all requests queued at t=0), then Poisson arrivals
     at fractions of the plain path's saturation rate, p50/p99 latency of both.
@@ -758,17 +814,9 @@ def run_gpu_serving(args, wl: dict) -> None:
     completion seen by the host), plus a host-array variant (pinned host
     buffers, copies through the server's staging)."""
     import torch
-
-    world, rank, local = dist_setup()
-    torch.cuda.set_device(local)
-    dev = torch.device("cuda", local)
-    dist = None
-    if world > 1:
-        import torch.distributed as dist
-        dist.init_process_group("nccl", device_id=dev)
-    from paper_2004_09883_gb300 import build as fbbuild
-    fbbuild.build()
-    from paper_2004_09883_gb300 import fbfft, serving
+    from paper_2004_09883_gb300 import serving
+    fbfft = ctx.fb
+    world, rank = ctx.world, ctx.rank
 
     cfg = wl["serving"]
     seed = wl["seed"] + 1000 * replica_rep(rank, 0)
@@ -787,24 +835,31 @@ def run_gpu_serving(args, wl: dict) -> None:
     serving.run_served(srv, wh, zero_h, host_io=True)
     serving.run_plain(plans, wh, zero_h, host_io=True)
 
-    def barrier():
-        torch.cuda.synchronize(dev)
-        if dist is not None:
-            dist.barrier()
-        torch.cuda.synchronize(dev)
-
-    clocks = ClockSampler(local) if rank == 0 else None
-    barrier()
+    steps = max(3, min(args.steps, 20))
+    clocks = ClockSampler(ctx.local) if rank == 0 else None
+    ctx.barrier()
     wall0 = time.time()
     l0 = fbfft.launch_count()
-    sat = [serving.run_served(srv, w, zero) for _ in range(args.steps)]
-    launches = (fbfft.launch_count() - l0) // max(1, args.steps)
+    sat = [serving.run_served(srv, w, zero) for _ in range(steps)]
+    launches = (fbfft.launch_count() - l0) // steps
     wall1 = time.time()
     clk = clocks.summary(wall0, wall1) if clocks else None
     if clocks:
         clocks.stop()
-    sat_plain = [serving.run_plain(plans, w, zero) for _ in range(max(1, min(args.steps, 3)))]
-    barrier()
+    # the served results of the last replay against the oracle
+    errors = None
+    if rank == 0:
+        k = min(cfg["checked"], len(shapes))
+        import oracle
+        refs = oracle_each([(w.x[i].cpu().numpy(), list(shapes[i])) for i in range(k)], host_threads())
+        e = np.array([oracle.rel_l2(w.y[i].cpu().numpy(), refs[i].reshape(-1))[0] for i in range(k)])
+        tols = np.array([2e-6 * math.log2(max(2, w.n[i])) for i in range(k)])
+        errors = {"forward_max_rel_l2": float(e.max()), "forward_median_rel_l2": float(np.median(e)),
+                  "max_error_over_tolerance": float((e / tols).max()),
+                  "tolerance_rel_l2": "2e-6 log2 N per request", "items": k, "of_items": len(shapes),
+                  "pass": bool((e <= tols).all())}
+    sat_plain = [serving.run_plain(plans, w, zero) for _ in range(3)]
+    ctx.barrier()
     best = max(sat, key=lambda r: r["throughput_req_s"])
     best_plain = max(sat_plain, key=lambda r: r["throughput_req_s"])
     rate_plain = best_plain["throughput_req_s"]
@@ -824,7 +879,8 @@ def run_gpu_serving(args, wl: dict) -> None:
     host_half = serving.run_served(srv, wh, arr, host_io=True)
     host_half_plain = serving.run_plain(plans, wh, arr, host_io=True)
     st = srv.stats()
-    value = max_over_ranks(best["throughput_gbs"], dist, dev)
+    value = ctx.max(best["throughput_gbs"])
+    line = None
     if rank == 0:
         nb = w.bytes_moved()
         kinds = {1: 0, 2: 0, 3: 0}
@@ -832,7 +888,7 @@ def run_gpu_serving(args, wl: dict) -> None:
             kinds[len(s)] += 1
         line = {
             "metric": METRIC, "value": round(value * world, 3), "unit": "GB/s", "n_gpus": world,
-            "steps": args.steps, "warmup": args.warmup,
+            "steps": steps, "warmup": args.warmup,
             "ms_per_step": round(best["wall_s"] * 1e3, 3), "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": wl["name"], "requests": len(shapes), "rank_mix": kinds,
@@ -845,7 +901,10 @@ def run_gpu_serving(args, wl: dict) -> None:
                            "plain_req_s": round(rate_plain, 1),
                            "served_gbs": round(best["throughput_gbs"], 2),
                            "plain_gbs": round(best_plain["throughput_gbs"], 2),
-                           "speedup_vs_plain": round(best["throughput_req_s"] / rate_plain, 3)},
+                           "speedup_vs_plain": round(best["throughput_req_s"] / rate_plain, 3),
+                           "served_p50_ms": round(best["p50_ms"], 4), "served_p99_ms": round(best["p99_ms"], 4),
+                           "plain_p50_ms": round(best_plain["p50_ms"], 4),
+                           "plain_p99_ms": round(best_plain["p99_ms"], 4)},
             "sweep_device_resident": sweep,
             "host_arrays": {"requests": len(hshapes),
                             "saturation_req_s": {"served": round(host_sat["throughput_req_s"], 1),
@@ -855,44 +914,79 @@ def run_gpu_serving(args, wl: dict) -> None:
                                                 "plain_p50_ms": round(host_half_plain["p50_ms"], 4),
                                                 "plain_p99_ms": round(host_half_plain["p99_ms"], 4)}},
             "server_stats": {k: st[k] for k in ("plans", "plan_builds", "arena_peak", "max_in_flight")},
+            "roofline": None,
+            "roofline_note": "a mix of 3000+ shapes: the per-kernel rooflines are those of the other workloads",
             "gpu_launches": int(launches), "clocks": clk, "kernel_hash": kernel_hash(),
+            "errors_vs_oracle": errors,
             "cpu_baseline": (lambda cb: {
-                "value": round(cb["value"], 4), "unit": "GB/s", "cores": len(os.sched_getaffinity(0)),
+                "value": round(cb["value"], 4), "unit": "GB/s", "cores": host_threads(),
                 "kind": "oracle", "sample": f"first {cb['transforms']} requests of the mix by the FP64 oracle, "
                                             f"one after another, in {cb['seconds']:.1f} s on {cpu_model()}"})(
-                oracle_uneven_sample(wl, float(args.cpu_budget), len(os.sched_getaffinity(0)))),
+                oracle_uneven_sample(wl, float(args.cpu_budget if headline else args.cpu_budget_sub),
+                                     host_threads())),
         }
-        print(json.dumps(line), flush=True)
     srv.close()
     for p in plans.values():
         p.close()
-    if dist is not None:
-        dist.barrier()
-        dist.destroy_process_group()
+    return line
+
+
+def run_workload(args, ctx: Ctx, key: str, headline: bool) -> dict:
+    wl = WORKLOADS[key]
+    if wl.get("lengths"):
+        return gpu_many(args, ctx, wl, headline)
+    if wl.get("serving"):
+        return gpu_serving(args, ctx, wl, headline)
+    return gpu_regular(args, ctx, wl, headline)
+
+
+# keys a nested workload line repeats from the headline line
+_SHARED_KEYS = ("metric", "unit", "n_gpus", "higher_is_better", "scaling", "vs_baseline", "data", "kernel_hash")
+
+
+def run_gpu(args) -> None:
+    ctx = Ctx()
+    if args.workload:
+        line = run_workload(args, ctx, args.workload, True)
+    else:
+        t0 = time.time()
+        line = run_workload(args, ctx, HEADLINE, True)
+        subs = {}
+        for key in SUITE:
+            t = time.time()
+            sub = run_workload(args, ctx, key, False)
+            if ctx.rank == 0:
+                sub = {k: v for k, v in sub.items() if k not in _SHARED_KEYS}
+                sub["wall_s"] = round(time.time() - t, 1)
+                subs[key] = sub
+        if ctx.rank == 0:
+            line["workloads"] = subs
+            line["wall_s_all_workloads"] = round(time.time() - t0, 1)
+    if ctx.rank == 0:
+        print(json.dumps(line), flush=True)
+    ctx.close()
 
 
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=200)
-    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="3d", choices=sorted(WORKLOADS))
+    ap.add_argument("--workload", default=None, choices=sorted(WORKLOADS),
+                    help="one workload alone (default: the headline with every other workload nested)")
     ap.add_argument("--cpu-budget", default=10.0, type=float, help="seconds of oracle time for cpu_baseline")
+    ap.add_argument("--cpu-budget-sub", default=3.0, type=float,
+                    help="seconds of oracle time for the cpu_baseline of each nested workload")
     ap.add_argument("--quick", action="store_true",
-                    help="timed loop only (no pre-roll, e2e or CPU baseline): for profiler runs")
+                    help="timed loop only (no pre-roll, e2e, error check or CPU baseline): for profiler runs")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
-    wl = WORKLOADS[args.workload]
     if args.impl == "reference":
-        run_reference(args, wl)
-    elif wl.get("lengths"):
-        run_gpu_many(args, wl)
-    elif wl.get("serving"):
-        run_gpu_serving(args, wl)
+        run_reference(args, WORKLOADS[args.workload or HEADLINE])
     else:
-        run_gpu(args, wl)
+        run_gpu(args)
 
 
 if __name__ == "__main__":

@@ -413,30 +413,39 @@ int fb_fft_server_stats_get(fb_fft_server_t srv, fb_fft_server_stats* stats);
 int fb_fft_server_destroy(fb_fft_server_t srv);
 
 /*
- * fb_fft_exec_1d_noalloc -- batched 1-D transform that allocates nothing.
- * The paper has no counterpart: this serves callers that cannot call
- * cudaMalloc (code running while a CUDA graph is being captured, real-time
- * or signal-context code that must stay out of allocators, embedders whose
- * device memory belongs to another allocator), for whom fb_fft_plan's
- * device-resident twiddle tables and scratch are not an option.
+ * fb_fft_exec_1d_noalloc -- batched 1-D transform that allocates no device
+ * memory.  The paper has no counterpart.  It is for callers that cannot call
+ * cudaMalloc: a plug-in or embedded library whose host application owns all
+ * device memory through its own allocator (and may forbid driver
+ * allocations), real-time code that must not enter an allocator that can
+ * block, or code that must run in a device-memory budget fixed in advance.
+ * For them fb_fft_plan's device-resident twiddle tables and scratch are not
+ * an option.
  *   in, out    device pointers, batch*n complex64 values each, 8-byte aligned;
  *              out == in runs in place, partial overlap is INVALID_ARG.
  *   n          5-smooth length, 1 <= n <= 4194304 (2^22) and splittable as the
  *              plan API's four-step (fb_fft_split); larger n is
- *              FB_FFT_ERR_UNSUPPORTED_SIZE.
+ *              FB_FFT_ERR_UNSUPPORTED_SIZE.  n = 1 is a copy.
  *   batch      >= 0 transforms back to back (any count: they run in chunks).
- *   direction  FB_FFT_FORWARD / FB_FFT_INVERSE;  flags 0 or FB_FFT_SCALE_INV_N.
+ *   direction  FB_FFT_FORWARD / FB_FFT_INVERSE.
+ *   flags      0, FB_FFT_SCALE_INV_N, and/or FB_FFT_NOALLOC_CHECK: wait for
+ *              the transform to finish (synchronises `stream`) and return
+ *              FB_FFT_ERR_TIMEOUT if one of its device-side waits gave up.
+ *              Without it the call returns once the work is enqueued and
+ *              a timed-out wait goes unreported.
  *   stream     cudaStream_t (NULL = legacy default stream).
- * Asynchronous on `stream`.  Twiddle tables and the four-step intermediate
- * live in one file-scope device array of the library (32 MiB + 256 KiB + 256
- * bytes, held by every GPU that loads the library until the process exits).
- * The first call on each device looks up that array's device address
- * (cudaGetSymbolAddress), so make it before any stream capture.  Every call
- * reuses and overwrites the array: calls that overlap on the GPU race, so
- * serialise them (one stream, or events).  A device-side wait that times out
- * is recorded in the array but not reported by this call.
- * Errors: INVALID_ARG, UNSUPPORTED_SIZE, CUDA.
+ * Runs the same kernels, tiles and four-step split as fb_fft_plan for this
+ * length, asynchronously on `stream`.  Twiddle tables, the four-step
+ * intermediate and the error word live in one file-scope device array of the
+ * library (32 MiB + 256 KiB + 256 bytes, held by every GPU that loads the
+ * library until the process exits).  The first call on each device looks up
+ * that array's device address (cudaGetSymbolAddress) with the device current.
+ * Every call reuses and overwrites the array: calls that overlap on the GPU
+ * race, so serialise them (one stream, or events).  The first launch of each
+ * kernel in the process also sets its shared-memory limit.
+ * Errors: INVALID_ARG, UNSUPPORTED_SIZE, CUDA, TIMEOUT (with the check flag).
  */
+#define FB_FFT_NOALLOC_CHECK 0x100u
 int fb_fft_exec_1d_noalloc(const void* in, void* out, long long n, long long batch, int direction,
                            unsigned flags, void* stream);
 

@@ -156,6 +156,10 @@ long long plane_smem_bytes(int lg1, int lg2, int threads);
 // Clusters of a cluster kernel that fit the GPU at once.
 cudaError_t line_cluster_occupancy(const LineKernel& k, size_t smem, int* clusters);
 LineKernel line_kernel_mixed(bool forward, int lg2);
+// Raise a kernel's dynamic shared-memory limit to the device's opt-in maximum,
+// once per (kernel, device); split_regs > 0 also checks the kernel's register
+// count (see LineKernel::split_regs).
+cudaError_t kernel_smem_optin(const void* fn, int split_regs);
 // Launch / occupancy / name of a table entry (shared-memory opt-in handled inside).
 cudaError_t line_launch(const LineKernel& k, const LineArgs& a, long long grid, size_t smem, cudaStream_t stream);
 cudaError_t line_occupancy(const LineKernel& k, size_t smem, int* blocks_per_sm);

@@ -1,8 +1,8 @@
 // fft_kernels.cu -- the generic line-pass kernel, the kernel table and the
 // launch path shared by all line-pass kernels.
+#include <cstdint>
 #include <cstdlib>
 #include <mutex>
-#include <unordered_map>
 
 #include "fft_p2.cuh"
 
@@ -51,6 +51,46 @@ LineKernel line_kernel_p2tc(int threads, bool forward, int lg, int io)
     return forward ? line_kernel_p2tc_fwd(threads, lg, io) : line_kernel_p2tc_inv(threads, lg, io);
 }
 
+// Kernels whose shared-memory limit is set, per device: a fixed open-addressing
+// table (no heap), keyed by the kernel's address.  A full table only means
+// the attribute is set again at every launch.
+cudaError_t kernel_smem_optin(const void* fn, int split_regs)
+{
+    constexpr int kSlots = 2048;
+    static std::mutex mu;
+    static const void* keys[kSlots];
+    static unsigned long long masks[kSlots];
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    const unsigned long long bit = 1ULL << (dev & 63);
+    std::lock_guard<std::mutex> g(mu);
+    int slot = -1;
+    for (int probe = 0, h = (int)(((uintptr_t)fn >> 4) % kSlots); probe < kSlots; ++probe, h = (h + 1) % kSlots) {
+        if (keys[h] == fn || keys[h] == nullptr) {
+            slot = h;
+            break;
+        }
+    }
+    if (slot >= 0 && keys[slot] == fn && (masks[slot] & bit)) return cudaSuccess;
+    int optin = 0;
+    e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    if (e != cudaSuccess) return e;
+    cudaFuncAttributes fa;
+    e = cudaFuncGetAttributes(&fa, fn);
+    if (e != cudaSuccess) return e;
+    // a kernel that rebalances registers with setmaxnreg must get exactly the
+    // pool its split was sized for; with fewer, setmaxnreg.inc would never return
+    if (split_regs > 0 && fa.numRegs != split_regs) return cudaErrorInvalidKernelImage;
+    e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, optin - (int)fa.sharedSizeBytes);
+    if (e != cudaSuccess) return e;
+    if (slot >= 0) {
+        keys[slot] = fn;
+        masks[slot] |= bit;
+    }
+    return cudaSuccess;
+}
+
 namespace {
 bool pdl_enabled()
 {
@@ -63,32 +103,7 @@ bool pdl_enabled()
 
 // The opt-in dynamic shared-memory limit is a per-device function attribute:
 // set it once per (kernel, device).
-cudaError_t ensure_smem_attr(const LineKernel& k)
-{
-    static std::mutex mu;
-    static std::unordered_map<const void*, unsigned long long> done;
-    int dev = 0;
-    cudaError_t e = cudaGetDevice(&dev);
-    if (e != cudaSuccess) return e;
-    const unsigned long long bit = 1ULL << (dev & 63);
-    std::lock_guard<std::mutex> g(mu);
-    unsigned long long& mask = done[(const void*)k.fn];
-    if (mask & bit) return cudaSuccess;
-    int optin = 0;
-    e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-    if (e != cudaSuccess) return e;
-    cudaFuncAttributes fa;
-    e = cudaFuncGetAttributes(&fa, (const void*)k.fn);
-    if (e != cudaSuccess) return e;
-    // a kernel that rebalances registers with setmaxnreg must get exactly the
-    // pool its split was sized for; with fewer, setmaxnreg.inc would never return
-    if (k.split_regs > 0 && fa.numRegs != k.split_regs) return cudaErrorInvalidKernelImage;
-    e = cudaFuncSetAttribute((const void*)k.fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             optin - (int)fa.sharedSizeBytes);
-    if (e != cudaSuccess) return e;
-    mask |= bit;
-    return cudaSuccess;
-}
+cudaError_t ensure_smem_attr(const LineKernel& k) { return kernel_smem_optin((const void*)k.fn, k.split_regs); }
 }  // namespace
 
 cudaError_t line_launch(const LineKernel& k, const LineArgs& a, long long grid, size_t smem, cudaStream_t stream)

@@ -2,8 +2,6 @@
 // launch (k_fft_mixed_multi), one kernel per direction and power-of-two factor,
 // with its launch and occupancy helpers.
 #include <cstdlib>
-#include <mutex>
-#include <unordered_map>
 
 #include "fft_device.cuh"
 
@@ -32,29 +30,7 @@ MultiFn multi_fn(int lg2)
 }
 
 // Opt-in dynamic shared memory, once per (kernel, device).
-cudaError_t prepare(MultiFn fn)
-{
-    static std::mutex mu;
-    static std::unordered_map<const void*, unsigned long long> done;
-    int dev = 0;
-    cudaError_t e = cudaGetDevice(&dev);
-    if (e != cudaSuccess) return e;
-    const unsigned long long bit = 1ULL << (dev & 63);
-    std::lock_guard<std::mutex> g(mu);
-    unsigned long long& mask = done[(const void*)fn];
-    if (mask & bit) return cudaSuccess;
-    int optin = 0;
-    e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-    if (e != cudaSuccess) return e;
-    cudaFuncAttributes fa;
-    e = cudaFuncGetAttributes(&fa, (const void*)fn);
-    if (e != cudaSuccess) return e;
-    e = cudaFuncSetAttribute((const void*)fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             optin - (int)fa.sharedSizeBytes);
-    if (e != cudaSuccess) return e;
-    mask |= bit;
-    return cudaSuccess;
-}
+cudaError_t prepare(MultiFn fn) { return kernel_smem_optin((const void*)fn, 0); }
 
 bool pdl_on()
 {

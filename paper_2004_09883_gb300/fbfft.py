@@ -19,6 +19,7 @@ FORWARD = -1
 INVERSE = 1
 SCALE_INV_N = 0x1
 TENSOR_CORES = 0x2
+NOALLOC_CHECK = 0x100  # fb_fft_exec_1d_noalloc: wait and report a timed-out device wait
 MAX_SMEM_LEN = 4096
 MAX_1D_LEN = 4096 * 4096
 
@@ -425,14 +426,18 @@ def autotune_many(lengths, x, out, direction: int = FORWARD, scale_inv_n: bool =
     return best, ms.value
 
 
-def exec_1d_noalloc(x, out, n: int, batch: int, direction: int = FORWARD, scale_inv_n: bool = False):
+def exec_1d_noalloc(x, out, n: int, batch: int, direction: int = FORWARD, scale_inv_n: bool = False,
+                    check: bool = False):
     """Batched 1-D transform through fb_fft_exec_1d_noalloc: no plan, no
     device allocation (the library's static workspace is used), on the
-    current torch stream.  ``x`` and ``out`` are complex64 CUDA tensors."""
+    current torch stream.  ``x`` and ``out`` are complex64 CUDA tensors.
+    ``check`` waits for the transform and raises FFTError (status
+    FB_FFT_ERR_TIMEOUT) if one of its device-side waits gave up."""
     import torch
     s = torch.cuda.current_stream(x.device).cuda_stream
+    flags = (SCALE_INV_N if scale_inv_n else 0) | (NOALLOC_CHECK if check else 0)
     _check(lib.fb_fft_exec_1d_noalloc(_vp(x.data_ptr()), _vp(out.data_ptr()), int(n), int(batch), int(direction),
-                                      SCALE_INV_N if scale_inv_n else 0, _vp(s)), "fb_fft_exec_1d_noalloc")
+                                      flags, _vp(s)), "fb_fft_exec_1d_noalloc")
     return out
 
 

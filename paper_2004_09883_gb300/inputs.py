@@ -23,6 +23,7 @@ WORKLOAD_3D_256x256x128 = 1      # 3-D 256x256x128, standard normal, fwd then in
 WORKLOAD_UNEVEN_4096 = 2         # 4096 uneven 1-D lengths in [64, 65536], uniform
 WORKLOAD_1D_2P20x32 = 3          # 1-D N=2^20, batch 32, standard normal
 WORKLOAD_SERVING = 4             # serving mix, uniform
+WORKLOAD_GRID_2048x2048 = 5      # 2-D 2048x2048 (the paper's FFT grid), standard normal
 
 
 def seed_for(workload: int, rep: int = 0) -> int:
