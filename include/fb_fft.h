@@ -122,11 +122,20 @@ int fb_fft_set_graph(fb_fft_plan_t plan, int enable);
  *   odd_radices_first  lengths with factors 3/5 (generic kernel): 1 runs the 5s and 3s
  *                      before the power-of-two radices
  *   max_lines          generic kernel: at most this many lines per tile (0 = no extra cap)
- *   per_length         1: one launch per length group for every kernel; 0 (default):
- *                      passes of lengths with a factor 3 or 5 that share a
- *                      power-of-two factor run as one launch (up to 64 lengths
- *                      each), four-step groups with disjoint scratch, in two phases
- *                      (single passes and four-step columns, then four-step rows)
+ *   engine             0 (default): one kernel for every pass, two launches per
+ *                      exec -- phase 0 all single passes and four-step columns,
+ *                      phase 1 all four-step rows -- over a device job table (each
+ *                      job one length group or four-step chunk, lines up to 2048
+ *                      points; longer lengths split into two such jobs).  Taken
+ *                      whenever every length fits it, else engine 1.
+ *                      1: the per-kernel schedule below (side streams, CUDA graph).
+ *   per_length         engine 1: one launch per length group for every kernel
+ *                      (1), or (0, default) passes of lengths with a factor 3 or 5
+ *                      that share a power-of-two factor run as one launch (up to
+ *                      64 lengths each), four-step groups with disjoint scratch, in
+ *                      two phases (single passes and four-step columns, then
+ *                      four-step rows).  per_length = 1 selects engine 1.
+ *   streams, use_graph, odd_radices_first, max_lines: engine 1 only.
  */
 typedef struct fb_fft_many_opts {
     int streams;
@@ -135,6 +144,7 @@ typedef struct fb_fft_many_opts {
     int odd_radices_first;
     int max_lines;
     int per_length;
+    int engine;
 } fb_fft_many_opts;
 int fb_fft_plan_many_ex(fb_fft_plan_t* plan, int count, const long long* lengths, unsigned flags, void* stream,
                         const fb_fft_many_opts* opts);
@@ -144,8 +154,9 @@ int fb_fft_plan_many_ex(fb_fft_plan_t* plan, int count, const long long* lengths
  * (the paper's verification step, Sec. 3.4 / Sec. 4.2: measure candidate
  * offload patterns in the target environment, keep the fastest).  Plans,
  * runs and times (CUDA events, `reps` execs after two warm-ups) candidate
- * knob settings by coordinate descent -- streams, chunk_bytes,
- * odd_radices_first, max_lines -- on the caller's device buffers `in`/`out`
+ * settings -- engine 0 with each chunk_bytes, then engine 1 by coordinate
+ * descent over streams, chunk_bytes, odd_radices_first, max_lines and
+ * per_length -- on the caller's device buffers `in`/`out`
  * (layout of fb_fft_many_layout; `out` is overwritten) in `direction`,
  * and writes the fastest settings to *best and their time per exec (ms)
  * to *best_ms.  Synchronous.  Errors: as fb_fft_plan_many / fb_fft_exec.

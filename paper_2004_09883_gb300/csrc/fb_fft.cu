@@ -34,6 +34,7 @@
 #include "fb_internal.h"
 #include "fb_plan.h"
 #include "fft_p2.cuh"
+#include "fft_uneven.cuh"
 
 using namespace fbfft;
 using namespace fbfft::plan;
@@ -97,7 +98,12 @@ struct MultiLaunch {
 struct TwiddleBuilder {
     std::vector<TwiddleJob> jobs;
     long long total = 0;
-    std::vector<std::pair<long long, std::vector<int>>> stage_cache;  // L -> offsets
+    struct Cached {
+        long long L;
+        std::vector<int> radix;
+        std::vector<int> off;
+    };
+    std::vector<Cached> stage_cache;  // (L, radix schedule) -> offsets
 
     long long add_linear(long long count, long long D, long long mult)
     {
@@ -111,14 +117,15 @@ struct TwiddleBuilder {
     // the 16 x 15 factor table of a split last stage (p2_tw_split), else 0.
     std::vector<int> add_stages(long long L, const int* radix, int nst)
     {
+        const std::vector<int> key(radix, radix + nst);
         for (auto& e : stage_cache)
-            if (e.first == L) return e.second;
+            if (e.L == L && e.radix == key) return e.off;
         std::vector<int> off(nst + 1, 0);
         TwiddleJob js[kMaxStages + 1];
         int nj = 0;
         total += stage_tables(L, radix, nst, total, js, &nj, off.data());
         jobs.insert(jobs.end(), js, js + nj);
-        stage_cache.emplace_back(L, off);
+        stage_cache.push_back({L, key, off});
         return off;
     }
     // the interface make_line_pass takes (tables in a growing buffer: always room)
@@ -216,6 +223,21 @@ struct fb_fft_plan_s {
     bool odd_first = false;
     int max_lines = 0;
     bool merge_mixed = true;               // batched uneven: merged mixed-kernel launches
+    // batched uneven, one-kernel engine (k_fft_uneven): every pass is a job of
+    // one of two launches (phase 0: single passes and four-step columns;
+    // phase 1: four-step rows); jobs and tile prefixes in device tables
+    bool uneven = false;
+    struct UnevenPhase {
+        std::vector<int> jobs;   // pass indices
+        long long tiles = 0;
+        long long grid = 0;
+        int land_max = 16, work_max = 16;
+        size_t smem = 0;
+        PassDesc* d_jobs = nullptr;
+        int* d_tiles = nullptr;
+    };
+    UnevenPhase uphase[2];
+    void* d_uneven = nullptr;              // one allocation: both phases' job and tile tables
     std::vector<MultiLaunch> multis;
     std::unique_ptr<MultiArgs> margs;      // launch-argument staging (copied at every launch)
     struct GraphEntry {
@@ -249,6 +271,7 @@ void free_plan(fb_fft_plan_s* p)
     if (p->staging) cudaFree(p->staging);
     if (p->err) cudaFree(p->err);
     if (p->d_off) cudaFree(p->d_off);
+    if (p->d_uneven) cudaFree(p->d_uneven);
     for (auto& g : p->graphs) cudaGraphExecDestroy(g.exec);
     for (cudaStream_t st : p->side) cudaStreamDestroy(st);
     if (p->capture) cudaStreamDestroy(p->capture);
@@ -269,6 +292,185 @@ long long many_layout(int count, const long long* lengths, long long* offsets)
         off += (lengths[i] + 1) & ~1LL;
     }
     return off;
+}
+
+// Whether a batched-uneven plan runs on the one-kernel engine: the default
+// (engine 0) unless one launch per length is asked for, and every length
+// either fits one job (<= 2048 points) or splits into two that do.
+bool use_uneven_engine(int count, const long long* lengths, const fb_fft_many_opts* opts)
+{
+    if (opts && (opts->engine != 0 || opts->per_length != 0)) return false;
+    for (int i = 0; i < count; ++i) {
+        const long long L = lengths[i];
+        if (L <= kUnevenMaxLen) continue;
+        long long best = 0;
+        for (long long d = 1; d * d <= L; ++d)
+            if (L % d == 0 && L / d <= kUnevenMaxLen) best = d;
+        if (best == 0) return false;
+    }
+    return true;
+}
+
+// Radix schedule of a line of the one-kernel batched-uneven engine
+// (k_fft_uneven): the power-of-two part as radix-8 stages and one radix-4 or
+// radix-2 stage, then the 5s, then the 3s -- the order of kinds the kernel
+// runs its middle stages in.  The kernel has no one-stage form, so a
+// schedule of a single radix ends with a radix-1 stage (a copy).  Returns the
+// stage count.
+int uneven_factorize(long long L, int* r)
+{
+    int c = 0, a = 0;
+    long long n = L;
+    while (n % 2 == 0) n /= 2, ++a;
+    for (int i = 0; i < a / 3; ++i) r[c++] = 8;
+    if (a % 3 == 2) r[c++] = 4;
+    if (a % 3 == 1) r[c++] = 2;
+    while (n % 5 == 0) n /= 5, r[c++] = 5;
+    while (n % 3 == 0) n /= 3, r[c++] = 3;
+    while (c < 2) r[c++] = 1;
+    return c;
+}
+
+// One job of the one-kernel engine: L-point DFTs over lines (o, c), strides in
+// elements (offsets into the exec buffers are set by the caller); tiles of T
+// lines, T L <= 2048 values.
+int make_uneven_pass(PassPlan& p, TwiddleBuilder& twb, long long L, long long O, long long C, long long in_sn,
+                     long long in_sc, long long in_so, long long out_sk, long long out_sc, long long out_so,
+                     bool in_tfast, bool out_tfast, bool ptw)
+{
+    p = PassPlan{};
+    PassDesc& d = p.d;
+    if (L < 1 || L > kUnevenMaxLen || !is_smooth(L)) return FB_FFT_ERR_UNSUPPORTED_SIZE;
+    p.kind = 4;
+    p.io = -1;
+    p.threads = kUnevenThreads;
+    d.nst = uneven_factorize(L, d.radix);
+    set_stage_products(d);
+    const std::vector<int> off = twb.add_stages(L, d.radix, d.nst);
+    for (int s = 0; s < d.nst; ++s) d.twoff[s] = off[s];
+    const bool cfast = in_tfast || out_tfast;
+    long long T = pow2floor(kUnevenCap / L);
+    T = std::min<long long>(T, cfast ? 32 : kUnevenThreads);
+    T = std::max<long long>(1, std::min(T, pow2ceil(C)));
+    d.L = (int)L;
+    d.LS = (int)(L + (L >> 4) + 1);
+    d.logT = ilog2ll(T);
+    d.in_sn = in_sn, d.in_sc = in_sc, d.in_so = in_so;
+    d.out_sk = out_sk, d.out_sc = out_sc, d.out_so = out_so;
+    d.C = C;
+    d.tiles_per_o = (C + T - 1) / T;
+    d.ntiles = O * d.tiles_per_o;
+    d.in_tfast = in_tfast ? 1 : 0;
+    d.out_tfast = out_tfast ? 1 : 0;
+    d.ptw = ptw ? 1 : 0;
+    d.scale = 1.0f;
+    d.land_stride = (int)((L * T + 15) & ~15LL);
+    p.async_ok = false;
+    p.smem = uneven_smem_bytes(d.land_stride, (int)(((long long)d.LS * T + 15) & ~15LL));
+    p.grid = 0;  // launched through its phase's launch only
+    return FB_FFT_OK;
+}
+
+// n = n1 * n2, both at most kUnevenMaxLen, n1 the largest such divisor <= sqrt(n).
+int split_uneven(long long n, long long* n1, long long* n2)
+{
+    long long best = 0;
+    for (long long d = 1; d * d <= n; ++d)
+        if (n % d == 0 && n / d <= kUnevenMaxLen) best = d;
+    if (best == 0) return FB_FFT_ERR_UNSUPPORTED_SIZE;
+    *n1 = best, *n2 = n / best;
+    return FB_FFT_OK;
+}
+
+// Batched uneven lengths on the one-kernel engine: every distinct length is
+// one job over all its transforms (offset tables), or, above 2048 points, a
+// four-step pair of jobs per chunk of transforms, each chunk with its own
+// scratch region.  Phase 0 holds single passes and four-step columns, phase
+// 1 the four-step rows; each phase is one launch of k_fft_uneven.
+int schedule_uneven(fb_fft_plan_s* p, TwiddleBuilder& twb)
+{
+    std::vector<std::pair<long long, std::vector<long long>>> groups;  // (L, transform indices)
+    {
+        std::vector<long long> order(p->lengths.size());
+        for (size_t i = 0; i < order.size(); ++i) order[i] = (long long)i;
+        std::stable_sort(order.begin(), order.end(),
+                         [&](long long a, long long b) { return p->lengths[a] > p->lengths[b]; });
+        for (long long i : order) {
+            if (groups.empty() || groups.back().first != p->lengths[i]) groups.push_back({p->lengths[i], {}});
+            groups.back().second.push_back(i);
+        }
+    }
+    p->group_names = {"many.uneven.phase0", "many.uneven.phase1"};
+    long long scratch_need = 0;
+    for (auto& g : groups) {
+        const long long L = g.first;
+        const std::vector<long long>& idx = g.second;
+        auto push_offsets = [&](size_t b0, size_t nb) {
+            const long long at = (long long)p->h_off.size();
+            for (size_t k = b0; k < b0 + nb; ++k) p->h_off.push_back(p->offsets[idx[k]]);
+            return at;
+        };
+        if (L <= kUnevenMaxLen) {
+            PassPlan q;
+            int rc = make_uneven_pass(q, twb, L, 1, (long long)idx.size(), 1, L, 0, 1, L, 0, false, false, false);
+            if (rc != FB_FFT_OK) return rc;
+            q.off_in_idx = q.off_out_idx = push_offsets(0, idx.size());
+            q.src = kBufIn, q.dst = kBufOut;
+            q.group = 0;
+            q.last = true;
+            q.scale_n = L;
+            p->passes.push_back(q);
+            p->smem_len_max = std::max(p->smem_len_max, L);
+            continue;
+        }
+        long long N1, N2;
+        int rc = split_uneven(L, &N1, &N2);
+        if (rc != FB_FFT_OK) return rc;
+        const int plog = (ilog2ll(L) + 1) / 2;
+        const long long lo_cnt = 1LL << plog, hi_cnt = (L + lo_cnt - 1) >> plog;
+        const long long lo_off = twb.add_linear(lo_cnt, L, 1);
+        const long long hi_off = twb.add_linear(hi_cnt, L, lo_cnt);
+        const long long cnt = (long long)idx.size();
+        const long long cbytes = p->chunk_bytes > 0 ? p->chunk_bytes : fourstep_chunk_bytes();
+        const long long chunk = std::max(1LL, std::min(cnt, cbytes / (L * 8)));
+        for (long long b0 = 0; b0 < cnt; b0 += chunk) {
+            const long long nb = std::min(chunk, cnt - b0);
+            const long long at = push_offsets((size_t)b0, (size_t)nb);
+            const long long region = scratch_need;
+            scratch_need += (nb * L + 31) & ~31LL;  // keep regions 256-byte aligned
+            PassPlan a, r;
+            rc = make_uneven_pass(a, twb, N1, nb, N2, N2, 1, L, N2, 1, L, true, true, true);
+            if (rc != FB_FFT_OK) return rc;
+            a.d.ptw_log = plog;
+            a.d.ptw_lo = reinterpret_cast<const float2*>(lo_off);
+            a.d.ptw_hi = reinterpret_cast<const float2*>(hi_off);
+            a.off_in_idx = at;
+            a.src = kBufIn, a.dst = kBufScratch, a.dst_off = region;
+            a.group = 0;
+            rc = make_uneven_pass(r, twb, N2, nb, N1, 1, N2, L, N1, 1, L, false, true, false);
+            if (rc != FB_FFT_OK) return rc;
+            r.off_out_idx = at;
+            r.src = kBufScratch, r.src_off = region, r.dst = kBufOut;
+            r.group = 1;
+            r.last = true;
+            r.scale_n = L;
+            p->passes.push_back(a);
+            p->passes.push_back(r);
+        }
+        p->smem_len_max = std::max(p->smem_len_max, std::max(N1, N2));
+    }
+    for (int i = 0; i < (int)p->passes.size(); ++i) {
+        PassPlan& q = p->passes[i];
+        fb_fft_plan_s::UnevenPhase& ph = p->uphase[q.group];
+        ph.jobs.push_back(i);
+        ph.tiles += q.d.ntiles;
+        ph.land_max = std::max(ph.land_max, q.d.land_stride);
+        ph.work_max = std::max(ph.work_max, (int)(((long long)q.d.LS * (1LL << q.d.logT) + 15) & ~15LL));
+    }
+    for (auto& ph : p->uphase) ph.smem = uneven_smem_bytes(ph.land_max, ph.work_max);
+    p->scratch_bytes = (size_t)scratch_need * sizeof(float2);
+    p->tw_elems = std::max(2LL, twb.total);
+    return FB_FFT_OK;
 }
 
 // Batched uneven lengths: one pass (or one four-step pair per chunk) per
@@ -430,6 +632,7 @@ int schedule_many(fb_fft_plan_s* p, TwiddleBuilder& twb)
 // Kernel launches one exec of a plan makes.
 long long launches_per_exec(const fb_fft_plan_s* p)
 {
+    if (p->uneven) return (p->uphase[0].jobs.empty() ? 0 : 1) + (p->uphase[1].jobs.empty() ? 0 : 1);
     long long n = (long long)p->multis.size();
     for (const PassPlan& q : p->passes) n += q.multi < 0 ? 1 : 0;
     return n;
@@ -496,7 +699,7 @@ bool use_plane_pass(const fb_fft_plan_s* p)
 int schedule_plan(fb_fft_plan_s* p, TwiddleBuilder& twb)
 {
     if (p->many) {
-        const int rc = schedule_many(p, twb);
+        const int rc = p->uneven ? schedule_uneven(p, twb) : schedule_many(p, twb);
         return rc != FB_FFT_OK ? rc : check_schedule(p);
     }
     const long long B = p->batch;
@@ -628,6 +831,15 @@ int build_plan(fb_fft_plan_s* p)
     for (PassPlan& q : p->passes) {
         int occ = 0;
         const LineKernel k = pass_kernel(q, true);
+        if (q.kind == 4) {  // batched-uneven job: bound into its phase's table below
+            q.d.err = p->err;
+            q.d.tw = p->tw;
+            if (q.d.ptw) {
+                q.d.ptw_lo = p->tw + reinterpret_cast<long long>(q.d.ptw_lo);
+                q.d.ptw_hi = p->tw + reinterpret_cast<long long>(q.d.ptw_hi);
+            }
+            continue;
+        }
         if (q.kind == 3) {  // persistent clusters: as many as fit at once
             int ncl = 0;
             FB_CK(line_cluster_occupancy(k, q.smem, &ncl));
@@ -671,6 +883,55 @@ int build_plan(fb_fft_plan_s* p)
         for (PassPlan& q : p->passes) {
             if (q.off_in_idx >= 0) q.d.off_in = p->d_off + q.off_in_idx;
             if (q.off_out_idx >= 0) q.d.off_out = p->d_off + q.off_out_idx;
+        }
+        if (p->uneven) {
+            // job tables: descriptors with buffer kinds and element offsets in
+            // place of the exec's pointers, and tile prefixes, both phases in
+            // one device allocation
+            std::vector<PassDesc> jobs;
+            std::vector<int> tiles;
+            size_t job_at[2], tile_at[2];
+            for (int ph = 0; ph < 2; ++ph) {
+                fb_fft_plan_s::UnevenPhase& u = p->uphase[ph];
+                job_at[ph] = jobs.size();
+                tile_at[ph] = tiles.size();
+                long long t = 0;
+                for (int i : u.jobs) {
+                    const PassPlan& q = p->passes[i];
+                    PassDesc d = q.d;
+                    d.in = reinterpret_cast<const float2*>(static_cast<uintptr_t>(q.src_off));
+                    d.in_buf = q.src == kBufIn ? 0 : (q.src == kBufOut ? 1 : 2);
+                    d.out = reinterpret_cast<float2*>(static_cast<uintptr_t>(q.dst_off));
+                    d.out_buf = q.dst == kBufOut ? 1 : 2;
+                    d.apply_scale = q.last ? 1 : 0;
+                    d.scale = (float)(1.0 / (double)(q.scale_n ? q.scale_n : 1));
+                    jobs.push_back(d);
+                    tiles.push_back((int)t);
+                    t += q.d.ntiles;
+                }
+                if (t >= (1LL << 31)) return FB_FFT_ERR_UNSUPPORTED_SIZE;
+                tiles.push_back((int)t);
+            }
+            const size_t jb = jobs.size() * sizeof(PassDesc), tb = tiles.size() * sizeof(int);
+            if (cudaMalloc(&p->d_uneven, jb + tb) != cudaSuccess) {
+                cudaGetLastError();
+                p->d_uneven = nullptr;
+                return FB_FFT_ERR_ALLOC;
+            }
+            PassDesc* dj = static_cast<PassDesc*>(p->d_uneven);
+            int* dt = reinterpret_cast<int*>(static_cast<char*>(p->d_uneven) + jb);
+            if (jb) FB_CK(cudaMemcpyAsync(dj, jobs.data(), jb, cudaMemcpyHostToDevice, p->stream));
+            FB_CK(cudaMemcpyAsync(dt, tiles.data(), tb, cudaMemcpyHostToDevice, p->stream));
+            for (int ph = 0; ph < 2; ++ph) {
+                fb_fft_plan_s::UnevenPhase& u = p->uphase[ph];
+                u.d_jobs = dj + job_at[ph];
+                u.d_tiles = dt + tile_at[ph];
+                if (u.jobs.empty()) continue;
+                int occ = 0;
+                FB_CK(uneven_occupancy(true, u.smem, &occ));
+                if (occ < 1) return cuda_fail(cudaErrorInvalidConfiguration, "uneven pass occupancy");
+                u.grid = std::min(u.tiles, (long long)sms * occ);
+            }
         }
         for (MultiLaunch& m : p->multis) {
             int occ = 0;
@@ -832,11 +1093,52 @@ int launch_many(fb_fft_plan_s* p, cudaStream_t origin, const float2* in, float2*
     return FB_FFT_OK;
 }
 
+// Batched uneven plan on the one-kernel engine: phase 0 (single passes,
+// four-step columns), then phase 1 (four-step rows), one launch each.
+int launch_uneven(fb_fft_plan_s* p, cudaStream_t stream, const float2* in, float2* out, bool fwd)
+{
+    for (int ph = 0; ph < 2; ++ph) {
+        const fb_fft_plan_s::UnevenPhase& u = p->uphase[ph];
+        if (u.jobs.empty()) continue;
+        UnevenArgs a;
+        a.jobs = u.d_jobs;
+        a.tile_start = u.d_tiles;
+        a.in = in;
+        a.out = out;
+        a.scratch = p->scratch;
+        a.njobs = (int)u.jobs.size();
+        a.land_max = u.land_max;
+        a.work_max = u.work_max;
+        a.scale_on = (!fwd && (p->flags & FB_FFT_SCALE_INV_N)) ? 1 : 0;
+        cudaEvent_t e1 = nullptr;
+        if (p->profiling) {
+            if (p->ev_used + 2 > p->ev.size()) {
+                for (int i = 0; i < 64; ++i) {
+                    cudaEvent_t e;
+                    FB_CK(cudaEventCreate(&e));
+                    p->ev.push_back(e);
+                }
+                p->ev_group.resize(p->ev.size() / 2, 0);
+            }
+            e1 = p->ev[p->ev_used + 1];
+            p->ev_group[p->ev_used / 2] = ph;
+            cudaEventRecord(p->ev[p->ev_used], stream);
+            p->ev_used += 2;
+        }
+        const cudaError_t le = uneven_launch(fwd, a, u.grid, u.smem, stream);
+        if (le != cudaSuccess) return cuda_fail(le, "k_fft_uneven");
+        g_launches.fetch_add(1, std::memory_order_relaxed);
+        if (e1) cudaEventRecord(e1, stream);
+    }
+    return FB_FFT_OK;
+}
+
 // Batched uneven plan, replayed as one CUDA graph per (in, out, direction):
 // the first exec with a new triple captures the fork/join launch sequence.
 int exec_many(fb_fft_plan_s* p, const float2* in, float2* out, int direction)
 {
     const bool fwd = direction == FB_FFT_FORWARD;
+    if (p->uneven) return launch_uneven(p, p->stream, in, out, fwd);
     if (!p->use_graph || p->profiling) return launch_many(p, p->stream, in, out, fwd, true);
     for (auto& g : p->graphs)
         if (g.in == in && g.out == out && g.dir == direction) {
@@ -1199,6 +1501,7 @@ int fb_fft_plan_many_ex(fb_fft_plan_t* plan, int count, const long long* lengths
         p->max_lines = opts->max_lines;
         p->merge_mixed = opts->per_length == 0;
     }
+    p->uneven = use_uneven_engine(count, lengths, opts);
     int rc = build_plan(p);
     if (rc != FB_FFT_OK) {
         free_plan(p);
@@ -1240,12 +1543,29 @@ int fb_fft_autotune_many(int count, const long long* lengths, unsigned flags, co
         *ms = t / reps;
         return rc;
     };
-    fb_fft_many_opts cur{4, 1, 32LL << 20, 0, 0};
-    float cur_ms = 0.f;
-    int rc = measure(cur, &cur_ms);
-    // coordinate descent, one knob at a time
-    const int streams[] = {1, 2, 8, 16, 32};
+    // engine 0 (one kernel, two launches): its only knob is the chunk size
     const long long chunks[] = {8LL << 20, 16LL << 20, 64LL << 20, 128LL << 20, 512LL << 20};
+    fb_fft_many_opts best0{4, 1, 512LL << 20, 0, 0, 0, 0};  // engine 1's knobs at their defaults
+    float best0_ms = 0.f;
+    int rc = FB_FFT_OK;
+    bool have0 = false;
+    if (use_uneven_engine(count, lengths, nullptr)) {
+        rc = measure(best0, &best0_ms);
+        have0 = rc == FB_FFT_OK;
+        for (long long v : chunks) {
+            if (rc != FB_FFT_OK || v == best0.chunk_bytes) continue;
+            fb_fft_many_opts o = best0;
+            o.chunk_bytes = v;
+            float ms;
+            rc = measure(o, &ms);
+            if (rc == FB_FFT_OK && ms < best0_ms) best0 = o, best0_ms = ms;
+        }
+    }
+    // engine 1 (per-kernel launches on side streams): coordinate descent, one knob at a time
+    fb_fft_many_opts cur{4, 1, 32LL << 20, 0, 0, 0, 1};
+    float cur_ms = 0.f;
+    if (rc == FB_FFT_OK) rc = measure(cur, &cur_ms);
+    const int streams[] = {1, 2, 8, 16, 32};
     const int lines[] = {4, 16, 64};
     for (int v : streams) {
         if (rc != FB_FFT_OK) break;
@@ -1288,6 +1608,7 @@ int fb_fft_autotune_many(int count, const long long* lengths, unsigned flags, co
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     if (rc != FB_FFT_OK) return rc;
+    if (have0 && best0_ms <= cur_ms) cur = best0, cur_ms = best0_ms;
     *best = cur;
     *best_ms = cur_ms;
     return FB_FFT_OK;
@@ -1311,6 +1632,7 @@ int fb_fft_plan_many_query(int count, const long long* lengths, unsigned flags, 
     p.offsets.resize(count);
     p.total = many_layout(count, lengths, p.offsets.data());
     p.nslots = many_streams();
+    p.uneven = use_uneven_engine(count, lengths, nullptr);
     TwiddleBuilder twb;
     const int rc = schedule_plan(&p, twb);
     p.magic = kDead;

@@ -69,6 +69,11 @@ struct PassDesc {
     // Contiguous layouts index them by line, strided ones by outer index.
     const long long* off_in;
     const long long* off_out;
+    // Batched-uneven job tables (k_fft_uneven): which exec buffer `in` and
+    // `out` refer to (0 the caller's input, 1 its output, 2 the plan's
+    // scratch); the pointer fields then hold element offsets into it.
+    int in_buf;
+    int out_buf;
 };
 
 // Fill ns[] (product of the earlier radices) and its multiply-high

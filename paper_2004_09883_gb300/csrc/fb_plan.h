@@ -46,7 +46,8 @@ struct PassPlan {
     int lg;       // log2(L) for a compile-time power-of-two kernel, 0 = generic kernel
     int io;       // IoMode of the power-of-two kernel
     int kind;     // 0 power-of-two kernel, 1 generic kernel, 2 mixed kernel (lg = log2 of the 2-factor),
-                  // 3 plane pass (two trailing axes, lg1 = log2 rows, lg = log2 row length)
+                  // 3 plane pass (two trailing axes, lg1 = log2 rows, lg = log2 row length),
+                  // 4 job of the batched-uneven kernel
     int lg1 = 0;
     long long grid;
     size_t smem;
@@ -160,7 +161,7 @@ inline long long stage_tables(long long L, const int* radix, int nst, long long 
     for (int s = 0; s <= nst; ++s) off[s] = 0;
     for (int s = 0; s < nst; ++s) {
         const long long cnt = Ns * (radix[s] - 1);
-        if (Ns > 1) {
+        if (Ns > 1 && cnt > 0) {
             jobs[(*njobs)++] = TwiddleJob{total, cnt, 0, 0, 1, radix[s], (int)Ns};
             off[s] = (int)total;
             total += (cnt + 1) & ~1LL;
@@ -178,6 +179,11 @@ inline long long stage_tables(long long L, const int* radix, int nst, long long 
 // The compiled kernel a pass runs in one direction.
 inline LineKernel pass_kernel(const PassPlan& q, bool fwd)
 {
+    if (q.kind == 4) {  // a job of the batched-uneven kernel: launched per phase, not per pass
+        LineKernel k{nullptr, q.threads, fwd, 0, -1};
+        k.kind = 4;
+        return k;
+    }
     if (q.tc) return line_kernel_p2tc(q.threads, fwd, q.lg, q.io);
     if (q.kind == 3) return line_kernel_plane(fwd, q.lg1, q.lg, q.threads);
     if (q.kind == 2) return line_kernel_mixed(fwd, q.lg);
@@ -192,6 +198,7 @@ inline size_t pass_smem(const PassPlan& q, bool async)
     const size_t ptw = q.d.ptw_smem ? (size_t)((1LL << q.d.ptw_log) + q.d.ptw_hi_cnt) * sizeof(float2) : 0;
     if (q.kind == 0) return (size_t)p2_smem_bytes(q.threads, q.lg, q.io, async, q.tc) + ptw;
     if (q.kind == 3) return (size_t)plane_smem_bytes(q.lg1, q.lg, q.threads);
+    if (q.kind == 4) return q.smem;
     return line_smem_bytes(q.d.land_stride, q.d.L, 1 << q.d.logT, q.d.nst, async, q.d.tws);
 }
 

@@ -1,0 +1,37 @@
+// fft_kernels_uneven.cu -- k_fft_uneven (one kernel per direction) with its
+// launch and occupancy helpers.
+#include <cstdlib>
+
+#include "fft_uneven.cuh"
+
+namespace fbfft {
+
+namespace {
+using UnevenFn = void (*)(UnevenArgs);
+UnevenFn uneven_fn(bool forward) { return forward ? k_fft_uneven<true> : k_fft_uneven<false>; }
+}  // namespace
+
+cudaError_t uneven_launch(bool forward, const UnevenArgs& a, long long grid, size_t smem, cudaStream_t stream)
+{
+    if (grid <= 0) return cudaSuccess;
+    const UnevenFn fn = uneven_fn(forward);
+    cudaError_t e = kernel_smem_optin((const void*)fn, 0);
+    if (e != cudaSuccess) return e;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)grid);
+    cfg.blockDim = dim3(kUnevenThreads);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = stream;
+    cfg.numAttrs = 0;
+    return cudaLaunchKernelEx(&cfg, fn, a);
+}
+
+cudaError_t uneven_occupancy(bool forward, size_t smem, int* blocks_per_sm)
+{
+    const UnevenFn fn = uneven_fn(forward);
+    cudaError_t e = kernel_smem_optin((const void*)fn, 0);
+    if (e != cudaSuccess) return e;
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, (const void*)fn, kUnevenThreads, smem);
+}
+
+}  // namespace fbfft

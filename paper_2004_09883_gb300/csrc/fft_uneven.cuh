@@ -1,0 +1,382 @@
+// fft_uneven.cuh -- the line pass of batched uneven lengths (fb_fft_plan_many):
+// every pass of one phase of such a batch -- single-pass lines, four-step
+// columns, four-step rows, any 5-smooth length up to 2048, power-of-two or
+// not -- in ONE launch.
+//
+// Jobs (one PassDesc per length group or four-step chunk, each with its own
+// offset tables, strides, radix schedule and twiddle tables) sit in a device
+// table; a device prefix table gives each job's first global tile.
+// Persistent CTAs walk the global tiles blockIdx.x, +gridDim.x, ...: the job
+// of a tile is found by walking the prefix table forward (tiles only grow).
+// Two landing buffers, each with its tile's descriptor in shared memory:
+// while tile i is transformed, every thread's cp.async copies bring tile i+1
+// (16-byte copies where the layout allows, else 8-byte).  The stages alternate
+// between two work buffers, so every stage needs one barrier.  Stage radices
+// come from the descriptor (8, 4, 2, 5, 3: at most 10 values of one thread in
+// flight, which keeps the kernel small enough for three CTAs per SM).
+#pragma once
+
+#include "fft_device.cuh"
+
+namespace fbfft {
+
+constexpr int kUnevenThreads = 256;
+constexpr int kUnevenElems = 8;                                 // values per thread and stage
+constexpr int kUnevenCap = kUnevenThreads * kUnevenElems;       // values per tile (2048)
+constexpr int kUnevenMaxLen = kUnevenCap;                       // longest line of a job
+
+// Kernel argument: the job table and the tile prefix table (device memory,
+// written once when the plan is built) and the buffers of this exec.  A job's
+// `in` / `out` fields hold element offsets into the buffer its in_buf /
+// out_buf names.
+struct UnevenArgs {
+    const PassDesc* jobs;   // [njobs]
+    const int* tile_start;  // [njobs + 1]: first global tile of each job; [njobs] = all tiles
+    const float2* in;       // buffer 0: the caller's input
+    float2* out;            // buffer 1: the caller's output
+    float2* scratch;        // buffer 2: the plan's four-step intermediate
+    int njobs;
+    int land_max;           // elements of one landing buffer (multiple of 16)
+    int work_max;           // elements of one work buffer (multiple of 16)
+    int scale_on;           // 1: jobs marked apply_scale multiply by their `scale`
+};
+
+#ifdef __CUDACC__
+
+// Tile t of job d: outer index o, first line c0, valid lines Tv (32-bit: a
+// job has fewer than 2^31 tiles and lines).
+struct UTileIdx {
+    int o, c0, Tv;
+};
+__device__ __forceinline__ UTileIdx utile_index(const PassDesc& d, int tile)
+{
+    UTileIdx ti;
+    const int tpo = (int)d.tiles_per_o;
+    ti.o = (int)((unsigned)tile / (unsigned)tpo);
+    ti.c0 = (tile - ti.o * tpo) << d.logT;
+    const int rem = (int)d.C - ti.c0;
+    const int T = 1 << d.logT;
+    ti.Tv = rem < T ? rem : T;
+    return ti;
+}
+
+__device__ __forceinline__ void cp_async16(void* smem_dst, const void* gsrc)
+{
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_u32(smem_dst)), "l"(gsrc) : "memory");
+}
+
+// A job's input / output base in this exec's buffers.
+__device__ __forceinline__ const float2* ubuf_in(const UnevenArgs& a, const PassDesc& d)
+{
+    const float2* b = d.in_buf == 0 ? a.in : (d.in_buf == 1 ? a.out : a.scratch);
+    return b + (long long)reinterpret_cast<uintptr_t>(d.in);
+}
+__device__ __forceinline__ float2* ubuf_out(const UnevenArgs& a, const PassDesc& d)
+{
+    float2* b = d.out_buf == 1 ? a.out : a.scratch;
+    return b + (long long)reinterpret_cast<uintptr_t>(d.out);
+}
+// Global start of line (o, c) of the input / output (offset tables or strides).
+__device__ __forceinline__ const float2* uline_in(const UnevenArgs& a, const PassDesc& d, int o, int c)
+{
+    const float2* in = ubuf_in(a, d);
+    if (d.off_in) return in + (d.in_tfast ? d.off_in[o] + c : d.off_in[c]);
+    return in + (long long)o * d.in_so + (long long)c * d.in_sc;
+}
+__device__ __forceinline__ float2* uline_out(const UnevenArgs& a, const PassDesc& d, int o, int c)
+{
+    float2* out = ubuf_out(a, d);
+    if (d.off_out) return out + (d.out_tfast ? d.off_out[o] + c : d.off_out[c]);
+    return out + (long long)o * d.out_so + (long long)c * d.out_sc;
+}
+
+// Copy tile ti of job d into `land` with cp.async (the caller commits and
+// waits).  Contiguous lines land as [t][n]: 2^lgt threads per line (T <= 256
+// lines, both powers of two), consecutive threads on consecutive values, so a
+// thread finds its line once per tile.  Strided tiles land as [n][t]:
+// consecutive threads on consecutive lines.  Pairs of values move as one
+// 16-byte copy when every address of the tile is 16-byte aligned.
+__device__ __forceinline__ void utile_load(const UnevenArgs& a, const PassDesc& d, const UTileIdx& ti, float2* land)
+{
+    constexpr int LGTH = 8;  // log2(kUnevenThreads)
+    const int L = d.L, logT = d.logT, tid = threadIdx.x;
+    if (!d.in_tfast) {
+        const int lgt = LGTH - logT, t = tid >> lgt, step = 1 << lgt;
+        if (t >= ti.Tv) return;
+        const float2* src = uline_in(a, d, ti.o, ti.c0 + t);
+        float2* dst = land + t * L;
+        if ((L & 1) == 0 && ((uintptr_t)src & 15) == 0) {
+            for (int n = 2 * (tid & (step - 1)); n < L; n += 2 * step) cp_async16(dst + n, src + n);
+        } else {
+            for (int n = tid & (step - 1); n < L; n += step) cp_async8(dst + n, src + n);
+        }
+    } else {
+        const float2* base = uline_in(a, d, ti.o, ti.c0);
+        const long long sn = d.in_sn;
+        const int T = 1 << logT;
+        if (logT >= 1 && (ti.Tv & 1) == 0 && (sn & 1) == 0 && ((uintptr_t)base & 15) == 0) {
+            const int lg = logT - 1, t = 2 * (tid & ((1 << lg) - 1)), step = kUnevenThreads >> lg;
+            if (t >= ti.Tv) return;
+            for (int n = tid >> lg; n < L; n += step) cp_async16(land + n * T + t, base + n * sn + t);
+        } else {
+            const int t = tid & (T - 1), step = kUnevenThreads >> logT;
+            if (t >= ti.Tv) return;
+            for (int n = tid >> logT; n < L; n += step) cp_async8(land + n * T + t, base + n * sn + t);
+        }
+    }
+}
+
+// The output value y of line c (within its job), index k, finished: the
+// four-step twiddle exp(s 2 pi i c k / N) and the 1/N scale, where asked.
+template <bool FWD>
+__device__ __forceinline__ float2 uout(const PassDesc& d, float2 y, int c, int k, bool scale)
+{
+    if (d.ptw) {
+        const unsigned m = (unsigned)c * (unsigned)k;  // < N < 2^31
+        const float2 w = cmul(__ldg(d.ptw_hi + (m >> d.ptw_log)), __ldg(d.ptw_lo + (m & ((1u << d.ptw_log) - 1))));
+        y = twmul<FWD>(y, w);
+    }
+    if (scale) y = d.scale * y;
+    return y;
+}
+
+// Store the finished tile from `land` (the load's layouts, output side), with
+// the four-step twiddle and the scale applied on the way.
+template <bool FWD>
+__device__ __forceinline__ void utile_store(const UnevenArgs& a, const PassDesc& d, const UTileIdx& ti,
+                                            const float2* land)
+{
+    const bool sc = a.scale_on && d.apply_scale;
+    constexpr int LGTH = 8;
+    const int L = d.L, logT = d.logT, tid = threadIdx.x;
+    if (!d.out_tfast) {
+        const int lgt = LGTH - logT, t = tid >> lgt, step = 1 << lgt;
+        if (t >= ti.Tv) return;
+        float2* dst = uline_out(a, d, ti.o, ti.c0 + t);
+        const float2* src = land + t * L;
+        const int c = ti.c0 + t;
+        if ((L & 1) == 0 && ((uintptr_t)dst & 15) == 0) {
+            for (int k = 2 * (tid & (step - 1)); k < L; k += 2 * step) {
+                const float4 p = *reinterpret_cast<const float4*>(src + k);
+                const float2 y0 = uout<FWD>(d, make_float2(p.x, p.y), c, k, sc);
+                const float2 y1 = uout<FWD>(d, make_float2(p.z, p.w), c, k + 1, sc);
+                *reinterpret_cast<float4*>(dst + k) = make_float4(y0.x, y0.y, y1.x, y1.y);
+            }
+        } else {
+            for (int k = tid & (step - 1); k < L; k += step) dst[k] = uout<FWD>(d, src[k], c, k, sc);
+        }
+    } else {
+        float2* base = uline_out(a, d, ti.o, ti.c0);
+        const long long sk = d.out_sk;
+        const int T = 1 << logT;
+        if (logT >= 1 && (ti.Tv & 1) == 0 && (sk & 1) == 0 && ((uintptr_t)base & 15) == 0) {
+            const int lg = logT - 1, t = 2 * (tid & ((1 << lg) - 1)), step = kUnevenThreads >> lg;
+            if (t >= ti.Tv) return;
+            for (int k = tid >> lg; k < L; k += step) {
+                const float4 p = *reinterpret_cast<const float4*>(land + k * T + t);
+                const float2 y0 = uout<FWD>(d, make_float2(p.x, p.y), ti.c0 + t, k, sc);
+                const float2 y1 = uout<FWD>(d, make_float2(p.z, p.w), ti.c0 + t + 1, k, sc);
+                *reinterpret_cast<float4*>(base + k * sk + t) = make_float4(y0.x, y0.y, y1.x, y1.y);
+            }
+        } else {
+            const int t = tid & (T - 1), step = kUnevenThreads >> logT;
+            if (t >= ti.Tv) return;
+            for (int k = tid >> logT; k < L; k += step) base[k * sk + t] = uout<FWD>(d, land[k * T + t], ti.c0 + t, k, sc);
+        }
+    }
+}
+
+// A shared-memory value read with a volatile load (see ustage).
+template <class T>
+__device__ __forceinline__ T uvol(const T& x)
+{
+    return *const_cast<const volatile T*>(&x);
+}
+
+// One Stockham stage of radix R over the tile (see fft_device.cuh for the
+// formula): stage 0 reads the landing buffer (input layout), the last stage
+// writes it (output layout, before the twiddle and scale of the store),
+// stages between alternate between the two padded work buffers (stage st
+// writes buffer st & 1 and reads the other), so no stage waits between its
+// reads and its writes except a one-stage schedule.
+template <int R, bool FWD, int POS>
+__device__ __forceinline__ void ustage(const PassDesc& d, int st, float2* land, float2* work, float2* work2, int Tv)
+{
+    constexpr int LGTH = 8;
+    constexpr int Q = (kUnevenElems + R - 1) / R;
+    constexpr bool first = POS == kPosOnly || POS == kPosFirst;
+    constexpr bool last = POS == kPosOnly || POS == kPosLast;
+    float2* wr = (st & 1) ? work2 : work;
+    const float2* rd = (st & 1) ? work : work2;
+    // Descriptor fields are read afresh in every stage (volatile): left to
+    // itself the compiler keeps every radix's derived values live across all
+    // stages of the tile, which costs more registers than the stages need.
+    const int L = uvol(d.L), LS = uvol(d.LS), logT = uvol(d.logT);
+    const int LR = L / R;
+    const bool in_tf = first && uvol(d.in_tfast) != 0;
+    const bool out_tf = last && uvol(d.out_tfast) != 0;
+    const bool tfast = in_tf || out_tf;
+    const int tid = threadIdx.x;
+    const int lgG = LGTH - logT, G = 1 << lgG;
+    const int t = tfast ? (tid & ((1 << logT) - 1)) : (tid >> lgG);
+    const int jb = tfast ? (tid >> logT) : (tid & (G - 1));
+    const bool tok = t < Tv;
+    float2 v[Q][R];
+#pragma unroll
+    for (int q = 0; q < Q; ++q) {
+        const int j = jb + q * G;
+        if (tok && j < LR) {
+            if constexpr (first) {
+                if (in_tf) {
+#pragma unroll
+                    for (int r = 0; r < R; ++r) v[q][r] = land[((j + r * LR) << logT) + t];
+                } else {
+#pragma unroll
+                    for (int r = 0; r < R; ++r) v[q][r] = land[t * L + j + r * LR];
+                }
+            } else {
+                const float2* p = rd + t * LS;
+#pragma unroll
+                for (int r = 0; r < R; ++r) v[q][r] = p[spad(j + r * LR)];
+            }
+        } else {
+            // defined on every path: otherwise the register allocator sees the
+            // values live around the tile loop (loaded and used under the same
+            // condition, which it cannot prove) and keeps every radix's set
+#pragma unroll
+            for (int r = 0; r < R; ++r) v[q][r] = make_float2(0.f, 0.f);
+        }
+    }
+    if constexpr (first && last) __syncthreads();  // one-stage schedule: reads and writes share the tile
+    const int Ns = first ? 1 : uvol(d.ns[st]);
+    const unsigned nsm = first ? 0u : (unsigned)uvol(d.ns_mag[st]);
+    const float2* twb = d.tw + (first ? 0 : uvol(d.twoff[st]));
+#pragma unroll
+    for (int q = 0; q < Q; ++q) {
+        const int j = jb + q * G;
+        if (tok && j < LR) {
+            const int k = first ? 0 : j - (int)__umulhi((unsigned)j, nsm) * Ns;
+            if constexpr (!first) {
+                const float2* tw = twb + k;
+#pragma unroll
+                for (int r = 1; r < R; ++r) v[q][r] = twmul<FWD>(v[q][r], __ldg(tw + (r - 1) * Ns));
+            }
+            dft<R, FWD>(v[q]);
+            const int base = (j - k) * R + k;
+            if constexpr (!last) {
+                float2* p = wr + t * LS;
+#pragma unroll
+                for (int r = 0; r < R; ++r) p[spad(base + r * Ns)] = v[q][r];
+            } else if (out_tf) {
+#pragma unroll
+                for (int r = 0; r < R; ++r) land[((base + r * Ns) << logT) + t] = v[q][r];
+            } else {
+#pragma unroll
+                for (int r = 0; r < R; ++r) land[t * L + base + r * Ns] = v[q][r];
+            }
+        }
+    }
+}
+
+// First or last stage: any radix of the schedule.
+template <bool FWD, int POS>
+__device__ __forceinline__ void ustage_any(const PassDesc& d, int st, float2* land, float2* work, float2* work2,
+                                           int Tv)
+{
+    switch (d.radix[st]) {
+    case 8: ustage<8, FWD, POS>(d, st, land, work, work2, Tv); break;
+    case 4: ustage<4, FWD, POS>(d, st, land, work, work2, Tv); break;
+    case 5: ustage<5, FWD, POS>(d, st, land, work, work2, Tv); break;
+    case 3: ustage<3, FWD, POS>(d, st, land, work, work2, Tv); break;
+    case 2: ustage<2, FWD, POS>(d, st, land, work, work2, Tv); break;
+    default:  // radix 1: a copy (length 1, and the stage that ends a one-radix schedule)
+        ustage<1, FWD, POS>(d, st, land, work, work2, Tv);
+        break;
+    }
+}
+// Middle stages of radix R, from stage s while the schedule has that radix
+// (schedules list their radices in the order 8, 4, 2, 5, 3).
+template <int R, bool FWD>
+__device__ __forceinline__ void ustage_run(const PassDesc& d, int& s, int nst, float2* land, float2* work,
+                                           float2* work2, int Tv)
+{
+    while (s < nst - 1 && d.radix[s] == R) {
+        ustage<R, FWD, kPosMid>(d, s, land, work, work2, Tv);
+        __syncthreads();
+        ++s;
+    }
+}
+
+template <bool FWD>
+__global__ void __launch_bounds__(kUnevenThreads, 3) k_fft_uneven(const __grid_constant__ UnevenArgs a)
+{
+    extern __shared__ __align__(128) unsigned char smem_dyn[];
+    unsigned char* smem_raw = smem_dyn + ((128u - (smem_u32(smem_dyn) & 127u)) & 127u);
+    float2* land0 = reinterpret_cast<float2*>(smem_raw);
+    float2* work = land0 + 2 * a.land_max;
+    float2* work2 = work + a.work_max;
+    __shared__ PassDesc sd[2];  // sd[b]: descriptor of the tile in landing buffer b
+    constexpr int TH = kUnevenThreads;
+    const int total = __ldg(a.tile_start + a.njobs);
+    const int step = gridDim.x;
+    auto copy_desc = [&](int job, int b) {
+        const int* src = reinterpret_cast<const int*>(a.jobs + job);
+        int* dst = reinterpret_cast<int*>(&sd[b]);
+        for (int w = threadIdx.x; w < (int)(sizeof(PassDesc) / 4); w += TH) dst[w] = __ldg(src + w);
+    };
+    pdl_start();
+    int g = blockIdx.x;
+    if (g >= total) return;
+    int j = 0;
+    while (g >= __ldg(a.tile_start + j + 1)) ++j;
+    int jstart = __ldg(a.tile_start + j);
+    copy_desc(j, 0);
+    __syncthreads();
+    utile_load(a, sd[0], utile_index(sd[0], g - jstart), land0);
+    cp_async_commit();
+    for (int i = 0; g < total; g += step, ++i) {
+        const int b = i & 1;
+        const int gl = g - jstart;  // this tile within its job
+        const int gn = g + step;
+        if (gn < total) {  // the next tile's job and descriptor, then its copies
+            while (gn >= __ldg(a.tile_start + j + 1)) ++j;
+            jstart = __ldg(a.tile_start + j);
+            copy_desc(j, b ^ 1);
+            __syncthreads();
+            utile_load(a, sd[b ^ 1], utile_index(sd[b ^ 1], gn - jstart), land0 + (b ^ 1) * a.land_max);
+            cp_async_commit();
+            cp_async_wait<1>();  // this tile's copies have landed (the next tile's may still fly)
+        } else {
+            cp_async_wait<0>();
+        }
+        __syncthreads();
+        const PassDesc& d = sd[b];
+        float2* land = land0 + b * a.land_max;
+        const UTileIdx ti = utile_index(d, gl);
+        const int nst = d.nst;  // >= 2: the planner ends a one-radix schedule with a radix-1 copy
+        ustage_any<FWD, kPosFirst>(d, 0, land, work, work2, ti.Tv);
+        __syncthreads();
+        int s = 1;
+        ustage_run<8, FWD>(d, s, nst, land, work, work2, ti.Tv);
+        ustage_run<4, FWD>(d, s, nst, land, work, work2, ti.Tv);
+        ustage_run<2, FWD>(d, s, nst, land, work, work2, ti.Tv);
+        ustage_run<5, FWD>(d, s, nst, land, work, work2, ti.Tv);
+        ustage_run<3, FWD>(d, s, nst, land, work, work2, ti.Tv);
+        ustage_any<FWD, kPosLast>(d, nst - 1, land, work, work2, ti.Tv);
+        __syncthreads();
+        utile_store<FWD>(a, d, ti, land);
+        __syncthreads();  // buffer b and sd[b] are free for the tile after next
+    }
+}
+
+#endif  // __CUDACC__
+
+// Host side (fft_kernels_uneven.cu).
+cudaError_t uneven_launch(bool forward, const UnevenArgs& a, long long grid, size_t smem, cudaStream_t stream);
+cudaError_t uneven_occupancy(bool forward, size_t smem, int* blocks_per_sm);
+inline size_t uneven_smem_bytes(int land_max, int work_max)
+{
+    return 128 + (size_t)(2LL * land_max + 2LL * work_max) * sizeof(float2);
+}
+
+}  // namespace fbfft

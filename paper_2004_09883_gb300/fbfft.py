@@ -49,7 +49,8 @@ class Info(ctypes.Structure):
 class ManyOpts(ctypes.Structure):
     """Knobs of a batched uneven plan (0 = default)."""
     _fields_ = [("streams", ctypes.c_int), ("use_graph", ctypes.c_int), ("chunk_bytes", ctypes.c_longlong),
-                ("odd_radices_first", ctypes.c_int), ("max_lines", ctypes.c_int), ("per_length", ctypes.c_int)]
+                ("odd_radices_first", ctypes.c_int), ("max_lines", ctypes.c_int), ("per_length", ctypes.c_int),
+                ("engine", ctypes.c_int)]
 
     def as_dict(self) -> dict:
         return {f: getattr(self, f) for f, _ in self._fields_}

@@ -123,13 +123,13 @@ def test_autotuner_returns_a_working_setting(fb):
 
 @pytest.mark.parametrize("direction,scale", [(-1, False), (1, True)])
 def test_merged_launches_equal_per_length_launches(fb, direction, scale):
-    """Merged mixed-kernel launches (default) and one launch per length agree,
+    """Engine 1: merged mixed-kernel launches and one launch per length agree,
     with far fewer launches."""
     import torch
     lens = list(inputs.uneven_lengths(300, 64, 65536, inputs.seed_for(inputs.WORKLOAD_UNEVEN_4096, 7)))
     lens += [75, 6000, 45000, 3 * 5 ** 6, 2, 3, 3000, 2187, 3125, 4050, 64, 128, 512, 2048, 4096, 8192, 65536]
     xs = _batch(lens, 950)
-    with fb.PlanMany(lens, scale_inv_n=scale) as pm, \
+    with fb.PlanMany(lens, scale_inv_n=scale, opts={"engine": 1}) as pm, \
             fb.PlanMany(lens, scale_inv_n=scale, opts={"per_length": 1}) as pl:
         d = torch.from_numpy(pm.pack(xs)).cuda()
         l0 = fb.launch_count()
@@ -152,3 +152,48 @@ def test_merged_launches_equal_per_length_launches(fb, direction, scale):
             assert np.array_equal(a, b), n
     _check(pm, xs, ys, direction, scale)
     _check(pl, xs, yls, direction, scale)
+
+
+ENGINE0_LENGTHS = ([1, 2, 3, 4, 5, 8, 9, 16, 27, 64, 100, 125, 243, 1000, 1024, 2000, 2048, 2187, 3000, 4096,
+                    4050, 6000, 8192, 45000, 59049, 65536, 1 << 20]
+                   + list(inputs.uneven_lengths(200, 64, 65536, inputs.seed_for(inputs.WORKLOAD_UNEVEN_4096, 9))))
+
+
+@pytest.mark.parametrize("direction,scale", [(-1, False), (1, True)])
+def test_one_kernel_engine_matches_oracle_in_two_launches(fb, direction, scale):
+    """Engine 0 (the default): every pass of the batch in one kernel, two
+    launches per exec (single passes and four-step columns, then four-step
+    rows); lengths 1 to 2^20, one-radix schedules, odd lengths, every result
+    against the oracle, in place and out of place, and the graph-free replay
+    gives the same bits."""
+    import torch
+    xs = _batch(ENGINE0_LENGTHS, 960)
+    with fb.PlanMany(ENGINE0_LENGTHS, scale_inv_n=scale) as p:
+        assert p.info()["passes"] == 2
+        d = torch.from_numpy(p.pack(xs)).cuda()
+        l0 = fb.launch_count()
+        y = p.exec(d, None, direction)
+        torch.cuda.synchronize()
+        assert fb.launch_count() - l0 == 2
+        y2 = p.exec(d, None, direction)
+        z = d.clone()
+        p.exec(z, z, direction)
+        p.check()
+        ys, ys2, zs = (p.unpack(t.cpu().numpy()) for t in (y, y2, z))
+    for a, b, c in zip(ys, ys2, zs):
+        assert np.array_equal(a, b) and np.array_equal(a, c)
+    _check(p, xs, ys, direction, scale)
+
+
+def test_both_engines_agree_with_the_oracle(fb):
+    import torch
+    lens = list(inputs.uneven_lengths(120, 64, 65536, inputs.seed_for(inputs.WORKLOAD_UNEVEN_4096, 11)))
+    xs = _batch(lens, 970)
+    with fb.PlanMany(lens) as p0, fb.PlanMany(lens, opts={"engine": 1}) as p1:
+        d = torch.from_numpy(p0.pack(xs)).cuda()
+        y0 = p0.unpack(p0.exec(d, None, -1).cpu().numpy())
+        y1 = p1.unpack(p1.exec(d, None, -1).cpu().numpy())
+        p0.check()
+        p1.check()
+    _check(p0, xs, y0, -1)
+    _check(p1, xs, y1, -1)
