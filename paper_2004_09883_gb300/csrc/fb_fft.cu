@@ -366,7 +366,8 @@ int make_uneven_pass(PassPlan& p, TwiddleBuilder& twb, long long L, long long O,
     d.scale = 1.0f;
     d.land_stride = (int)((L * T + 15) & ~15LL);
     p.async_ok = false;
-    p.smem = uneven_smem_bytes(d.land_stride, (int)(((long long)d.LS * T + 15) & ~15LL));
+    const int padded = (int)(((long long)d.LS * T + 15) & ~15LL);
+    p.smem = uneven_smem_bytes(std::max(d.land_stride, padded), padded);
     p.grid = 0;  // launched through its phase's launch only
     return FB_FFT_OK;
 }
@@ -464,8 +465,9 @@ int schedule_uneven(fb_fft_plan_s* p, TwiddleBuilder& twb)
         fb_fft_plan_s::UnevenPhase& ph = p->uphase[q.group];
         ph.jobs.push_back(i);
         ph.tiles += q.d.ntiles;
-        ph.land_max = std::max(ph.land_max, q.d.land_stride);
-        ph.work_max = std::max(ph.work_max, (int)(((long long)q.d.LS * (1LL << q.d.logT) + 15) & ~15LL));
+        const int padded = (int)(((long long)q.d.LS * (1LL << q.d.logT) + 15) & ~15LL);
+        ph.land_max = std::max(ph.land_max, std::max(q.d.land_stride, padded));  // also a work buffer
+        ph.work_max = std::max(ph.work_max, padded);
     }
     for (auto& ph : p->uphase) ph.smem = uneven_smem_bytes(ph.land_max, ph.work_max);
     p->scratch_bytes = (size_t)scratch_need * sizeof(float2);

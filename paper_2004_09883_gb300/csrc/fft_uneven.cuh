@@ -11,9 +11,11 @@
 // Two landing buffers, each with its tile's descriptor in shared memory:
 // while tile i is transformed, every thread's cp.async copies bring tile i+1
 // (16-byte copies where the layout allows, else 8-byte).  The stages alternate
-// between two work buffers, so every stage needs one barrier.  Stage radices
-// come from the descriptor (8, 4, 2, 5, 3: at most 10 values of one thread in
-// flight, which keeps the kernel small enough for three CTAs per SM).
+// between the work buffer and the tile's own landing buffer, so every stage
+// needs one barrier; the last stage stores to global memory directly.  Stage
+// radices come from the descriptor (8, 4, 2, 5, 3: at most 10 values of one
+// thread in flight), which keeps the kernel at 64 registers and three
+// buffers, four CTAs per SM.
 #pragma once
 
 #include "fft_device.cuh"
@@ -36,8 +38,8 @@ struct UnevenArgs {
     float2* out;            // buffer 1: the caller's output
     float2* scratch;        // buffer 2: the plan's four-step intermediate
     int njobs;
-    int land_max;           // elements of one landing buffer (multiple of 16)
-    int work_max;           // elements of one work buffer (multiple of 16)
+    int land_max;           // elements of one landing buffer (multiple of 16; holds a padded work tile too)
+    int work_max;           // elements of the work buffer (multiple of 16)
     int scale_on;           // 1: jobs marked apply_scale multiply by their `scale`
 };
 
@@ -140,52 +142,6 @@ __device__ __forceinline__ float2 uout(const PassDesc& d, float2 y, int c, int k
     return y;
 }
 
-// Store the finished tile from `land` (the load's layouts, output side), with
-// the four-step twiddle and the scale applied on the way.
-template <bool FWD>
-__device__ __forceinline__ void utile_store(const UnevenArgs& a, const PassDesc& d, const UTileIdx& ti,
-                                            const float2* land)
-{
-    const bool sc = a.scale_on && d.apply_scale;
-    constexpr int LGTH = 8;
-    const int L = d.L, logT = d.logT, tid = threadIdx.x;
-    if (!d.out_tfast) {
-        const int lgt = LGTH - logT, t = tid >> lgt, step = 1 << lgt;
-        if (t >= ti.Tv) return;
-        float2* dst = uline_out(a, d, ti.o, ti.c0 + t);
-        const float2* src = land + t * L;
-        const int c = ti.c0 + t;
-        if ((L & 1) == 0 && ((uintptr_t)dst & 15) == 0) {
-            for (int k = 2 * (tid & (step - 1)); k < L; k += 2 * step) {
-                const float4 p = *reinterpret_cast<const float4*>(src + k);
-                const float2 y0 = uout<FWD>(d, make_float2(p.x, p.y), c, k, sc);
-                const float2 y1 = uout<FWD>(d, make_float2(p.z, p.w), c, k + 1, sc);
-                *reinterpret_cast<float4*>(dst + k) = make_float4(y0.x, y0.y, y1.x, y1.y);
-            }
-        } else {
-            for (int k = tid & (step - 1); k < L; k += step) dst[k] = uout<FWD>(d, src[k], c, k, sc);
-        }
-    } else {
-        float2* base = uline_out(a, d, ti.o, ti.c0);
-        const long long sk = d.out_sk;
-        const int T = 1 << logT;
-        if (logT >= 1 && (ti.Tv & 1) == 0 && (sk & 1) == 0 && ((uintptr_t)base & 15) == 0) {
-            const int lg = logT - 1, t = 2 * (tid & ((1 << lg) - 1)), step = kUnevenThreads >> lg;
-            if (t >= ti.Tv) return;
-            for (int k = tid >> lg; k < L; k += step) {
-                const float4 p = *reinterpret_cast<const float4*>(land + k * T + t);
-                const float2 y0 = uout<FWD>(d, make_float2(p.x, p.y), ti.c0 + t, k, sc);
-                const float2 y1 = uout<FWD>(d, make_float2(p.z, p.w), ti.c0 + t + 1, k, sc);
-                *reinterpret_cast<float4*>(base + k * sk + t) = make_float4(y0.x, y0.y, y1.x, y1.y);
-            }
-        } else {
-            const int t = tid & (T - 1), step = kUnevenThreads >> logT;
-            if (t >= ti.Tv) return;
-            for (int k = tid >> logT; k < L; k += step) base[k * sk + t] = uout<FWD>(d, land[k * T + t], ti.c0 + t, k, sc);
-        }
-    }
-}
-
 // A shared-memory value read with a volatile load (see ustage).
 template <class T>
 __device__ __forceinline__ T uvol(const T& x)
@@ -194,23 +150,26 @@ __device__ __forceinline__ T uvol(const T& x)
 }
 
 // One Stockham stage of radix R over the tile (see fft_device.cuh for the
-// formula): stage 0 reads the landing buffer (input layout), the last stage
-// writes it (output layout, before the twiddle and scale of the store),
-// stages between alternate between the two padded work buffers (stage st
-// writes buffer st & 1 and reads the other), so no stage waits between its
-// reads and its writes except a one-stage schedule.
+// formula).  Buffers: stage 0 reads the landing buffer (the input layout) and
+// writes the padded work buffer; from then on the tile's own landing buffer
+// is free and serves as the second work buffer: stage st >= 1 reads the work
+// buffer and writes the landing buffer when st is odd, the other way round
+// when st is even, so no stage waits between its reads and its writes.  The
+// last stage stores straight to global memory (coalesced in both output
+// layouts), with the four-step twiddle and the scale applied.
 template <int R, bool FWD, int POS>
-__device__ __forceinline__ void ustage(const PassDesc& d, int st, float2* land, float2* work, float2* work2, int Tv)
+__device__ __forceinline__ void ustage(const UnevenArgs& a, const PassDesc& d, int st, float2* land, float2* work,
+                                       const UTileIdx& ti)
 {
     constexpr int LGTH = 8;
     constexpr int Q = (kUnevenElems + R - 1) / R;
-    constexpr bool first = POS == kPosOnly || POS == kPosFirst;
-    constexpr bool last = POS == kPosOnly || POS == kPosLast;
-    float2* wr = (st & 1) ? work2 : work;
-    const float2* rd = (st & 1) ? work : work2;
-    // Descriptor fields are read afresh in every stage (volatile): left to
-    // itself the compiler keeps every radix's derived values live across all
-    // stages of the tile, which costs more registers than the stages need.
+    constexpr bool first = POS == kPosFirst;
+    constexpr bool last = POS == kPosLast;
+    static_assert(POS == kPosFirst || POS == kPosMid || POS == kPosLast, "stage positions of the uneven kernel");
+    const float2* rd = (st & 1) ? work : land;
+    float2* wr = (st & 1) ? land : work;
+    // Descriptor fields are read afresh in every stage (volatile loads), so
+    // nothing derived from them stays live from one stage to the next.
     const int L = uvol(d.L), LS = uvol(d.LS), logT = uvol(d.logT);
     const int LR = L / R;
     const bool in_tf = first && uvol(d.in_tfast) != 0;
@@ -220,7 +179,7 @@ __device__ __forceinline__ void ustage(const PassDesc& d, int st, float2* land, 
     const int lgG = LGTH - logT, G = 1 << lgG;
     const int t = tfast ? (tid & ((1 << logT) - 1)) : (tid >> lgG);
     const int jb = tfast ? (tid >> logT) : (tid & (G - 1));
-    const bool tok = t < Tv;
+    const bool tok = t < ti.Tv;
     float2 v[Q][R];
 #pragma unroll
     for (int q = 0; q < Q; ++q) {
@@ -247,10 +206,19 @@ __device__ __forceinline__ void ustage(const PassDesc& d, int st, float2* land, 
             for (int r = 0; r < R; ++r) v[q][r] = make_float2(0.f, 0.f);
         }
     }
-    if constexpr (first && last) __syncthreads();  // one-stage schedule: reads and writes share the tile
     const int Ns = first ? 1 : uvol(d.ns[st]);
     const unsigned nsm = first ? 0u : (unsigned)uvol(d.ns_mag[st]);
     const float2* twb = d.tw + (first ? 0 : uvol(d.twoff[st]));
+    float2* dst = nullptr;
+    long long sk = 0;
+    bool sc = false;
+    if constexpr (last) {
+        // line c0 + t of the output (contiguous output), or the tile's first
+        // column plus t (strided output)
+        dst = out_tf ? uline_out(a, d, ti.o, ti.c0) + t : uline_out(a, d, ti.o, ti.c0 + (tok ? t : 0));
+        sk = out_tf ? d.out_sk : 1;
+        sc = a.scale_on && d.apply_scale;
+    }
 #pragma unroll
     for (int q = 0; q < Q; ++q) {
         const int j = jb + q * G;
@@ -267,12 +235,12 @@ __device__ __forceinline__ void ustage(const PassDesc& d, int st, float2* land, 
                 float2* p = wr + t * LS;
 #pragma unroll
                 for (int r = 0; r < R; ++r) p[spad(base + r * Ns)] = v[q][r];
-            } else if (out_tf) {
-#pragma unroll
-                for (int r = 0; r < R; ++r) land[((base + r * Ns) << logT) + t] = v[q][r];
             } else {
 #pragma unroll
-                for (int r = 0; r < R; ++r) land[t * L + base + r * Ns] = v[q][r];
+                for (int r = 0; r < R; ++r) {
+                    const int kk = base + r * Ns;
+                    dst[kk * sk] = uout<FWD>(d, v[q][r], ti.c0 + t, kk, sc);
+                }
             }
         }
     }
@@ -280,41 +248,40 @@ __device__ __forceinline__ void ustage(const PassDesc& d, int st, float2* land, 
 
 // First or last stage: any radix of the schedule.
 template <bool FWD, int POS>
-__device__ __forceinline__ void ustage_any(const PassDesc& d, int st, float2* land, float2* work, float2* work2,
-                                           int Tv)
+__device__ __forceinline__ void ustage_any(const UnevenArgs& a, const PassDesc& d, int st, float2* land,
+                                           float2* work, const UTileIdx& ti)
 {
     switch (d.radix[st]) {
-    case 8: ustage<8, FWD, POS>(d, st, land, work, work2, Tv); break;
-    case 4: ustage<4, FWD, POS>(d, st, land, work, work2, Tv); break;
-    case 5: ustage<5, FWD, POS>(d, st, land, work, work2, Tv); break;
-    case 3: ustage<3, FWD, POS>(d, st, land, work, work2, Tv); break;
-    case 2: ustage<2, FWD, POS>(d, st, land, work, work2, Tv); break;
+    case 8: ustage<8, FWD, POS>(a, d, st, land, work, ti); break;
+    case 4: ustage<4, FWD, POS>(a, d, st, land, work, ti); break;
+    case 5: ustage<5, FWD, POS>(a, d, st, land, work, ti); break;
+    case 3: ustage<3, FWD, POS>(a, d, st, land, work, ti); break;
+    case 2: ustage<2, FWD, POS>(a, d, st, land, work, ti); break;
     default:  // radix 1: a copy (length 1, and the stage that ends a one-radix schedule)
-        ustage<1, FWD, POS>(d, st, land, work, work2, Tv);
+        ustage<1, FWD, POS>(a, d, st, land, work, ti);
         break;
     }
 }
 // Middle stages of radix R, from stage s while the schedule has that radix
 // (schedules list their radices in the order 8, 4, 2, 5, 3).
 template <int R, bool FWD>
-__device__ __forceinline__ void ustage_run(const PassDesc& d, int& s, int nst, float2* land, float2* work,
-                                           float2* work2, int Tv)
+__device__ __forceinline__ void ustage_run(const UnevenArgs& a, const PassDesc& d, int& s, int nst, float2* land,
+                                           float2* work, const UTileIdx& ti)
 {
     while (s < nst - 1 && d.radix[s] == R) {
-        ustage<R, FWD, kPosMid>(d, s, land, work, work2, Tv);
+        ustage<R, FWD, kPosMid>(a, d, s, land, work, ti);
         __syncthreads();
         ++s;
     }
 }
 
 template <bool FWD>
-__global__ void __launch_bounds__(kUnevenThreads, 3) k_fft_uneven(const __grid_constant__ UnevenArgs a)
+__global__ void __launch_bounds__(kUnevenThreads, 4) k_fft_uneven(const __grid_constant__ UnevenArgs a)
 {
     extern __shared__ __align__(128) unsigned char smem_dyn[];
     unsigned char* smem_raw = smem_dyn + ((128u - (smem_u32(smem_dyn) & 127u)) & 127u);
     float2* land0 = reinterpret_cast<float2*>(smem_raw);
     float2* work = land0 + 2 * a.land_max;
-    float2* work2 = work + a.work_max;
     __shared__ PassDesc sd[2];  // sd[b]: descriptor of the tile in landing buffer b
     constexpr int TH = kUnevenThreads;
     const int total = __ldg(a.tile_start + a.njobs);
@@ -354,17 +321,15 @@ __global__ void __launch_bounds__(kUnevenThreads, 3) k_fft_uneven(const __grid_c
         float2* land = land0 + b * a.land_max;
         const UTileIdx ti = utile_index(d, gl);
         const int nst = d.nst;  // >= 2: the planner ends a one-radix schedule with a radix-1 copy
-        ustage_any<FWD, kPosFirst>(d, 0, land, work, work2, ti.Tv);
+        ustage_any<FWD, kPosFirst>(a, d, 0, land, work, ti);
         __syncthreads();
         int s = 1;
-        ustage_run<8, FWD>(d, s, nst, land, work, work2, ti.Tv);
-        ustage_run<4, FWD>(d, s, nst, land, work, work2, ti.Tv);
-        ustage_run<2, FWD>(d, s, nst, land, work, work2, ti.Tv);
-        ustage_run<5, FWD>(d, s, nst, land, work, work2, ti.Tv);
-        ustage_run<3, FWD>(d, s, nst, land, work, work2, ti.Tv);
-        ustage_any<FWD, kPosLast>(d, nst - 1, land, work, work2, ti.Tv);
-        __syncthreads();
-        utile_store<FWD>(a, d, ti, land);
+        ustage_run<8, FWD>(a, d, s, nst, land, work, ti);
+        ustage_run<4, FWD>(a, d, s, nst, land, work, ti);
+        ustage_run<2, FWD>(a, d, s, nst, land, work, ti);
+        ustage_run<5, FWD>(a, d, s, nst, land, work, ti);
+        ustage_run<3, FWD>(a, d, s, nst, land, work, ti);
+        ustage_any<FWD, kPosLast>(a, d, nst - 1, land, work, ti);
         __syncthreads();  // buffer b and sd[b] are free for the tile after next
     }
 }
@@ -376,7 +341,7 @@ cudaError_t uneven_launch(bool forward, const UnevenArgs& a, long long grid, siz
 cudaError_t uneven_occupancy(bool forward, size_t smem, int* blocks_per_sm);
 inline size_t uneven_smem_bytes(int land_max, int work_max)
 {
-    return 128 + (size_t)(2LL * land_max + 2LL * work_max) * sizeof(float2);
+    return 128 + (size_t)(2LL * land_max + work_max) * sizeof(float2);
 }
 
 }  // namespace fbfft
