@@ -589,6 +589,12 @@ __device__ __forceinline__ void stage(const PassDesc& d, int st, float2* land, f
 #pragma unroll
                 for (int r = 0; r < R; ++r) v[q][r] = p[spad(j + r * LR)];
             }
+        } else {
+            // defined on every path: loaded and used under the same condition,
+            // which the register allocator cannot prove, the values would
+            // otherwise stay live around the tile loop
+#pragma unroll
+            for (int r = 0; r < R; ++r) v[q][r] = make_float2(0.f, 0.f);
         }
     }
     if constexpr (first == last && (!PP || first)) __syncthreads();  // reads and writes share one buffer

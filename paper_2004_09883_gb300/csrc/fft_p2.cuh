@@ -187,6 +187,13 @@ __device__ __forceinline__ void p2_stage(const PassDesc& d, float2* land, float2
 #pragma unroll
                 for (int r = 0; r < R; ++r) v[q][r] = p[spad(j + r * LR)];
             }
+        } else if constexpr (C::NST >= 3) {
+            // defined on every path: loaded and used under the same condition,
+            // which the register allocator cannot prove, the values of every
+            // stage would otherwise stay live around the tile loop (three-stage
+            // schedules spilled; two-stage ones measured faster without this)
+#pragma unroll
+            for (int r = 0; r < R; ++r) v[q][r] = make_float2(0.f, 0.f);
         }
     }
     if constexpr (first == last) compute_sync<THREADS>();  // reads and writes share the landing buffer
