@@ -342,12 +342,18 @@ typedef struct fb_fft_server_s* fb_fft_server_t;
 
 /* One finished request.  Times are seconds on the server's monotonic clock
  * (fb_fft_server_clock): t_submit at fb_fft_server_submit, t_admit when it
- * went to a slot, t_done when a submit/poll/drain saw its completion event. */
+ * went to a slot, t_done when a submit/poll/drain saw its completion event.
+ * t_dev_start / t_dev_end: when the request's work began and ended on the
+ * device (CUDA event timestamps on its slot's stream, seconds after an
+ * event the server recorded at creation), -1 when it did not run or failed;
+ * requests on different slots whose device intervals intersect overlapped
+ * on the GPU. */
 typedef struct fb_fft_server_done {
     long long tag;     /* the caller's tag from submit */
     int status;        /* FB_FFT_OK, FB_FFT_ERR_CANCELLED, _TIMEOUT or _CUDA */
     int slot;          /* stream slot it ran on, -1 if it never ran */
     double t_submit, t_admit, t_done;
+    double t_dev_start, t_dev_end;
 } fb_fft_server_done;
 
 typedef struct fb_fft_server_stats {

@@ -123,9 +123,11 @@ struct Req {
 
 struct Slot {
     cudaStream_t stream = nullptr;
-    cudaEvent_t done = nullptr;
+    cudaEvent_t start = nullptr;  // device time the request's work begins
+    cudaEvent_t done = nullptr;   // ... and ends (the completion the server polls)
     int* err_dev = nullptr;   // int[16] bounded-wait error word of this slot's launches
     int* err_host = nullptr;  // pinned copy, refreshed at the end of every request
+    bool err_mapped = false;  // err_dev is err_host mapped into the device: no copy per request
     bool busy = false;
     Req r;
     long long off = -1;  // arena block
@@ -140,6 +142,7 @@ struct fb_fft_server_s {
     int max_plans = 1;
     std::chrono::steady_clock::time_point t0;
     cudaStream_t build = nullptr;  // plans are built here
+    cudaEvent_t ref = nullptr;     // device-clock origin of the done records' device times
     Arena arena;
     std::vector<Slot> slots;
     std::map<ShapeKey, PlanEntry> plans;
@@ -208,6 +211,14 @@ void finish(fb_fft_server_s* s, Slot& sl, int slot_index, int status)
     d.t_submit = sl.r.t_submit;
     d.t_admit = sl.r.t_admit;
     d.t_done = now_s(s);
+    d.t_dev_start = d.t_dev_end = -1.0;
+    float a = 0.f, b = 0.f;
+    if (status == FB_FFT_OK && cudaEventElapsedTime(&a, s->ref, sl.start) == cudaSuccess &&
+        cudaEventElapsedTime(&b, s->ref, sl.done) == cudaSuccess) {
+        d.t_dev_start = a * 1e-3;
+        d.t_dev_end = b * 1e-3;
+    }
+    cudaGetLastError();
     s->done.push_back(d);
     if (sl.off >= 0) s->arena.release(sl.off, sl.r.need);
     sl.off = -1;
@@ -231,11 +242,13 @@ int retire(fb_fft_server_s* s)
         int status = FB_FFT_OK;
         if (q != cudaSuccess) {
             status = host::fail(q, "request completion");
-        } else if (sl.err_host[0] != 0) {
+        } else if (*static_cast<volatile int*>(sl.err_host) != 0) {
             status = FB_FFT_ERR_TIMEOUT;
             std::memset(sl.err_host, 0, 16 * sizeof(int));
-            const cudaError_t e = cudaMemsetAsync(sl.err_dev, 0, 16 * sizeof(int), sl.stream);
-            if (e != cudaSuccess) status = host::fail(e, "cudaMemsetAsync");
+            if (!sl.err_mapped) {
+                const cudaError_t e = cudaMemsetAsync(sl.err_dev, 0, 16 * sizeof(int), sl.stream);
+                if (e != cudaSuccess) status = host::fail(e, "cudaMemsetAsync");
+            }
         }
         finish(s, sl, i, status);
     }
@@ -250,6 +263,7 @@ int start(fb_fft_server_s* s, Slot& sl, const Req& r, long long off)
     void* scratch = r.pe->scratch ? block : nullptr;
     const void* in = r.in;
     void* out = r.out;
+    SV_CK(cudaEventRecord(sl.start, sl.stream));
     if (r.host_io) {
         void* stage = block + scr_bytes;
         SV_CK(cudaMemcpyAsync(stage, r.in, (size_t)r.pe->io, cudaMemcpyHostToDevice, sl.stream));
@@ -259,7 +273,8 @@ int start(fb_fft_server_s* s, Slot& sl, const Req& r, long long off)
     int rc = host::plan_exec_on(r.pe->plan, in, out, r.direction, sl.stream, scratch, sl.err_dev);
     if (rc != FB_FFT_OK) return rc;
     if (r.host_io) SV_CK(cudaMemcpyAsync(r.out, out, (size_t)r.pe->io, cudaMemcpyDeviceToHost, sl.stream));
-    SV_CK(cudaMemcpyAsync(sl.err_host, sl.err_dev, sizeof(int), cudaMemcpyDeviceToHost, sl.stream));
+    if (!sl.err_mapped)
+        SV_CK(cudaMemcpyAsync(sl.err_host, sl.err_dev, sizeof(int), cudaMemcpyDeviceToHost, sl.stream));
     SV_CK(cudaEventRecord(sl.done, sl.stream));
     return FB_FFT_OK;
 }
@@ -326,12 +341,14 @@ void free_server(fb_fft_server_s* s)
     for (Slot& sl : s->slots) {
         if (sl.stream) cudaStreamSynchronize(sl.stream);
         if (sl.done) cudaEventDestroy(sl.done);
+        if (sl.start) cudaEventDestroy(sl.start);
         if (sl.stream) cudaStreamDestroy(sl.stream);
         if (sl.err_host) cudaFreeHost(sl.err_host);
-        if (sl.err_dev) cudaFree(sl.err_dev);
+        if (sl.err_dev && !sl.err_mapped) cudaFree(sl.err_dev);
     }
     for (auto& kv : s->plans) host::plan_free(kv.second.plan);
     if (s->arena.base) cudaFree(s->arena.base);
+    if (s->ref) cudaEventDestroy(s->ref);
     if (s->build) cudaStreamDestroy(s->build);
     s->magic = 0;
     delete s;
@@ -363,15 +380,36 @@ int fb_fft_server_create(fb_fft_server_t* srv, int slots, long long hbm_cap_byte
         if (e != cudaSuccess && rc == FB_FFT_OK) rc = host::fail(e, what);
     };
     ck(cudaStreamCreateWithFlags(&s->build, cudaStreamNonBlocking), "cudaStreamCreate");
+    ck(cudaEventCreate(&s->ref), "cudaEventCreate");
+    if (rc == FB_FFT_OK) {
+        ck(cudaEventRecord(s->ref, s->build), "cudaEventRecord");
+        ck(cudaEventSynchronize(s->ref), "cudaEventSynchronize");
+    }
+    // Error words in host memory mapped into the device, where the device's
+    // atomics reach host memory natively: the kernels then record a timed-out
+    // wait there directly, and no request needs a copy of its error word.
+    int native = 0;
+    if (cudaDeviceGetAttribute(&native, cudaDevAttrHostNativeAtomicSupported, s->device) != cudaSuccess) {
+        cudaGetLastError();
+        native = 0;
+    }
     for (Slot& sl : s->slots) {
         if (rc != FB_FFT_OK) break;
         ck(cudaStreamCreateWithFlags(&sl.stream, cudaStreamNonBlocking), "cudaStreamCreate");
-        ck(cudaEventCreateWithFlags(&sl.done, cudaEventDisableTiming), "cudaEventCreate");
-        ck(cudaHostAlloc((void**)&sl.err_host, 16 * sizeof(int), cudaHostAllocDefault), "cudaHostAlloc");
-        ck(cudaMalloc((void**)&sl.err_dev, 16 * sizeof(int)), "cudaMalloc");
-        if (rc == FB_FFT_OK) {
-            std::memset(sl.err_host, 0, 16 * sizeof(int));
-            ck(cudaMemset(sl.err_dev, 0, 16 * sizeof(int)), "cudaMemset");
+        ck(cudaEventCreate(&sl.start), "cudaEventCreate");
+        ck(cudaEventCreate(&sl.done), "cudaEventCreate");
+        if (native) {
+            ck(cudaHostAlloc((void**)&sl.err_host, 16 * sizeof(int), cudaHostAllocMapped), "cudaHostAlloc");
+            if (rc == FB_FFT_OK) ck(cudaHostGetDevicePointer((void**)&sl.err_dev, sl.err_host, 0), "cudaHostGetDevicePointer");
+            sl.err_mapped = rc == FB_FFT_OK;
+            if (rc == FB_FFT_OK) std::memset(sl.err_host, 0, 16 * sizeof(int));
+        } else {
+            ck(cudaHostAlloc((void**)&sl.err_host, 16 * sizeof(int), cudaHostAllocDefault), "cudaHostAlloc");
+            ck(cudaMalloc((void**)&sl.err_dev, 16 * sizeof(int)), "cudaMalloc");
+            if (rc == FB_FFT_OK) {
+                std::memset(sl.err_host, 0, 16 * sizeof(int));
+                ck(cudaMemset(sl.err_dev, 0, 16 * sizeof(int)), "cudaMemset");
+            }
         }
     }
     if (rc == FB_FFT_OK && hbm_cap_bytes > 0) {
@@ -494,6 +532,7 @@ int fb_fft_server_cancel(fb_fft_server_t srv, long long tag)
         d.t_submit = it->t_submit;
         d.t_admit = -1.0;
         d.t_done = now_s(s);
+        d.t_dev_start = d.t_dev_end = -1.0;
         it->pe->users--;
         s->pending.erase(it);
         s->done.push_back(d);

@@ -58,7 +58,8 @@ class ManyOpts(ctypes.Structure):
 
 class ServerDone(ctypes.Structure):
     _fields_ = [("tag", ctypes.c_longlong), ("status", ctypes.c_int), ("slot", ctypes.c_int),
-                ("t_submit", ctypes.c_double), ("t_admit", ctypes.c_double), ("t_done", ctypes.c_double)]
+                ("t_submit", ctypes.c_double), ("t_admit", ctypes.c_double), ("t_done", ctypes.c_double),
+                ("t_dev_start", ctypes.c_double), ("t_dev_end", ctypes.c_double)]
 
 
 class ServerStats(ctypes.Structure):
@@ -496,8 +497,9 @@ class Server:
                                         int(direction), _vp(in_ptr), _vp(out_ptr), 1 if host_io else 0, int(tag)),
                "fb_fft_server_submit")
 
-    def poll(self, wait: bool = False) -> list[tuple]:
-        """Finished requests as (tag, status, slot, t_submit, t_admit, t_done)."""
+    def poll(self, wait: bool = False, device_times: bool = False) -> list[tuple]:
+        """Finished requests as (tag, status, slot, t_submit, t_admit, t_done),
+        plus (t_dev_start, t_dev_end) with ``device_times``."""
         out = []
         while True:
             n = _int(0)
@@ -505,7 +507,8 @@ class Server:
                    "fb_fft_server_poll")
             for i in range(n.value):
                 d = self._buf[i]
-                out.append((d.tag, d.status, d.slot, d.t_submit, d.t_admit, d.t_done))
+                rec = (d.tag, d.status, d.slot, d.t_submit, d.t_admit, d.t_done)
+                out.append(rec + (d.t_dev_start, d.t_dev_end) if device_times else rec)
             if n.value < len(self._buf):
                 return out
             wait = False

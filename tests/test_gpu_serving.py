@@ -194,3 +194,34 @@ def test_server_handle_errors(fb):
             x = torch.zeros(1 << 16, dtype=torch.complex64, device="cuda")
             srv.submit_ptr([1 << 16], x.data_ptr(), x.data_ptr(), 0, FWD)
         assert e.value.status == -9
+
+
+def test_requests_overlap_on_the_device(fb):
+    """Continuous batching means requests run at the same time on the GPU:
+    with 8 slots, more than one request is in flight at once, and the device
+    intervals [t_dev_start, t_dev_end] of requests on different slots
+    intersect (CUDA event timestamps on the slots' streams).  Every result
+    still matches the oracle."""
+    import torch
+    n, batch, count = 1 << 22, 2, 12
+    xs = [torch.from_numpy(inputs.uniform_c64((batch * n,), 7300 + i)).cuda() for i in range(count)]
+    ys = [torch.empty_like(x) for x in xs]
+    torch.cuda.synchronize()
+    with fb.Server(slots=8, hbm_cap_bytes=2 << 30) as srv:
+        srv.prepare([n], batch)
+        for i in range(count):
+            srv.submit_ptr([n], xs[i].data_ptr(), ys[i].data_ptr(), i, FWD, batch=batch)
+        srv.drain()
+        recs = srv.poll(device_times=True)
+        st = srv.stats()
+    assert sorted(r[0] for r in recs) == list(range(count)) and all(r[1] == 0 for r in recs)
+    assert st["max_in_flight"] > 1
+    iv = [(r[6], r[7], r[2]) for r in recs]
+    assert all(0.0 <= a < b for a, b, _ in iv), iv
+    overlapping = sum(1 for i in range(count) for j in range(i + 1, count)
+                      if iv[i][2] != iv[j][2] and iv[i][0] < iv[j][1] and iv[j][0] < iv[i][1])
+    assert overlapping > 0, iv
+    for i in (0, count - 1):
+        ref = oracle.fft(xs[i].cpu().numpy().astype(np.complex128), [n], FWD, False, 8)
+        err = oracle.rel_l2(ys[i].cpu().numpy().reshape(batch, n), ref.reshape(batch, n))
+        assert err.max() <= tol(n)
