@@ -229,20 +229,31 @@ __device__ __forceinline__ void p2_stage(const PassDesc& d, float2* land, float2
                 for (int r = 0; r < R; ++r) p[spad(base + r * NS)] = v[q][r];
             } else {
                 // last stage: NS = L / R, so k == j and output index kk = j + r * LR
+                // Four-step twiddle exp(-2 pi i c kk / N) of output kk of line c:
+                // read from the split tables for r = 0 and r = 8, and stepped by
+                // exp(-2 pi i c LR / N) for the r between (at most 7 products in a
+                // row: a few ulp).  The table reads are gathers over the 16
+                // lines of a half-warp at stride kk, which land on few banks:
+                // three per butterfly instead of one per value.
+                float2 w = make_float2(1.f, 0.f), wstep = make_float2(1.f, 0.f);
+                const unsigned c = (unsigned)(c0 + t);
+                auto ptw_at = [&](unsigned m) {  // m = c kk < N < 2^31
+                    const unsigned mlo = m & ((1u << d.ptw_log) - 1), mhi = m >> d.ptw_log;
+                    if (d.ptw_smem) {  // tables copied behind the stage twiddles
+                        const float2* pt = tws + C::TWS;
+                        return cmul(pt[(1u << d.ptw_log) + mhi], pt[mlo]);
+                    }
+                    return cmul(__ldg(d.ptw_hi + mhi), __ldg(d.ptw_lo + mlo));
+                };
+                if constexpr (C::PTW) {
+                    if constexpr (R > 1) wstep = ptw_at(c * (unsigned)LR);
+                }
 #pragma unroll
                 for (int r = 0; r < R; ++r) {
                     const int kk = j + r * LR;
                     float2 y = v[q][r];
                     if constexpr (C::PTW) {
-                        const unsigned m = (unsigned)(c0 + t) * (unsigned)kk;  // < N < 2^31
-                        const unsigned mlo = m & ((1u << d.ptw_log) - 1), mhi = m >> d.ptw_log;
-                        float2 w;
-                        if (d.ptw_smem) {  // tables copied behind the stage twiddles
-                            const float2* pt = tws + C::TWS;
-                            w = cmul(pt[(1u << d.ptw_log) + mhi], pt[mlo]);
-                        } else {
-                            w = cmul(__ldg(d.ptw_hi + mhi), __ldg(d.ptw_lo + mlo));
-                        }
+                        w = (r % 8 == 0) ? ptw_at(c * (unsigned)kk) : cmul(w, wstep);
                         y = twmul<FWD>(y, w);
                     }
                     if (d.apply_scale) y = d.scale * y;
