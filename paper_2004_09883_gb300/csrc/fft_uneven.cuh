@@ -128,18 +128,10 @@ __device__ __forceinline__ void utile_load(const UnevenArgs& a, const PassDesc& 
     }
 }
 
-// The output value y of line c (within its job), index k, finished: the
-// four-step twiddle exp(s 2 pi i c k / N) and the 1/N scale, where asked.
-template <bool FWD>
-__device__ __forceinline__ float2 uout(const PassDesc& d, float2 y, int c, int k, bool scale)
+// exp(-2 pi i m / N) from the job's two split four-step tables (m < N < 2^31).
+__device__ __forceinline__ float2 uptw(const PassDesc& d, unsigned m)
 {
-    if (d.ptw) {
-        const unsigned m = (unsigned)c * (unsigned)k;  // < N < 2^31
-        const float2 w = cmul(__ldg(d.ptw_hi + (m >> d.ptw_log)), __ldg(d.ptw_lo + (m & ((1u << d.ptw_log) - 1))));
-        y = twmul<FWD>(y, w);
-    }
-    if (scale) y = d.scale * y;
-    return y;
+    return cmul(__ldg(d.ptw_hi + (m >> d.ptw_log)), __ldg(d.ptw_lo + (m & ((1u << d.ptw_log) - 1))));
 }
 
 // A shared-memory value read with a volatile load (see ustage).
@@ -236,10 +228,24 @@ __device__ __forceinline__ void ustage(const UnevenArgs& a, const PassDesc& d, i
 #pragma unroll
                 for (int r = 0; r < R; ++r) p[spad(base + r * Ns)] = v[q][r];
             } else {
+                // last stage: Ns = L / R, so base = j and kk = j + r Ns.  The
+                // four-step twiddle exp(-2 pi i c kk / N) is read from the split
+                // tables for r = 0 and stepped by exp(-2 pi i c Ns / N) for the
+                // rest (at most 7 products in a row): one gather per butterfly
+                const unsigned c = (unsigned)(ti.c0 + t);
+                const bool ptw = d.ptw != 0;
+                float2 w = make_float2(1.f, 0.f), wstep = make_float2(1.f, 0.f);
+                if (ptw && R > 1) wstep = uptw(d, c * (unsigned)Ns);
 #pragma unroll
                 for (int r = 0; r < R; ++r) {
                     const int kk = base + r * Ns;
-                    dst[kk * sk] = uout<FWD>(d, v[q][r], ti.c0 + t, kk, sc);
+                    float2 y = v[q][r];
+                    if (ptw) {
+                        w = r == 0 ? uptw(d, c * (unsigned)kk) : cmul(w, wstep);
+                        y = twmul<FWD>(y, w);
+                    }
+                    if (sc) y = d.scale * y;
+                    dst[kk * sk] = y;
                 }
             }
         }
