@@ -702,6 +702,35 @@ def uneven_lengths(wl: dict) -> np.ndarray:
     return inputs.uneven_lengths(count, lo, hi, wl["seed"])
 
 
+def uneven_roofline(passes, prof_steps, lens, bytes_step, ms, launches_per_exec, wl_name, peaks):
+    """Roofline of a batched uneven exec.  One-kernel engine: the dominant of
+    its two launches, phase 0 moving one read and one write of every value,
+    phase 1 of every value of a length above 2048 (the four-step rows).  The
+    per-kernel engine: the whole exec (all its launches)."""
+    phase_bytes = {"many.uneven.phase0": bytes_step,
+                   "many.uneven.phase1": float(sum(16 * int(n) for n in lens if int(n) > 2048))}
+    dom = max(passes, key=lambda r: r[1]) if passes else None
+    if dom and dom[0] in phase_bytes and dom[2] > 0:
+        per_launch_ms = dom[1] / dom[2]
+        achieved = phase_bytes[dom[0]] / (per_launch_ms / 1e3) / 1e9
+        tr = load_traffic(wl_name)
+        traffic = tr["dram_bytes_per_launch"] if tr and tr.get("pass") == dom[0] else None
+        r = {"bound": "hbm", "achieved": round(achieved, 2), "peak": peaks["hbm_gbs"], "unit": "GB/s",
+             "frac": round(achieved / peaks["hbm_gbs"], 4), "traffic": traffic, "kernel_pass": dom[0],
+             "launch_ms": round(per_launch_ms, 5), "algorithmic_bytes_per_launch": phase_bytes[dom[0]],
+             "launches_per_exec": round(launches_per_exec, 2),
+             "basis": "one read + one write of the values the launch transforms / its event-timed duration"}
+        if traffic is not None:
+            r["traffic_note"] = ("dram__bytes_read.sum + dram__bytes_write.sum of this launch in one ncu capture "
+                                 "(reads plus the write-back during the launch)")
+        return r
+    return {"bound": "hbm", "achieved": round(bytes_step / (ms / 1e3) / 1e9, 2), "peak": peaks["hbm_gbs"],
+            "unit": "GB/s", "frac": round(bytes_step / (ms / 1e3) / 1e9 / peaks["hbm_gbs"], 4), "traffic": None,
+            "kernel_pass": "whole exec", "launches_per_exec": round(launches_per_exec, 2),
+            "algorithmic_bytes_per_launch": bytes_step,
+            "basis": "one read + one write of every transform / exec time (all launches of one exec)"}
+
+
 def gpu_many(args, ctx: Ctx, wl: dict, headline: bool) -> dict:
     """Batched uneven 1-D lengths: one exec of the autotuned batched plan
     (fb_fft_plan_many) per step against the plain per-call path (one
@@ -749,9 +778,36 @@ def gpu_many(args, ctx: Ctx, wl: dict, headline: bool) -> dict:
             plans[int(n)].exec_ptr(a + 8 * int(o), b + 8 * int(o), fbfft.FORWARD)
 
     ms_plain, _ = event_timed(ctx, per_call, max(3, min(args.steps, 20)), 3)
+    # per-launch times of the batched plan (a separate loop: the event pairs
+    # around each launch would serialise the timed loop's launches)
+    prof_steps = max(3, min(args.steps, 20))
+    plan.profile(True)
+    for i in range(prof_steps):
+        batched(i)
+    ctx.barrier()
+    passes = plan.profile_read()
+    plan.profile(False)
     clk = clocks.summary(wall0, wall1) if clocks else None
     if clocks:
         clocks.stop()
+    # end to end through the host-array call on pinned packed arrays: the
+    # packed batch in, one exec, the packed result out, every step
+    e2e = None
+    if not args.quick:
+        hbuf = [torch.from_numpy(h).pin_memory() for h in host_in]
+        hres = [torch.empty_like(hbuf[0]).pin_memory() for _ in range(nbuf)]
+        e2e_steps = max(3, min(args.steps, 10))
+        for i in range(2):
+            plan.exec_host(hbuf[i % nbuf].numpy(), hres[i % nbuf].numpy(), fbfft.FORWARD)
+        ctx.barrier()
+        t0 = time.perf_counter()
+        for i in range(e2e_steps):
+            plan.exec_host(hbuf[i % nbuf].numpy(), hres[i % nbuf].numpy(), fbfft.FORWARD)
+        ctx.barrier()
+        e2e_ms = ctx.max((time.perf_counter() - t0) / e2e_steps * 1e3)
+        e2e = {"value": round(whole_job_rate(world, bytes_step, e2e_ms) / 1e9, 3), "unit": "GB/s",
+               "h2d_bytes_per_step": 8 * total, "d2h_bytes_per_step": 8 * total, "ms_per_step": e2e_ms,
+               "path": "fb_fft_exec_host (pinned packed host arrays), forward"}
     errors = None
     if rank == 0 and not args.quick:
         y = plan.exec(xin[0], None, fbfft.FORWARD)
@@ -779,16 +835,14 @@ def gpu_many(args, ctx: Ctx, wl: dict, headline: bool) -> dict:
                        else "single GPU", "path": "fb_fft_plan_many, autotuned, one exec per step"},
             "gflops": round(whole_job_rate(world, flops_step, ms) / 1e9, 2),
             "hbm_frac_effective": round(value / world / peaks["hbm_gbs"], 4),
-            "roofline": {"bound": "hbm", "achieved": round(bytes_step / (ms / 1e3) / 1e9, 2),
-                         "peak": peaks["hbm_gbs"], "unit": "GB/s",
-                         "frac": round(bytes_step / (ms / 1e3) / 1e9 / peaks["hbm_gbs"], 4), "traffic": None,
-                         "kernel_pass": "whole exec", "launches_per_exec": round(launches / max(1, args.steps), 2),
-                         "algorithmic_bytes_per_launch": bytes_step,
-                         "basis": "one read + one write of every transform / exec time (all launches of one exec)"},
+            "roofline": uneven_roofline(passes, prof_steps, lens, bytes_step, ms, launches / max(1, args.steps),
+                                        wl["name"], peaks),
+            "passes": [{"pass": p[0], "ms_per_launch": round(p[1] / max(1, p[2]), 5), "launches": p[2]}
+                       for p in passes],
             "plain_per_call": {"value": round(whole_job_rate(world, bytes_step, ms_plain) / 1e9, 3), "unit": "GB/s",
                                "ms_per_step": round(ms_plain, 4), "execs_per_step": len(lens)},
             "speedup_vs_plain_per_call": round(ms_plain / ms, 3),
-            "autotuned": tuned.as_dict(), "untuned_plan_ms_per_step": round(ms_default, 4),
+            "autotuned": tuned.as_dict(), "untuned_plan_ms_per_step": round(ms_default, 4), "e2e": e2e,
             "cpu_baseline": None if args.quick else (lambda cb: {
                 "value": round(cb["value"], 4), "unit": "GB/s", "cores": host_threads(),
                 "kind": "oracle", "sample": f"first {cb['transforms']} transforms of the workload by the FP64 "
@@ -913,6 +967,11 @@ def gpu_serving(args, ctx: Ctx, wl: dict, headline: bool) -> dict:
                                                 "served_p99_ms": round(host_half["p99_ms"], 4),
                                                 "plain_p50_ms": round(host_half_plain["p50_ms"], 4),
                                                 "plain_p99_ms": round(host_half_plain["p99_ms"], 4)}},
+            "e2e": {"value": round(host_sat["throughput_gbs"] * world, 3), "unit": "GB/s",
+                    "h2d_bytes_per_step": wh.bytes_moved() // 2, "d2h_bytes_per_step": wh.bytes_moved() // 2,
+                    "ms_per_step": round(host_sat["wall_s"] * 1e3, 3),
+                    "path": f"fb_fft_server_submit on pinned host arrays, the first {len(hshapes)} requests of "
+                            "the mix at t=0, copies through the server's staging"},
             "server_stats": {k: st[k] for k in ("plans", "plan_builds", "arena_peak", "max_in_flight")},
             "roofline": None,
             "roofline_note": "a mix of 3000+ shapes: the per-kernel rooflines are those of the other workloads",
