@@ -65,7 +65,7 @@ WORKLOADS = {
                      seed=inputs.seed_for(inputs.WORKLOAD_1D_2P20x32), dist="normal", inverse=False, tc=True),
     "serving": dict(name="serving_mix_2000_requests_1d_2d_3d_poisson", dims=None, batch=1,
                     seed=inputs.seed_for(inputs.WORKLOAD_SERVING), dist="uniform", inverse=False,
-                    serving=dict(requests=2000, host_requests=600, slots=8, hbm_cap=40 * 10 ** 9,
+                    serving=dict(requests=2000, host_requests=600, slots=8, hbm_cap=40 * 10 ** 9, max_batch=64,
                                  fractions=[0.1, 0.25, 0.5, 0.75, 0.9, 1.1], checked=100)),
     "grid2048": dict(name="2d_c2c_2048x2048_fwd_then_inv_scaled", dims=[2048, 2048], batch=1,
                      seed=inputs.seed_for(inputs.WORKLOAD_GRID_2048x2048), dist="normal", inverse=True),
@@ -878,7 +878,7 @@ def gpu_serving(args, ctx: Ctx, wl: dict, headline: bool) -> dict:
     w = serving.Workload(shapes, seed)
     hshapes = shapes[:cfg["host_requests"]]
     wh = serving.Workload(hshapes, seed, host=True)
-    srv = fbfft.Server(slots=cfg["slots"], hbm_cap_bytes=cfg["hbm_cap"])
+    srv = fbfft.Server(slots=cfg["slots"], hbm_cap_bytes=cfg["hbm_cap"], max_batch=cfg["max_batch"])
     for s in set(shapes):
         srv.prepare(list(s))
     plans = serving.plain_plans(w)
@@ -913,6 +913,11 @@ def gpu_serving(args, ctx: Ctx, wl: dict, headline: bool) -> dict:
                   "tolerance_rel_l2": "2e-6 log2 N per request", "items": k, "of_items": len(shapes),
                   "pass": bool((e <= tols).all())}
     sat_plain = [serving.run_plain(plans, w, zero) for _ in range(3)]
+    # the same server with batching off: every request alone through its plan
+    srv.set_batch(1)
+    serving.run_served(srv, w, zero)
+    sat_alone = max((serving.run_served(srv, w, zero) for _ in range(3)), key=lambda r: r["throughput_req_s"])
+    srv.set_batch(cfg["max_batch"])
     ctx.barrier()
     best = max(sat, key=lambda r: r["throughput_req_s"])
     best_plain = max(sat_plain, key=lambda r: r["throughput_req_s"])
@@ -947,7 +952,7 @@ def gpu_serving(args, ctx: Ctx, wl: dict, headline: bool) -> dict:
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": wl["name"], "requests": len(shapes), "rank_mix": kinds,
                        "distinct_shapes": len(set(shapes)), "elements": int(sum(w.n)),
-                       "slots": cfg["slots"], "hbm_cap_bytes": cfg["hbm_cap"],
+                       "slots": cfg["slots"], "hbm_cap_bytes": cfg["hbm_cap"], "max_batch": cfg["max_batch"],
                        "step": "one replay of the whole request list, all arriving at t=0",
                        "l2": f"{nb / 2 / 2 ** 30:.1f} GiB of distinct inputs per step > 126 MB L2",
                        "parallelism": "replicas" if world > 1 else "single GPU"},
@@ -956,6 +961,7 @@ def gpu_serving(args, ctx: Ctx, wl: dict, headline: bool) -> dict:
                            "served_gbs": round(best["throughput_gbs"], 2),
                            "plain_gbs": round(best_plain["throughput_gbs"], 2),
                            "speedup_vs_plain": round(best["throughput_req_s"] / rate_plain, 3),
+                           "unbatched_server_req_s": round(sat_alone["throughput_req_s"], 1),
                            "served_p50_ms": round(best["p50_ms"], 4), "served_p99_ms": round(best["p99_ms"], 4),
                            "plain_p50_ms": round(best_plain["p50_ms"], 4),
                            "plain_p99_ms": round(best_plain["p99_ms"], 4)},
@@ -972,7 +978,8 @@ def gpu_serving(args, ctx: Ctx, wl: dict, headline: bool) -> dict:
                     "ms_per_step": round(host_sat["wall_s"] * 1e3, 3),
                     "path": f"fb_fft_server_submit on pinned host arrays, the first {len(hshapes)} requests of "
                             "the mix at t=0, copies through the server's staging"},
-            "server_stats": {k: st[k] for k in ("plans", "plan_builds", "arena_peak", "max_in_flight")},
+            "server_stats": {k: st[k] for k in ("plans", "plan_builds", "arena_peak", "max_in_flight", "batches",
+                                                "batched_requests", "largest_batch", "max_busy_slots")},
             "roofline": None,
             "roofline_note": "a mix of 3000+ shapes: the per-kernel rooflines are those of the other workloads",
             "gpu_launches": int(launches), "clocks": clk, "kernel_hash": kernel_hash(),

@@ -324,16 +324,18 @@ int fb_fft_twiddles(long long d, long long count, float* host_out);
  * in its production environment (Sec. 3.1, Sec. 5.1(c)); when many callers
  * offload transforms of mixed shapes to one GPU, calling fb_fft_plan/exec per
  * call serialises them.  A server keeps plans resident (one per shape, shared
- * by all slots: twiddle tables are read-only) and runs each admitted request
- * on one of `slots` CUDA streams, so the copies and kernels of requests that
- * arrive while others run overlap on the device.  A request is admitted, in
+ * by all slots: twiddle tables are read-only) and runs each admitted request,
+ * or batch of queued requests (fb_fft_server_set_batch), on one of `slots`
+ * CUDA streams, so the copies and kernels of requests that arrive while
+ * others run overlap on the device.  A request is admitted, in
  * arrival (FIFO) order, as soon as a slot is free and its device bytes fit in
  * the server's memory budget: an arena of `hbm_cap_bytes` reserved once at
  * creation, from which each request takes its four-step scratch and, for
  * host-array requests, one staging buffer; both return to the arena when the
  * request completes.  Completion is observed with a CUDA event per slot; every
- * submit and poll first retires finished requests and admits waiting ones,
- * with no batch barrier.  Nothing blocks except poll with wait != 0 and drain.
+ * submit and poll first retires finished requests and admits waiting ones;
+ * slots never wait for one another (the requests of one batch are reported
+ * done together).  Nothing blocks except poll with wait != 0 and drain.
  *
  * Not thread-safe: one host thread drives a server.  The device current at
  * fb_fft_server_create must be current on every later call.
@@ -361,9 +363,13 @@ typedef struct fb_fft_server_stats {
     long long pending, in_flight;          /* now */
     long long plans, plan_builds, plan_bytes; /* resident plans, plans built, their device bytes */
     long long arena_bytes, arena_in_use, arena_peak;
-    long long max_in_flight;               /* most requests on slots at once */
+    long long max_in_flight;               /* most requests admitted and not yet retired at once */
     int slots;
     int reserved;
+    long long batches;                     /* batches run (see fb_fft_server_set_batch) */
+    long long batched_requests;            /* requests that ran in them */
+    long long largest_batch;               /* most requests in one batch */
+    long long max_busy_slots;              /* most slots busy at once (<= slots) */
 } fb_fft_server_stats;
 
 /*
@@ -378,6 +384,28 @@ typedef struct fb_fft_server_stats {
  * Errors: INVALID_ARG, ALLOC, CUDA, NO_DEVICE.
  */
 int fb_fft_server_create(fb_fft_server_t* srv, int slots, long long hbm_cap_bytes, int max_plans);
+
+/*
+ * fb_fft_server_set_batch -- how many queued requests one slot may take at
+ * once (default 64: with 8 slots, batches of 64 keep several slots' batches
+ * overlapping on the device; larger ones leave fewer, longer batches).  A shape whose every axis (or, for a 1-D length above
+ * 2048, both four-step factors) is at most 2048 points and that does not ask
+ * for the tensor cores has a resident batch recipe; when a slot frees up, the
+ * queue's head and the recipe requests right behind it (FIFO, as long as
+ * the memory budget holds them, at most max_requests and 1024 jobs) run
+ * together: their job descriptors, with each request's own addresses, go to
+ * the device in one copy and run as one launch per phase and direction (at
+ * most six launches for the whole batch).  The batch grows with the queue:
+ * a request that finds a slot free starts at once, alone.  Results do not
+ * depend on what else is in the batch (same bits alone and in any batch);
+ * they can differ in the last bits from the per-request path, which uses the
+ * plan's own kernels.
+ *   max_requests  <= 1: no batching, every request runs alone through its
+ *                 shape's plan (the per-call kernels).  Applies to requests
+ *                 submitted after the call.
+ * Errors: BAD_PLAN.
+ */
+int fb_fft_server_set_batch(fb_fft_server_t srv, int max_requests);
 
 /*
  * fb_fft_server_submit -- queue one transform (rank, dims, batch, flags as
@@ -397,6 +425,34 @@ int fb_fft_server_create(fb_fft_server_t* srv, int slots, long long hbm_cap_byte
  */
 int fb_fft_server_submit(fb_fft_server_t srv, int rank, const long long* dims, long long batch, unsigned flags,
                          int direction, const void* in, void* out, int host_io, long long tag);
+
+/* One request of fb_fft_server_submit_many: the arguments of
+ * fb_fft_server_submit (dims[rank..2] are ignored). */
+typedef struct fb_fft_server_request {
+    long long dims[3];
+    long long batch;
+    long long tag;
+    const void* in;
+    void* out;
+    int rank;
+    unsigned flags;
+    int direction;
+    int host_io;
+} fb_fft_server_request;
+
+/*
+ * fb_fft_server_submit_many -- queue `count` requests in this order, then
+ * admit once: what a caller holding several requests that arrived together
+ * hands over in one call, so that the queue they form can run as one batch
+ * (fb_fft_server_set_batch) instead of each being admitted while the next
+ * is still being submitted.  status[i] receives what fb_fft_server_submit
+ * would return for reqs[i] (a rejected request is not queued; the others
+ * still are).  reqs and status: `count` entries, owned by the caller, not
+ * kept after the call.
+ * Errors (nothing queued): BAD_PLAN, INVALID_ARG (count < 0, or a null
+ * array with count > 0); CUDA from the admission.
+ */
+int fb_fft_server_submit_many(fb_fft_server_t srv, const fb_fft_server_request* reqs, int count, int* status);
 
 /* fb_fft_server_prepare -- build (or touch) the resident plan of a shape now. */
 int fb_fft_server_prepare(fb_fft_server_t srv, int rank, const long long* dims, long long batch, unsigned flags);

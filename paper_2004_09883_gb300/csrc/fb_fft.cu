@@ -24,6 +24,7 @@
 #include <cstring>
 #include <map>
 #include <memory>
+#include <mutex>
 #include <new>
 #include <vector>
 
@@ -1379,6 +1380,166 @@ int plan_exec_on(fb_fft_plan_t p, const void* in, void* out, int direction, cuda
 void plan_free(fb_fft_plan_t p)
 {
     if (plan_ok(p)) free_plan(p);
+}
+
+// The jobs of one request shape on the one-kernel engine, with the same
+// pass geometry as a regular plan: a 1-D length up to 2048 is one job over
+// the batch's lines; a longer one a four-step pair through the request's
+// scratch (columns with the post-twiddle, then rows written transposed); a
+// 2-D / 3-D shape one job per axis, last axis first, the first reading the
+// input and the others in place on the output.
+int recipe_create(BatchRecipe** out, int rank, const long long* dims, long long batch, unsigned flags,
+                  cudaStream_t stream)
+{
+    if (!out) return FB_FFT_ERR_INVALID_ARG;
+    *out = nullptr;
+    if (rank < 1 || rank > 3 || !dims || batch < 1) return FB_FFT_ERR_INVALID_ARG;
+    if (flags & FB_FFT_TENSOR_CORES) return FB_FFT_ERR_UNSUPPORTED_SIZE;
+    long long N = 1;
+    for (int e = 0; e < rank; ++e) {
+        if (dims[e] < 1 || !is_smooth(dims[e])) return FB_FFT_ERR_UNSUPPORTED_SIZE;
+        N *= dims[e];
+    }
+    if (N * batch >= (1LL << 40)) return FB_FFT_ERR_UNSUPPORTED_SIZE;
+    TwiddleBuilder twb;
+    std::vector<PassPlan> passes;
+    long long scratch = 0;
+    int rc = FB_FFT_OK;
+    if (rank == 1 && N > kUnevenMaxLen) {
+        long long N1, N2;
+        rc = split_uneven(N, &N1, &N2);
+        if (rc != FB_FFT_OK) return rc;
+        const int plog = (ilog2ll(N) + 1) / 2;
+        const long long lo_cnt = 1LL << plog, hi_cnt = (N + lo_cnt - 1) >> plog;
+        const long long lo_off = twb.add_linear(lo_cnt, N, 1);
+        const long long hi_off = twb.add_linear(hi_cnt, N, lo_cnt);
+        PassPlan a, r;
+        rc = make_uneven_pass(a, twb, N1, batch, N2, N2, 1, N, N2, 1, N, true, true, true);
+        if (rc != FB_FFT_OK) return rc;
+        a.d.ptw_log = plog;
+        a.d.ptw_lo = reinterpret_cast<const float2*>(lo_off);
+        a.d.ptw_hi = reinterpret_cast<const float2*>(hi_off);
+        a.src = kBufIn, a.dst = kBufScratch, a.group = 0;
+        rc = make_uneven_pass(r, twb, N2, batch, N1, 1, N2, N, N1, 1, N, false, true, false);
+        if (rc != FB_FFT_OK) return rc;
+        r.src = kBufScratch, r.dst = kBufOut, r.group = 1, r.last = true;
+        passes.push_back(a);
+        passes.push_back(r);
+        scratch = batch * N;
+    } else {
+        for (int ax = rank - 1; ax >= 0; --ax) {
+            const long long L = dims[ax];
+            if (L == 1 && !(ax == 0 && passes.empty())) continue;  // a shape of ones still copies
+            long long S = 1, Opre = 1;
+            for (int e = ax + 1; e < rank; ++e) S *= dims[e];
+            for (int e = 0; e < ax; ++e) Opre *= dims[e];
+            PassPlan q;
+            if (S == 1 || L == 1)
+                rc = make_uneven_pass(q, twb, L, 1, batch * N / L, 1, L, 0, 1, L, 0, false, false, false);
+            else
+                rc = make_uneven_pass(q, twb, L, batch * Opre, S, S, 1, L * S, S, 1, L * S, true, true, false);
+            if (rc != FB_FFT_OK) return rc;
+            q.src = passes.empty() ? kBufIn : kBufOut;
+            q.dst = kBufOut;
+            q.group = (int)passes.size();
+            passes.push_back(q);
+        }
+        passes.back().last = true;
+    }
+    for (const PassPlan& q : passes)
+        if (q.d.ntiles >= (1LL << 30)) return FB_FFT_ERR_UNSUPPORTED_SIZE;
+    BatchRecipe* r = new (std::nothrow) BatchRecipe();
+    if (!r) return FB_FFT_ERR_ALLOC;
+    const long long tw_elems = std::max(2LL, twb.total);
+    if (cudaMalloc(&r->tw, (size_t)tw_elems * sizeof(float2)) != cudaSuccess) {
+        cudaGetLastError();
+        delete r;
+        return FB_FFT_ERR_ALLOC;
+    }
+    for (const TwiddleJob& j : twb.jobs) {
+        const cudaError_t e = launch_twiddles(r->tw, j, stream);
+        if (e != cudaSuccess) {
+            recipe_free(r);
+            return cuda_fail(e, "recipe twiddles");
+        }
+    }
+    r->table_bytes = tw_elems * (long long)sizeof(float2);
+    r->scratch_bytes = scratch * (long long)sizeof(float2);
+    r->scale = (float)(1.0 / (double)N);
+    for (const PassPlan& q : passes) {
+        BatchJob j;
+        j.d = q.d;
+        j.d.tw = r->tw;
+        if (j.d.ptw) {
+            j.d.ptw_lo = r->tw + reinterpret_cast<long long>(q.d.ptw_lo);
+            j.d.ptw_hi = r->tw + reinterpret_cast<long long>(q.d.ptw_hi);
+        }
+        j.d.in = nullptr;
+        j.d.out = nullptr;
+        j.d.apply_scale = q.last ? 1 : 0;
+        j.d.scale = r->scale;
+        j.phase = q.group;
+        j.src = q.src == kBufIn ? 0 : (q.src == kBufOut ? 1 : 2);
+        j.dst = q.dst == kBufOut ? 1 : 2;
+        j.last = q.last;
+        const int padded = (int)(((long long)q.d.LS * (1LL << q.d.logT) + 15) & ~15LL);
+        j.land = std::max(q.d.land_stride, padded);  // also serves as a work buffer
+        j.work = padded;
+        r->jobs.push_back(j);
+        r->phases = std::max(r->phases, q.group + 1);
+        r->tiles += q.d.ntiles;
+    }
+    *out = r;
+    return FB_FFT_OK;
+}
+
+void recipe_free(BatchRecipe* r)
+{
+    if (!r) return;
+    if (r->tw) cudaFree(r->tw);
+    delete r;
+}
+
+int batch_launch(bool forward, const PassDesc* jobs, const int* tile_start, int njobs, long long tiles,
+                 int land_max, int work_max, cudaStream_t stream)
+{
+    if (njobs <= 0 || tiles <= 0) return FB_FFT_OK;
+    if (tiles >= (1LL << 31)) return FB_FFT_ERR_UNSUPPORTED_SIZE;
+    const size_t smem = uneven_smem_bytes(land_max, work_max);
+    // resident CTAs per device for this shared-memory size, asked once per size
+    static std::mutex mu;
+    static std::map<std::pair<int, size_t>, long long> fit;
+    int dev = 0;
+    FB_CK(cudaGetDevice(&dev));
+    long long cap = 0;
+    {
+        std::lock_guard<std::mutex> lock(mu);
+        auto it = fit.find({dev, smem});
+        if (it != fit.end()) cap = it->second;
+    }
+    if (cap == 0) {
+        int occ = 0, sms = 0;
+        FB_CK(uneven_occupancy(forward, smem, &occ));
+        FB_CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+        if (occ < 1) return cuda_fail(cudaErrorInvalidConfiguration, "batch launch occupancy");
+        cap = (long long)occ * sms;
+        std::lock_guard<std::mutex> lock(mu);
+        fit[{dev, smem}] = cap;
+    }
+    UnevenArgs a;
+    a.jobs = jobs;
+    a.tile_start = tile_start;
+    a.in = nullptr;
+    a.out = nullptr;
+    a.scratch = nullptr;
+    a.njobs = njobs;
+    a.land_max = land_max;
+    a.work_max = work_max;
+    a.scale_on = 1;  // each job's apply_scale says whether it scales
+    const cudaError_t e = uneven_launch(forward, a, std::min(tiles, cap), smem, stream);
+    if (e != cudaSuccess) return cuda_fail(e, "k_fft_uneven (server batch)");
+    g_launches.fetch_add(1, std::memory_order_relaxed);
+    return FB_FFT_OK;
 }
 
 int fail(cudaError_t e, const char* what) { return cuda_fail(e, what); }

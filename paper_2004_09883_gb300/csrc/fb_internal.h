@@ -71,7 +71,8 @@ struct PassDesc {
     const long long* off_out;
     // Batched-uneven job tables (k_fft_uneven): which exec buffer `in` and
     // `out` refer to (0 the caller's input, 1 its output, 2 the plan's
-    // scratch); the pointer fields then hold element offsets into it.
+    // scratch; the pointer fields then hold element offsets into it), or 3:
+    // the pointer fields are the addresses themselves.
     int in_buf;
     int out_buf;
 };

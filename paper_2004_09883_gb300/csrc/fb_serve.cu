@@ -14,6 +14,17 @@
 //            list; the slot is free for the next admission at once.
 // Every submit / poll / drain runs retire-then-admit, so requests arriving
 // while others are on the GPU start as soon as a slot and memory free up.
+//
+// Batching: shapes whose axes (or four-step factors) fit one job of the
+// one-kernel engine (k_fft_uneven) have a resident recipe of job
+// descriptors.  When a slot frees up, admission takes the whole FIFO prefix
+// of such requests that fits the budget (up to max_batch), writes their jobs
+// with the requests' own addresses into the slot's pinned job table, copies
+// it to the device with one copy and runs it as one launch per phase and
+// direction (at most six).  Host work per request is then filling two or
+// three descriptors instead of encoding tensor maps and launching kernels;
+// the batch grows by itself with the queue, so an idle server still starts
+// each request at once.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -105,10 +116,19 @@ struct ShapeKey {
 
 struct PlanEntry {
     fb_fft_plan_t plan = nullptr;
+    host::BatchRecipe* recipe = nullptr;  // null: this shape runs per request
+    unsigned flags = 0;
     long long scratch = 0, io = 0, table = 0;
     long long last_use = 0;
     int users = 0;  // queued + running requests holding it
 };
+
+// Jobs one slot's table holds (a batch of up to 1024 jobs: 341 four-step or
+// 3-D requests, more of the others).
+constexpr int kBatchJobs = 1024;
+constexpr int kBatchGroups = 6;  // launches per batch: three phases x two directions
+constexpr size_t kTableBytes =
+    ((kBatchJobs * sizeof(PassDesc) + (kBatchJobs + kBatchGroups) * sizeof(int)) + 255) / 256 * 256;
 
 struct Req {
     long long tag = 0;
@@ -117,7 +137,8 @@ struct Req {
     const void* in = nullptr;
     void* out = nullptr;
     bool host_io = false;
-    long long need = 0;  // arena bytes
+    bool batched = false;  // runs through its shape's recipe in a batch
+    long long need = 0;    // arena bytes
     double t_submit = 0, t_admit = 0;
 };
 
@@ -129,9 +150,11 @@ struct Slot {
     int* err_host = nullptr;  // pinned copy, refreshed at the end of every request
     bool err_mapped = false;  // err_dev is err_host mapped into the device: no copy per request
     bool busy = false;
-    Req r;
-    long long off = -1;  // arena block
-    long long seq = 0;   // admission order
+    std::vector<Req> reqs;        // the request on this slot, or the batch
+    std::vector<long long> offs;  // their arena blocks (-1: none)
+    long long seq = 0;            // admission order
+    char* tab_host = nullptr;     // batch job table: written here (pinned) ...
+    char* tab_dev = nullptr;      // ... and copied here for the launches
 };
 
 }  // namespace
@@ -149,6 +172,8 @@ struct fb_fft_server_s {
     std::deque<Req> pending;
     std::deque<fb_fft_server_done> done;
     long long use_clock = 0, seq = 0;
+    int max_batch = 64;  // requests per batch; <= 1: every request alone through its plan
+    int busy_slots = 0;
     fb_fft_server_stats st{};
 };
 
@@ -171,6 +196,7 @@ void evict_idle(fb_fft_server_s* s)
         if (victim == s->plans.end()) return;  // every plan is in use
         s->st.plan_bytes -= victim->second.table;
         host::plan_free(victim->second.plan);
+        host::recipe_free(victim->second.recipe);
         s->plans.erase(victim);
     }
 }
@@ -184,9 +210,30 @@ int get_plan(fb_fft_server_s* s, int rank, const long long* dims, long long batc
         PlanEntry e;
         int rc = host::plan_create(&e.plan, rank, dims, batch, flags, s->build, true);
         if (rc != FB_FFT_OK) return rc;
+        e.flags = flags;
         e.scratch = host::plan_scratch_bytes(e.plan);
         e.io = host::plan_io_bytes(e.plan);
         e.table = host::plan_table_bytes(e.plan);
+        // the batch recipe; a shape it cannot take runs per request
+        rc = host::recipe_create(&e.recipe, rank, dims, batch, flags, s->build);
+        if (rc == FB_FFT_ERR_UNSUPPORTED_SIZE) {
+            e.recipe = nullptr;
+        } else if (rc != FB_FFT_OK) {
+            host::plan_free(e.plan);
+            return rc;
+        } else if ((long long)e.recipe->jobs.size() > kBatchJobs) {
+            host::recipe_free(e.recipe);
+            e.recipe = nullptr;
+        }
+        if (e.recipe) e.table += e.recipe->table_bytes;
+        // the twiddle tables are written on the build stream; requests run on
+        // the slots' streams, so the tables must be complete before the first
+        const cudaError_t se = cudaStreamSynchronize(s->build);
+        if (se != cudaSuccess) {
+            host::plan_free(e.plan);
+            host::recipe_free(e.recipe);
+            return host::fail(se, "plan build");
+        }
         s->st.plan_builds++;
         s->st.plan_bytes += e.table;
         it = s->plans.emplace(k, e).first;
@@ -196,36 +243,51 @@ int get_plan(fb_fft_server_s* s, int rank, const long long* dims, long long batc
     return FB_FFT_OK;
 }
 
-long long request_need(const PlanEntry* pe, bool host_io)
+long long up_align(long long n) { return (n + kArenaAlign - 1) / kArenaAlign * kArenaAlign; }
+
+long long scratch_of(const PlanEntry* pe, bool batched)
 {
-    auto up = [](long long n) { return (n + kArenaAlign - 1) / kArenaAlign * kArenaAlign; };
-    return up(pe->scratch) + (host_io ? up(pe->io) : 0);
+    return batched ? pe->recipe->scratch_bytes : pe->scratch;
 }
 
+long long request_need(const PlanEntry* pe, bool host_io, bool batched)
+{
+    return up_align(scratch_of(pe, batched)) + (host_io ? up_align(pe->io) : 0);
+}
+
+// Report every request on the slot done with `status` and free the slot.
 void finish(fb_fft_server_s* s, Slot& sl, int slot_index, int status)
 {
-    fb_fft_server_done d;
-    d.tag = sl.r.tag;
-    d.status = status;
-    d.slot = slot_index;
-    d.t_submit = sl.r.t_submit;
-    d.t_admit = sl.r.t_admit;
-    d.t_done = now_s(s);
-    d.t_dev_start = d.t_dev_end = -1.0;
+    const double t = now_s(s);
+    double dev0 = -1.0, dev1 = -1.0;
     float a = 0.f, b = 0.f;
     if (status == FB_FFT_OK && cudaEventElapsedTime(&a, s->ref, sl.start) == cudaSuccess &&
         cudaEventElapsedTime(&b, s->ref, sl.done) == cudaSuccess) {
-        d.t_dev_start = a * 1e-3;
-        d.t_dev_end = b * 1e-3;
+        dev0 = a * 1e-3;
+        dev1 = b * 1e-3;
     }
     cudaGetLastError();
-    s->done.push_back(d);
-    if (sl.off >= 0) s->arena.release(sl.off, sl.r.need);
-    sl.off = -1;
-    sl.r.pe->users--;
+    for (size_t i = 0; i < sl.reqs.size(); ++i) {
+        const Req& r = sl.reqs[i];
+        fb_fft_server_done d;
+        d.tag = r.tag;
+        d.status = status;
+        d.slot = slot_index;
+        d.t_submit = r.t_submit;
+        d.t_admit = r.t_admit;
+        d.t_done = t;
+        d.t_dev_start = dev0;
+        d.t_dev_end = dev1;
+        s->done.push_back(d);
+        if (sl.offs[i] >= 0) s->arena.release(sl.offs[i], r.need);
+        r.pe->users--;
+        s->st.completed++;
+        s->st.in_flight--;
+    }
+    sl.reqs.clear();
+    sl.offs.clear();
     sl.busy = false;
-    s->st.completed++;
-    s->st.in_flight--;
+    s->busy_slots--;
 }
 
 // Retire every slot whose completion event has fired.
@@ -258,6 +320,7 @@ int retire(fb_fft_server_s* s)
 // Put request r on slot sl: copies and passes on the slot's stream, then its event.
 int start(fb_fft_server_s* s, Slot& sl, const Req& r, long long off)
 {
+    (void)s;
     char* block = off >= 0 ? s->arena.base + off : nullptr;
     const long long scr_bytes = (r.pe->scratch + kArenaAlign - 1) / kArenaAlign * kArenaAlign;
     void* scratch = r.pe->scratch ? block : nullptr;
@@ -279,6 +342,140 @@ int start(fb_fft_server_s* s, Slot& sl, const Req& r, long long off)
     return FB_FFT_OK;
 }
 
+// Tile prefixes are gathered at the end of the slot's host table while the
+// jobs are written, then moved right behind the last job.
+int* tile_scratch_of(Slot& sl)
+{
+    return reinterpret_cast<int*>(sl.tab_host + kBatchJobs * sizeof(PassDesc));
+}
+
+// Put the batch on slot sl: its job table (every request's jobs with their
+// addresses, grouped by phase and direction, each group with its tile
+// prefixes) goes to the device in one copy, then one launch per group, all on
+// the slot's stream, between the slot's two events.
+int start_batch(fb_fft_server_s* s, Slot& sl)
+{
+    // jobs first; the tile prefixes go right behind the last job (one copy)
+    PassDesc* jobs = reinterpret_cast<PassDesc*>(sl.tab_host);
+    int* tiles = tile_scratch_of(sl);
+    struct Group {
+        bool fwd;
+        int job0, njobs, tile0, land, work;
+        long long ntiles;
+    };
+    Group groups[kBatchGroups];
+    int ng = 0, nj = 0, nt = 0, phases = 0;
+    for (const Req& r : sl.reqs) phases = std::max(phases, r.pe->recipe->phases);
+    for (int ph = 0; ph < phases; ++ph) {
+        for (int dir = 0; dir < 2; ++dir) {
+            const bool fwd = dir == 0;
+            Group g{fwd, nj, 0, nt, 16, 16, 0};
+            for (size_t i = 0; i < sl.reqs.size(); ++i) {
+                const Req& r = sl.reqs[i];
+                if ((r.direction == FB_FFT_FORWARD) != fwd) continue;
+                char* block = sl.offs[i] >= 0 ? s->arena.base + sl.offs[i] : nullptr;
+                const long long scr = up_align(r.pe->recipe->scratch_bytes);
+                // host arrays: the transform runs in place in the staging buffer
+                const float2* in = r.host_io ? reinterpret_cast<const float2*>(block + scr)
+                                             : static_cast<const float2*>(r.in);
+                float2* out = r.host_io ? reinterpret_cast<float2*>(block + scr) : static_cast<float2*>(r.out);
+                float2* scratch = reinterpret_cast<float2*>(block);
+                const bool scale = !fwd && (r.pe->flags & FB_FFT_SCALE_INV_N);
+                for (const host::BatchJob& j : r.pe->recipe->jobs) {
+                    if (j.phase != ph) continue;
+                    PassDesc& d = jobs[nj];
+                    d = j.d;
+                    d.in = j.src == 0 ? in : (j.src == 1 ? out : scratch);
+                    d.out = j.dst == 1 ? out : scratch;
+                    d.in_buf = 3;
+                    d.out_buf = 3;
+                    d.err = sl.err_dev;
+                    d.apply_scale = (j.last && scale) ? 1 : 0;
+                    tiles[nt++] = (int)g.ntiles;
+                    g.ntiles += j.d.ntiles;
+                    g.land = std::max(g.land, j.land);
+                    g.work = std::max(g.work, j.work);
+                    ++nj;
+                    ++g.njobs;
+                }
+            }
+            if (g.njobs == 0) {
+                nt = g.tile0;
+                continue;
+            }
+            tiles[nt++] = (int)g.ntiles;
+            groups[ng++] = g;
+        }
+    }
+    SV_CK(cudaEventRecord(sl.start, sl.stream));
+    for (size_t i = 0; i < sl.reqs.size(); ++i) {
+        const Req& r = sl.reqs[i];
+        if (!r.host_io) continue;
+        char* stage = s->arena.base + sl.offs[i] + up_align(r.pe->recipe->scratch_bytes);
+        SV_CK(cudaMemcpyAsync(stage, r.in, (size_t)r.pe->io, cudaMemcpyHostToDevice, sl.stream));
+    }
+    int* packed_tiles = reinterpret_cast<int*>(sl.tab_host + (size_t)nj * sizeof(PassDesc));
+    std::memmove(packed_tiles, tiles, (size_t)nt * sizeof(int));
+    SV_CK(cudaMemcpyAsync(sl.tab_dev, sl.tab_host, (size_t)nj * sizeof(PassDesc) + (size_t)nt * sizeof(int),
+                          cudaMemcpyHostToDevice, sl.stream));
+    const PassDesc* djobs = reinterpret_cast<const PassDesc*>(sl.tab_dev);
+    const int* dtiles = reinterpret_cast<const int*>(sl.tab_dev + (size_t)nj * sizeof(PassDesc));
+    for (int k = 0; k < ng; ++k) {
+        const Group& g = groups[k];
+        const int rc = host::batch_launch(g.fwd, djobs + g.job0, dtiles + g.tile0, g.njobs, g.ntiles, g.land, g.work,
+                                          sl.stream);
+        if (rc != FB_FFT_OK) return rc;
+    }
+    for (size_t i = 0; i < sl.reqs.size(); ++i) {
+        const Req& r = sl.reqs[i];
+        if (!r.host_io) continue;
+        const char* stage = s->arena.base + sl.offs[i] + up_align(r.pe->recipe->scratch_bytes);
+        SV_CK(cudaMemcpyAsync(r.out, stage, (size_t)r.pe->io, cudaMemcpyDeviceToHost, sl.stream));
+    }
+    if (!sl.err_mapped)
+        SV_CK(cudaMemcpyAsync(sl.err_host, sl.err_dev, sizeof(int), cudaMemcpyDeviceToHost, sl.stream));
+    SV_CK(cudaEventRecord(sl.done, sl.stream));
+    s->st.batches++;
+    s->st.batched_requests += (long long)sl.reqs.size();
+    s->st.largest_batch = std::max(s->st.largest_batch, (long long)sl.reqs.size());
+    return FB_FFT_OK;
+}
+
+// Move the FIFO head (and, for a batched head, the batched requests right
+// behind it that fit the arena and the slot's table) onto slot sl.
+// Returns the number moved: 0 when the head's memory is not free yet.
+int take_requests(fb_fft_server_s* s, Slot& sl)
+{
+    const double t = now_s(s);
+    int jobs = 0;
+    long long tiles = 0;
+    while (!s->pending.empty()) {
+        Req& r = s->pending.front();
+        if (!sl.reqs.empty()) {  // joining a batch
+            if (!r.batched || (int)sl.reqs.size() >= s->max_batch) break;
+            if (jobs + (int)r.pe->recipe->jobs.size() > kBatchJobs) break;
+            if (tiles + r.pe->recipe->tiles >= (1LL << 30)) break;
+        }
+        long long off = -1;
+        if (r.need > 0) {
+            off = s->arena.alloc(r.need);
+            if (off < 0) break;  // wait for memory (FIFO: no overtaking)
+        }
+        if (r.batched) {
+            jobs += (int)r.pe->recipe->jobs.size();
+            tiles += r.pe->recipe->tiles;
+        }
+        sl.reqs.push_back(r);
+        sl.reqs.back().t_admit = t;
+        sl.offs.push_back(off);
+        s->pending.pop_front();
+        s->st.pending--;
+        s->st.in_flight++;
+        if (!sl.reqs.front().batched) break;  // a per-request head goes alone
+    }
+    return (int)sl.reqs.size();
+}
+
 // Admit FIFO heads while a slot is free and the arena holds the head's needs.
 int admit(fb_fft_server_s* s)
 {
@@ -290,23 +487,14 @@ int admit(fb_fft_server_s* s)
                 break;
             }
         if (free_slot < 0) return FB_FFT_OK;
-        Req& r = s->pending.front();
-        long long off = -1;
-        if (r.need > 0) {
-            off = s->arena.alloc(r.need);
-            if (off < 0) return FB_FFT_OK;  // wait for memory (FIFO: no overtaking)
-        }
         Slot& sl = s->slots[free_slot];
-        sl.r = r;
-        sl.r.t_admit = now_s(s);
-        sl.off = off;
+        if (take_requests(s, sl) == 0) return FB_FFT_OK;
         sl.busy = true;
         sl.seq = ++s->seq;
-        s->pending.pop_front();
-        s->st.pending--;
-        s->st.in_flight++;
+        s->busy_slots++;
         s->st.max_in_flight = std::max(s->st.max_in_flight, s->st.in_flight);
-        const int rc = start(s, sl, sl.r, off);
+        s->st.max_busy_slots = std::max(s->st.max_busy_slots, (long long)s->busy_slots);
+        const int rc = sl.reqs.front().batched ? start_batch(s, sl) : start(s, sl, sl.reqs.front(), sl.offs.front());
         if (rc != FB_FFT_OK) {
             // nothing usable was queued behind a failed launch: report it done with the error
             cudaStreamSynchronize(sl.stream);
@@ -345,14 +533,22 @@ void free_server(fb_fft_server_s* s)
         if (sl.stream) cudaStreamDestroy(sl.stream);
         if (sl.err_host) cudaFreeHost(sl.err_host);
         if (sl.err_dev && !sl.err_mapped) cudaFree(sl.err_dev);
+        if (sl.tab_host) cudaFreeHost(sl.tab_host);
+        if (sl.tab_dev) cudaFree(sl.tab_dev);
     }
-    for (auto& kv : s->plans) host::plan_free(kv.second.plan);
+    for (auto& kv : s->plans) {
+        host::plan_free(kv.second.plan);
+        host::recipe_free(kv.second.recipe);
+    }
     if (s->arena.base) cudaFree(s->arena.base);
     if (s->ref) cudaEventDestroy(s->ref);
     if (s->build) cudaStreamDestroy(s->build);
     s->magic = 0;
     delete s;
 }
+
+int queue_one(fb_fft_server_s* s, int rank, const long long* dims, long long batch, unsigned flags, int direction,
+              const void* in, void* out, int host_io, long long tag);
 
 }  // namespace
 
@@ -398,6 +594,8 @@ int fb_fft_server_create(fb_fft_server_t* srv, int slots, long long hbm_cap_byte
         ck(cudaStreamCreateWithFlags(&sl.stream, cudaStreamNonBlocking), "cudaStreamCreate");
         ck(cudaEventCreate(&sl.start), "cudaEventCreate");
         ck(cudaEventCreate(&sl.done), "cudaEventCreate");
+        ck(cudaHostAlloc((void**)&sl.tab_host, kTableBytes, cudaHostAllocDefault), "cudaHostAlloc");
+        ck(cudaMalloc((void**)&sl.tab_dev, kTableBytes), "cudaMalloc");
         if (native) {
             ck(cudaHostAlloc((void**)&sl.err_host, 16 * sizeof(int), cudaHostAllocMapped), "cudaHostAlloc");
             if (rc == FB_FFT_OK) ck(cudaHostGetDevicePointer((void**)&sl.err_dev, sl.err_host, 0), "cudaHostGetDevicePointer");
@@ -444,7 +642,30 @@ int fb_fft_server_submit(fb_fft_server_t srv, int rank, const long long* dims, l
                          int direction, const void* in, void* out, int host_io, long long tag)
 {
     if (!server_ok(srv)) return FB_FFT_ERR_BAD_PLAN;
-    fb_fft_server_s* s = srv;
+    const int rc = queue_one(srv, rank, dims, batch, flags, direction, in, out, host_io, tag);
+    if (rc != FB_FFT_OK) return rc;
+    return pump(srv);
+}
+
+int fb_fft_server_submit_many(fb_fft_server_t srv, const fb_fft_server_request* reqs, int count, int* status)
+{
+    if (!server_ok(srv)) return FB_FFT_ERR_BAD_PLAN;
+    if (count < 0 || (count > 0 && (!reqs || !status))) return FB_FFT_ERR_INVALID_ARG;
+    for (int i = 0; i < count; ++i) {
+        const fb_fft_server_request& q = reqs[i];
+        status[i] = queue_one(srv, q.rank, q.dims, q.batch, q.flags, q.direction, q.in, q.out, q.host_io, q.tag);
+    }
+    return pump(srv);
+}
+
+}  // extern "C"
+
+namespace {
+
+// Validate one request and append it to the FIFO (no admission).
+int queue_one(fb_fft_server_s* s, int rank, const long long* dims, long long batch, unsigned flags, int direction,
+              const void* in, void* out, int host_io, long long tag)
+{
     if (direction != FB_FFT_FORWARD && direction != FB_FFT_INVERSE) {
         s->st.rejected++;
         return FB_FFT_ERR_INVALID_ARG;
@@ -459,7 +680,8 @@ int fb_fft_server_submit(fb_fft_server_t srv, int rank, const long long* dims, l
     }
     Req r;
     if (rc == FB_FFT_OK) {
-        r.need = request_need(pe, host_io != 0);
+        r.batched = pe->recipe != nullptr && s->max_batch > 1;
+        r.need = request_need(pe, host_io != 0, r.batched);
         if (r.need > s->arena.cap) rc = FB_FFT_ERR_OVER_BUDGET;
     }
     if (rc != FB_FFT_OK) {
@@ -479,8 +701,12 @@ int fb_fft_server_submit(fb_fft_server_t srv, int rank, const long long* dims, l
     s->st.submitted++;
     s->st.pending++;
     evict_idle(s);
-    return pump(s);
+    return FB_FFT_OK;
 }
+
+}  // namespace
+
+extern "C" {
 
 int fb_fft_server_poll(fb_fft_server_t srv, int wait, fb_fft_server_done* done, int capacity, int* n_done)
 {
@@ -541,6 +767,13 @@ int fb_fft_server_cancel(fb_fft_server_t srv, long long tag)
         return pump(s);
     }
     return FB_FFT_ERR_INVALID_ARG;
+}
+
+int fb_fft_server_set_batch(fb_fft_server_t srv, int max_requests)
+{
+    if (!server_ok(srv)) return FB_FFT_ERR_BAD_PLAN;
+    srv->max_batch = max_requests < 1 ? 1 : max_requests;
+    return FB_FFT_OK;
 }
 
 double fb_fft_server_clock(fb_fft_server_t srv) { return server_ok(srv) ? now_s(srv) : -1.0; }

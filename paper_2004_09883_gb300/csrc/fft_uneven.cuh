@@ -28,9 +28,9 @@ constexpr int kUnevenCap = kUnevenThreads * kUnevenElems;       // values per ti
 constexpr int kUnevenMaxLen = kUnevenCap;                       // longest line of a job
 
 // Kernel argument: the job table and the tile prefix table (device memory,
-// written once when the plan is built) and the buffers of this exec.  A job's
-// `in` / `out` fields hold element offsets into the buffer its in_buf /
-// out_buf names.
+// written once when the plan is built, or per launch by the request server)
+// and the buffers of this exec.  A job's `in` / `out` fields hold element
+// offsets into the buffer its in_buf / out_buf names, or (kind 3) addresses.
 struct UnevenArgs {
     const PassDesc* jobs;   // [njobs]
     const int* tile_start;  // [njobs + 1]: first global tile of each job; [njobs] = all tiles
@@ -67,14 +67,17 @@ __device__ __forceinline__ void cp_async16(void* smem_dst, const void* gsrc)
     asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_u32(smem_dst)), "l"(gsrc) : "memory");
 }
 
-// A job's input / output base in this exec's buffers.
+// A job's input / output base in this exec's buffers; kind 3: the field is
+// the address itself (jobs of different requests in one server launch).
 __device__ __forceinline__ const float2* ubuf_in(const UnevenArgs& a, const PassDesc& d)
 {
+    if (d.in_buf == 3) return d.in;
     const float2* b = d.in_buf == 0 ? a.in : (d.in_buf == 1 ? a.out : a.scratch);
     return b + (long long)reinterpret_cast<uintptr_t>(d.in);
 }
 __device__ __forceinline__ float2* ubuf_out(const UnevenArgs& a, const PassDesc& d)
 {
+    if (d.out_buf == 3) return d.out;
     float2* b = d.out_buf == 1 ? a.out : a.scratch;
     return b + (long long)reinterpret_cast<uintptr_t>(d.out);
 }

@@ -62,11 +62,18 @@ class ServerDone(ctypes.Structure):
                 ("t_dev_start", ctypes.c_double), ("t_dev_end", ctypes.c_double)]
 
 
+class ServerRequest(ctypes.Structure):
+    _fields_ = [("dims", ctypes.c_longlong * 3), ("batch", ctypes.c_longlong), ("tag", ctypes.c_longlong),
+                ("in_ptr", ctypes.c_void_p), ("out_ptr", ctypes.c_void_p), ("rank", ctypes.c_int),
+                ("flags", ctypes.c_uint), ("direction", ctypes.c_int), ("host_io", ctypes.c_int)]
+
+
 class ServerStats(ctypes.Structure):
     _fields_ = [(f, ctypes.c_longlong) for f in (
         "submitted", "completed", "rejected", "cancelled", "pending", "in_flight", "plans", "plan_builds",
         "plan_bytes", "arena_bytes", "arena_in_use", "arena_peak", "max_in_flight")] + [
-        ("slots", ctypes.c_int), ("reserved", ctypes.c_int)]
+        ("slots", ctypes.c_int), ("reserved", ctypes.c_int)] + [
+        (f, ctypes.c_longlong) for f in ("batches", "batched_requests", "largest_batch", "max_busy_slots")]
 
     def as_dict(self) -> dict:
         return {f: getattr(self, f) for f, _ in self._fields_ if f != "reserved"}
@@ -116,6 +123,8 @@ _sig = {
     "fb_fft_server_cancel": (_int, [_vp, _ll]),
     "fb_fft_server_clock": (ctypes.c_double, [_vp]),
     "fb_fft_server_stats_get": (_int, [_vp, ctypes.POINTER(ServerStats)]),
+    "fb_fft_server_set_batch": (_int, [_vp, _int]),
+    "fb_fft_server_submit_many": (_int, [_vp, ctypes.POINTER(ServerRequest), _int, ctypes.POINTER(_int)]),
     "fb_fft_server_destroy": (_int, [_vp]),
     "fb_fft_plan_many_query": (_int, [_int, ctypes.POINTER(_ll), ctypes.c_uint, ctypes.POINTER(Info)]),
     "fb_fft_plan_many_ex": (_int, [ctypes.POINTER(_vp), _int, ctypes.POINTER(_ll), ctypes.c_uint, _vp,
@@ -452,14 +461,22 @@ def fft(x, dims, direction: int = FORWARD, scale_inv_n: bool = False, out=None):
 
 class Server:
     """Continuous-batching request server (``fb_fft_server_*``): ``slots``
-    concurrent requests, ``hbm_cap_bytes`` of device memory for their scratch
-    and staging, resident plans (at most ``max_plans``)."""
+    concurrent requests or batches, ``hbm_cap_bytes`` of device memory for
+    their scratch and staging, resident plans (at most ``max_plans``); up to
+    ``max_batch`` queued requests run as one batch (1: each alone through its
+    plan)."""
 
-    def __init__(self, slots: int = 8, hbm_cap_bytes: int = 40 * 10**9, max_plans: int = 4096):
+    def __init__(self, slots: int = 8, hbm_cap_bytes: int = 40 * 10**9, max_plans: int = 4096,
+                 max_batch: int = 64):
         self._h = _vp()
         _check(lib.fb_fft_server_create(ctypes.byref(self._h), int(slots), int(hbm_cap_bytes), int(max_plans)),
                "fb_fft_server_create")
         self._buf = (ServerDone * 256)()
+        self._shape_args = {}
+        self.set_batch(max_batch)
+
+    def set_batch(self, max_requests: int) -> None:
+        _check(lib.fb_fft_server_set_batch(self._h, int(max_requests)), "fb_fft_server_set_batch")
 
     def close(self) -> None:
         if self._h:
@@ -492,10 +509,44 @@ class Server:
     def submit_ptr(self, dims, in_ptr: int, out_ptr: int, tag: int, direction: int = FORWARD, batch: int = 1,
                    scale_inv_n: bool = False, host_io: bool = False, tensor_cores: bool = False) -> None:
         """Queue one transform on raw pointers (device, or host when host_io)."""
-        r, cd = self._dims(dims)
+        key = dims if isinstance(dims, tuple) else None
+        rc = self._shape_args.get(key) if key is not None else None
+        if rc is None:
+            rc = self._dims(dims)
+            if key is not None:
+                self._shape_args[key] = rc
+        r, cd = rc
         _check(lib.fb_fft_server_submit(self._h, r, cd, int(batch), _flags(scale_inv_n, tensor_cores),
                                         int(direction), _vp(in_ptr), _vp(out_ptr), 1 if host_io else 0, int(tag)),
                "fb_fft_server_submit")
+
+    @staticmethod
+    def requests(items) -> "ctypes.Array":
+        """Pack (dims, in_ptr, out_ptr, tag, direction[, batch, scale_inv_n,
+        host_io, tensor_cores]) tuples into a request array for submit_many."""
+        arr = (ServerRequest * len(items))()
+        for k, it in enumerate(items):
+            dims, in_ptr, out_ptr, tag, direction = it[:5]
+            batch, scale, host_io, tc = (tuple(it[5:]) + (1, False, False, False)[len(it) - 5:])[:4]
+            dims = [int(d) for d in (dims if hasattr(dims, "__len__") else [dims])]
+            q = arr[k]
+            q.rank = len(dims)
+            for e, d in enumerate(dims):
+                q.dims[e] = d
+            q.batch, q.tag, q.in_ptr, q.out_ptr = int(batch), int(tag), int(in_ptr), int(out_ptr)
+            q.flags, q.direction, q.host_io = _flags(scale, tc), int(direction), 1 if host_io else 0
+        return arr
+
+    def submit_many(self, reqs, first: int = 0, count: int | None = None) -> list[int]:
+        """Queue reqs[first:first+count] (an array from ``requests``) in one
+        call; returns each request's status (0 = queued)."""
+        n = len(reqs) - first if count is None else int(count)
+        if first < 0 or n < 0 or first + n > len(reqs):
+            raise ValueError("request range out of bounds")
+        st = (_int * max(1, n))()
+        base = ctypes.cast(ctypes.byref(reqs, first * ctypes.sizeof(ServerRequest)), ctypes.POINTER(ServerRequest))
+        _check(lib.fb_fft_server_submit_many(self._h, base, n, st), "fb_fft_server_submit_many")
+        return list(st[:n])
 
     def poll(self, wait: bool = False, device_times: bool = False) -> list[tuple]:
         """Finished requests as (tag, status, slot, t_submit, t_admit, t_done),

@@ -73,6 +73,16 @@ class Workload:
             self.hx = [v.cpu().pin_memory() for v in self.x]
             self.hy = [torch.empty_like(v).pin_memory() for v in self.hx]
         torch.cuda.synchronize()
+        self._reqs = {}
+
+    def requests(self, host_io: bool = False):
+        """The whole request list as one fb_fft_server_request array (tag = index)."""
+        if host_io not in self._reqs:
+            xs, ys = (self.hx, self.hy) if host_io else (self.x, self.y)
+            self._reqs[host_io] = fbfft.Server.requests(
+                [(s, xs[i].data_ptr(), ys[i].data_ptr(), i, self.directions[i], 1, False, host_io)
+                 for i, s in enumerate(self.shapes)])
+        return self._reqs[host_io]
 
     def bytes_moved(self) -> int:
         """Algorithmic bytes of all requests: one read and one write of each array."""
@@ -87,11 +97,19 @@ def _stats(lat_s: np.ndarray, wall_s: float, nbytes: int) -> dict:
             "throughput_req_s": lat.size / wall_s, "throughput_gbs": nbytes / wall_s / 1e9, "wall_s": wall_s}
 
 
-def run_served(server: fbfft.Server, w: Workload, arrivals: np.ndarray, host_io: bool = False) -> dict:
-    """Replay `arrivals` against `server`; returns latency/throughput stats."""
+def run_served(server: fbfft.Server, w: Workload, arrivals: np.ndarray, host_io: bool = False,
+               together: bool = True) -> dict:
+    """Replay `arrivals` against `server`; returns latency/throughput stats.
+    together: every request whose arrival time has passed is handed over in
+    one fb_fft_server_submit_many call (what a front end that collects
+    requests does); False: one fb_fft_server_submit per request."""
     count = len(w.shapes)
     done_at = np.full(count, np.nan)
     status = np.zeros(count, dtype=np.int64)
+    arrivals = np.asarray(arrivals, dtype=np.float64)
+    if together and count and np.any(np.diff(arrivals) < 0):
+        together = False
+    reqs = w.requests(host_io) if together else None
 
     def take(items):
         for tag, st, _slot, _ts, _ta, td in items:
@@ -99,7 +117,17 @@ def run_served(server: fbfft.Server, w: Workload, arrivals: np.ndarray, host_io:
             status[tag] = st
 
     t0 = server.clock()
-    for i in range(count):
+    i = 0
+    while i < count:
+        if together:
+            j = int(np.searchsorted(arrivals, server.clock() - t0, side="right"))
+            if j > i:
+                st = server.submit_many(reqs, i, j - i)
+                if any(st):
+                    raise RuntimeError(f"requests rejected: {[(i + k, v) for k, v in enumerate(st) if v][:5]}")
+                i = j
+            take(server.poll())
+            continue
         due = t0 + arrivals[i]
         while server.clock() < due:
             take(server.poll())
@@ -108,6 +136,7 @@ def run_served(server: fbfft.Server, w: Workload, arrivals: np.ndarray, host_io:
         else:
             server.submit_ptr(w.shapes[i], w.x[i].data_ptr(), w.y[i].data_ptr(), i, w.directions[i])
         take(server.poll())
+        i += 1
     server.drain()
     take(server.poll())
     if np.isnan(done_at).any() or (status != 0).any():

@@ -149,12 +149,13 @@ def test_struct_layouts_match_the_binding(fb, tmp_path):
     """Sizes and field offsets of the ABI structs, from a C compile of the
     header, equal those of the ctypes mirrors."""
     structs = {"fb_fft_info": fb.Info, "fb_fft_many_opts": fb.ManyOpts, "fb_fft_server_done": fb.ServerDone,
-               "fb_fft_server_stats": fb.ServerStats}
+               "fb_fft_server_stats": fb.ServerStats, "fb_fft_server_request": fb.ServerRequest}
+    cfield = {"in_ptr": "in", "out_ptr": "out"}  # C names that are Python keywords
     lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "fb_fft.h"', 'int main(void){']
     for cname, py in structs.items():
         lines.append(f'printf("{cname} size %zu\\n", sizeof({cname}));')
         for f, _ in py._fields_:
-            lines.append(f'printf("{cname} {f} %zu\\n", offsetof({cname}, {f}));')
+            lines.append(f'printf("{cname} {f} %zu\\n", offsetof({cname}, {cfield.get(f, f)}));')
     lines.append('return 0; }')
     src = tmp_path / "layout.c"
     src.write_text("\n".join(lines) + "\n")
@@ -184,6 +185,18 @@ def test_server_calls_without_device(fb):
     if not torch.cuda.is_available():
         assert fb.lib.fb_fft_server_create(ctypes.byref(h), 1, 0, 1) == -7
         assert not h.value
+
+
+def test_server_request_packing(fb):
+    """Server.requests fills the request array the way submit_many reads it."""
+    arr = fb.Server.requests([((64,), 0x1000, 0x2000, 7, -1), ((8, 12, 20), 0x3000, 0x3000, 8, 1, 2, True, True)])
+    a, b = arr[0], arr[1]
+    assert (a.rank, a.dims[0], a.batch, a.tag, a.in_ptr, a.out_ptr, a.direction, a.flags, a.host_io) == \
+        (1, 64, 1, 7, 0x1000, 0x2000, -1, 0, 0)
+    assert (b.rank, list(b.dims), b.batch, b.tag, b.in_ptr, b.out_ptr, b.direction, b.host_io) == \
+        (3, [8, 12, 20], 2, 8, 0x3000, 0x3000, 1, 1)
+    assert b.flags == fb.SCALE_INV_N
+    assert fb.lib.fb_fft_server_submit_many(None, None, 0, None) == -6
 
 
 def test_launch_counter_starts_at_zero_without_gpu(fb):

@@ -1,6 +1,6 @@
 """Request server (fb_fft_server_*): every result is the same alone and in the
-mix, matches the FP64 oracle, admission respects the device-memory budget,
-cancellation and rejection behave as documented."""
+mix (batched or not), matches the FP64 oracle, admission respects the
+device-memory budget, cancellation and rejection behave as documented."""
 import math
 
 import numpy as np
@@ -18,8 +18,10 @@ def tol(n: int) -> float:
     return 2e-6 * math.log2(n) if n > 1 else 1e-7
 
 
+# 5 ** 9 has no split into two factors <= 2048: it runs per request, through its plan
 MIX = [(4096,), (256,), (1 << 20,), (1 << 22,), (6000,), (3 * 5 ** 6,), (60, 45), (512, 512), (16, 250),
-       (128, 128, 128), (8, 100, 27), (1,), (2,), (1000, 1), (80000,), (96, 96), (8, 8, 8), (45, 64, 125)]
+       (128, 128, 128), (8, 100, 27), (1,), (2,), (1000, 1), (80000,), (96, 96), (8, 8, 8), (45, 64, 125),
+       (5 ** 9,), (1, 8), (6, 4, 1)]
 
 
 def _mix(seed, copies=3):
@@ -39,22 +41,41 @@ def _alone(fb, torch, shape, direction, x):
     return y
 
 
-@pytest.mark.parametrize("slots", [1, 8])
-def test_mix_equals_alone_and_oracle(fb, slots):
+def _served_alone(fb, torch, shape, direction, x, scale=False):
+    """The request on its own through a fresh batching server (a batch of one)."""
+    y = torch.empty_like(x)
+    with fb.Server(slots=1, hbm_cap_bytes=1 << 30) as srv:
+        srv.submit_ptr(tuple(shape), x.data_ptr(), y.data_ptr(), 0, direction, scale_inv_n=scale)
+        srv.drain()
+        assert [r[:2] for r in srv.poll()] == [(0, 0)]
+    return y
+
+
+@pytest.mark.parametrize("slots,max_batch", [(1, 1), (8, 1), (1, 256), (8, 256)])
+def test_mix_equals_alone_and_oracle(fb, slots, max_batch):
+    """Without batching every result has the per-call plan's bits; with it,
+    the bits of the same request served alone."""
     import torch
     from paper_2004_09883_gb300 import serving
     shapes, dirs = _mix(1200 + slots)
     w = serving.Workload(shapes, 7000, dirs)
     arrivals = serving.poisson_arrivals(len(shapes), 20000.0, 5)
-    with fb.Server(slots=slots, hbm_cap_bytes=1 << 30) as srv:
+    with fb.Server(slots=slots, hbm_cap_bytes=1 << 30, max_batch=max_batch) as srv:
         serving.run_served(srv, w, arrivals)
         st = srv.stats()
     assert st["completed"] == len(shapes) and st["rejected"] == 0
-    assert st["max_in_flight"] <= slots
+    assert st["max_busy_slots"] <= slots
     assert st["arena_peak"] <= st["arena_bytes"]
+    if max_batch == 1:
+        assert st["batches"] == 0 and st["max_in_flight"] <= slots
+    else:
+        assert st["batched_requests"] == sum(1 for s in shapes if s != (5 ** 9,))
     checked = set()
     for i, (s, d) in enumerate(zip(shapes, dirs)):
-        y_alone = _alone(fb, torch, s, d, w.x[i])
+        if max_batch == 1 or s == (5 ** 9,):
+            y_alone = _alone(fb, torch, s, d, w.x[i])
+        else:
+            y_alone = _served_alone(fb, torch, s, d, w.x[i])
         assert torch.equal(w.y[i], y_alone), f"request {i} {s}: mix result differs from alone"
         if (s, d) not in checked:  # each distinct request kind once against the oracle
             checked.add((s, d))
@@ -63,17 +84,25 @@ def test_mix_equals_alone_and_oracle(fb, slots):
             assert err <= tol(int(np.prod(s))), f"{s} dir {d}: rel L2 {err:.3e}"
 
 
-def test_host_arrays_through_staging(fb):
+@pytest.mark.parametrize("max_batch", [1, 256])
+def test_host_arrays_through_staging(fb, max_batch):
+    """Host arrays, all queued at once (so batches form): each result equals
+    the same request on device arrays alone."""
     import torch
     from paper_2004_09883_gb300 import serving
     shapes, dirs = _mix(1300, copies=1)
     w = serving.Workload(shapes, 7100, dirs, host=True)
-    with fb.Server(slots=4, hbm_cap_bytes=256 << 20) as srv:
+    with fb.Server(slots=4, hbm_cap_bytes=256 << 20, max_batch=max_batch) as srv:
         serving.run_served(srv, w, np.zeros(len(shapes)), host_io=True)
         st = srv.stats()
     assert st["arena_in_use"] == 0 and 0 < st["arena_peak"] <= 256 << 20
+    if max_batch > 1:
+        assert st["largest_batch"] > 1
     for i, (s, d) in enumerate(zip(shapes, dirs)):
-        y_alone = _alone(fb, torch, s, d, w.x[i]).cpu()
+        if max_batch == 1 or s == (5 ** 9,):
+            y_alone = _alone(fb, torch, s, d, w.x[i]).cpu()
+        else:
+            y_alone = _served_alone(fb, torch, s, d, w.x[i]).cpu()
         assert torch.equal(w.hy[i], y_alone), f"request {i} {s}"
 
 
@@ -175,7 +204,7 @@ def test_plan_cache_eviction_keeps_results(fb):
         st = srv.stats()
     assert st["plan_builds"] > 5
     for i, s in enumerate(shapes):
-        assert torch.equal(w.y[i], _alone(fb, torch, s, FWD, w.x[i]))
+        assert torch.equal(w.y[i], _served_alone(fb, torch, s, FWD, w.x[i]))
 
 
 def test_server_handle_errors(fb):
@@ -225,3 +254,127 @@ def test_requests_overlap_on_the_device(fb):
         ref = oracle.fft(xs[i].cpu().numpy().astype(np.complex128), [n], FWD, False, 8)
         err = oracle.rel_l2(ys[i].cpu().numpy().reshape(batch, n), ref.reshape(batch, n))
         assert err.max() <= tol(n)
+
+
+HOLD_TAG = 10 ** 6
+
+
+def _hold_slot(srv, torch):
+    """Occupy a slot for about a millisecond: a 2^24-point host-array request
+    (128 MiB copied each way; its factors exceed 2048, so it runs alone
+    through its plan).  Returns its buffers (keep them alive until drained)."""
+    n = 1 << 24
+    h = torch.zeros(n, dtype=torch.complex64).pin_memory()
+    srv.submit_ptr((n,), h.data_ptr(), h.data_ptr(), HOLD_TAG, FWD, host_io=True)
+    return h
+
+
+def test_batches_form_under_load(fb):
+    """One slot held busy while the whole mix is queued: the queue then runs
+    as batches (fewer launches than requests), forward and scaled inverse
+    requests in the same batch, with a per-request shape (5^9) in the FIFO;
+    every result equals the request served alone and matches the oracle."""
+    import torch
+    from paper_2004_09883_gb300 import serving
+    shapes, dirs = _mix(1400, copies=4)
+    w = serving.Workload(shapes, 7400, dirs)
+    scale = [d == INV and i % 2 == 0 for i, d in enumerate(dirs)]
+    with fb.Server(slots=1, hbm_cap_bytes=1 << 30) as srv:
+        for s in set(shapes):
+            srv.prepare(list(s))
+            srv.prepare(list(s), scale_inv_n=True)
+        srv.prepare([1 << 24])
+        hold = _hold_slot(srv, torch)
+        l0 = fb.launch_count()
+        for i, s in enumerate(shapes):
+            srv.submit_ptr(s, w.x[i].data_ptr(), w.y[i].data_ptr(), i, dirs[i], scale_inv_n=scale[i])
+        srv.drain()
+        torch.cuda.synchronize()
+        launches = fb.launch_count() - l0
+        done = srv.poll()
+        st = srv.stats()
+    del hold
+    done = [d for d in done if d[0] != HOLD_TAG]
+    assert sorted(d[0] for d in done) == list(range(len(shapes))) and all(d[1] == 0 for d in done)
+    assert st["largest_batch"] > 4 and st["batches"] < st["batched_requests"]
+    assert launches < len(shapes)
+    checked = set()
+    for i, (s, d) in enumerate(zip(shapes, dirs)):
+        if s == (5 ** 9,):
+            continue
+        y_alone = _served_alone(fb, torch, s, d, w.x[i], scale=scale[i])
+        assert torch.equal(w.y[i], y_alone), f"request {i} {s}"
+        if (s, d, scale[i]) not in checked:
+            checked.add((s, d, scale[i]))
+            ref = oracle.fft(w.x[i].cpu().numpy().astype(np.complex128).reshape(s), list(s), d, scale[i])
+            err = oracle.rel_l2(w.y[i].cpu().numpy().reshape(1, -1), ref.reshape(1, -1))[0]
+            assert err <= tol(int(np.prod(s))), f"{s} dir {d} scale {scale[i]}: rel L2 {err:.3e}"
+
+
+def test_batched_requests_with_batch_dimension_and_in_place(fb):
+    """Requests with batch > 1 (1-D single job, four-step, 2-D, 3-D) and in
+    place (in == out) inside one batch, against the oracle."""
+    import torch
+    cases = [((4096,), 3), ((1000,), 5), ((6000,), 2), ((24, 40), 3), ((8, 12, 20), 2), ((1,), 4)]
+    xs = [torch.from_numpy(inputs.uniform_c64((b * int(np.prod(s)),), 7500 + i)).cuda()
+          for i, (s, b) in enumerate(cases)]
+    x0 = [x.clone() for x in xs]
+    with fb.Server(slots=1, hbm_cap_bytes=1 << 30) as srv:
+        for s, b in cases:
+            srv.prepare(list(s), b)
+        srv.prepare([1 << 24])
+        hold = _hold_slot(srv, torch)  # the others queue behind it
+        for i, (s, b) in enumerate(cases):
+            srv.submit_ptr(s, xs[i].data_ptr(), xs[i].data_ptr(), i, FWD, batch=b)
+        srv.drain()
+        done = srv.poll()
+        st = srv.stats()
+    del hold
+    assert all(d[1] == 0 for d in done) and len(done) == len(cases) + 1
+    assert st["largest_batch"] == len(cases)
+    for i, (s, b) in enumerate(cases):
+        n = int(np.prod(s))
+        ref = oracle.fft(x0[i].cpu().numpy().astype(np.complex128), list(s), FWD)
+        err = oracle.rel_l2(xs[i].cpu().numpy().reshape(b, n), ref.reshape(b, n))
+        assert err.max() <= tol(max(2, n)), f"{s} x {b}: {err.max():.3e}"
+
+
+def test_submit_many_queues_the_valid_and_reports_the_rest(fb):
+    """submit_many: every request's status as submit would give it; the valid
+    ones are queued (in order) and run, a rejected one is not."""
+    import torch
+    shapes = [(4096,), (7,), (24, 40), (1 << 20,), (96, 96)]
+    xs = [torch.from_numpy(inputs.uniform_c64((int(np.prod(s)),), 7700 + i)).cuda() for i, s in enumerate(shapes)]
+    ys = [torch.empty_like(x) for x in xs]
+    with fb.Server(slots=2, hbm_cap_bytes=1 << 30) as srv:
+        reqs = srv.requests([(s, xs[i].data_ptr(), ys[i].data_ptr(), i, FWD) for i, s in enumerate(shapes)])
+        st = srv.submit_many(reqs)
+        srv.drain()
+        done = sorted(srv.poll())
+        stats = srv.stats()
+    assert st == [0, -2, 0, 0, 0]
+    assert [d[:2] for d in done] == [(0, 0), (2, 0), (3, 0), (4, 0)]
+    assert stats["rejected"] == 1 and stats["completed"] == 4
+    for i, s in enumerate(shapes):
+        if i == 1:
+            continue
+        ref = oracle.fft(xs[i].cpu().numpy().astype(np.complex128), list(s), FWD)
+        err = oracle.rel_l2(ys[i].cpu().numpy().reshape(1, -1), ref.reshape(1, -1))[0]
+        assert err <= tol(int(np.prod(s))), f"{s}: {err:.3e}"
+
+
+def test_replay_together_equals_one_by_one(fb):
+    """The replay that hands over every arrived request in one call and the
+    one that submits them one by one give the same bits."""
+    import torch
+    from paper_2004_09883_gb300 import serving
+    shapes, dirs = _mix(1500, copies=2)
+    w = serving.Workload(shapes, 7800, dirs)
+    with fb.Server(slots=4, hbm_cap_bytes=1 << 30) as srv:
+        serving.run_served(srv, w, np.zeros(len(shapes)), together=True)
+        y1 = [y.clone() for y in w.y]
+        st = srv.stats()
+        serving.run_served(srv, w, np.zeros(len(shapes)), together=False)
+    assert st["largest_batch"] > 1
+    for i in range(len(shapes)):
+        assert torch.equal(y1[i], w.y[i]), f"request {i} {shapes[i]}"
