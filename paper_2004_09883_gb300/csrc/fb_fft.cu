@@ -332,6 +332,28 @@ int uneven_factorize(long long L, int* r)
     return c;
 }
 
+// Row stride (elements) of a tile's work rows in k_fft_uneven: at least
+// L + L/16 (room for the in-row padding i + i/16), and chosen so that the
+// 16 threads of a half-warp never meet on one bank of 8-byte words across
+// rows.  A stage that maps consecutive threads to consecutive lines (the
+// strided sides of four-step jobs) puts H = 16/T positions of each of T
+// lines in a half-warp; a stage that maps them along a line puts H = G =
+// 256/T positions of each of 16/G lines there (short lines, G < 16).  Rows
+// then start H * (odd) banks apart when stride mod 2H == H.  (A tile of 32
+// strided lines has both kinds of stage; its lines-fast stages win: H = 1.)
+// The widest tile stays 2304 elements, as with the previous stride.
+int uneven_line_stride(long long L, long long T, bool cfast)
+{
+    const long long G = kUnevenThreads / T;
+    long long H = 1;
+    if (cfast && T <= 16) H = 16 / T;
+    else if (!cfast && G < 16) H = G;
+    long long ls = L + (L >> 4);
+    if (H < 16)
+        while (ls % (2 * H) != H) ++ls;
+    return (int)ls;
+}
+
 // One job of the one-kernel engine: L-point DFTs over lines (o, c), strides in
 // elements (offsets into the exec buffers are set by the caller); tiles of T
 // lines, T L <= 2048 values.
@@ -354,7 +376,7 @@ int make_uneven_pass(PassPlan& p, TwiddleBuilder& twb, long long L, long long O,
     T = std::min<long long>(T, cfast ? 32 : kUnevenThreads);
     T = std::max<long long>(1, std::min(T, pow2ceil(C)));
     d.L = (int)L;
-    d.LS = (int)(L + (L >> 4) + 1);
+    d.LS = uneven_line_stride(L, T, cfast);
     d.logT = ilog2ll(T);
     d.in_sn = in_sn, d.in_sc = in_sc, d.in_so = in_so;
     d.out_sk = out_sk, d.out_sc = out_sc, d.out_so = out_so;
