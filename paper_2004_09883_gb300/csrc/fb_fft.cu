@@ -332,23 +332,24 @@ int uneven_factorize(long long L, int* r)
     return c;
 }
 
-// Row stride (elements) of a tile's work rows in k_fft_uneven: at least
-// L + L/16 (room for the in-row padding i + i/16), and chosen so that the
-// 16 threads of a half-warp never meet on one bank of 8-byte words across
-// rows.  A stage that maps consecutive threads to consecutive lines (the
+// Row stride (elements) of a tile's work rows in k_fft_uneven (rows are
+// not padded inside): at least L, and chosen so that the 16 threads of a
+// half-warp never meet on one bank of 8-byte words across rows.  A stage that maps consecutive threads to consecutive lines (the
 // strided sides of four-step jobs) puts H = 16/T positions of each of T
 // lines in a half-warp; a stage that maps them along a line puts H = G =
 // 256/T positions of each of 16/G lines there (short lines, G < 16).  Rows
 // then start H * (odd) banks apart when stride mod 2H == H.  (A tile of 32
 // strided lines has both kinds of stage; its lines-fast stages win: H = 1.)
-// The widest tile stays 2304 elements, as with the previous stride.
+// Padding inside the rows (i + i/16) bought no fewer shared-memory
+// wavefronts on the batched-uneven mix once the rows are placed this way,
+// and cost an address step per access.
 int uneven_line_stride(long long L, long long T, bool cfast)
 {
     const long long G = kUnevenThreads / T;
     long long H = 1;
     if (cfast && T <= 16) H = 16 / T;
     else if (!cfast && G < 16) H = G;
-    long long ls = L + (L >> 4);
+    long long ls = L;
     if (H < 16)
         while (ls % (2 * H) != H) ++ls;
     return (int)ls;

@@ -189,9 +189,9 @@ __device__ __forceinline__ void ustage(const UnevenArgs& a, const PassDesc& d, i
                     for (int r = 0; r < R; ++r) v[q][r] = land[t * L + j + r * LR];
                 }
             } else {
-                const float2* p = rd + t * LS;
+                const float2* p = rd + t * LS + j;
 #pragma unroll
-                for (int r = 0; r < R; ++r) v[q][r] = p[spad(j + r * LR)];
+                for (int r = 0; r < R; ++r) v[q][r] = p[r * LR];
             }
         } else {
             // defined on every path: otherwise the register allocator sees the
@@ -227,9 +227,9 @@ __device__ __forceinline__ void ustage(const UnevenArgs& a, const PassDesc& d, i
             dft<R, FWD>(v[q]);
             const int base = (j - k) * R + k;
             if constexpr (!last) {
-                float2* p = wr + t * LS;
+                float2* p = wr + t * LS + base;
 #pragma unroll
-                for (int r = 0; r < R; ++r) p[spad(base + r * Ns)] = v[q][r];
+                for (int r = 0; r < R; ++r) p[r * Ns] = v[q][r];
             } else {
                 // last stage: Ns = L / R, so base = j and kk = j + r Ns.  The
                 // four-step twiddle exp(-2 pi i c kk / N) is read from the split
