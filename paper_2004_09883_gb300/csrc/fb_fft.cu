@@ -209,6 +209,8 @@ struct fb_fft_plan_s {
     bool debug_timeout = false;  // test hook: make every TMA wait run out
     bool no_plane = false;       // plane passes disabled (their cluster does not fit this GPU)
     bool no_evict_first = false; // FB_FFT_EVICT_FIRST=0: first-pass loads without the L2 evict-first policy
+    bool no_evict_last = false;  // FB_FFT_EVICT_LAST=0: intermediate stores without the L2 evict-last policy
+    long long l2_bytes = 0;      // the device's L2 size
     // batched uneven lengths (fb_fft_plan_many)
     bool many = false;
     long long total = 0;                 // elements of the packed layout
@@ -1044,6 +1046,12 @@ int launch_pass(fb_fft_plan_s* p, const PassPlan& q, const float2* in, float2* o
     const size_t smem = line_args(args, q, src + q.src_off, dst + q.dst_off, err);
     PassDesc& d = args.d;
     d.evict_first = (q.src == kBufIn && in != out && !p->many && !p->no_evict_first) ? 1 : 0;
+    // a pass whose output the next pass reads keeps it in L2 when it fits
+    // with room to spare (the caller's input, loaded evict-first, and other
+    // work share the cache); the last pass stores with the default policy, so
+    // nothing stays favoured after the exec
+    const long long out_bytes = (long long)q.d.L * q.d.C * (q.d.ntiles / std::max(1LL, q.d.tiles_per_o)) * 8;
+    d.evict_last = (!q.last && !p->many && !p->no_evict_last && out_bytes * 10 <= p->l2_bytes * 6) ? 1 : 0;
     if (p->debug_timeout && d.async_io) d.debug_extra_tx = 16;
     if (q.last && !fwd && (p->flags & FB_FFT_SCALE_INV_N)) {
         d.apply_scale = 1;
@@ -1316,6 +1324,13 @@ int plan_new(fb_fft_plan_s** out, int rank, const long long* dims, long long bat
     p->N = N;
     p->ext_scratch = ext_scratch;
     if (const char* s = std::getenv("FB_FFT_EVICT_FIRST")) p->no_evict_first = s[0] == '0';
+    if (const char* s = std::getenv("FB_FFT_EVICT_LAST")) p->no_evict_last = s[0] == '0';
+    int l2 = 0;
+    if (cudaDeviceGetAttribute(&l2, cudaDevAttrL2CacheSize, p->device) != cudaSuccess) {
+        cudaGetLastError();
+        l2 = 0;
+    }
+    p->l2_bytes = l2;
     int rc = build_plan(p);
     if (rc != FB_FFT_OK) {
         free_plan(p);

@@ -64,6 +64,7 @@ struct PassDesc {
     int ptw_smem;          // 1: the kernel copies the four-step tables (ptw_lo, ptw_hi) to shared memory
     int ptw_hi_cnt;        // entries of ptw_hi (ptw_lo has 2^ptw_log)
     int evict_first;       // 1: tile loads of `in` take the L2 evict-first policy (the caller's input, read once)
+    int evict_last;        // 1: tile stores take the L2 evict-last policy (read again by the next pass)
     // Batched uneven lengths: element offset of each transform's start in
     // in / out (device arrays, or null for the regular strides above).
     // Contiguous layouts index them by line, strided ones by outer index.

@@ -295,6 +295,14 @@ __device__ __forceinline__ unsigned long long l2_evict_first_policy()
     asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(pol));
     return pol;
 }
+// L2 policy for data the next pass of the same exec reads: its lines stay
+// while others can go.
+__device__ __forceinline__ unsigned long long l2_evict_last_policy()
+{
+    unsigned long long pol;
+    asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(pol));
+    return pol;
+}
 // global -> shared, contiguous bytes; completion counted on `bar`; with
 // `hint`, the source lines take the L2 policy `pol`.
 __device__ __forceinline__ void bulk_load_1d(void* dst, const void* src, unsigned bytes, unsigned long long* bar,
@@ -313,13 +321,20 @@ __device__ __forceinline__ void bulk_load_1d(void* dst, const void* src, unsigne
                      "l"(src), "r"(bytes), "r"(smem_u32(bar))
                      : "memory");
 }
-// shared -> global, contiguous bytes; tracked by the issuing thread's bulk group.
-__device__ __forceinline__ void bulk_store_1d(void* dst, const void* src, unsigned bytes, int* err = nullptr)
+// shared -> global, contiguous bytes; tracked by the issuing thread's bulk
+// group; with `hint`, the written lines take the L2 policy `pol`.
+__device__ __forceinline__ void bulk_store_1d(void* dst, const void* src, unsigned bytes, int* err = nullptr,
+                                              bool hint = false, unsigned long long pol = 0)
 {
     if (err) FB_SELFCHECK(err, 12, dst, src, bytes, 16, 16);
-    asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;" ::"l"(dst), "r"(smem_u32(src)),
-                 "r"(bytes)
-                 : "memory");
+    if (hint)
+        asm volatile("cp.async.bulk.global.shared::cta.bulk_group.L2::cache_hint [%0], [%1], %2, %3;" ::"l"(dst),
+                     "r"(smem_u32(src)), "r"(bytes), "l"(pol)
+                     : "memory");
+    else
+        asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;" ::"l"(dst), "r"(smem_u32(src)),
+                     "r"(bytes)
+                     : "memory");
 }
 // 3-D tiled tensor copies (coordinates innermost first).
 __device__ __forceinline__ void tma_load_3d(void* dst, const void* tmap, int x, int y, int z, unsigned long long* bar,
@@ -340,12 +355,20 @@ __device__ __forceinline__ void tma_load_3d(void* dst, const void* tmap, int x, 
             : "memory");
 }
 __device__ __forceinline__ void tma_store_3d(const void* tmap, int x, int y, int z, const void* src,
-                                             int* err = nullptr)
+                                             int* err = nullptr, bool hint = false, unsigned long long pol = 0)
 {
     if (err) FB_SELFCHECK(err, 14, tmap, src, 16u, 64, 128);
-    asm volatile("cp.async.bulk.tensor.3d.global.shared::cta.tile.bulk_group [%0, {%1, %2, %3}], [%4];" ::"l"(tmap),
-                 "r"(x), "r"(y), "r"(z), "r"(smem_u32(src))
-                 : "memory");
+    if (hint)
+        asm volatile(
+            "cp.async.bulk.tensor.3d.global.shared::cta.tile.bulk_group.L2::cache_hint [%0, {%1, %2, %3}], [%4], "
+            "%5;" ::"l"(tmap),
+            "r"(x), "r"(y), "r"(z), "r"(smem_u32(src)), "l"(pol)
+            : "memory");
+    else
+        asm volatile("cp.async.bulk.tensor.3d.global.shared::cta.tile.bulk_group [%0, {%1, %2, %3}], [%4];" ::"l"(
+                         tmap),
+                     "r"(x), "r"(y), "r"(z), "r"(smem_u32(src))
+                     : "memory");
 }
 __device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
 __device__ __forceinline__ void bulk_wait_read_all() { asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory"); }

@@ -454,20 +454,23 @@ __device__ __forceinline__ void p2_issue_store(const PassDesc& d, const CUtensor
     using C = P2<THREADS, LG, IO>;
     const TileIdx ti = p2_tile_index(d, tile, C::LOGT, C::T);
     float2* dst = tile_out_base(d, ti, C::OUT_T);
+    // output the next pass of this exec reads again, small enough to stay in L2
+    const bool el = d.evict_last != 0;
+    const unsigned long long pol = el ? l2_evict_last_policy() : 0ull;
     if constexpr (!C::OUT_T) {
         if (C::OLS == C::L && !d.off_out) {
-            if (lane == 0) bulk_store_1d(dst, land, (unsigned)(ti.Tv * C::L) * 8u, d.err);
+            if (lane == 0) bulk_store_1d(dst, land, (unsigned)(ti.Tv * C::L) * 8u, d.err, el, pol);
         } else {
             for (int t = lane; t < ti.Tv; t += 32)
-                bulk_store_1d(line_out(d, ti, dst, t), land + t * C::OLS, C::L * 8u, d.err);
+                bulk_store_1d(line_out(d, ti, dst, t), land + t * C::OLS, C::L * 8u, d.err, el, pol);
         }
     } else if (!d.off_out) {
         if (lane == 0)
             for (int k0 = 0; k0 < C::L; k0 += C::BR)
-                tma_store_3d(tm, (int)ti.c0, k0, (int)ti.o, land + k0 * C::T, d.err);
+                tma_store_3d(tm, (int)ti.c0, k0, (int)ti.o, land + k0 * C::T, d.err, el, pol);
     } else {
         for (int k = lane; k < C::L; k += 32)
-            bulk_store_1d(dst + (long long)k * d.out_sk, land + k * C::T, (unsigned)ti.Tv * 8u, d.err);
+            bulk_store_1d(dst + (long long)k * d.out_sk, land + k * C::T, (unsigned)ti.Tv * 8u, d.err, el, pol);
     }
     bulk_commit();
 }
