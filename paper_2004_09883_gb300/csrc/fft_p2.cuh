@@ -75,15 +75,24 @@ __host__ __device__ constexpr int p2_land_elems(int threads, int lg, int io)
 }
 
 // Padded work-buffer line stride.  Strided modes read/write it across lines
-// (consecutive threads on consecutive lines): an odd stride.  The contiguous
-// mode with G < 16 threads per line puts 16/G lines in one half-warp: a stride
-// of G (mod 16) values puts them on disjoint banks.
+// (consecutive threads on consecutive lines): a half-warp holds H = 16/T
+// positions of each of its T lines (T < 16), so rows must start H * (odd)
+// banks apart: stride mod 2H == H (T >= 16: an odd stride).  On the 1024-
+// and 2048-point strided passes this halved the last stage's bank conflicts.
+// The contiguous mode with G < 16 threads per line puts 16/G lines in one
+// half-warp: a stride of G (mod 16) values puts them on disjoint banks.
+__host__ __device__ constexpr int p2_strided_stride(int ls0, int h)
+{
+    return ls0 % (2 * h) == h ? ls0 : p2_strided_stride(ls0 + 1, h);
+}
 __host__ __device__ constexpr int p2_work_stride(int threads, int lg, int io)
 {
     const int L = 1 << lg;
     const int LS0 = L + L / 16;
-    const int G = threads / p2_tile_lines(threads, lg, io);
-    return (io == kIoNN && G < 16) ? LS0 + ((G - LS0 % 16) % 16 + 16) % 16 : LS0 + 1;
+    const int T = p2_tile_lines(threads, lg, io);
+    const int G = threads / T;
+    if (io == kIoNN) return G < 16 ? LS0 + ((G - LS0 % 16) % 16 + 16) % 16 : LS0 + 1;
+    return p2_strided_stride(LS0, T < 16 ? 16 / T : 1);
 }
 // Dynamic shared memory of a power-of-two line pass: alignment slack and
 // mbarriers (256 B), landing buffer(s), the work buffer (when there is more
