@@ -195,7 +195,7 @@ inline LineKernel pass_kernel(const PassPlan& q, bool fwd)
 // power-of-two kernels, a bound for the others).
 inline size_t pass_smem(const PassPlan& q, bool async)
 {
-    const size_t ptw = q.d.ptw_smem ? (size_t)((1LL << q.d.ptw_log) + q.d.ptw_hi_cnt) * sizeof(float2) : 0;
+    const size_t ptw = q.d.ptw_smem ? (size_t)(ptw_pad((int)((1LL << q.d.ptw_log) + q.d.ptw_hi_cnt - 1)) + 1) * sizeof(float2) : 0;
     if (q.kind == 0) return (size_t)p2_smem_bytes(q.threads, q.lg, q.io, async, q.tc) + ptw;
     if (q.kind == 3) return (size_t)plane_smem_bytes(q.lg1, q.lg, q.threads);
     if (q.kind == 4) return q.smem;

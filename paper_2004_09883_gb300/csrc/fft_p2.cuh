@@ -94,6 +94,25 @@ __host__ __device__ constexpr int p2_work_stride(int threads, int lg, int io)
     if (io == kIoNN) return G < 16 ? LS0 + ((G - LS0 % 16) % 16 + 16) % 16 : LS0 + 1;
     return p2_strided_stride(LS0, T < 16 ? 16 / T : 1);
 }
+// First work-buffer generation of strided tiles with fewer than 16 lines:
+// the first stage writes radix-R groups (positions R j + r) of T lines, and
+// a half-warp holds 16/T groups side by side, R positions apart, which the
+// row stride alone cannot spread (same banks for j and j + 1).  XOR-ing the
+// low two index bits with the next two moves group j + 1 by an odd amount
+// (then the usual i + i/16 padding); the next stage reads it back with one
+// per-thread XOR, its offsets r * L/16 keeping the low four bits.  On the
+// 1024- and 2048-point strided passes this removed the first stage's store
+// conflicts.
+__host__ __device__ constexpr bool p2_swz0(int threads, int lg, int io)
+{
+    return io_in_strided(io) && p2_tile_lines(threads, lg, io) < 16 && pow2_nst(lg) >= 2 &&
+           pow2_radix(lg, 0) < 16 && pow2_radix(lg, 1) == 16;
+}
+__device__ __forceinline__ int spad_x(int i) { return spad(i ^ ((i >> 2) & 3)); }
+// Index of entry e of the four-step tables kept in shared memory (lo, then
+// hi): one pad entry every 32 spreads the gathers of a half-warp's lines.
+__host__ __device__ constexpr int ptw_pad(int e) { return e + (e >> 5); }
+
 // Dynamic shared memory of a power-of-two line pass: alignment slack and
 // mbarriers (256 B), landing buffer(s), the work buffer (when there is more
 // than one stage), stage twiddles, and for tensor-core kernels B^T + alignment.
@@ -126,6 +145,7 @@ struct P2 {
     static constexpr int NBUF = p2_nbuf(THREADS);  // landing buffers
     static constexpr int BR = L < 256 ? L : 256;  // rows per 3-D TMA box
     static constexpr int TWS = p2_smem_twiddles(LG);  // twiddle entries kept in shared memory (0: global)
+    static constexpr bool SWZ0 = p2_swz0(THREADS, LG, IO);  // first work-buffer generation XOR-swizzled
     static_assert(T * L <= THREADS * kElemsPerThread, "tile exceeds the CTA's registers");
     static_assert(T >= 1 && G >= 1, "bad tile shape");
 };
@@ -191,6 +211,12 @@ __device__ __forceinline__ void p2_stage(const PassDesc& d, float2* land, float2
 #pragma unroll
                 for (int r = 0; r < R; ++r)
                     v[q][r] = C::IN_T ? land[(j + r * LR) * T + t] : land[t * C::LLS + j + r * LR];
+            } else if constexpr (S == 1 && C::SWZ0) {
+                static_assert(LR % 16 == 0, "second-stage offsets keep the low four index bits");
+                const float2* p = work + t * C::LS;
+                const int jx = j ^ ((j >> 2) & 3);
+#pragma unroll
+                for (int r = 0; r < R; ++r) v[q][r] = p[spad(jx + r * LR)];
             } else {
                 const float2* p = work + t * C::LS;
 #pragma unroll
@@ -234,8 +260,13 @@ __device__ __forceinline__ void p2_stage(const PassDesc& d, float2* land, float2
             if constexpr (!last) {
                 float2* p = work + t * C::LS;
                 const int base = (j - k) * R + k;
+                if constexpr (S == 0 && C::SWZ0) {
 #pragma unroll
-                for (int r = 0; r < R; ++r) p[spad(base + r * NS)] = v[q][r];
+                    for (int r = 0; r < R; ++r) p[spad_x(base + r * NS)] = v[q][r];
+                } else {
+#pragma unroll
+                    for (int r = 0; r < R; ++r) p[spad(base + r * NS)] = v[q][r];
+                }
             } else {
                 // last stage: NS = L / R, so k == j and output index kk = j + r * LR
                 // Four-step twiddle exp(-2 pi i c kk / N) of output kk of line c:
@@ -250,7 +281,7 @@ __device__ __forceinline__ void p2_stage(const PassDesc& d, float2* land, float2
                     const unsigned mlo = m & ((1u << d.ptw_log) - 1), mhi = m >> d.ptw_log;
                     if (d.ptw_smem) {  // tables copied behind the stage twiddles
                         const float2* pt = tws + C::TWS;
-                        return cmul(pt[(1u << d.ptw_log) + mhi], pt[mlo]);
+                        return cmul(pt[ptw_pad((1 << d.ptw_log) + (int)mhi)], pt[ptw_pad((int)mlo)]);
                     }
                     return cmul(__ldg(d.ptw_hi + mhi), __ldg(d.ptw_lo + mlo));
                 };
@@ -295,6 +326,7 @@ __device__ __forceinline__ void p2_stage_tc(const PassDesc& d, float2* land, flo
     static_assert(pow2_radix(LG, S) == 16 && C::NST >= 2, "tensor-core stage: radix 16, not the only stage");
     static_assert(T * LR == THREADS && THREADS % 128 == 0, "tensor-core stage: one butterfly per thread");
     static_assert(T * L * 8 <= T * C::LS * 8, "A tiles fit the work buffer");
+    static_assert(!(S == 0 && C::SWZ0), "the swizzled first generation is written by an FP32 stage");
     const int tid = threadIdx.x;
     const int t = tfast ? (tid & (T - 1)) : (tid / G);
     const int j = tfast ? (tid >> C::LOGT) : (tid & (G - 1));
@@ -304,6 +336,12 @@ __device__ __forceinline__ void p2_stage_tc(const PassDesc& d, float2* land, flo
         if constexpr (first) {
 #pragma unroll
             for (int r = 0; r < R; ++r) v[r] = C::IN_T ? land[(j + r * LR) * T + t] : land[t * C::LLS + j + r * LR];
+        } else if constexpr (S == 1 && C::SWZ0) {
+            static_assert(LR % 16 == 0, "second-stage offsets keep the low four index bits");
+            const float2* p = work + t * C::LS;
+            const int jx = j ^ ((j >> 2) & 3);
+#pragma unroll
+            for (int r = 0; r < R; ++r) v[r] = p[spad(jx + r * LR)];
         } else {
             const float2* p = work + t * C::LS;
 #pragma unroll
@@ -647,8 +685,8 @@ __global__ void __maxnreg__((P2Regs<THREADS, LG>::LAUNCH)) k_fft_p2(const __grid
         if (d.ptw_smem) {  // four-step tables: lo then hi, behind the stage twiddles
             float2* pt = tws + C::TWS;
             const int lo = 1 << d.ptw_log;
-            for (int e = threadIdx.x; e < lo; e += THREADS) pt[e] = __ldg(d.ptw_lo + e);
-            for (int e = threadIdx.x; e < d.ptw_hi_cnt; e += THREADS) pt[lo + e] = __ldg(d.ptw_hi + e);
+            for (int e = threadIdx.x; e < lo; e += THREADS) pt[ptw_pad(e)] = __ldg(d.ptw_lo + e);
+            for (int e = threadIdx.x; e < d.ptw_hi_cnt; e += THREADS) pt[ptw_pad(lo + e)] = __ldg(d.ptw_hi + e);
             compute_sync<THREADS>();
         }
     }
