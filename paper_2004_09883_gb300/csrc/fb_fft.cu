@@ -398,7 +398,17 @@ int make_uneven_pass(PassPlan& p, TwiddleBuilder& twb, long long L, long long O,
     d.out_tfast = out_tfast ? 1 : 0;
     d.ptw = ptw ? 1 : 0;
     d.scale = 1.0f;
-    d.land_stride = (int)((L * T + 15) & ~15LL);
+    // contiguous input in tiles of 2 to 8 lines: rows start H = 16/T banks
+    // apart (stride mod 2H == H, even: 16-byte copies stay aligned), and the
+    // first stage maps threads across them
+    long long lrow = L;
+    d.land_row = 0;
+    if (!in_tfast && T >= 2 && T <= 8) {
+        const long long H = 16 / T;
+        while (lrow % (2 * H) != H) ++lrow;
+        d.land_row = (int)lrow;
+    }
+    d.land_stride = (int)((lrow * T + 15) & ~15LL);
     p.async_ok = false;
     const int padded = (int)(((long long)d.LS * T + 15) & ~15LL);
     p.smem = uneven_smem_bytes(std::max(d.land_stride, padded), padded);

@@ -76,6 +76,10 @@ struct PassDesc {
     // the pointer fields are the addresses themselves.
     int in_buf;
     int out_buf;
+    // k_fft_uneven, contiguous input: 0 = lines land as rows of L and the
+    // first stage maps threads along a line; > 0 = rows of land_row elements
+    // and the first stage maps threads across lines (tiles of 2 to 8 lines).
+    int land_row;
 };
 
 // Fill ns[] (product of the earlier radices) and its multiply-high

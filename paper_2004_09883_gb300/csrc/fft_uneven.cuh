@@ -109,8 +109,9 @@ __device__ __forceinline__ void utile_load(const UnevenArgs& a, const PassDesc& 
         const int lgt = LGTH - logT, t = tid >> lgt, step = 1 << lgt;
         if (t >= ti.Tv) return;
         const float2* src = uline_in(a, d, ti.o, ti.c0 + t);
-        float2* dst = land + t * L;
-        if ((L & 1) == 0 && ((uintptr_t)src & 15) == 0) {
+        const int lrow = d.land_row ? d.land_row : L;
+        float2* dst = land + t * lrow;
+        if ((L & 1) == 0 && (lrow & 1) == 0 && ((uintptr_t)src & 15) == 0) {
             for (int n = 2 * (tid & (step - 1)); n < L; n += 2 * step) cp_async16(dst + n, src + n);
         } else {
             for (int n = tid & (step - 1); n < L; n += step) cp_async8(dst + n, src + n);
@@ -169,7 +170,11 @@ __device__ __forceinline__ void ustage(const UnevenArgs& a, const PassDesc& d, i
     const int LR = L / R;
     const bool in_tf = first && uvol(d.in_tfast) != 0;
     const bool out_tf = last && uvol(d.out_tfast) != 0;
-    const bool tfast = in_tf || out_tf;
+    // contiguous input with padded landing rows: the first stage too maps
+    // threads across lines (its radix-R groups would otherwise fill a
+    // half-warp at stride R)
+    const int lrow = first ? uvol(d.land_row) : 0;
+    const bool tfast = in_tf || out_tf || lrow != 0;
     const int tid = threadIdx.x;
     const int lgG = LGTH - logT, G = 1 << lgG;
     const int t = tfast ? (tid & ((1 << logT) - 1)) : (tid >> lgG);
@@ -185,8 +190,9 @@ __device__ __forceinline__ void ustage(const UnevenArgs& a, const PassDesc& d, i
 #pragma unroll
                     for (int r = 0; r < R; ++r) v[q][r] = land[((j + r * LR) << logT) + t];
                 } else {
+                    const float2* p = land + t * (lrow ? lrow : L) + j;
 #pragma unroll
-                    for (int r = 0; r < R; ++r) v[q][r] = land[t * L + j + r * LR];
+                    for (int r = 0; r < R; ++r) v[q][r] = p[r * LR];
                 }
             } else {
                 const float2* p = rd + t * LS + j;
