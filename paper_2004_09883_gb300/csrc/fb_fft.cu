@@ -344,29 +344,6 @@ long long uneven_tile_lines(long long L, long long C, bool cfast)
     return std::max<long long>(1, std::min(T, pow2ceil(C)));
 }
 
-// Row stride (elements) of a tile's work rows in k_fft_uneven (rows are
-// not padded inside): at least L, and chosen so that the 16 threads of a
-// half-warp never meet on one bank of 8-byte words across rows.  A stage that maps consecutive threads to consecutive lines (the
-// strided sides of four-step jobs) puts H = 16/T positions of each of T
-// lines in a half-warp; a stage that maps them along a line puts H = G =
-// 256/T positions of each of 16/G lines there (short lines, G < 16).  Rows
-// then start H * (odd) banks apart when stride mod 2H == H.  (A tile of 32
-// strided lines has both kinds of stage; its lines-fast stages win: H = 1.)
-// Padding inside the rows (i + i/16) bought no fewer shared-memory
-// wavefronts on the batched-uneven mix once the rows are placed this way,
-// and cost an address step per access.
-int uneven_line_stride(long long L, long long T, bool cfast)
-{
-    const long long G = kUnevenThreads / T;
-    long long H = 1;
-    if (cfast && T <= 16) H = 16 / T;
-    else if (!cfast && G < 16) H = G;
-    long long ls = L;
-    if (H < 16)
-        while (ls % (2 * H) != H) ++ls;
-    return (int)ls;
-}
-
 // One job of the one-kernel engine: L-point DFTs over lines (o, c), strides in
 // elements (offsets into the exec buffers are set by the caller); tiles of T
 // lines, T L <= 2048 values.
@@ -398,17 +375,8 @@ int make_uneven_pass(PassPlan& p, TwiddleBuilder& twb, long long L, long long O,
     d.out_tfast = out_tfast ? 1 : 0;
     d.ptw = ptw ? 1 : 0;
     d.scale = 1.0f;
-    // contiguous input in tiles of 2 to 8 lines: rows start H = 16/T banks
-    // apart (stride mod 2H == H, even: 16-byte copies stay aligned), and the
-    // first stage maps threads across them
-    long long lrow = L;
-    d.land_row = 0;
-    if (!in_tfast && T >= 2 && T <= 8) {
-        const long long H = 16 / T;
-        while (lrow % (2 * H) != H) ++lrow;
-        d.land_row = (int)lrow;
-    }
-    d.land_stride = (int)((lrow * T + 15) & ~15LL);
+    d.land_row = uneven_land_row(L, T, in_tfast);
+    d.land_stride = (int)(((d.land_row ? d.land_row : L) * T + 15) & ~15LL);
     p.async_ok = false;
     const int padded = (int)(((long long)d.LS * T + 15) & ~15LL);
     p.smem = uneven_smem_bytes(std::max(d.land_stride, padded), padded);

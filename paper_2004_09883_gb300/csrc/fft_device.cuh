@@ -203,7 +203,7 @@ __host__ __device__ constexpr int ilog2(int x) { return x <= 1 ? 0 : 1 + ilog2(x
 
 // Padded shared-memory index of element i of a line: one gap every 16 values
 // keeps the stride-R writes of early stages free of bank conflicts.
-__device__ __forceinline__ int spad(int i) { return i + (i >> 4); }
+__host__ __device__ __forceinline__ int spad(int i) { return i + (i >> 4); }
 
 // ---------------------------------------------------------------------------
 // TMA (bulk asynchronous copy) and mbarrier primitives, in inline PTX.

@@ -108,7 +108,7 @@ __host__ __device__ constexpr bool p2_swz0(int threads, int lg, int io)
     return io_in_strided(io) && p2_tile_lines(threads, lg, io) < 16 && pow2_nst(lg) >= 2 &&
            pow2_radix(lg, 0) < 16 && pow2_radix(lg, 1) == 16;
 }
-__device__ __forceinline__ int spad_x(int i) { return spad(i ^ ((i >> 2) & 3)); }
+__host__ __device__ __forceinline__ int spad_x(int i) { return spad(i ^ ((i >> 2) & 3)); }
 // Index of entry e of the four-step tables kept in shared memory (lo, then
 // hi): one pad entry every 32 spreads the gathers of a half-warp's lines.
 __host__ __device__ constexpr int ptw_pad(int e) { return e + (e >> 5); }

@@ -359,4 +359,41 @@ inline size_t uneven_smem_bytes(int land_max, int work_max)
     return 128 + (size_t)(2LL * land_max + work_max) * sizeof(float2);
 }
 
+// Row stride (elements) of a tile's work rows (rows are not padded inside):
+// at least L, and chosen so that the 16 threads of a half-warp never meet on
+// one bank of 8-byte words across rows.  A stage that maps consecutive
+// threads to consecutive lines (the strided sides of four-step jobs) puts
+// H = 16/T positions of each of T lines in a half-warp; a stage that maps
+// them along a line puts H = G = 256/T positions of each of 16/G lines there
+// (short lines, G < 16).  Rows then start H * (odd) banks apart when
+// stride mod 2H == H.  (A tile of 32 strided lines has both kinds of stage;
+// its lines-fast stages win: H = 1.)  Padding inside the rows (i + i/16)
+// bought no fewer shared-memory wavefronts on the batched-uneven mix once
+// the rows are placed this way, and cost an address step per access.
+inline int uneven_line_stride(long long L, long long T, bool cfast)
+{
+    const long long G = kUnevenThreads / T;
+    long long H = 1;
+    if (cfast && T <= 16) H = 16 / T;
+    else if (!cfast && G < 16) H = G;
+    long long ls = L;
+    if (H < 16)
+        while (ls % (2 * H) != H) ++ls;
+    return (int)ls;
+}
+
+// Landing row stride of a contiguous-input tile (0: rows of L, first stage
+// along a line).  Tiles of 2 to 8 lines land in rows H = 16/T banks apart
+// (stride mod 2H == H, even, so the 16-byte copies stay aligned) and their
+// first stage maps threads across lines: its radix-R groups would otherwise
+// fill a half-warp at stride R (8-way for radix 8).
+inline int uneven_land_row(long long L, long long T, bool in_tfast)
+{
+    if (in_tfast || T < 2 || T > 8) return 0;
+    const long long H = 16 / T;
+    long long lr = L;
+    while (lr % (2 * H) != H) ++lr;
+    return (int)lr;
+}
+
 }  // namespace fbfft

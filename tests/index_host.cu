@@ -5,13 +5,22 @@
 //  (2) the split last-stage twiddle factors of the 2048- and 4096-point
 //      schedules (p2_tw_split): the entries the kernel multiplies, taken from
 //      the middle stage's table and the 16 x 15 factor table at the offsets
-//      the kernel uses, give exp(-2 pi i k r / L) for every k and r.
+//      the kernel uses, give exp(-2 pi i k r / L) for every k and r;
+//  (3) the XOR-swizzled first work generation of the strided power-of-two
+//      passes (p2_swz0): one-to-one on a row, inside the row stride, and the
+//      second stage's per-thread shortcut reads the same slots;
+//  (4) the work-row strides: the 16 threads of a half-warp of a stage that
+//      maps them across lines touch 16 different banks (8-byte words mod 16),
+//      for the strided power-of-two passes and for every line length and
+//      tile shape of the batched-uneven kernel, and its padded landing rows.
 // Prints one line per check: name, cases, failures (or worst error).
 #include <cmath>
 #include <complex>
 #include <cstdio>
+#include <vector>
 
 #include "fft_p2.cuh"
+#include "fft_uneven.cuh"
 
 using namespace fbfft;
 using cd = std::complex<double>;
@@ -19,6 +28,20 @@ using cd = std::complex<double>;
 static unsigned umulhi32(unsigned a, unsigned b) { return (unsigned)(((unsigned long long)a * b) >> 32); }
 
 static cd w(long long m, long long D) { return std::polar(1.0, -2.0 * M_PI * (double)(m % D) / (double)D); }
+
+// 1 when the 8-byte words of one half-warp (n of them) fall on n different
+// banks, or repeat a word (a broadcast), 0 otherwise.
+static int banks_distinct(const long long* words, int n)
+{
+    long long seen[16];
+    for (int b = 0; b < 16; ++b) seen[b] = -1;
+    for (int i = 0; i < n; ++i) {
+        const int b = (int)(words[i] & 15);
+        if (seen[b] >= 0 && seen[b] != words[i]) return 0;
+        seen[b] = words[i];
+    }
+    return 1;
+}
 
 int main()
 {
@@ -71,6 +94,115 @@ int main()
         const bool sizes_ok = ns2 * r2 == L && ns2 == 16 * ns1 && p2_tws_off(lg, 2) + 16 * 15 == total;
         std::printf("split_lg%d %lld %.3e %d\n", lg, n, worst, sizes_ok ? 1 : 0);
         delete[] tws;
+    }
+
+    // (3) swizzled first generation
+    {
+        long long n = 0, bad = 0, configs = 0;
+        const int ios[2] = {kIoCC, kIoCCP};
+        for (int threads : {256, 512})
+            for (int lg = 9; lg <= 11; ++lg)
+                for (int io : ios) {
+                    if (!p2_swz0(threads, lg, io)) continue;
+                    ++configs;
+                    const int L = 1 << lg, LS = p2_work_stride(threads, lg, io);
+                    const int LR1 = L / pow2_radix(lg, 1);
+                    std::vector<char> used(LS, 0);
+                    for (int i = 0; i < L; ++i) {
+                        const int x = spad_x(i);
+                        ++n;
+                        if (x < 0 || x >= LS || used[x]) ++bad;
+                        else used[x] = 1;
+                    }
+                    for (int j = 0; j < LR1; ++j)
+                        for (int r = 0; r < 16; ++r) {
+                            ++n;
+                            if (spad_x(j + r * LR1) != spad((j ^ ((j >> 2) & 3)) + r * LR1)) ++bad;
+                        }
+                }
+        std::printf("swizzle %lld %lld %lld\n", n, bad, configs);
+    }
+
+    // (4a) strided power-of-two passes: the last stage reads the work rows
+    // across lines (t fastest), positions j + r L/R
+    {
+        long long n = 0, bad = 0;
+        const int ios[3] = {kIoCC, kIoCCP, kIoNC};
+        for (int threads : {256, 512})
+            for (int lg = 7; lg <= 12; ++lg)
+                for (int io : ios) {
+                    const int T = p2_tile_lines(threads, lg, io);
+                    if (T > 16 || pow2_nst(lg) < 2) continue;
+                    const int L = 1 << lg, LS = p2_work_stride(threads, lg, io);
+                    const int R = pow2_radix(lg, pow2_nst(lg) - 1), LR = L / R, H = 16 / T;
+                    for (int j0 = 0; j0 < LR; j0 += H)
+                        for (int r = 0; r < R; ++r) {
+                            long long wd[16];
+                            int m = 0;
+                            for (int t = 0; t < T; ++t)
+                                for (int h = 0; h < H && j0 + h < LR; ++h) wd[m++] = (long long)t * LS + spad(j0 + h + r * LR);
+                            ++n;
+                            if (!banks_distinct(wd, m)) ++bad;
+                        }
+                }
+        std::printf("p2_rows %lld %lld\n", n, bad);
+    }
+
+    // (4b) batched-uneven kernel: every 5-smooth L <= 2048, every tile shape
+    // the planner can pick; work rows for lines-fast and positions-fast
+    // stages, padded landing rows for the first stage of contiguous tiles
+    {
+        long long n = 0, bad = 0, land = 0, land_bad = 0;
+        for (int L = 1; L <= kUnevenCap; ++L) {
+            int x = L;
+            for (int p : {2, 3, 5})
+                while (x % p == 0) x /= p;
+            if (x != 1) continue;
+            for (int cf = 0; cf < 2; ++cf)
+                for (long long T = 1; T * L <= kUnevenCap && T <= (cf ? 32 : kUnevenThreads); T *= 2) {
+                    const int LS = uneven_line_stride(L, T, cf != 0);
+                    if (LS < L) ++bad;
+                    const long long G = kUnevenThreads / T;
+                    if (cf && T <= 16) {  // lines fast: T lines x 16/T positions
+                        const int H = (int)(16 / T);
+                        for (int j0 = 0; j0 + H <= L; j0 += H) {
+                            long long wd[16];
+                            int m = 0;
+                            for (int t = 0; t < T; ++t)
+                                for (int h = 0; h < H; ++h) wd[m++] = (long long)t * LS + j0 + h;
+                            ++n;
+                            if (!banks_distinct(wd, m)) ++bad;
+                        }
+                    }
+                    if (!cf && G < 16) {  // positions fast: 16/G lines x G positions
+                        for (int j0 = 0; j0 + G <= L; j0 += (int)G) {
+                            long long wd[16];
+                            int m = 0;
+                            for (long long t = 0; t < 16 / G; ++t)
+                                for (long long h = 0; h < G; ++h) wd[m++] = t * LS + j0 + h;
+                            ++n;
+                            if (!banks_distinct(wd, m)) ++bad;
+                        }
+                    }
+                    const int lr = uneven_land_row(L, T, false);
+                    if (T >= 2 && T <= 8) {
+                        ++land;
+                        const int H = (int)(16 / T);
+                        if (lr < L || (lr & 1)) ++land_bad;
+                        for (int j0 = 0; j0 + H <= L; j0 += H) {
+                            long long wd[16];
+                            int m = 0;
+                            for (int t = 0; t < T; ++t)
+                                for (int h = 0; h < H; ++h) wd[m++] = (long long)t * lr + j0 + h;
+                            if (!banks_distinct(wd, m)) ++land_bad;
+                        }
+                    } else if (lr != 0) {
+                        ++land_bad;
+                    }
+                }
+        }
+        std::printf("uneven_rows %lld %lld\n", n, bad);
+        std::printf("uneven_land %lld %lld\n", land, land_bad);
     }
     return 0;
 }

@@ -1,7 +1,9 @@
 """Index arithmetic of the line-pass kernels, compiled for the host from the
 kernels' own headers: j mod Ns by multiply-high reciprocals (exact for every
 case the kernels meet), and the split last-stage twiddle tables of the 2048-
-and 4096-point schedules (their products equal exp(-2 pi i k r / L))."""
+and 4096-point schedules (their products equal exp(-2 pi i k r / L)), the
+swizzled first work generation, and the bank placement of work and landing
+rows."""
 import math
 import os
 import shutil
@@ -29,6 +31,17 @@ def test_index_arithmetic(tmp_path):
     for lg in (11, 12):
         n, worst, sizes_ok = rows[f"split_lg{lg}"]
         assert int(n) == (1 << lg) // 16 * 15 and float(worst) < 1e-13 and sizes_ok == "1"
+    # the swizzled first work generation: one-to-one, inside the row, and
+    # the second stage's shortcut reads the slots the first stage wrote
+    n, bad, configs = map(int, rows["swizzle"])
+    assert configs >= 3 and n > 10_000 and bad == 0
+    # work-row strides: half-warps of lines-fast stages on 16 distinct banks
+    n, bad = map(int, rows["p2_rows"])
+    assert n > 1000 and bad == 0
+    n, bad = map(int, rows["uneven_rows"])
+    assert n > 10_000 and bad == 0
+    n, bad = map(int, rows["uneven_land"])
+    assert n > 100 and bad == 0
 
 
 def test_plane_pass_emulation(tmp_path):
