@@ -1,7 +1,9 @@
 """Launch variants that change scheduling, not arithmetic, give the same bits:
-programmatic dependent launch off (FB_FFT_PDL=0) and the CTA size of passes
-over short contiguous lines (FB_FFT_NN_SMALL_THREADS=64/128/256).  Each runs in a subprocess
-(the library reads the variables once)."""
+programmatic dependent launch off (FB_FFT_PDL=0), the CTA size of passes
+over short contiguous lines (FB_FFT_NN_SMALL_THREADS=64/128/256), and the L2
+policies of the first pass's loads and the intermediate passes' stores
+(FB_FFT_EVICT_FIRST=0, FB_FFT_EVICT_LAST=0).  Each runs in a subprocess (the
+library reads the variables once)."""
 import os
 import subprocess
 import sys
@@ -42,6 +44,7 @@ def _run(tmp_path, name, env_extra):
 def test_launch_variants_give_identical_bits(fb, tmp_path):
     base = _run(tmp_path, "base", {})
     for name, env in [("no_pdl", {"FB_FFT_PDL": "0"}), ("nn256", {"FB_FFT_NN_SMALL_THREADS": "256"}),
-                      ("nn128", {"FB_FFT_NN_SMALL_THREADS": "128"}), ("nn64", {"FB_FFT_NN_SMALL_THREADS": "64"})]:
+                      ("nn128", {"FB_FFT_NN_SMALL_THREADS": "128"}), ("nn64", {"FB_FFT_NN_SMALL_THREADS": "64"}),
+                      ("no_evict_first", {"FB_FFT_EVICT_FIRST": "0"}), ("no_evict_last", {"FB_FFT_EVICT_LAST": "0"})]:
         got = _run(tmp_path, name, env)
         assert np.array_equal(base, got), name
