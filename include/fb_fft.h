@@ -466,6 +466,16 @@ int fb_fft_server_prepare(fb_fft_server_t srv, int rank, const long long* dims, 
  */
 int fb_fft_server_poll(fb_fft_server_t srv, int wait, fb_fft_server_done* done, int capacity, int* n_done);
 
+/*
+ * fb_fft_server_wait -- retire and admit (as poll does) until a request has
+ * finished, nothing is running, or the server clock (fb_fft_server_clock)
+ * reaches until_s, whichever comes first; finished requests stay for poll.
+ * For a caller that has nothing to submit before until_s (its next
+ * arrival): completions are seen as they happen, not at the caller's next
+ * poll.  It spins on the host (no sleep).  Errors: BAD_PLAN, CUDA.
+ */
+int fb_fft_server_wait(fb_fft_server_t srv, double until_s);
+
 /* fb_fft_server_drain -- block until nothing is queued or running; finished
  * requests stay available to poll. */
 int fb_fft_server_drain(fb_fft_server_t srv);

@@ -26,6 +26,7 @@
 #include <memory>
 #include <mutex>
 #include <new>
+#include <tuple>
 #include <vector>
 
 #include <cudaTypedefs.h>
@@ -1562,32 +1563,41 @@ void recipe_free(BatchRecipe* r)
     delete r;
 }
 
+// Resident CTAs of k_fft_uneven (or its inline form) on the current device
+// for one shared-memory size, asked once per (device, size, form).
+int uneven_resident(bool forward, size_t smem, bool inl, long long* cap)
+{
+    static std::mutex mu;
+    static std::map<std::tuple<int, size_t, bool>, long long> fit;
+    int dev = 0;
+    FB_CK(cudaGetDevice(&dev));
+    {
+        std::lock_guard<std::mutex> lock(mu);
+        auto it = fit.find({dev, smem, inl});
+        if (it != fit.end()) {
+            *cap = it->second;
+            return FB_FFT_OK;
+        }
+    }
+    int occ = 0, sms = 0;
+    FB_CK(inl ? uneven_occupancy_inline(forward, smem, &occ) : uneven_occupancy(forward, smem, &occ));
+    FB_CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    if (occ < 1) return cuda_fail(cudaErrorInvalidConfiguration, "batch launch occupancy");
+    *cap = (long long)occ * sms;
+    std::lock_guard<std::mutex> lock(mu);
+    fit[{dev, smem, inl}] = *cap;
+    return FB_FFT_OK;
+}
+
 int batch_launch(bool forward, const PassDesc* jobs, const int* tile_start, int njobs, long long tiles,
                  int land_max, int work_max, cudaStream_t stream)
 {
     if (njobs <= 0 || tiles <= 0) return FB_FFT_OK;
     if (tiles >= (1LL << 31)) return FB_FFT_ERR_UNSUPPORTED_SIZE;
     const size_t smem = uneven_smem_bytes(land_max, work_max);
-    // resident CTAs per device for this shared-memory size, asked once per size
-    static std::mutex mu;
-    static std::map<std::pair<int, size_t>, long long> fit;
-    int dev = 0;
-    FB_CK(cudaGetDevice(&dev));
     long long cap = 0;
-    {
-        std::lock_guard<std::mutex> lock(mu);
-        auto it = fit.find({dev, smem});
-        if (it != fit.end()) cap = it->second;
-    }
-    if (cap == 0) {
-        int occ = 0, sms = 0;
-        FB_CK(uneven_occupancy(forward, smem, &occ));
-        FB_CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-        if (occ < 1) return cuda_fail(cudaErrorInvalidConfiguration, "batch launch occupancy");
-        cap = (long long)occ * sms;
-        std::lock_guard<std::mutex> lock(mu);
-        fit[{dev, smem}] = cap;
-    }
+    int rc = uneven_resident(forward, smem, false, &cap);
+    if (rc != FB_FFT_OK) return rc;
     UnevenArgs a;
     a.jobs = jobs;
     a.tile_start = tile_start;
@@ -1600,6 +1610,30 @@ int batch_launch(bool forward, const PassDesc* jobs, const int* tile_start, int 
     a.scale_on = 1;  // each job's apply_scale says whether it scales
     const cudaError_t e = uneven_launch(forward, a, std::min(tiles, cap), smem, stream);
     if (e != cudaSuccess) return cuda_fail(e, "k_fft_uneven (server batch)");
+    g_launches.fetch_add(1, std::memory_order_relaxed);
+    return FB_FFT_OK;
+}
+
+int batch_launch_inline(bool forward, const PassDesc* jobs, const int* tile_start, int njobs, long long tiles,
+                        int land_max, int work_max, cudaStream_t stream)
+{
+    if (njobs <= 0 || tiles <= 0) return FB_FFT_OK;
+    if (njobs > kUnevenInlineJobs) return FB_FFT_ERR_INVALID_ARG;
+    if (tiles >= (1LL << 31)) return FB_FFT_ERR_UNSUPPORTED_SIZE;
+    const size_t smem = uneven_smem_bytes(land_max, work_max);
+    long long cap = 0;
+    int rc = uneven_resident(forward, smem, true, &cap);
+    if (rc != FB_FFT_OK) return rc;
+    UnevenInlineArgs p;
+    std::memset(&p, 0, sizeof(p));
+    p.a.njobs = njobs;
+    p.a.land_max = land_max;
+    p.a.work_max = work_max;
+    p.a.scale_on = 1;
+    std::memcpy(p.jobs, jobs, (size_t)njobs * sizeof(PassDesc));
+    std::memcpy(p.tile_start, tile_start, (size_t)(njobs + 1) * sizeof(int));
+    const cudaError_t e = uneven_launch_inline(forward, p, std::min(tiles, cap), smem, stream);
+    if (e != cudaSuccess) return cuda_fail(e, "k_fft_uneven_inline (server batch)");
     g_launches.fetch_add(1, std::memory_order_relaxed);
     return FB_FFT_OK;
 }

@@ -56,6 +56,10 @@ void recipe_free(BatchRecipe* r);
 // memory (njobs jobs, `tiles` tiles in all); the launch counter counts it.
 int batch_launch(bool forward, const PassDesc* jobs, const int* tile_start, int njobs, long long tiles,
                  int land_max, int work_max, cudaStream_t stream);
+// The same launch with the tables (host memory, at most 16 jobs) copied
+// into the kernel parameter: nothing to copy to the device beforehand.
+int batch_launch_inline(bool forward, const PassDesc* jobs, const int* tile_start, int njobs, long long tiles,
+                        int land_max, int work_max, cudaStream_t stream);
 // Record a failed CUDA call for fb_fft_last_error and map it to a status.
 int fail(cudaError_t e, const char* what);
 

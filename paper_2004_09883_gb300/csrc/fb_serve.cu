@@ -38,6 +38,7 @@
 
 #include "fb_fft.h"
 #include "fb_host.h"
+#include "fft_uneven.cuh"
 
 using namespace fbfft;
 
@@ -416,14 +417,22 @@ int start_batch(fb_fft_server_s* s, Slot& sl)
     }
     int* packed_tiles = reinterpret_cast<int*>(sl.tab_host + (size_t)nj * sizeof(PassDesc));
     std::memmove(packed_tiles, tiles, (size_t)nt * sizeof(int));
-    SV_CK(cudaMemcpyAsync(sl.tab_dev, sl.tab_host, (size_t)nj * sizeof(PassDesc) + (size_t)nt * sizeof(int),
-                          cudaMemcpyHostToDevice, sl.stream));
+    // groups of few jobs carry their tables in the kernel parameter; the
+    // table goes to the device only for a larger group
+    bool copy = false;
+    for (int k = 0; k < ng; ++k) copy = copy || groups[k].njobs > kUnevenInlineJobs;
+    if (copy)
+        SV_CK(cudaMemcpyAsync(sl.tab_dev, sl.tab_host, (size_t)nj * sizeof(PassDesc) + (size_t)nt * sizeof(int),
+                              cudaMemcpyHostToDevice, sl.stream));
     const PassDesc* djobs = reinterpret_cast<const PassDesc*>(sl.tab_dev);
     const int* dtiles = reinterpret_cast<const int*>(sl.tab_dev + (size_t)nj * sizeof(PassDesc));
     for (int k = 0; k < ng; ++k) {
         const Group& g = groups[k];
-        const int rc = host::batch_launch(g.fwd, djobs + g.job0, dtiles + g.tile0, g.njobs, g.ntiles, g.land, g.work,
-                                          sl.stream);
+        const int rc = g.njobs <= kUnevenInlineJobs
+                           ? host::batch_launch_inline(g.fwd, jobs + g.job0, packed_tiles + g.tile0, g.njobs,
+                                                       g.ntiles, g.land, g.work, sl.stream)
+                           : host::batch_launch(g.fwd, djobs + g.job0, dtiles + g.tile0, g.njobs, g.ntiles, g.land,
+                                                g.work, sl.stream);
         if (rc != FB_FFT_OK) return rc;
     }
     for (size_t i = 0; i < sl.reqs.size(); ++i) {
@@ -767,6 +776,17 @@ int fb_fft_server_cancel(fb_fft_server_t srv, long long tag)
         return pump(s);
     }
     return FB_FFT_ERR_INVALID_ARG;
+}
+
+int fb_fft_server_wait(fb_fft_server_t srv, double until_s)
+{
+    if (!server_ok(srv)) return FB_FFT_ERR_BAD_PLAN;
+    fb_fft_server_s* s = srv;
+    for (;;) {
+        const int rc = pump(s);
+        if (rc != FB_FFT_OK) return rc;
+        if (!s->done.empty() || s->st.in_flight == 0 || now_s(s) >= until_s) return FB_FFT_OK;
+    }
 }
 
 int fb_fft_server_set_batch(fb_fft_server_t srv, int max_requests)

@@ -43,6 +43,15 @@ struct UnevenArgs {
     int scale_on;           // 1: jobs marked apply_scale multiply by their `scale`
 };
 
+// Kernel argument of the inline form: the tables themselves (a.jobs and
+// a.tile_start unused).  About 5.8 KB, well under the 32 KB parameter limit.
+constexpr int kUnevenInlineJobs = 16;
+struct UnevenInlineArgs {
+    UnevenArgs a;
+    PassDesc jobs[kUnevenInlineJobs];
+    int tile_start[kUnevenInlineJobs + 1];
+};
+
 #ifdef __CUDACC__
 
 // Tile t of job d: outer index o, first line c0, valid lines Tv (32-bit: a
@@ -290,8 +299,19 @@ __device__ __forceinline__ void ustage_run(const UnevenArgs& a, const PassDesc& 
     }
 }
 
-template <bool FWD>
-__global__ void __launch_bounds__(kUnevenThreads, 4) k_fft_uneven(const __grid_constant__ UnevenArgs a)
+// A word of the job or tile-prefix table: read-only global memory, or (INL)
+// the kernel's own parameter, which takes plain generic loads.
+template <bool INL>
+__device__ __forceinline__ int utab(const int* p)
+{
+    if constexpr (INL)
+        return *p;
+    else
+        return __ldg(p);
+}
+
+template <bool FWD, bool INL>
+__device__ __forceinline__ void uneven_body(const UnevenArgs& a, const PassDesc* jobs, const int* tile_start)
 {
     extern __shared__ __align__(128) unsigned char smem_dyn[];
     unsigned char* smem_raw = smem_dyn + ((128u - (smem_u32(smem_dyn) & 127u)) & 127u);
@@ -299,19 +319,19 @@ __global__ void __launch_bounds__(kUnevenThreads, 4) k_fft_uneven(const __grid_c
     float2* work = land0 + 2 * a.land_max;
     __shared__ PassDesc sd[2];  // sd[b]: descriptor of the tile in landing buffer b
     constexpr int TH = kUnevenThreads;
-    const int total = __ldg(a.tile_start + a.njobs);
+    const int total = utab<INL>(tile_start + a.njobs);
     const int step = gridDim.x;
     auto copy_desc = [&](int job, int b) {
-        const int* src = reinterpret_cast<const int*>(a.jobs + job);
+        const int* src = reinterpret_cast<const int*>(jobs + job);
         int* dst = reinterpret_cast<int*>(&sd[b]);
-        for (int w = threadIdx.x; w < (int)(sizeof(PassDesc) / 4); w += TH) dst[w] = __ldg(src + w);
+        for (int w = threadIdx.x; w < (int)(sizeof(PassDesc) / 4); w += TH) dst[w] = utab<INL>(src + w);
     };
     pdl_start();
     int g = blockIdx.x;
     if (g >= total) return;
     int j = 0;
-    while (g >= __ldg(a.tile_start + j + 1)) ++j;
-    int jstart = __ldg(a.tile_start + j);
+    while (g >= utab<INL>(tile_start + j + 1)) ++j;
+    int jstart = utab<INL>(tile_start + j);
     copy_desc(j, 0);
     __syncthreads();
     utile_load(a, sd[0], utile_index(sd[0], g - jstart), land0);
@@ -321,8 +341,8 @@ __global__ void __launch_bounds__(kUnevenThreads, 4) k_fft_uneven(const __grid_c
         const int gl = g - jstart;  // this tile within its job
         const int gn = g + step;
         if (gn < total) {  // the next tile's job and descriptor, then its copies
-            while (gn >= __ldg(a.tile_start + j + 1)) ++j;
-            jstart = __ldg(a.tile_start + j);
+            while (gn >= utab<INL>(tile_start + j + 1)) ++j;
+            jstart = utab<INL>(tile_start + j);
             copy_desc(j, b ^ 1);
             __syncthreads();
             utile_load(a, sd[b ^ 1], utile_index(sd[b ^ 1], gn - jstart), land0 + (b ^ 1) * a.land_max);
@@ -349,11 +369,29 @@ __global__ void __launch_bounds__(kUnevenThreads, 4) k_fft_uneven(const __grid_c
     }
 }
 
+template <bool FWD>
+__global__ void __launch_bounds__(kUnevenThreads, 4) k_fft_uneven(const __grid_constant__ UnevenArgs a)
+{
+    uneven_body<FWD, false>(a, a.jobs, a.tile_start);
+}
+
+// The same pass with its job and tile-prefix tables inside the kernel
+// parameter (at most kUnevenInlineJobs jobs): a small batch then needs no
+// copy of its tables to the device before it can start.
+template <bool FWD>
+__global__ void __launch_bounds__(kUnevenThreads, 4) k_fft_uneven_inline(const __grid_constant__ UnevenInlineArgs p)
+{
+    uneven_body<FWD, true>(p.a, p.jobs, p.tile_start);
+}
+
 #endif  // __CUDACC__
 
 // Host side (fft_kernels_uneven.cu).
 cudaError_t uneven_launch(bool forward, const UnevenArgs& a, long long grid, size_t smem, cudaStream_t stream);
 cudaError_t uneven_occupancy(bool forward, size_t smem, int* blocks_per_sm);
+cudaError_t uneven_launch_inline(bool forward, const UnevenInlineArgs& a, long long grid, size_t smem,
+                                 cudaStream_t stream);
+cudaError_t uneven_occupancy_inline(bool forward, size_t smem, int* blocks_per_sm);
 inline size_t uneven_smem_bytes(int land_max, int work_max)
 {
     return 128 + (size_t)(2LL * land_max + work_max) * sizeof(float2);

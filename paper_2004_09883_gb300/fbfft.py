@@ -124,6 +124,7 @@ _sig = {
     "fb_fft_server_clock": (ctypes.c_double, [_vp]),
     "fb_fft_server_stats_get": (_int, [_vp, ctypes.POINTER(ServerStats)]),
     "fb_fft_server_set_batch": (_int, [_vp, _int]),
+    "fb_fft_server_wait": (_int, [_vp, ctypes.c_double]),
     "fb_fft_server_submit_many": (_int, [_vp, ctypes.POINTER(ServerRequest), _int, ctypes.POINTER(_int)]),
     "fb_fft_server_destroy": (_int, [_vp]),
     "fb_fft_plan_many_query": (_int, [_int, ctypes.POINTER(_ll), ctypes.c_uint, ctypes.POINTER(Info)]),
@@ -563,6 +564,11 @@ class Server:
             if n.value < len(self._buf):
                 return out
             wait = False
+
+    def wait(self, until_s: float) -> None:
+        """Spin until a request finishes, nothing runs, or the server clock
+        reaches ``until_s`` (see fb_fft_server_wait)."""
+        _check(lib.fb_fft_server_wait(self._h, float(until_s)), "fb_fft_server_wait")
 
     def drain(self) -> None:
         _check(lib.fb_fft_server_drain(self._h), "fb_fft_server_drain")

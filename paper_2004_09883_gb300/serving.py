@@ -126,6 +126,8 @@ def run_served(server: fbfft.Server, w: Workload, arrivals: np.ndarray, host_io:
                 if any(st):
                     raise RuntimeError(f"requests rejected: {[(i + k, v) for k, v in enumerate(st) if v][:5]}")
                 i = j
+            else:  # nothing due yet: watch the running requests until the next arrival
+                server.wait(t0 + arrivals[i])
             take(server.poll())
             continue
         due = t0 + arrivals[i]

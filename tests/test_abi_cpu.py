@@ -197,6 +197,7 @@ def test_server_request_packing(fb):
         (3, [8, 12, 20], 2, 8, 0x3000, 0x3000, 1, 1)
     assert b.flags == fb.SCALE_INV_N
     assert fb.lib.fb_fft_server_submit_many(None, None, 0, None) == -6
+    assert fb.lib.fb_fft_server_wait(None, 0.0) == -6
 
 
 def test_launch_counter_starts_at_zero_without_gpu(fb):

@@ -378,3 +378,25 @@ def test_replay_together_equals_one_by_one(fb):
     assert st["largest_batch"] > 1
     for i in range(len(shapes)):
         assert torch.equal(y1[i], w.y[i]), f"request {i} {shapes[i]}"
+
+
+def test_wait_returns_on_completion_or_deadline(fb):
+    """fb_fft_server_wait: returns once a request has finished (it is then
+    ready for poll), at once with nothing running, and at the deadline."""
+    import time
+    import torch
+    x = torch.from_numpy(inputs.uniform_c64((1 << 20,), 7900)).cuda()
+    y = torch.empty_like(x)
+    with fb.Server(slots=2, hbm_cap_bytes=1 << 30) as srv:
+        t0 = time.perf_counter()
+        srv.wait(srv.clock() + 0.05)  # nothing running: at once
+        assert time.perf_counter() - t0 < 0.04
+        srv.submit_ptr((1 << 20,), x.data_ptr(), y.data_ptr(), 5, FWD)
+        srv.wait(srv.clock() + 10.0)
+        done = srv.poll()
+        assert [d[:2] for d in done] == [(5, 0)]
+        t0 = time.perf_counter()
+        srv.wait(srv.clock() + 0.01)  # idle again
+        assert time.perf_counter() - t0 < 0.04
+    ref = oracle.fft(x.cpu().numpy().astype(np.complex128), [1 << 20], FWD)
+    assert oracle.rel_l2(y.cpu().numpy().reshape(1, -1), ref.reshape(1, -1))[0] <= tol(1 << 20)
