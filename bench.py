@@ -594,7 +594,7 @@ def gpu_regular(args, ctx: Ctx, wl: dict, headline: bool) -> dict:
     if not args.quick:
         hbuf = [torch.from_numpy(h.reshape(-1)).pin_memory() for h in host_inputs[:2]]
         hres = [torch.empty_like(hbuf[0]).pin_memory() for _ in range(2)]
-        e2e_steps = max(3, min(args.steps, 20 if headline else 5))
+        e2e_steps = max(3, min(args.steps, 20 if headline else 10))
 
         def e2e_step(i):
             src, dst = hbuf[i % 2], hres[i % 2]
