@@ -703,12 +703,15 @@ def uneven_lengths(wl: dict) -> np.ndarray:
 
 
 def uneven_roofline(passes, prof_steps, lens, bytes_step, ms, launches_per_exec, wl_name, peaks):
-    """Roofline of a batched uneven exec.  One-kernel engine: the dominant of
-    its two launches, phase 0 moving one read and one write of every value,
-    phase 1 of every value of a length above 2048 (the four-step rows).  The
-    per-kernel engine: the whole exec (all its launches)."""
-    phase_bytes = {"many.uneven.phase0": bytes_step,
-                   "many.uneven.phase1": float(sum(16 * int(n) for n in lens if int(n) > 2048))}
+    """Roofline of a batched uneven exec.  One-kernel engine: its one launch
+    moves one read and one write of every value (the single passes and the
+    four-step columns) plus one of every value of a length above 2048 (the
+    four-step rows); in its two-launch form, the dominant launch (phase 0 the
+    first part, phase 1 the rows).  The per-kernel engine: the whole exec (all
+    its launches)."""
+    rows = float(sum(16 * int(n) for n in lens if int(n) > 2048))
+    phase_bytes = {"many.uneven": bytes_step + rows, "many.uneven.phase0": bytes_step,
+                   "many.uneven.phase1": rows}
     dom = max(passes, key=lambda r: r[1]) if passes else None
     if dom and dom[0] in phase_bytes and dom[2] > 0:
         per_launch_ms = dom[1] / dom[2]

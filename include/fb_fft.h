@@ -100,9 +100,12 @@ int fb_fft_plan(fb_fft_plan_t* plan, int rank, const long long* dims, long long 
  * lengths (each <= FB_FFT_MAX_1D_LEN) laid out as above; fb_fft_exec /
  * fb_fft_exec_host then take buffers of fb_fft_many_layout(...) elements.
  * Transforms of one length run as one pass through an offset table (long
- * ones as a four-step pair); different lengths run concurrently on
- * plan-owned side streams, and each exec is replayed as one CUDA graph
- * launch (captured on the first exec with a given in/out/direction).
+ * ones as a four-step pair).  By default (engine 0 below) every pass of the
+ * batch is one persistent kernel launch; otherwise different lengths run
+ * concurrently on plan-owned side streams.  Each exec is replayed as one
+ * CUDA graph launch (captured on the first exec with a given
+ * in/out/direction).  One exec of a plan at a time: the plan's device
+ * counters and scratch serve one exec.
  * FB_FFT_SCALE_INV_N scales each inverse result by 1/its length.
  * Errors: as fb_fft_plan.
  *
@@ -122,12 +125,17 @@ int fb_fft_set_graph(fb_fft_plan_t plan, int enable);
  *   odd_radices_first  lengths with factors 3/5 (generic kernel): 1 runs the 5s and 3s
  *                      before the power-of-two radices
  *   max_lines          generic kernel: at most this many lines per tile (0 = no extra cap)
- *   engine             0 (default): one kernel for every pass, two launches per
- *                      exec -- phase 0 all single passes and four-step columns,
- *                      phase 1 all four-step rows -- over a device job table (each
- *                      job one length group or four-step chunk, lines up to 2048
- *                      points; longer lengths split into two such jobs).  Taken
- *                      whenever every length fits it, else engine 1.
+ *   engine             0 (default): one kernel for every pass, ONE launch per
+ *                      exec over a device job table (each job one length group
+ *                      or four-step chunk, lines up to 2048 points; longer
+ *                      lengths split into two such jobs): CTAs claim tiles in
+ *                      table order from a device counter, and a four-step row
+ *                      tile waits (bounded) until its chunk's column tiles are
+ *                      done.  Taken whenever every length fits it, else
+ *                      engine 1.
+ *                      2: the same kernel in two launches per exec (all single
+ *                      passes and four-step columns, then all rows; the same
+ *                      results), when every length fits it, else engine 1.
  *                      1: the per-kernel schedule below (side streams, CUDA graph).
  *   per_length         engine 1: one launch per length group for every kernel
  *                      (1), or (0, default) passes of lengths with a factor 3 or 5
@@ -154,7 +162,8 @@ int fb_fft_plan_many_ex(fb_fft_plan_t* plan, int count, const long long* lengths
  * (the paper's verification step, Sec. 3.4 / Sec. 4.2: measure candidate
  * offload patterns in the target environment, keep the fastest).  Plans,
  * runs and times (CUDA events, `reps` execs after two warm-ups) candidate
- * settings -- engine 0 with each chunk_bytes, then engine 1 by coordinate
+ * settings -- engine 0 with each chunk_bytes, engine 2 at the best of them,
+ * then engine 1 by coordinate
  * descent over streams, chunk_bytes, odd_radices_first, max_lines and
  * per_length -- on the caller's device buffers `in`/`out`
  * (layout of fb_fft_many_layout; `out` is overwritten) in `direction`,
@@ -203,7 +212,10 @@ int fb_fft_check(fb_fft_plan_t plan);
  * enabled, every TMA-fed kernel of this plan announces 16 more bytes per tile
  * than it copies, so its bounded wait runs out (after about one second),
  * the kernel records the error and returns early, and the next fb_fft_check
- * reports FB_FFT_ERR_TIMEOUT.  Nothing faults and the context stays usable;
+ * reports FB_FFT_ERR_TIMEOUT.  In a one-launch batched uneven exec every
+ * four-step row's dependency target is raised out of reach instead: the
+ * first wait to run out (after about a second) ends the others, the tiles
+ * run on, and the check reports the same error.  Nothing faults and the context stays usable;
  * the output of such an exec is undefined.  Not for production use.
  */
 int fb_fft_debug_inject_timeout(fb_fft_plan_t plan, int enable);

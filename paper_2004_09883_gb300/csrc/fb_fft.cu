@@ -241,7 +241,14 @@ struct fb_fft_plan_s {
         int* d_tiles = nullptr;
     };
     UnevenPhase uphase[2];
-    void* d_uneven = nullptr;              // one allocation: both phases' job and tile tables
+    // one launch per exec (k_fft_uneven_one, the default): both phases' jobs
+    // in one table (phase 0, then phase 1), four-step rows waiting on their
+    // chunk's columns through device counters
+    bool uneven_one = false;
+    int uneven_slots = 0;                  // dependency slots: one per four-step chunk
+    UnevenPhase uone;                      // the merged table's jobs, tiles, grid, shared memory
+    unsigned long long* d_sync = nullptr;  // [2 + uneven_slots] counters, zero between execs
+    void* d_uneven = nullptr;              // one allocation: job and tile tables, counters
     std::vector<MultiLaunch> multis;
     std::unique_ptr<MultiArgs> margs;      // launch-argument staging (copied at every launch)
     struct GraphEntry {
@@ -299,11 +306,12 @@ long long many_layout(int count, const long long* lengths, long long* offsets)
 }
 
 // Whether a batched-uneven plan runs on the one-kernel engine: the default
-// (engine 0) unless one launch per length is asked for, and every length
-// either fits one job (<= 2048 points) or splits into two that do.
+// (engine 0: one launch per exec; engine 2: one launch per phase) unless one
+// launch per length is asked for, and every length either fits one job
+// (<= 2048 points) or splits into two that do.
 bool use_uneven_engine(int count, const long long* lengths, const fb_fft_many_opts* opts)
 {
-    if (opts && (opts->engine != 0 || opts->per_length != 0)) return false;
+    if (opts && ((opts->engine != 0 && opts->engine != 2) || opts->per_length != 0)) return false;
     for (int i = 0; i < count; ++i) {
         const long long L = lengths[i];
         if (L <= kUnevenMaxLen) continue;
@@ -452,7 +460,10 @@ int schedule_uneven(fb_fft_plan_s* p, TwiddleBuilder& twb)
             groups.back().second.push_back(i);
         }
     }
-    p->group_names = {"many.uneven.phase0", "many.uneven.phase1"};
+    if (p->uneven_one)
+        p->group_names = {"many.uneven"};
+    else
+        p->group_names = {"many.uneven.phase0", "many.uneven.phase1"};
     long long scratch_need = 0;
     for (auto& g : groups) {
         const long long L = g.first;
@@ -506,6 +517,12 @@ int schedule_uneven(fb_fft_plan_s* p, TwiddleBuilder& twb)
             r.group = 1;
             r.last = true;
             r.scale_n = L;
+            // one launch: the rows of this chunk wait for all its column tiles
+            const int slot = p->uneven_slots++;
+            a.d.dep_post = slot + 1;
+            r.d.dep = slot + 1;
+            if (a.d.ntiles >= (1LL << 31)) return FB_FFT_ERR_UNSUPPORTED_SIZE;
+            r.d.dep_need = (int)a.d.ntiles;
             p->passes.push_back(a);
             p->passes.push_back(r);
         }
@@ -521,6 +538,14 @@ int schedule_uneven(fb_fft_plan_s* p, TwiddleBuilder& twb)
         ph.work_max = std::max(ph.work_max, padded);
     }
     for (auto& ph : p->uphase) ph.smem = uneven_smem_bytes(ph.land_max, ph.work_max);
+    fb_fft_plan_s::UnevenPhase& one = p->uone;
+    for (const fb_fft_plan_s::UnevenPhase& ph : p->uphase) {
+        one.jobs.insert(one.jobs.end(), ph.jobs.begin(), ph.jobs.end());
+        one.tiles += ph.tiles;
+        one.land_max = std::max(one.land_max, ph.land_max);
+        one.work_max = std::max(one.work_max, ph.work_max);
+    }
+    one.smem = uneven_smem_bytes(one.land_max, one.work_max);
     p->scratch_bytes = (size_t)scratch_need * sizeof(float2);
     p->tw_elems = std::max(2LL, twb.total);
     return FB_FFT_OK;
@@ -685,6 +710,7 @@ int schedule_many(fb_fft_plan_s* p, TwiddleBuilder& twb)
 // Kernel launches one exec of a plan makes.
 long long launches_per_exec(const fb_fft_plan_s* p)
 {
+    if (p->uneven && p->uneven_one) return p->uone.jobs.empty() ? 0 : 1;
     if (p->uneven) return (p->uphase[0].jobs.empty() ? 0 : 1) + (p->uphase[1].jobs.empty() ? 0 : 1);
     long long n = (long long)p->multis.size();
     for (const PassPlan& q : p->passes) n += q.multi < 0 ? 1 : 0;
@@ -939,13 +965,15 @@ int build_plan(fb_fft_plan_s* p)
         }
         if (p->uneven) {
             // job tables: descriptors with buffer kinds and element offsets in
-            // place of the exec's pointers, and tile prefixes, both phases in
-            // one device allocation
+            // place of the exec's pointers, and tile prefixes -- each phase's,
+            // and both phases' for the one-launch form -- and that form's
+            // counters, in one device allocation
             std::vector<PassDesc> jobs;
             std::vector<int> tiles;
-            size_t job_at[2], tile_at[2];
-            for (int ph = 0; ph < 2; ++ph) {
-                fb_fft_plan_s::UnevenPhase& u = p->uphase[ph];
+            fb_fft_plan_s::UnevenPhase* tabs[3] = {&p->uphase[0], &p->uphase[1], &p->uone};
+            size_t job_at[3], tile_at[3];
+            for (int ph = 0; ph < 3; ++ph) {
+                fb_fft_plan_s::UnevenPhase& u = *tabs[ph];
                 job_at[ph] = jobs.size();
                 tile_at[ph] = tiles.size();
                 long long t = 0;
@@ -966,22 +994,30 @@ int build_plan(fb_fft_plan_s* p)
                 tiles.push_back((int)t);
             }
             const size_t jb = jobs.size() * sizeof(PassDesc), tb = tiles.size() * sizeof(int);
-            if (cudaMalloc(&p->d_uneven, jb + tb) != cudaSuccess) {
+            const size_t sb_at = (jb + tb + 15) & ~(size_t)15;
+            const int nsync = 2 + p->uneven_slots;
+            const size_t sb = (size_t)nsync * sizeof(unsigned long long);
+            if (cudaMalloc(&p->d_uneven, sb_at + sb) != cudaSuccess) {
                 cudaGetLastError();
                 p->d_uneven = nullptr;
                 return FB_FFT_ERR_ALLOC;
             }
             PassDesc* dj = static_cast<PassDesc*>(p->d_uneven);
             int* dt = reinterpret_cast<int*>(static_cast<char*>(p->d_uneven) + jb);
+            p->d_sync = reinterpret_cast<unsigned long long*>(static_cast<char*>(p->d_uneven) + sb_at);
             if (jb) FB_CK(cudaMemcpyAsync(dj, jobs.data(), jb, cudaMemcpyHostToDevice, p->stream));
             FB_CK(cudaMemcpyAsync(dt, tiles.data(), tb, cudaMemcpyHostToDevice, p->stream));
-            for (int ph = 0; ph < 2; ++ph) {
-                fb_fft_plan_s::UnevenPhase& u = p->uphase[ph];
+            FB_CK(cudaMemsetAsync(p->d_sync, 0, sb, p->stream));
+            for (int ph = 0; ph < 3; ++ph) {
+                fb_fft_plan_s::UnevenPhase& u = *tabs[ph];
                 u.d_jobs = dj + job_at[ph];
                 u.d_tiles = dt + tile_at[ph];
                 if (u.jobs.empty()) continue;
                 int occ = 0;
-                FB_CK(uneven_occupancy(true, u.smem, &occ));
+                if (ph == 2)
+                    FB_CK(uneven_occupancy_one(true, u.smem, &occ));
+                else
+                    FB_CK(uneven_occupancy(true, u.smem, &occ));
                 if (occ < 1) return cuda_fail(cudaErrorInvalidConfiguration, "uneven pass occupancy");
                 u.grid = std::min(u.tiles, (long long)sms * occ);
             }
@@ -1152,14 +1188,16 @@ int launch_many(fb_fft_plan_s* p, cudaStream_t origin, const float2* in, float2*
     return FB_FFT_OK;
 }
 
-// Batched uneven plan on the one-kernel engine: phase 0 (single passes,
-// four-step columns), then phase 1 (four-step rows), one launch each.
-int launch_uneven(fb_fft_plan_s* p, cudaStream_t stream, const float2* in, float2* out, bool fwd)
+// Batched uneven plan on the one-kernel engine: one launch of every pass
+// (k_fft_uneven_one), or phase 0 (single passes, four-step columns) then
+// phase 1 (four-step rows), one launch each.
+int launch_uneven(fb_fft_plan_s* p, cudaStream_t stream, const float2* in, float2* out, bool fwd, bool count)
 {
-    for (int ph = 0; ph < 2; ++ph) {
-        const fb_fft_plan_s::UnevenPhase& u = p->uphase[ph];
+    const bool one = p->uneven_one;
+    for (int ph = 0; ph < (one ? 1 : 2); ++ph) {
+        const fb_fft_plan_s::UnevenPhase& u = one ? p->uone : p->uphase[ph];
         if (u.jobs.empty()) continue;
-        UnevenArgs a;
+        UnevenArgs a{};
         a.jobs = u.d_jobs;
         a.tile_start = u.d_tiles;
         a.in = in;
@@ -1169,6 +1207,9 @@ int launch_uneven(fb_fft_plan_s* p, cudaStream_t stream, const float2* in, float
         a.land_max = u.land_max;
         a.work_max = u.work_max;
         a.scale_on = (!fwd && (p->flags & FB_FFT_SCALE_INV_N)) ? 1 : 0;
+        a.sync = p->d_sync;
+        a.nsync = 2 + p->uneven_slots;
+        a.dep_extra = p->debug_timeout ? (1 << 30) : 0;
         cudaEvent_t e1 = nullptr;
         if (p->profiling) {
             if (p->ev_used + 2 > p->ev.size()) {
@@ -1184,21 +1225,26 @@ int launch_uneven(fb_fft_plan_s* p, cudaStream_t stream, const float2* in, float
             cudaEventRecord(p->ev[p->ev_used], stream);
             p->ev_used += 2;
         }
-        const cudaError_t le = uneven_launch(fwd, a, u.grid, u.smem, stream);
-        if (le != cudaSuccess) return cuda_fail(le, "k_fft_uneven");
-        g_launches.fetch_add(1, std::memory_order_relaxed);
+        const cudaError_t le =
+            one ? uneven_launch_one(fwd, a, u.grid, u.smem, stream) : uneven_launch(fwd, a, u.grid, u.smem, stream);
+        if (le != cudaSuccess) return cuda_fail(le, one ? "k_fft_uneven_one" : "k_fft_uneven");
+        if (count) g_launches.fetch_add(1, std::memory_order_relaxed);
         if (e1) cudaEventRecord(e1, stream);
     }
     return FB_FFT_OK;
 }
 
 // Batched uneven plan, replayed as one CUDA graph per (in, out, direction):
-// the first exec with a new triple captures the fork/join launch sequence.
+// the first exec with a new triple captures its launch sequence (the
+// one-kernel engine's single launch, or the fork/join sequence of engine 1).
 int exec_many(fb_fft_plan_s* p, const float2* in, float2* out, int direction)
 {
     const bool fwd = direction == FB_FFT_FORWARD;
-    if (p->uneven) return launch_uneven(p, p->stream, in, out, fwd);
-    if (!p->use_graph || p->profiling) return launch_many(p, p->stream, in, out, fwd, true);
+    auto launch_all = [&](cudaStream_t st, bool count) {
+        return p->uneven ? launch_uneven(p, st, in, out, fwd, count) : launch_many(p, st, in, out, fwd, count);
+    };
+    if (!p->use_graph || p->profiling || p->debug_timeout || (p->uneven && !p->uneven_one))
+        return launch_all(p->stream, true);
     for (auto& g : p->graphs)
         if (g.in == in && g.out == out && g.dir == direction) {
             FB_CK(cudaGraphLaunch(g.exec, p->stream));
@@ -1208,7 +1254,7 @@ int exec_many(fb_fft_plan_s* p, const float2* in, float2* out, int direction)
     // capture on the plan's own stream (the caller's may be the legacy
     // default stream, which cannot be captured), launch on the caller's
     FB_CK(cudaStreamBeginCapture(p->capture, cudaStreamCaptureModeThreadLocal));
-    const int rc = launch_many(p, p->capture, in, out, fwd, false);
+    const int rc = launch_all(p->capture, false);
     cudaGraph_t graph = nullptr;
     const cudaError_t ce = cudaStreamEndCapture(p->capture, &graph);
     if (rc != FB_FFT_OK) {
@@ -1761,6 +1807,7 @@ int fb_fft_plan_many_ex(fb_fft_plan_t* plan, int count, const long long* lengths
         p->merge_mixed = opts->per_length == 0;
     }
     p->uneven = use_uneven_engine(count, lengths, opts);
+    p->uneven_one = p->uneven && !(opts && opts->engine == 2);
     int rc = build_plan(p);
     if (rc != FB_FFT_OK) {
         free_plan(p);
@@ -1802,7 +1849,8 @@ int fb_fft_autotune_many(int count, const long long* lengths, unsigned flags, co
         *ms = t / reps;
         return rc;
     };
-    // engine 0 (one kernel, two launches): its only knob is the chunk size
+    // engine 0 (one kernel, one launch): its knob is the chunk size; then the
+    // same kernel in one launch per phase (engine 2) at the best chunk size
     const long long chunks[] = {8LL << 20, 16LL << 20, 64LL << 20, 128LL << 20, 512LL << 20};
     fb_fft_many_opts best0{4, 1, 512LL << 20, 0, 0, 0, 0};  // engine 1's knobs at their defaults
     float best0_ms = 0.f;
@@ -1815,6 +1863,13 @@ int fb_fft_autotune_many(int count, const long long* lengths, unsigned flags, co
             if (rc != FB_FFT_OK || v == best0.chunk_bytes) continue;
             fb_fft_many_opts o = best0;
             o.chunk_bytes = v;
+            float ms;
+            rc = measure(o, &ms);
+            if (rc == FB_FFT_OK && ms < best0_ms) best0 = o, best0_ms = ms;
+        }
+        if (rc == FB_FFT_OK) {
+            fb_fft_many_opts o = best0;
+            o.engine = 2;
             float ms;
             rc = measure(o, &ms);
             if (rc == FB_FFT_OK && ms < best0_ms) best0 = o, best0_ms = ms;
@@ -1892,6 +1947,7 @@ int fb_fft_plan_many_query(int count, const long long* lengths, unsigned flags, 
     p.total = many_layout(count, lengths, p.offsets.data());
     p.nslots = many_streams();
     p.uneven = use_uneven_engine(count, lengths, nullptr);
+    p.uneven_one = p.uneven;
     TwiddleBuilder twb;
     const int rc = schedule_plan(&p, twb);
     p.magic = kDead;

@@ -80,6 +80,13 @@ struct PassDesc {
     // first stage maps threads along a line; > 0 = rows of land_row elements
     // and the first stage maps threads across lines (tiles of 2 to 8 lines).
     int land_row;
+    // Batched uneven lengths in one launch (k_fft_uneven_one): dependency
+    // slot s + 1 whose finished-tile counter this job's tiles raise (four-step
+    // columns), or that it waits for (four-step rows) until the counter
+    // reaches dep_need; 0 = none.
+    int dep_post;
+    int dep;
+    int dep_need;
 };
 
 // Fill ns[] (product of the earlier radices) and its multiply-high

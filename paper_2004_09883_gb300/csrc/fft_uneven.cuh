@@ -41,6 +41,12 @@ struct UnevenArgs {
     int land_max;           // elements of one landing buffer (multiple of 16; holds a padded work tile too)
     int work_max;           // elements of the work buffer (multiple of 16)
     int scale_on;           // 1: jobs marked apply_scale multiply by their `scale`
+    // One-launch form (k_fft_uneven_one) only: device counters, nsync of
+    // them, zero between execs -- [0] tiles claimed, [1] CTAs finished,
+    // [1 + s] finished tiles of dependency slot s (PassDesc::dep_post / dep).
+    unsigned long long* sync;
+    int nsync;
+    int dep_extra;          // test hook: added to every dependency target (the waits then run out)
 };
 
 // Kernel argument of the inline form: the tables themselves (a.jobs and
@@ -375,6 +381,195 @@ __global__ void __launch_bounds__(kUnevenThreads, 4) k_fft_uneven(const __grid_c
     uneven_body<FWD, false>(a, a.jobs, a.tile_start);
 }
 
+// ---------------------------------------------------------------------------
+// Every pass of a batched uneven exec in ONE launch.  The job table holds the
+// single passes and four-step columns, then the four-step rows; a row reads
+// what the columns of its chunk wrote, so it may start only once they are
+// done.  Tiles are claimed in table order from a device counter (one atomic
+// per tile, issued a tile ahead), not assigned round robin: a claimed tile
+// always belongs to a running CTA, so a row tile waits only for column tiles
+// already held by running CTAs, and a column tile never waits (every tile a
+// CTA holds before it also is a column tile).  No CTA can therefore wait on
+// one that is not resident, whatever else shares the GPU.  A column tile, once
+// stored, raises its chunk's counter (every thread fences its own stores, a
+// barrier, then one release add, just before the CTA's next last stage); a
+// row tile's inputs load once an acquire read sees the counter at the
+// chunk's column-tile count.  Where the next
+// tile's inputs are not ready when it is
+// claimed, its copies wait until the current tile is done (bounded: past the
+// limit the error word is set and the tile runs anyway).  The last CTA to
+// finish zeroes the counters for the next exec.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ unsigned long long ld_acquire_u64(const unsigned long long* p)
+{
+    unsigned long long v;
+    asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ void red_release_add_u64(unsigned long long* p, unsigned long long v)
+{
+    asm volatile("red.release.gpu.global.add.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+// Thread 0: whether the inputs of job `job` are ready.  `seen` is the last
+// dependency slot this CTA found complete: counters only grow during an
+// exec, and the acquire that found it complete (then a barrier) already
+// orders every later load of the CTA, so that slot needs no further read.
+__device__ __forceinline__ bool udeps_ready(const UnevenArgs& a, const PassDesc* job, int& seen)
+{
+    const int dep = __ldg(&job->dep);
+    if (dep == 0 || dep == seen) return true;
+    if (ld_acquire_u64(a.sync + 1 + dep) <
+        (unsigned long long)__ldg(&job->dep_need) + (unsigned long long)a.dep_extra)
+        return false;
+    seen = dep;
+    return true;
+}
+// Thread 0: wait until they are, at most kWaitLimitNs; past it set the error
+// word.  Once the word is set (by any CTA) no wait lasts longer, so a launch
+// whose waits cannot end still ends within about one limit.
+__device__ __forceinline__ void udeps_wait(const UnevenArgs& a, const PassDesc* job, int* err, int& seen)
+{
+    if (udeps_ready(a, job, seen)) return;
+    const unsigned long long t0 = global_ns();
+    while (!udeps_ready(a, job, seen)) {
+        if (*reinterpret_cast<volatile int*>(err) != 0) return;
+        if (global_ns() - t0 > kWaitLimitNs) {
+            atomicExch(err, 1);
+            return;
+        }
+        __nanosleep(200);
+    }
+}
+
+template <bool FWD>
+__device__ __forceinline__ void uneven_body_one(const UnevenArgs& a)
+{
+    extern __shared__ __align__(128) unsigned char smem_dyn[];
+    unsigned char* smem_raw = smem_dyn + ((128u - (smem_u32(smem_dyn) & 127u)) & 127u);
+    float2* land0 = reinterpret_cast<float2*>(smem_raw);
+    float2* work = land0 + 2 * a.land_max;
+    __shared__ PassDesc sd[2];  // sd[b]: descriptor of the tile in landing buffer b
+    __shared__ int s_tk[2];     // claimed tickets, handed from thread 0 to the CTA
+    __shared__ int s_ok;        // 1: the next tile's inputs are ready
+    __shared__ int s_ok0;       // the same for the first tile (s_ok may change before every warp read it)
+    __shared__ int s_last;      // 1: this CTA finished last
+    constexpr int TH = kUnevenThreads;
+    const int tid = threadIdx.x;
+    const PassDesc* jobs = a.jobs;
+    const int* tile_start = a.tile_start;
+    const int total = __ldg(tile_start + a.njobs);
+    auto copy_desc = [&](int job, int b) {
+        const int* src = reinterpret_cast<const int*>(jobs + job);
+        int* dst = reinterpret_cast<int*>(&sd[b]);
+        for (int w = tid; w < (int)(sizeof(PassDesc) / 4); w += TH) dst[w] = __ldg(src + w);
+    };
+    pdl_start();
+    if (tid == 0) {
+        s_tk[0] = (int)atomicAdd(a.sync, 1ull);
+        s_tk[1] = (int)atomicAdd(a.sync, 1ull);
+    }
+    __syncthreads();
+    int g = s_tk[0], gn = s_tk[1];
+    int jg = 0;              // job of tile g
+    bool cur_loaded = false; // tile g's copies issued
+    // A column tile is counted one tile late, just before the next tile's
+    // last stage: a fence orders only the fencing thread's own stores, so
+    // every thread fences its share of the counted tile's stores, then a
+    // barrier, then one release add -- by then those stores have drained and
+    // the fences cost little (fencing right after the stores stalled every
+    // column tile).  Pending counts go out before any dependency wait.
+    int pend = 0;  // dependency slot + 1 of a finished column tile not yet counted
+    int seen = 0;  // thread 0: the last dependency slot + 1 found complete
+    auto flush = [&]() {
+        if (pend) {
+            __threadfence();
+            __syncthreads();
+            if (tid == 0) red_release_add_u64(a.sync + 1 + pend, 1ull);
+            pend = 0;
+        }
+    };
+    if (g < total) {
+        while (g >= __ldg(tile_start + jg + 1)) ++jg;
+        copy_desc(jg, 0);
+        if (tid == 0) s_ok0 = udeps_ready(a, jobs + jg, seen) ? 1 : 0;
+        __syncthreads();
+        cur_loaded = s_ok0 != 0;
+        if (cur_loaded) utile_load(a, sd[0], utile_index(sd[0], g - __ldg(tile_start + jg)), land0);
+        cp_async_commit();
+    }
+    for (int i = 0; g < total; ++i) {
+        const int b = i & 1;
+        float2* land = land0 + b * a.land_max;
+        const int gl = g - __ldg(tile_start + jg);  // this tile within its job
+        if (!cur_loaded) {  // inputs not ready when it was claimed: wait, then copy
+            flush();
+            if (tid == 0) udeps_wait(a, jobs + jg, sd[b].err, seen);
+            __syncthreads();
+            utile_load(a, sd[b], utile_index(sd[b], gl), land);
+            cp_async_commit();
+        }
+        // the ticket of the tile after next, used one iteration later
+        unsigned long long claim = 0;
+        if (tid == 0) claim = atomicAdd(a.sync, 1ull);
+        bool next_loaded = false;
+        int jn = jg;
+        if (gn < total) {  // the next tile's job and descriptor, then its copies when its inputs are ready
+            while (gn >= __ldg(tile_start + jn + 1)) ++jn;
+            copy_desc(jn, b ^ 1);
+            if (tid == 0) s_ok = udeps_ready(a, jobs + jn, seen) ? 1 : 0;
+            __syncthreads();
+            next_loaded = s_ok != 0;
+            if (next_loaded)
+                utile_load(a, sd[b ^ 1], utile_index(sd[b ^ 1], gn - __ldg(tile_start + jn)),
+                           land0 + (b ^ 1) * a.land_max);
+            cp_async_commit();
+            cp_async_wait<1>();  // this tile's copies have landed (the next tile's may still fly)
+        } else {
+            cp_async_wait<0>();
+        }
+        __syncthreads();
+        const PassDesc& d = sd[b];
+        const UTileIdx ti = utile_index(d, gl);
+        const int nst = d.nst;
+        const int post = d.dep_post;
+        ustage_any<FWD, kPosFirst>(a, d, 0, land, work, ti);
+        __syncthreads();
+        int s = 1;
+        ustage_run<8, FWD>(a, d, s, nst, land, work, ti);
+        ustage_run<4, FWD>(a, d, s, nst, land, work, ti);
+        ustage_run<2, FWD>(a, d, s, nst, land, work, ti);
+        ustage_run<5, FWD>(a, d, s, nst, land, work, ti);
+        ustage_run<3, FWD>(a, d, s, nst, land, work, ti);
+        flush();  // the previous column tile's count
+        ustage_any<FWD, kPosLast>(a, d, nst - 1, land, work, ti);
+        if (tid == 0) s_tk[i & 1] = (int)claim;
+        __syncthreads();  // buffer b and sd[b] are free
+        pend = post;
+        g = gn;
+        jg = jn;
+        gn = s_tk[i & 1];
+        cur_loaded = next_loaded;
+    }
+    flush();
+    // the last CTA out zeroes the counters (every other CTA's atomics are
+    // ordered before its finish count by the fences)
+    __syncthreads();
+    if (tid == 0) {
+        __threadfence();
+        s_last = atomicAdd(a.sync + 1, 1ull) == (unsigned long long)gridDim.x - 1 ? 1 : 0;
+        if (s_last) __threadfence();
+    }
+    __syncthreads();
+    if (s_last)
+        for (int k = tid; k < a.nsync; k += TH) a.sync[k] = 0ull;
+}
+
+template <bool FWD>
+__global__ void __launch_bounds__(kUnevenThreads, 4) k_fft_uneven_one(const __grid_constant__ UnevenArgs a)
+{
+    uneven_body_one<FWD>(a);
+}
+
 // The same pass with its job and tile-prefix tables inside the kernel
 // parameter (at most kUnevenInlineJobs jobs): a small batch then needs no
 // copy of its tables to the device before it can start.
@@ -392,6 +587,8 @@ cudaError_t uneven_occupancy(bool forward, size_t smem, int* blocks_per_sm);
 cudaError_t uneven_launch_inline(bool forward, const UnevenInlineArgs& a, long long grid, size_t smem,
                                  cudaStream_t stream);
 cudaError_t uneven_occupancy_inline(bool forward, size_t smem, int* blocks_per_sm);
+cudaError_t uneven_launch_one(bool forward, const UnevenArgs& a, long long grid, size_t smem, cudaStream_t stream);
+cudaError_t uneven_occupancy_one(bool forward, size_t smem, int* blocks_per_sm);
 inline size_t uneven_smem_bytes(int land_max, int work_max)
 {
     return 128 + (size_t)(2LL * land_max + work_max) * sizeof(float2);

@@ -285,10 +285,8 @@ def test_many_planner_schedules_pass_host_checks(fb, seed):
     info = fb.plan_many_query(lens)
     offs, total = fb.many_layout(lens)
     assert info["elements"] == total and info["batch"] == len(lens)
-    distinct_small = len({n for n in lens if n <= fb.MAX_SMEM_LEN})
-    per_length = distinct_small + 2 * len({n for n in lens if n > fb.MAX_SMEM_LEN})
-    # lengths sharing a kernel (3/5 factors, same power-of-two factor) merge into one launch
-    assert 2 <= info["passes"] < per_length
+    # the one-kernel engine (every length fits it here): every pass of the batch in one launch
+    assert info["passes"] == 1
     # every four-step transform owns its scratch (the merged launches run them together)
     assert info["scratch_bytes"] >= 8 * sum(int(n) for n in lens if n > fb.MAX_SMEM_LEN)
 

@@ -160,29 +160,98 @@ ENGINE0_LENGTHS = ([1, 2, 3, 4, 5, 8, 9, 16, 27, 64, 100, 125, 243, 1000, 1024, 
 
 
 @pytest.mark.parametrize("direction,scale", [(-1, False), (1, True)])
-def test_one_kernel_engine_matches_oracle_in_two_launches(fb, direction, scale):
-    """Engine 0 (the default): every pass of the batch in one kernel, two
-    launches per exec (single passes and four-step columns, then four-step
-    rows); lengths 1 to 2^20, one-radix schedules, odd lengths, every result
-    against the oracle, in place and out of place, and the graph-free replay
-    gives the same bits."""
+def test_one_kernel_engine_matches_oracle_in_one_launch(fb, direction, scale):
+    """Engine 0 (the default): every pass of the batch -- single passes,
+    four-step columns and the rows that wait for them -- in one launch per
+    exec (a replayed graph); lengths 1 to 2^20, one-radix schedules, odd
+    lengths, every result against the oracle, in place and out of place, and
+    repeated and graph-free execs give the same bits."""
     import torch
     xs = _batch(ENGINE0_LENGTHS, 960)
     with fb.PlanMany(ENGINE0_LENGTHS, scale_inv_n=scale) as p:
-        assert p.info()["passes"] == 2
+        assert p.info()["passes"] == 1
         d = torch.from_numpy(p.pack(xs)).cuda()
         l0 = fb.launch_count()
         y = p.exec(d, None, direction)
         torch.cuda.synchronize()
-        assert fb.launch_count() - l0 == 2
+        assert fb.launch_count() - l0 == 1
         y2 = p.exec(d, None, direction)
         z = d.clone()
         p.exec(z, z, direction)
+        p.set_graph(False)
+        y3 = p.exec(d, None, direction)
         p.check()
-        ys, ys2, zs = (p.unpack(t.cpu().numpy()) for t in (y, y2, z))
-    for a, b, c in zip(ys, ys2, zs):
-        assert np.array_equal(a, b) and np.array_equal(a, c)
+        ys, ys2, ys3, zs = (p.unpack(t.cpu().numpy()) for t in (y, y2, y3, z))
+    for a, b, c, e in zip(ys, ys2, zs, ys3):
+        assert np.array_equal(a, b) and np.array_equal(a, c) and np.array_equal(a, e)
     _check(p, xs, ys, direction, scale)
+
+
+def test_one_launch_and_two_launch_forms_give_identical_bits(fb):
+    """Engine 2 runs the same jobs as two launches (all single passes and
+    four-step columns, then all rows): the same bits as the one launch."""
+    import torch
+    xs = _batch(ENGINE0_LENGTHS, 960)
+    with fb.PlanMany(ENGINE0_LENGTHS) as p1, fb.PlanMany(ENGINE0_LENGTHS, opts={"engine": 2}) as p2:
+        assert p1.info()["passes"] == 1 and p2.info()["passes"] == 2
+        d = torch.from_numpy(p1.pack(xs)).cuda()
+        l0 = fb.launch_count()
+        y2 = p2.exec(d, None, -1)
+        torch.cuda.synchronize()
+        assert fb.launch_count() - l0 == 2
+        y1 = p1.exec(d, None, -1)
+        p1.check()
+        p2.check()
+        # transforms only: the pad value after an odd length is never written
+        for a, b in zip(p1.unpack(y1.cpu().numpy()), p2.unpack(y2.cpu().numpy())):
+            assert np.array_equal(a, b)
+
+
+def test_one_launch_beside_other_work_on_the_gpu(fb):
+    """The one-launch exec while another stream keeps part of the GPU busy (so
+    not every CTA of it is resident at once): a row tile only ever waits for
+    column tiles that running CTAs hold, so it finishes, with the same bits."""
+    import torch
+    lens = list(inputs.uneven_lengths(300, 64, 65536, inputs.seed_for(inputs.WORKLOAD_UNEVEN_4096, 13)))
+    xs = _batch(lens, 990)
+    with fb.PlanMany(lens) as p:
+        d = torch.from_numpy(p.pack(xs)).cuda()
+        want = p.unpack(p.exec(d, None, -1).cpu().numpy())
+        side = torch.cuda.Stream()
+        a = torch.randn(4096, 4096, device="cuda")
+        for it in range(6):
+            with torch.cuda.stream(side):
+                for _ in range(8):
+                    a = torch.tanh(a @ a * 1e-3)
+            got = p.exec(d, None, -1)
+            torch.cuda.synchronize()
+            p.check()
+            # transforms only: the pad value after an odd length is never written
+            for n, g, w in zip(lens, p.unpack(got.cpu().numpy()), want):
+                assert np.array_equal(g, w), f"exec {it}, n={n}"
+    _check(p, xs, want, -1)
+
+
+def test_one_launch_reports_a_dependency_wait_that_runs_out(fb):
+    """The test hook raises every four-step row's dependency target out of
+    reach: the waits give up after about a second (the first one to run out
+    ends the others), the plan reports FB_FFT_ERR_TIMEOUT, and the next exec
+    without the hook is correct again (the counters were zeroed)."""
+    import torch
+    lens = [8192, 64, 45000, 100, 65536]
+    xs = _batch(lens, 995)
+    with fb.PlanMany(lens) as p:
+        d = torch.from_numpy(p.pack(xs)).cuda()
+        p.debug_inject_timeout(True)
+        p.exec(d, None, -1)
+        with pytest.raises(fb.FFTError) as e:
+            p.check()
+        assert e.value.status == -5
+        p.debug_inject_timeout(False)
+        y = p.exec(d, None, -1)
+        p.check()
+        ys = p.unpack(y.cpu().numpy())
+    _check(p, xs, ys, -1)
 
 
 def test_both_engines_agree_with_the_oracle(fb):
