@@ -392,9 +392,9 @@ __global__ void __launch_bounds__(kUnevenThreads, 4) k_fft_uneven(const __grid_c
 // CTA holds before it also is a column tile).  No CTA can therefore wait on
 // one that is not resident, whatever else shares the GPU.  A column tile, once
 // stored, raises its chunk's counter (every thread fences its own stores, a
-// barrier, then one release add, just before the CTA's next last stage); a
-// row tile's inputs load once an acquire read sees the counter at the
-// chunk's column-tile count.  Where the next
+// barrier, then one release add, at the barrier after the CTA's next first
+// stage); a row tile's inputs load once an acquire read sees the counter at
+// the chunk's column-tile count.  Where the next
 // tile's inputs are not ready when it is
 // claimed, its copies wait until the current tile is done (bounded: past the
 // limit the error word is set and the tile runs anyway).  The last CTA to
@@ -472,12 +472,13 @@ __device__ __forceinline__ void uneven_body_one(const UnevenArgs& a)
     int g = s_tk[0], gn = s_tk[1];
     int jg = 0;              // job of tile g
     bool cur_loaded = false; // tile g's copies issued
-    // A column tile is counted one tile late, just before the next tile's
-    // last stage: a fence orders only the fencing thread's own stores, so
-    // every thread fences its share of the counted tile's stores, then a
-    // barrier, then one release add -- by then those stores have drained and
-    // the fences cost little (fencing right after the stores stalled every
-    // column tile).  Pending counts go out before any dependency wait.
+    // A column tile is counted one tile late, at the barrier after the next
+    // tile's first stage: a fence orders only the fencing thread's own
+    // stores, so every thread fences its share of the counted tile's stores,
+    // then the barrier, then one release add -- by then those stores have
+    // drained and the fences cost little (fencing right after the stores
+    // stalled every column tile).  Pending counts go out before any
+    // dependency wait and after the last tile.
     int pend = 0;  // dependency slot + 1 of a finished column tile not yet counted
     int seen = 0;  // thread 0: the last dependency slot + 1 found complete
     auto flush = [&]() {
@@ -533,14 +534,16 @@ __device__ __forceinline__ void uneven_body_one(const UnevenArgs& a)
         const int nst = d.nst;
         const int post = d.dep_post;
         ustage_any<FWD, kPosFirst>(a, d, 0, land, work, ti);
+        if (pend) __threadfence();  // the previous column tile's stores (see flush)
         __syncthreads();
+        if (tid == 0 && pend) red_release_add_u64(a.sync + 1 + pend, 1ull);
+        pend = 0;
         int s = 1;
         ustage_run<8, FWD>(a, d, s, nst, land, work, ti);
         ustage_run<4, FWD>(a, d, s, nst, land, work, ti);
         ustage_run<2, FWD>(a, d, s, nst, land, work, ti);
         ustage_run<5, FWD>(a, d, s, nst, land, work, ti);
         ustage_run<3, FWD>(a, d, s, nst, land, work, ti);
-        flush();  // the previous column tile's count
         ustage_any<FWD, kPosLast>(a, d, nst - 1, land, work, ti);
         if (tid == 0) s_tk[i & 1] = (int)claim;
         __syncthreads();  // buffer b and sd[b] are free
