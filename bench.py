@@ -106,18 +106,21 @@ def load_peaks() -> dict:
     return {"hbm_gbs": 6800.0, "source": "fallback"}
 
 
-def load_traffic(workload: str) -> dict | None:
+def load_traffic(workload: str, pass_name: str | None = None) -> dict | None:
     """DRAM bytes per launch from a committed ncu capture, valid only while the
-    kernel sources are unchanged since the capture."""
+    kernel sources are unchanged since the capture.  A workload holds one
+    entry, or a list of them (one per pass role, e.g. the batched uneven exec
+    in one launch and in two)."""
     p = os.path.join(ROOT, "profiles", "traffic.json")
     if not os.path.exists(p):
         return None
     with open(p) as f:
         d = json.load(f)
     e = d.get(workload)
-    if not e or e.get("kernel_hash") != kernel_hash():
-        return None
-    return e
+    for x in (e if isinstance(e, list) else [e] if e else []):
+        if x.get("kernel_hash") == kernel_hash() and (pass_name is None or x.get("pass") == pass_name):
+            return x
+    return None
 
 
 class ClockSampler:
@@ -475,8 +478,8 @@ def roofline_of(passes, prof_steps: int, execs: int, bytes_per_exec: float, wl_n
     launches_per_exec = dom[2] / (prof_steps * execs)
     launch_bytes = bytes_per_exec / launches_per_exec
     achieved = launch_bytes / (per_launch_ms / 1e3) / 1e9
-    tr = load_traffic(wl_name)
-    traffic = tr["dram_bytes_per_launch"] if tr and tr.get("pass") == dom[0] else None
+    tr = load_traffic(wl_name, dom[0])
+    traffic = tr["dram_bytes_per_launch"] if tr else None
     r = {"bound": "hbm", "achieved": round(achieved, 2), "peak": peaks["hbm_gbs"], "unit": "GB/s",
          "frac": round(achieved / peaks["hbm_gbs"], 4), "traffic": traffic,
          "kernel_pass": dom[0], "launch_ms": round(per_launch_ms, 5), "algorithmic_bytes_per_launch": launch_bytes,
@@ -716,8 +719,8 @@ def uneven_roofline(passes, prof_steps, lens, bytes_step, ms, launches_per_exec,
     if dom and dom[0] in phase_bytes and dom[2] > 0:
         per_launch_ms = dom[1] / dom[2]
         achieved = phase_bytes[dom[0]] / (per_launch_ms / 1e3) / 1e9
-        tr = load_traffic(wl_name)
-        traffic = tr["dram_bytes_per_launch"] if tr and tr.get("pass") == dom[0] else None
+        tr = load_traffic(wl_name, dom[0])
+        traffic = tr["dram_bytes_per_launch"] if tr else None
         r = {"bound": "hbm", "achieved": round(achieved, 2), "peak": peaks["hbm_gbs"], "unit": "GB/s",
              "frac": round(achieved / peaks["hbm_gbs"], 4), "traffic": traffic, "kernel_pass": dom[0],
              "launch_ms": round(per_launch_ms, 5), "algorithmic_bytes_per_launch": phase_bytes[dom[0]],
@@ -751,7 +754,7 @@ def gpu_many(args, ctx: Ctx, wl: dict, headline: bool) -> dict:
     # the library's autotuner picks the plan knobs on this workload (untimed;
     # --quick keeps the defaults so profiler runs stay short)
     if args.quick:
-        tuned = fbfft.ManyOpts()
+        tuned = fbfft.ManyOpts(engine=args.uneven_engine or 0)
     else:
         tuned, _ = fbfft.autotune_many(lens, xin[0], xout[0], fbfft.FORWARD, reps=3)
     default_plan = fbfft.PlanMany(lens, stream=stream)
@@ -1049,6 +1052,9 @@ def main():
                     help="seconds of oracle time for the cpu_baseline of each nested workload")
     ap.add_argument("--quick", action="store_true",
                     help="timed loop only (no pre-roll, e2e, error check or CPU baseline): for profiler runs")
+    ap.add_argument("--uneven-engine", type=int, default=None, choices=[0, 1, 2],
+                    help="with --quick, the uneven workload's plan takes this engine (0: one launch per exec, "
+                         "2: two launches; the default run lets the autotuner choose)")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
