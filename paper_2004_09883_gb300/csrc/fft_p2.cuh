@@ -240,12 +240,31 @@ __device__ __forceinline__ void p2_stage(const PassDesc& d, float2* land, float2
             const int k = j & (NS - 1);
             if constexpr (NS > 1) {
                 if constexpr (p2_tw_split(LG) && S == 2) {
+                    // w_L^{k r} = w_{L/16}^{kh r} w_L^{kl r} from the two tables for r = 1
+                    // and r = 8 only; the others by one complex multiply each from
+                    // those (w^r = w^{r-1} w: at most seven products in a row, as
+                    // for the four-step twiddle), 4 shared loads per butterfly
+                    // instead of 30
+                    static_assert(R == 16, "the split stage is radix 16");
                     constexpr int NS1 = pow2_ns(LG, 1);
                     const float2* th = tws + p2_tws_off(LG, 1) + (k >> 4);  // w_{L/16}^{kh r}
                     const float2* tl = tws + p2_tws_off(LG, 2) + (k & 15);  // w_L^{kl r}
+                    const float2 w1 = cmul(th[0], tl[0]);
+                    const float2 w8 = cmul(th[7 * NS1], tl[7 * 16]);
+                    float2 w = w1;
+                    v[q][1] = twmul<FWD>(v[q][1], w1);
 #pragma unroll
-                    for (int r = 1; r < R; ++r)
-                        v[q][r] = twmul<FWD>(v[q][r], cmul(th[(r - 1) * NS1], tl[(r - 1) * 16]));
+                    for (int r = 2; r < 8; ++r) {
+                        w = cmul(w, w1);
+                        v[q][r] = twmul<FWD>(v[q][r], w);
+                    }
+                    w = w8;
+                    v[q][8] = twmul<FWD>(v[q][8], w8);
+#pragma unroll
+                    for (int r = 9; r < 16; ++r) {
+                        w = cmul(w, w1);
+                        v[q][r] = twmul<FWD>(v[q][r], w);
+                    }
                 } else if constexpr (C::TWS > 0) {
                     const float2* tw = tws + p2_tws_off(LG, S) + k;
 #pragma unroll

@@ -93,6 +93,27 @@ int main()
             }
         const bool sizes_ok = ns2 * r2 == L && ns2 == 16 * ns1 && p2_tws_off(lg, 2) + 16 * 15 == total;
         std::printf("split_lg%d %lld %.3e %d\n", lg, n, worst, sizes_ok ? 1 : 0);
+        // the kernel's arithmetic in FP32: table entries rounded to float, the
+        // factors for r = 1 and 8 as table products, the others stepped by one
+        // complex multiply each (the kernel's cmul)
+        double worst_step = 0;
+        long long ns_ = 0;
+        auto f2 = [](cd z) { return make_float2((float)z.real(), (float)z.imag()); };
+        for (int k = 0; k < ns2; ++k) {
+            const float2 th0 = f2(tws[p2_tws_off(lg, 1) + (k >> 4)]), tl0 = f2(tws[p2_tws_off(lg, 2) + (k & 15)]);
+            const float2 th7 = f2(tws[p2_tws_off(lg, 1) + (k >> 4) + 7 * ns1]);
+            const float2 tl7 = f2(tws[p2_tws_off(lg, 2) + (k & 15) + 7 * 16]);
+            const float2 w1 = cmul(th0, tl0), w8 = cmul(th7, tl7);
+            float2 wr = w1;
+            for (int r = 1; r < 16; ++r) {
+                if (r == 8) wr = w8;
+                else if (r > 1) wr = cmul(wr, w1);
+                const cd want = w((long long)k * r, (long long)ns2 * r2);
+                worst_step = std::fmax(worst_step, std::abs(cd(wr.x, wr.y) - want));
+                ++ns_;
+            }
+        }
+        std::printf("split_step_lg%d %lld %.3e\n", lg, ns_, worst_step);
         delete[] tws;
     }
 

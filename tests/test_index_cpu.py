@@ -31,6 +31,10 @@ def test_index_arithmetic(tmp_path):
     for lg in (11, 12):
         n, worst, sizes_ok = rows[f"split_lg{lg}"]
         assert int(n) == (1 << lg) // 16 * 15 and float(worst) < 1e-13 and sizes_ok == "1"
+        # the kernel's FP32 factors (two table products, the rest stepped):
+        # within a few ulp of 1 (at most seven products in a row)
+        n, worst = rows[f"split_step_lg{lg}"]
+        assert int(n) == (1 << lg) // 16 * 15 and float(worst) < 1e-6
     # the swizzled first work generation: one-to-one, inside the row, and
     # the second stage's shortcut reads the slots the first stage wrote
     n, bad, configs = map(int, rows["swizzle"])
