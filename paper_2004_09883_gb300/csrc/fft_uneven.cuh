@@ -241,9 +241,31 @@ __device__ __forceinline__ void ustage(const UnevenArgs& a, const PassDesc& d, i
         if (tok && j < LR) {
             const int k = first ? 0 : j - (int)__umulhi((unsigned)j, nsm) * Ns;
             if constexpr (!first) {
+                // the factors are the powers w^r of w = w_{Ns R}^k (table entry
+                // (r-1) Ns + k): radix 8 loads w and w^4 and forms the other five
+                // by complex multiplies (at most three deep), radix 4 and 5 load w
+                // and w^2 -- fewer loads from tables that mostly miss L1
                 const float2* tw = twb + k;
+                if constexpr (R == 8) {
+                    const float2 w1 = __ldg(tw), w4 = __ldg(tw + 3 * Ns);
+                    const float2 w2 = cmul(w1, w1), w3 = cmul(w2, w1);
+                    v[q][1] = twmul<FWD>(v[q][1], w1);
+                    v[q][2] = twmul<FWD>(v[q][2], w2);
+                    v[q][3] = twmul<FWD>(v[q][3], w3);
+                    v[q][4] = twmul<FWD>(v[q][4], w4);
+                    v[q][5] = twmul<FWD>(v[q][5], cmul(w4, w1));
+                    v[q][6] = twmul<FWD>(v[q][6], cmul(w4, w2));
+                    v[q][7] = twmul<FWD>(v[q][7], cmul(w4, w3));
+                } else if constexpr (R == 4 || R == 5) {
+                    const float2 w1 = __ldg(tw), w2 = __ldg(tw + Ns);
+                    v[q][1] = twmul<FWD>(v[q][1], w1);
+                    v[q][2] = twmul<FWD>(v[q][2], w2);
+                    v[q][3] = twmul<FWD>(v[q][3], cmul(w2, w1));
+                    if constexpr (R == 5) v[q][4] = twmul<FWD>(v[q][4], cmul(w2, w2));
+                } else {
 #pragma unroll
-                for (int r = 1; r < R; ++r) v[q][r] = twmul<FWD>(v[q][r], __ldg(tw + (r - 1) * Ns));
+                    for (int r = 1; r < R; ++r) v[q][r] = twmul<FWD>(v[q][r], __ldg(tw + (r - 1) * Ns));
+                }
             }
             dft<R, FWD>(v[q]);
             const int base = (j - k) * R + k;
