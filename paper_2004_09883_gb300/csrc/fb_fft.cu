@@ -227,9 +227,10 @@ struct fb_fft_plan_s {
     bool odd_first = false;
     int max_lines = 0;
     bool merge_mixed = true;               // batched uneven: merged mixed-kernel launches
-    // batched uneven, one-kernel engine (k_fft_uneven): every pass is a job of
-    // one of two launches (phase 0: single passes and four-step columns;
-    // phase 1: four-step rows); jobs and tile prefixes in device tables
+    // batched uneven, one-kernel engine: every pass is a job of phase 0 (single
+    // passes and four-step columns) or phase 1 (four-step rows), one launch of
+    // k_fft_uneven each (engine 2), or both in the one launch below; jobs and
+    // tile prefixes in device tables
     bool uneven = false;
     struct UnevenPhase {
         std::vector<int> jobs;   // pass indices
@@ -446,7 +447,9 @@ int split_uneven(long long n, long long* n1, long long* n2)
 // one job over all its transforms (offset tables), or, above 2048 points, a
 // four-step pair of jobs per chunk of transforms, each chunk with its own
 // scratch region.  Phase 0 holds single passes and four-step columns, phase
-// 1 the four-step rows; each phase is one launch of k_fft_uneven.
+// 1 the four-step rows; the default plan runs both in one launch of
+// k_fft_uneven_one (each row chunk after its columns, through a dependency
+// slot per chunk), engine 2 each phase as one launch of k_fft_uneven.
 int schedule_uneven(fb_fft_plan_s* p, TwiddleBuilder& twb)
 {
     std::vector<std::pair<long long, std::vector<long long>>> groups;  // (L, transform indices)
