@@ -410,14 +410,14 @@ __global__ void __launch_bounds__(kUnevenThreads, 4) k_fft_uneven(const __grid_c
 // done.  Tiles are claimed in table order from a device counter (one atomic
 // per tile, issued a tile ahead), not assigned round robin: a claimed tile
 // always belongs to a running CTA, so a row tile waits only for column tiles
-// already held by running CTAs, and a column tile never waits (every tile a
-// CTA holds before it also is a column tile).  No CTA can therefore wait on
-// one that is not resident, whatever else shares the GPU.  A column tile, once
-// stored, raises its chunk's counter (every thread fences its own stores, a
-// barrier, then one release add, at the barrier after the CTA's next first
-// stage); a row tile's inputs load once an acquire read sees the counter at
-// the chunk's column-tile count.  Where the next
-// tile's inputs are not ready when it is
+// already held by running CTAs, and a column tile never waits (a CTA claims
+// in increasing order, so whatever it holds before a column tile is a column
+// tile too).  No CTA can therefore wait on one that is not resident,
+// whatever else shares the GPU.  A column tile, once stored, raises its
+// chunk's counter (every thread fences its own stores, a barrier, then one
+// release add, at the barrier after the CTA's next first stage); a row tile's
+// inputs load once an acquire read sees the counter at the chunk's
+// column-tile count.  Where the next tile's inputs are not ready when it is
 // claimed, its copies wait until the current tile is done (bounded: past the
 // limit the error word is set and the tile runs anyway).  The last CTA to
 // finish zeroes the counters for the next exec.
