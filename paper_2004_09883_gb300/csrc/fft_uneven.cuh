@@ -1,13 +1,16 @@
 // fft_uneven.cuh -- the line pass of batched uneven lengths (fb_fft_plan_many):
-// every pass of one phase of such a batch -- single-pass lines, four-step
-// columns, four-step rows, any 5-smooth length up to 2048, power-of-two or
-// not -- in ONE launch.
+// single-pass lines, four-step columns and four-step rows of any 5-smooth
+// length up to 2048, power-of-two or not.  k_fft_uneven runs every pass of
+// one phase of such a batch in one launch (phase 0: single passes and
+// columns; phase 1: rows); k_fft_uneven_one (below) runs both phases in ONE
+// launch, each row chunk after its columns.
 //
 // Jobs (one PassDesc per length group or four-step chunk, each with its own
 // offset tables, strides, radix schedule and twiddle tables) sit in a device
 // table; a device prefix table gives each job's first global tile.
-// Persistent CTAs walk the global tiles blockIdx.x, +gridDim.x, ...: the job
-// of a tile is found by walking the prefix table forward (tiles only grow).
+// k_fft_uneven's persistent CTAs walk the global tiles blockIdx.x,
+// +gridDim.x, ... (k_fft_uneven_one's claim them from a counter): the job of a
+// tile is found by walking the prefix table forward (tiles only grow).
 // Two landing buffers, each with its tile's descriptor in shared memory:
 // while tile i is transformed, every thread's cp.async copies bring tile i+1
 // (16-byte copies where the layout allows, else 8-byte).  The stages alternate
