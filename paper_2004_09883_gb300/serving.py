@@ -126,9 +126,19 @@ def run_served(server: fbfft.Server, w: Workload, arrivals: np.ndarray, host_io:
                 if any(st):
                     raise RuntimeError(f"requests rejected: {[(i + k, v) for k, v in enumerate(st) if v][:5]}")
                 i = j
+                take(server.poll())
             else:  # nothing due yet: watch the running requests until the next arrival
-                server.wait(t0 + arrivals[i])
-            take(server.poll())
+                due = t0 + arrivals[i]
+                server.wait(due)
+                items = server.poll()
+                take(items)
+                if not items:
+                    # the wait ended with nothing finished before `due`:
+                    # nothing is running, so no completion can be missed;
+                    # spin to the arrival as the plain replay does (a turn
+                    # of this loop is several microseconds of Python)
+                    while server.clock() < due:
+                        pass
             continue
         due = t0 + arrivals[i]
         while server.clock() < due:
