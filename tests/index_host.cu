@@ -13,6 +13,8 @@
 //      maps them across lines touch 16 different banks (8-byte words mod 16),
 //      for the strided power-of-two passes and for every line length and
 //      tile shape of the batched-uneven kernel, and its padded landing rows.
+//  (5) the batched-uneven kernel's stage twiddles formed as powers (radix 8
+//      from w and w^4, radix 4 and 5 from w and w^2) in FP32: within a few ulp.
 // Prints one line per check: name, cases, failures (or worst error).
 #include <cmath>
 #include <complex>
@@ -224,6 +226,47 @@ int main()
         }
         std::printf("uneven_rows %lld %lld\n", n, bad);
         std::printf("uneven_land %lld %lld\n", land, land_bad);
+    }
+
+    // (5) stage twiddles of the batched-uneven kernel by powers: for a
+    // butterfly with k < Ns of a radix-R stage the factors are w^r, w =
+    // w_{Ns R}^k; radix 8 takes w and w^4 from the table (rounded to FP32)
+    // and forms w^2 = w w, w^3 = w^2 w, w^5 = w^4 w, w^6 = w^4 w^2, w^7 = w^4 w^3,
+    // radix 4 and 5 take w and w^2 and form w^3 = w^2 w (and w^4 = w^2 w^2),
+    // all with the kernel's FP32 cmul: every 5-smooth Ns with Ns R <= 2048
+    {
+        auto f2 = [](cd z) { return make_float2((float)z.real(), (float)z.imag()); };
+        double worst = 0;
+        long long n = 0;
+        for (int R : {8, 4, 5})
+            for (long long Ns = 1; Ns * R <= 2048; ++Ns) {
+                long long m = Ns;
+                for (long long p : {2LL, 3LL, 5LL})
+                    while (m % p == 0) m /= p;
+                if (m != 1) continue;
+                const long long D = Ns * R;
+                for (long long k = 0; k < Ns; ++k) {
+                    float2 f[8];
+                    f[1] = f2(w(k, D));
+                    if (R == 8) {
+                        f[4] = f2(w(4 * k, D));
+                        f[2] = cmul(f[1], f[1]);
+                        f[3] = cmul(f[2], f[1]);
+                        f[5] = cmul(f[4], f[1]);
+                        f[6] = cmul(f[4], f[2]);
+                        f[7] = cmul(f[4], f[3]);
+                    } else {
+                        f[2] = f2(w(2 * k, D));
+                        f[3] = cmul(f[2], f[1]);
+                        f[4] = cmul(f[2], f[2]);
+                    }
+                    for (int r = 1; r < R; ++r) {
+                        worst = std::fmax(worst, std::abs(cd(f[r].x, f[r].y) - w(k * r, D)));
+                        ++n;
+                    }
+                }
+            }
+        std::printf("uneven_step %lld %.3e\n", n, worst);
     }
     return 0;
 }

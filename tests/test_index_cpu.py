@@ -35,6 +35,10 @@ def test_index_arithmetic(tmp_path):
         # within a few ulp of 1 (at most seven products in a row)
         n, worst = rows[f"split_step_lg{lg}"]
         assert int(n) == (1 << lg) // 16 * 15 and float(worst) < 1e-6
+    # the batched-uneven kernel's stage twiddles formed as powers (at most
+    # three products deep): within a few ulp of 1
+    n, worst = rows["uneven_step"]
+    assert int(n) > 10_000 and float(worst) < 5e-7
     # the swizzled first work generation: one-to-one, inside the row, and
     # the second stage's shortcut reads the slots the first stage wrote
     n, bad, configs = map(int, rows["swizzle"])
